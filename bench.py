@@ -1,0 +1,351 @@
+#!/usr/bin/env python
+"""ProgOT solves/sec on one GB300 (or N independent replicas).
+
+Workload (default): n = m = 8192 points in d = 64, source an 8-component Gaussian
+mixture (means ~ N(0, 4 I), sigma = 1), target an 8-component mixture with its own
+means and random SPD covariances (eigenvalues U[0.5, 2]), seed 1; K = 8 constant-speed
+steps; eps_k from the epsilon scheduler (Alg. 4) run once on the GPU before timing;
+tau = 1e-5 (float32 path) or 1e-4 (bf16x3 path); uniform weights. Synthetic stand-in
+for the paper's n ~ 1e4, d in {16, 64, 256} single-cell workloads.
+
+One step = one full ProgOT solve (Alg. 2: norms, warm starts, every Sinkhorn sweep,
+every map sweep) through the C ABI on device-resident inputs. L2 is flushed between
+timed steps (a 256 MiB write; the inputs are 2 MiB each). Prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2406_05061_gb300 import workloads as W  # noqa: E402
+
+WORKLOADS = {
+    # name: (generator kwargs, K, tau by precision, nominal sweeps per solve used only to
+    # convert the reference arm's oracle sweep rate into solves/s; measured on GB300
+    # with the float32 path)
+    "gmm8_8192_d64": dict(gen=dict(n=8192, m=8192, d=64, seed=1, k=8), K=8, tau={"fp32": 1e-5, "bf16x3": 1e-4,
+                                                                               "bf16": 1e-4},
+                          nominal_sweeps=None),
+}
+
+# Measured peaks (MEASURED_PEAKS.json when present) and the unit counts used for the
+# CUDA-core roofline: 152 SMs x 128 FP32 FMA lanes x 2 flop at the max SM clock.
+FALLBACK_PEAKS = dict(hbm_gbs=6800.0, bf16_tflops=1900.0, bf16_tflops_sustained=1700.0, sm_max_mhz=2070.0)
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            pk = json.load(fh)
+        pk["source"] = "measured"
+        return pk
+    pk = dict(FALLBACK_PEAKS)
+    pk["source"] = "fallback"
+    return pk
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region (200 ms period)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:  # nvidia-smi missing: no clock record
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def oracle_sweep_rate(x, y, eps, budget_s=12.0, rows=128):
+    """Time the FP64 oracle's Sinkhorn f-update (Alg. 1) on blocks of `rows` source
+    rows against all targets until `budget_s` seconds have passed; return
+    (pairs/s, rows done, seconds, threads)."""
+    from oracle import progot_oracle as O
+    X = np.asarray(x, dtype=np.float64)
+    Y = np.asarray(y, dtype=np.float64)
+    n, m = X.shape[0], Y.shape[0]
+    g = np.zeros(m)
+    a = np.full(n, 1.0 / n)
+    done = 0
+    t0 = time.perf_counter()
+    i0 = 0
+    while True:
+        Xb = X[i0:i0 + rows]
+        C = O.CostOperator(Xb, Y, cache_limit=0)
+        O._update_f(C, np.zeros(Xb.shape[0]), g, eps, a[i0:i0 + rows])
+        done += Xb.shape[0]
+        i0 = (i0 + rows) % n
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    return done * m / el, done, el, 1
+
+
+def run_reference(args, rank, world):
+    """The oracle as the reference arm: a bounded sample of the workload's sweeps."""
+    if rank != 0:
+        return 0
+    wl = WORKLOADS[args.workload]
+    p = W.gmm_pair(**wl["gen"])
+    from oracle import progot_oracle as O
+    eps = 5.0 * O.mean_cost(p.x[:1024], p.y[:1024]) / 20.0
+    rates = []
+    for _ in range(args.warmup):
+        oracle_sweep_rate(p.x, p.y, eps, budget_s=2.0)
+    for _ in range(args.steps):
+        r, rows, el, thr = oracle_sweep_rate(p.x, p.y, eps, budget_s=args.ref_budget)
+        rates.append(r)
+    pair_rate = statistics.mean(rates)
+    sweeps = wl["nominal_sweeps"] or 0
+    nm = p.n * p.m
+    value = pair_rate / (sweeps * nm) if sweeps else None
+    line = {
+        "impl": "reference", "metric": "progot_solves_per_sec", "value": value, "unit": "solves/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": (1000.0 / value) if value else None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n": p.n, "m": p.m, "d": p.d, "K": wl["K"]},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": f"FP64 oracle Sinkhorn f-update sweeps on 128-row blocks x {p.m} targets for "
+                                   f"{args.ref_budget:.0f} s per step; pairs/s {pair_rate:.3e} divided by "
+                                   f"{sweeps} sweeps x n x m per solve"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "pairs_per_sec": pair_rate,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3", "bf16"])
+    ap.add_argument("--workload", default="gmm8_8192_d64", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--ref-budget", type=float, default=10.0)
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    from paper_2406_05061_gb300 import native
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    wl = WORKLOADS[args.workload]
+    p = W.gmm_pair(**wl["gen"])
+    yt = W.heldout_target(p)
+    K = wl["K"]
+    tau = [wl["tau"][args.precision]] * K
+    native.lib()
+    x_h = torch.from_numpy(p.x).pin_memory()
+    y_h = torch.from_numpy(p.y).pin_memory()
+    x = x_h.to(dev)
+    y = y_h.to(dev)
+    y_test = torch.from_numpy(yt).to(dev)
+    ws = native.Workspace(max(p.n, p.m, yt.shape[0]), max(p.n, p.m, yt.shape[0]), p.d, args.precision)
+    alpha = native.progot_schedule_alpha(K, "constant")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    eps, scores, pstar = native.progot_schedule_eps(x, y, y_test, alpha, tau=tau[-1], precision=args.precision,
+                                                    workspace=ws)
+    torch.cuda.synchronize()
+    schedule_ms = (time.perf_counter() - t0) * 1e3
+    out = dict(x_out=torch.empty_like(x), g_all=torch.empty((K, p.m), device=dev), f_last=torch.empty(p.n, device=dev),
+               x_last=torch.empty_like(x))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def solve():
+        return native.progot_solve(x, y, alpha, eps, tau, max_iter=10000, precision=args.precision,
+                                   workspace=ws, out=out)
+
+    for _ in range(args.warmup):
+        res = solve()
+    torch.cuda.synchronize()
+    # ------------------------------------------------ timed region (device-resident)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    native.profile(True)
+    native.launch_count(reset=True)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    step_ms = []
+    iters_seen = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = solve()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        iters_seen.append(list(res.iters))
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    launches = native.launch_count()
+    lse = native.profile_read("lse_sweep")
+    mp = native.profile_read("map_sweep")
+    native.profile(False)
+    clk = clocks.stop()
+    total_ms = sum(step_ms)
+    if pg:
+        t = torch.tensor([total_ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = args.steps * world / (total_ms / 1e3)
+    # ------------------------------------------------ end to end from host buffers
+    x_back = torch.empty((p.n, p.d), dtype=torch.float32).pin_memory()
+    g_back = torch.empty((K, p.m), dtype=torch.float32).pin_memory()
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        x.copy_(x_h, non_blocking=True)
+        y.copy_(y_h, non_blocking=True)
+        solve()
+        x_back.copy_(out["x_out"], non_blocking=True)
+        g_back.copy_(out["g_all"], non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    e2e_total = sum(e2e_ms)
+    if pg:
+        t = torch.tensor([e2e_total], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = args.steps * world / (e2e_total / 1e3)
+    # ------------------------------------------------ roofline of the dominant kernel
+    peaks = load_peaks()
+    sm_max_ghz = float(peaks.get("sm_max_mhz", 2070.0)) / 1e3
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    avg_ms = lse["ms"] / max(1, lse["launches"])
+    pairs_per_launch = lse["pairs"] / max(1, lse["launches"])
+    if args.precision == "fp32":
+        flops_pair = 2.0 * p.d
+        peak = sms * 128 * 2 * sm_max_ghz * 1e9 / 1e12  # TFLOP/s, FP32 FMA pipe
+        bound, peak_src = "alu", f"derived: {sms} SMs x 128 FP32 FMA/clk x 2 flop x {sm_max_ghz:.2f} GHz"
+    else:
+        split = 3.0 if args.precision == "bf16x3" else 1.0
+        flops_pair = 2.0 * p.d * split
+        peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+        bound, peak_src = "tensor", f"{peaks['source']} bf16_tflops_sustained"
+    achieved = flops_pair * pairs_per_launch / (avg_ms / 1e3) / 1e12
+    sweeps_per_solve = (lse["launches"] + mp["launches"]) / args.steps
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "lse_sweep_fp32" if args.precision == "fp32" else "lse_sweep_tc",
+                "launches": lse["launches"], "avg_launch_ms": avg_ms, "pairs_per_launch": pairs_per_launch,
+                "pairs_per_sec": pairs_per_launch / (avg_ms / 1e3), "peak_source": peak_src,
+                "share_of_step": lse["ms"] / total_ms if total_ms else None}
+    line = {
+        "metric": "progot_solves_per_sec", "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32"
+        else "bf16x3->f32" if args.precision == "bf16x3" else "bf16->f32", "data": "synthetic",
+        "config": {"workload": args.workload, "n": p.n, "m": p.m, "d": p.d, "K": K, "tau": tau[-1],
+                   "precision": args.precision, "eps": [round(float(e), 6) for e in eps], "p_star": pstar,
+                   "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
+        "iters_per_step": iters_seen[-1], "schedule_ms": schedule_ms,
+        "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(2 * p.n * p.d * 4),
+                "d2h_bytes_per_step": int((p.n * p.d + K * p.m) * 4)},
+        "gpu_launches": launches // args.steps * args.steps if launches else 0,
+        "roofline": roofline,
+        "map_sweep": {"launches": mp["launches"], "avg_launch_ms": mp["ms"] / max(1, mp["launches"])},
+        "sweeps_per_solve": sweeps_per_solve,
+        "clocks": clk,
+        "status": res.status,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, rows, el, thr = oracle_sweep_rate(p.x, p.y, float(eps[0]), budget_s=args.cpu_budget)
+        cpu_val = rate / (sweeps_per_solve * p.n * p.m)
+        line["cpu_baseline"] = {"value": cpu_val, "unit": "solves/s", "cores": thr, "kind": "oracle",
+                                "sample": f"FP64 oracle f-update sweep over {rows} source rows x {p.m} targets "
+                                          f"({el:.1f} s, {rate:.3e} pairs/s), scaled by {sweeps_per_solve:.1f} "
+                                          f"n x m sweeps per solve measured in this run"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,215 @@
+/*
+ * progot.h - C ABI of the GB300 (sm_103a) ProgOT hot path.
+ *
+ * ProgOT (arXiv 2406.05061) estimates an optimal-transport coupling and map between a
+ * source cloud X (n x d) and a target cloud Y (m x d) by K warm-started entropic
+ * (Sinkhorn) solves, each followed by a partial move of X along the entropic map
+ * (Alg. 2). The cost is the squared Euclidean distance c(x, y) = ||x - y||^2
+ * (h = ||.||^2 in Sec. 2) and is never stored: every row or column log-sum-exp over it
+ * is computed tile by tile from x . y, |x|^2 and |y|^2.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Point clouds are row-major float32 arrays with leading dimension d (point i at
+ *   x[i*d .. i*d+d-1]). Weights a (n) and b (m) are float32 probability vectors, or
+ *   NULL for the uniform weights 1/n and 1/m.
+ * - Arrays named as "device" are device pointers (cudaMalloc / torch CUDA tensors on the
+ *   current device); they are caller-allocated and caller-owned and the library never
+ *   frees them. Arrays named as "host" are host memory.
+ * - Potentials follow the dual convention of eq. (5): the coupling is
+ *   P_ij = exp((f_i + g_j - c(x_i, y_j)) / eps); g absorbs eps log b_j.
+ * - workspace / ws_bytes: device scratch owned by the caller, at least
+ *   progot_workspace_size(...) bytes, 256-byte aligned. Its contents need not be
+ *   initialised and are garbage after the call. Two calls in flight at the same time
+ *   must not share a workspace.
+ * - stream: a cudaStream_t (NULL = legacy default stream). Entry points that return
+ *   host results (iteration counts, errors) synchronise that stream before
+ *   returning; the others are asynchronous.
+ * - precision: PROGOT_FP32 evaluates the cross term x . y with float32 FMAs on CUDA
+ *   cores; PROGOT_BF16X3 uses tcgen05 tensor cores on a bf16 hi/lo split of both
+ *   operands (x.y ~ xh.yh + xh.yl + xl.yh, float32 accumulation); PROGOT_BF16 uses the
+ *   hi parts only. Log-sum-exps and potentials are float32 in every mode; squared norms
+ *   and the marginal-error reduction accumulate in float64.
+ * - Return value: PROGOT_OK or an error code below. progot_last_error_string()
+ *   describes the last error on the calling thread. On PROGOT_ERR_NOT_CONVERGED all
+ *   outputs are still written (the last iterate).
+ */
+#ifndef PROGOT_H
+#define PROGOT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef void* progot_stream_t; /* a cudaStream_t */
+
+enum progot_status {
+  PROGOT_OK = 0,
+  PROGOT_ERR_INVALID_ARG = 1,   /* n, m, d <= 0, eps <= 0, alpha outside (0, 1], NULL required pointer, misaligned */
+  PROGOT_ERR_NOT_CONVERGED = 2, /* marginal error still above tau after max_iter iterations (or stalled) */
+  PROGOT_ERR_NUMERIC = 3,       /* NaN or Inf in the marginal-error reduction */
+  PROGOT_ERR_OOM = 4,           /* a host-side allocation failed */
+  PROGOT_ERR_CUDA = 5,          /* a CUDA runtime call failed */
+  PROGOT_ERR_TIMEOUT = 6,       /* a bounded device-side wait expired */
+  PROGOT_ERR_WORKSPACE = 7      /* workspace NULL, too small or not 256-byte aligned */
+};
+
+typedef enum { PROGOT_FP32 = 0, PROGOT_BF16X3 = 1, PROGOT_BF16 = 2 } progot_precision;
+
+typedef enum { PROGOT_ALPHA_CONSTANT = 0, PROGOT_ALPHA_ACCELERATED = 1, PROGOT_ALPHA_DECELERATED = 2 } progot_alpha_kind;
+
+/* Text of the last error on the calling thread ("" when none). Never NULL. */
+const char* progot_last_error_string(void);
+
+/* Library version, e.g. "0.1.0". */
+const char* progot_version(void);
+
+/* Bytes of device workspace that every entry point below needs for a problem with at
+ * most n rows, m columns and dimension d (for entropic_map_apply pass nq as n). */
+size_t progot_workspace_size(int64_t n, int64_t m, int32_t d, int32_t precision);
+
+/*
+ * sinkhorn_potentials - Sink(a, X, b, Y, eps, tau, f_init, g_init) of Alg. 1.
+ *
+ * While the row-marginal error ||P 1 - a||_1 exceeds tau, alternate
+ *   f_i <- eps log a_i - eps log sum_j exp((g_j - c(x_i, y_j)) / eps)
+ *   g_j <- eps log b_j - eps log sum_i exp((f_i - c(x_i, y_j)) / eps)
+ * (the soft-min updates of Alg. 1 with the sign of the paper's min_eps term read as +).
+ * The error is checked before each iteration, so the returned (f, g) is the last pair
+ * whose error was measured; after the g-update the column marginal is exact.
+ *
+ * x (device, n x d), a (device, n, or NULL), y (device, m x d), b (device, m, or NULL).
+ * eps > 0, tau >= 0, max_iter >= 0.
+ * f (device, n) and g (device, m): in = initial potentials unless init_zero != 0 (then
+ *   zero); out = the final potentials.
+ * iters_out (host, may be NULL): completed (f, g) iterations. err_out (host, may be
+ *   NULL): the last measured row-marginal L1 error (float64).
+ * Returns PROGOT_ERR_NOT_CONVERGED when tau was not met within max_iter iterations or
+ * the error stopped decreasing (see progot_set_stall_window).
+ */
+int sinkhorn_potentials(const float* x, const float* a, int64_t n, const float* y, const float* b, int64_t m,
+                        int32_t d, double eps, double tau, int32_t max_iter, int32_t precision, float* f, float* g,
+                        int32_t init_zero, int32_t* iters_out, double* err_out, void* workspace, size_t ws_bytes,
+                        progot_stream_t stream);
+
+/*
+ * entropic_map_apply - T_Prog[b, Y, (g^(k), eps_k, alpha_k)_k] of Alg. 3 on nq points.
+ *
+ * For k = 1..K: p_j = softmax_j((g^(k)_j - c(z, y_j)) / eps_k),
+ *   z <- (1 - alpha_k) z + alpha_k sum_j p_j y_j,
+ * which is Alg. 3's z <- z - alpha_k grad h*(p^T [grad h(z - y_j)]_j) for h = ||.||^2.
+ * With K = 1 and alpha = 1 this is the entropic map of eq. (7).
+ * alpha_K is taken as 1 whatever alpha[K-1] holds (Alg. 3 resets it).
+ *
+ * xq (device, nq x d) query points; y (device, m x d); g_all (device, K x m) the stored
+ * g^(k); eps (host, K) and alpha (host, K) float64; out (device, nq x d) may alias xq.
+ */
+int entropic_map_apply(const float* xq, int64_t nq, const float* y, int64_t m, int32_t d, int32_t K,
+                       const float* g_all, const double* eps, const double* alpha, int32_t precision, float* out,
+                       void* workspace, size_t ws_bytes, progot_stream_t stream);
+
+/*
+ * coupling_marginals - r = P 1_m and c = P^T 1_n of P_ij = exp((f_i + g_j - c(x_i, y_j))/eps)
+ * (the coupling returned by Alg. 1 / Alg. 2), and the marginal constraint violation
+ * ||r - a||_1 + ||c - b||_1 reported with the coupling metrics of Sec. 5.2.
+ *
+ * row (device, n) and col (device, m) may be NULL (not written). a, b (device) may be
+ * NULL for uniform weights. err_l1_out (host, may be NULL) is accumulated in float64.
+ */
+int coupling_marginals(const float* x, int64_t n, const float* y, int64_t m, int32_t d, const float* f,
+                       const float* g, double eps, int32_t precision, float* row, float* col, const float* a,
+                       const float* b, double* err_l1_out, void* workspace, size_t ws_bytes, progot_stream_t stream);
+
+/*
+ * progot_solve - ProgOT(a, X, b, Y, (eps_k, alpha_k, tau_k)_k) of Alg. 2, K solves.
+ *
+ * f = 0, g^(0) = 0. For k = 1..K: warm start f, g <- (1 - alpha_k) f, (1 - alpha_k) g^(k-1);
+ * (f, g^(k)) <- Sinkhorn at (eps_k, tau_k); Q = diag(1 / P 1) P;
+ * x_i <- (1 - alpha_k) x_i + alpha_k sum_j Q_ij y_j (the barycentric displacement
+ * X <- X - alpha_k Z with Z_i = grad h*(sum_j Q_ij grad h(x_i - y_j))).
+ *
+ * x (device, n x d) is not modified. alpha, eps, tau (host, K, float64); alpha_K should be
+ * 1 so that x_out = T_Prog(x_i) (Def. 1). max_iter bounds each solve.
+ * x_out (device, n x d): the displaced cloud after step K.
+ * g_all (device, K x m): g^(k) of every step (the map-estimator state of Alg. 3).
+ * f_last (device, n, may be NULL): f of the last solve; with x_last (device, n x d, may
+ *   be NULL: the cloud X^(K) the last solve ran on) and g_all[K-1] it defines the
+ *   returned coupling P.
+ * iters (host, K, may be NULL), errs (host, K, may be NULL): per-step iteration counts and
+ *   final row-marginal errors.
+ * Returns PROGOT_ERR_NOT_CONVERGED if any step did not reach its tau (all outputs are
+ * still written).
+ */
+int progot_solve(const float* x, const float* a, int64_t n, const float* y, const float* b, int64_t m, int32_t d,
+                 int32_t K, const double* alpha, const double* eps, const double* tau, int32_t max_iter,
+                 int32_t precision, float* x_out, float* g_all, float* f_last, float* x_last, int32_t* iters,
+                 double* errs, void* workspace, size_t ws_bytes, progot_stream_t stream);
+
+/*
+ * progot_schedule_alpha - alpha_1..alpha_K of the step-length schedules of Sec. 4
+ * (Table 7), with alpha_K = 1. Each alpha_k is the fraction of the remaining path that
+ * step k covers: alpha_k = (t_k - t_{k-1}) / (1 - t_{k-1}) for the target progress
+ * t_k = k/K (constant speed) or (k/K)^2 (accelerated); decelerated uses alpha_k = 1/e.
+ * out (host, K).
+ */
+int progot_schedule_alpha(int32_t K, int32_t kind, double* out);
+
+/*
+ * progot_mean_cost - (1/(n m)) sum_ij ||x_i - y_j||^2, the mean of the cost matrix used
+ * for eps0 and sigma in Alg. 4, in closed form
+ * mean ||x||^2 + mean ||y||^2 - 2 xbar . ybar (float64 sums on the device).
+ * out (host). Synchronises the stream.
+ */
+int progot_mean_cost(const float* x, int64_t n, const float* y, int64_t m, int32_t d, double* out, void* workspace,
+                     size_t ws_bytes, progot_stream_t stream);
+
+/*
+ * progot_schedule_eps - the epsilon scheduler of Alg. 4.
+ *
+ * eps0 = mean cost(X, Y) / 20, sigma = mean cost(Y, Y) / 20. For each s_p of s_grid
+ * (host, P): solve Sink(b, Y, b, Y, s_p sigma, tau) on the device, map y_test
+ * (device, mt x d) with (g, s_p sigma, alpha = 1) and score sum ||y~ - T(y~)||^2 (float64).
+ * eps_K = s_{p*} sigma for the first minimiser p*; eps_out (host, K) receives
+ * (1 - t_k) beta0 eps0 + t_k eps_K with t_k = 1 - prod_{l<=k}(1 - alpha_l) from alpha
+ * (host, K). errors_out (host, P, may be NULL) receives the scores; p_star_out (host,
+ * may be NULL) the chosen index. workspace must cover (max(n, m, mt), max(m, n), d).
+ */
+int progot_schedule_eps(const float* x, int64_t n, const float* y, const float* b, int64_t m,
+                        const float* y_test, int64_t mt, int32_t d, int32_t K, const double* alpha,
+                        const double* s_grid, int32_t P, double beta0, double tau, int32_t max_iter, int32_t precision,
+                        double* eps_out, double* errors_out, int32_t* p_star_out, void* workspace, size_t ws_bytes,
+                        progot_stream_t stream);
+
+/*
+ * progot_set_stall_window - Sinkhorn stops with PROGOT_ERR_NOT_CONVERGED when its
+ * marginal error has not fallen below 0.99 x its best value for `iters` consecutive
+ * iterations (float32 potentials reach a rounding floor). 0 disables the check.
+ * Default 512. Process-wide setting.
+ */
+int progot_set_stall_window(int32_t iters);
+
+/* Number of kernels this library launched since the last call (process-wide counter);
+ * used to report launches inside a timed region. */
+int64_t progot_launch_count(int32_t reset);
+
+/*
+ * progot_profile - enable (1) or disable (0) per-kernel timing on the calling thread
+ * and reset its totals. While enabled, every log-sum-exp sweep and map sweep the
+ * library launches is bracketed by CUDA events recorded on the launching stream;
+ * launches of a Sinkhorn loop after its stop (which return at entry) are not counted.
+ * progot_profile_read - totals since the last progot_profile call for kernel 0 (the
+ * row/column log-sum-exp sweep) or 1 (the map sweep): counted launches, summed
+ * device time in ms, and summed point pairs (rows x columns) those launches covered.
+ * Reading synchronises on the recorded events.
+ */
+int progot_profile(int32_t enable);
+int progot_profile_read(int32_t kernel, int64_t* launches, double* total_ms, double* pairs);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PROGOT_H */

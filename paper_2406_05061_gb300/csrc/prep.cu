@@ -1,0 +1,145 @@
+// Small O((n + m) d) kernels: squared norms (float64 accumulation), potential scaling
+// for the warm start of Alg. 2, state initialisation, and deterministic float64
+// reductions (first moments for the closed-form mean cost of Alg. 4, squared error
+// for the Alg. 4 score).
+#include "progot_internal.h"
+
+namespace progot {
+
+constexpr int kParts = 304;  // partial sums of the two-pass reductions
+
+int reduce_parts() { return kParts; }
+
+// One warp per row: |x_i|^2 summed in float64, stored as float32.
+__global__ void row_sqnorm_kernel(const float* __restrict__ X, int64_t n, int32_t d, float* __restrict__ out) {
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  const float* x = X + row * (int64_t)d;
+  double s = 0.0;
+  for (int k = lane; k < d; k += 32) {
+    const double v = (double)x[k];
+    s += v * v;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (lane == 0) out[row] = (float)s;
+}
+
+__global__ void scale_kernel(float* v, int64_t n, float factor) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] *= factor;
+}
+
+__global__ void init_state_kernel(SolverState* st) {
+  st->it = 0;
+  st->done = 0;
+  st->status = kRunning;
+  st->fcur = 0;
+  st->best_it = 0;
+  st->err = 0.0;
+  st->best_err = INFINITY;
+}
+
+// Pass 1: block b sums rows b, b + parts, ... of (|x|^2, x_1 .. x_d) into partial[b].
+__global__ void moments_pass1(const float* __restrict__ X, int64_t n, int32_t d, double* __restrict__ partial) {
+  extern __shared__ double acc[];  // d + 1 per warp
+  const int warps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k = threadIdx.x; k < warps * (d + 1); k += blockDim.x) acc[k] = 0.0;
+  __syncthreads();
+  for (int64_t row = (int64_t)blockIdx.x * warps + warp; row < n; row += (int64_t)gridDim.x * warps) {
+    const float* x = X + row * (int64_t)d;
+    double s = 0.0;
+    for (int k = lane; k < d; k += 32) {
+      const double v = (double)x[k];
+      s += v * v;
+      acc[warp * (d + 1) + 1 + k] += v;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) acc[warp * (d + 1)] += s;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < d + 1; k += blockDim.x) {
+    double t = 0.0;
+    for (int w = 0; w < warps; ++w) t += acc[w * (d + 1) + k];
+    partial[(int64_t)blockIdx.x * (d + 1) + k] = t;
+  }
+}
+
+// Pass 2: out[k] = sum_b partial[b][k], in block order.
+__global__ void sum_parts(const double* __restrict__ partial, int parts, int width, double* __restrict__ out) {
+  for (int k = threadIdx.x; k < width; k += blockDim.x) {
+    double t = 0.0;
+    for (int b = 0; b < parts; ++b) t += partial[(int64_t)b * width + k];
+    out[k] = t;
+  }
+}
+
+__global__ void sq_error_pass1(const float* __restrict__ A, const float* __restrict__ B, int64_t n, int32_t d,
+                               double* __restrict__ partial) {
+  __shared__ double red[32];
+  double s = 0.0;
+  const int64_t total = n * (int64_t)d;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const double v = (double)A[e] - (double)B[e];
+    s += v * v;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    partial[blockIdx.x] = t;
+  }
+}
+
+cudaError_t launch_row_sqnorm(const float* X, int64_t n, int32_t d, float* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int rows_per_block = 8;
+  const int64_t blocks = (n + rows_per_block - 1) / rows_per_block;
+  row_sqnorm_kernel<<<(unsigned)blocks, 256, 0, s>>>(X, n, d, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale(float* v, int64_t n, float factor, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  scale_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(v, n, factor);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_state(SolverState* st, cudaStream_t s) {
+  init_state_kernel<<<1, 1, 0, s>>>(st);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_moments(const float* X, int64_t n, int32_t d, double* partial, int parts, double* out,
+                           cudaStream_t s) {
+  const int threads = 256;
+  const size_t smem = sizeof(double) * (threads / 32) * (size_t)(d + 1);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(moments_pass1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  moments_pass1<<<parts, threads, smem, s>>>(X, n, d, partial);
+  count_launch();
+  sum_parts<<<1, 256, 0, s>>>(partial, parts, d + 1, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sq_error(const float* A, const float* B, int64_t n, int32_t d, double* partial, int parts,
+                            double* out, cudaStream_t s) {
+  sq_error_pass1<<<parts, 256, 0, s>>>(A, B, n, d, partial);
+  count_launch();
+  sum_parts<<<1, 32, 0, s>>>(partial, parts, 1, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace progot

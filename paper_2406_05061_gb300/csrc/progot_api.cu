@@ -1,0 +1,734 @@
+// Host orchestration of the ProgOT hot path and its C ABI (include/progot.h).
+//
+// The Sinkhorn loop of Alg. 1 runs without a host round trip per iteration: every
+// f-sweep measures the row-marginal error of the current (f, g) in its epilogue and
+// the last CTA decides on the device whether to stop (SolverState). Later sweeps of a
+// stopped loop return at entry, so the host enqueues iterations in growing chunks and
+// reads the state back (pinned memory, one event per chunk) while the next chunk is
+// already queued.
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/progot.h"
+#include "progot_internal.h"
+
+namespace progot {
+
+static std::atomic<int64_t> g_launches{0};
+static std::atomic<int32_t> g_stall_window{512};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+static thread_local std::string t_last_error;
+
+// Opt-in per-kernel timing (progot_profile): CUDA events recorded on the launching
+// stream around every sweep. Launches of a Sinkhorn loop after its stop (no-op
+// launches) are discarded once the loop's final iteration count is known.
+enum ProfKind { kProfLse = 0, kProfMap = 1, kProfKinds = 2 };
+struct ProfRec {
+  cudaEvent_t a, b;
+  int kind;
+  double pairs;
+  bool counted;
+};
+struct Profiler {
+  bool on = false;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> pool;
+  double ms[kProfKinds] = {0, 0};
+  double pairs[kProfKinds] = {0, 0};
+  int64_t launches[kProfKinds] = {0, 0};
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+};
+static thread_local Profiler t_prof;
+
+static void prof_begin(ProfRec& r, cudaStream_t s) {
+  r.a = t_prof.get();
+  r.b = t_prof.get();
+  cudaEventRecord(r.a, s);
+}
+static void prof_end(ProfRec& r, cudaStream_t s, int kind, double pairs) {
+  cudaEventRecord(r.b, s);
+  r.kind = kind;
+  r.pairs = pairs;
+  r.counted = true;
+  t_prof.recs.push_back(r);
+}
+// Fold finished records into the totals (synchronises on their events).
+static void prof_collect() {
+  for (ProfRec& r : t_prof.recs) {
+    if (r.counted) {
+      float ms = 0.f;
+      cudaEventSynchronize(r.b);
+      cudaEventElapsedTime(&ms, r.a, r.b);
+      t_prof.ms[r.kind] += ms;
+      t_prof.pairs[r.kind] += r.pairs;
+      t_prof.launches[r.kind] += 1;
+    } else {
+      cudaEventSynchronize(r.b);
+    }
+    t_prof.pool.push_back(r.a);
+    t_prof.pool.push_back(r.b);
+  }
+  t_prof.recs.clear();
+}
+
+static int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  t_last_error = buf;
+  return code;
+}
+
+#define CK(call)                                                                                    \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess) return fail(PROGOT_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+static int num_sms() {
+  static thread_local int cached = 0;
+  if (cached) return cached;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 152;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) return 152;
+  cached = sms;
+  return sms;
+}
+
+static int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+static size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+// Column splits of a sweep of nA rows against nB columns: enough CTAs to fill the GPU
+// (ctas_per_sm resident CTAs on every SM), never more splits than column tiles.
+static int plan_splits(int64_t nA, int64_t nB, int ctas_per_sm, int extra_mult = 1) {
+  const int64_t rb = cdiv(nA, fp32_tile_rows()) * extra_mult;
+  const int64_t ct = cdiv(nB, fp32_tile_cols());
+  const int64_t target = (int64_t)num_sms() * ctas_per_sm;
+  int64_t s = target / rb;
+  if (s < 1) s = 1;
+  if (s > ct) s = ct;
+  return (int)s;
+}
+
+// Device workspace carved from the caller's buffer.
+struct Workspace {
+  float* xn;        // nmax
+  float* yn;        // nmax
+  float* f0;        // nmax
+  float* f1;        // nmax
+  float* gaux;      // nmax
+  float* L;         // nmax
+  float* T;         // nmax * d
+  float2* partial;  // partial_elems
+  double* errpart;  // rbmax + 2
+  unsigned* cnt;    // rbmax + 2
+  unsigned* mcnt;   // rbmax + 2
+  SolverState* state;
+  double* rpart;    // parts * (d + 1)
+  double* rout;     // 2 * (d + 1)
+  float* Opart;     // opart_elems
+  float* Rpart;     // rpart_elems
+  size_t bytes;
+};
+
+struct WsDims {
+  int64_t nmax, rbmax, partial_elems, opart_elems, rpart_elems;
+  int32_t d;
+};
+
+static WsDims ws_dims(int64_t n, int64_t m, int32_t d) {
+  WsDims w;
+  w.nmax = std::max<int64_t>(std::max<int64_t>(n, m), 1);
+  w.d = d;
+  w.rbmax = cdiv(w.nmax, fp32_tile_rows());
+  // lse sweep: splits * nA over both directions and every (nA, nB) <= (nmax, nmax)
+  const int64_t s_lse = plan_splits(1, w.nmax, 2);  // largest split count for the smallest nA
+  (void)s_lse;
+  // splits * nA <= max(nA, (target / rb) * rb * BM) <= max(nmax, target * BM)
+  const int64_t target = (int64_t)num_sms() * 2;
+  w.partial_elems = std::max<int64_t>(w.nmax, target * fp32_tile_rows()) + fp32_tile_rows();
+  const int64_t dch = cdiv(d, map_dchunk());
+  const int64_t mtarget = (int64_t)num_sms();
+  const int64_t rows_cap = std::max<int64_t>(w.nmax, (mtarget / dch + 1) * fp32_tile_rows());
+  w.opart_elems = rows_cap * d + fp32_tile_rows() * (int64_t)d;
+  w.rpart_elems = rows_cap + fp32_tile_rows();
+  return w;
+}
+
+static size_t ws_layout(const WsDims& w, Workspace* out, char* base) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* {
+    char* p = base ? base + off : nullptr;
+    off += align256(bytes);
+    return p;
+  };
+  Workspace ws;
+  ws.xn = (float*)take(sizeof(float) * w.nmax);
+  ws.yn = (float*)take(sizeof(float) * w.nmax);
+  ws.f0 = (float*)take(sizeof(float) * w.nmax);
+  ws.f1 = (float*)take(sizeof(float) * w.nmax);
+  ws.gaux = (float*)take(sizeof(float) * w.nmax);
+  ws.L = (float*)take(sizeof(float) * w.nmax);
+  ws.T = (float*)take(sizeof(float) * w.nmax * (size_t)w.d);
+  ws.partial = (float2*)take(sizeof(float2) * w.partial_elems);
+  ws.errpart = (double*)take(sizeof(double) * (w.rbmax + 2));
+  ws.cnt = (unsigned*)take(sizeof(unsigned) * (w.rbmax + 2));
+  ws.mcnt = (unsigned*)take(sizeof(unsigned) * (w.rbmax + 2));
+  ws.state = (SolverState*)take(sizeof(SolverState));
+  ws.rpart = (double*)take(sizeof(double) * reduce_parts() * (size_t)(w.d + 1));
+  ws.rout = (double*)take(sizeof(double) * 2 * (size_t)(w.d + 1));
+  ws.Opart = (float*)take(sizeof(float) * w.opart_elems);
+  ws.Rpart = (float*)take(sizeof(float) * w.rpart_elems);
+  ws.bytes = off;
+  if (out) *out = ws;
+  return off;
+}
+
+static int carve(int64_t n, int64_t m, int32_t d, void* workspace, size_t ws_bytes, Workspace* ws) {
+  if (workspace == nullptr) return fail(PROGOT_ERR_WORKSPACE, "workspace is NULL");
+  if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
+    return fail(PROGOT_ERR_WORKSPACE, "workspace is not 256-byte aligned");
+  const WsDims w = ws_dims(n, m, d);
+  const size_t need = ws_layout(w, ws, (char*)workspace);
+  if (ws_bytes < need)
+    return fail(PROGOT_ERR_WORKSPACE, "workspace has %zu bytes, %zu needed", ws_bytes, need);
+  return PROGOT_OK;
+}
+
+// Pinned host mirror of the solver state, one pair per host thread.
+struct HostMirror {
+  SolverState* hs = nullptr;  // [2], pinned
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  double* hd = nullptr;  // pinned doubles for reductions
+  bool ok = false;
+  int init() {
+    if (ok) return PROGOT_OK;
+    CK(cudaHostAlloc((void**)&hs, 2 * sizeof(SolverState), cudaHostAllocDefault));
+    CK(cudaHostAlloc((void**)&hd, 1024 * sizeof(double), cudaHostAllocDefault));
+    CK(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+    ok = true;
+    return PROGOT_OK;
+  }
+};
+static thread_local HostMirror t_host;
+
+static int check_common(const float* x, int64_t n, const float* y, int64_t m, int32_t d, int32_t precision) {
+  if (x == nullptr || y == nullptr) return fail(PROGOT_ERR_INVALID_ARG, "x and y must not be NULL");
+  if (n <= 0 || m <= 0 || d <= 0) return fail(PROGOT_ERR_INVALID_ARG, "n, m, d must be positive (got %lld, %lld, %d)",
+                                              (long long)n, (long long)m, d);
+  if (n > (int64_t)1 << 31 || m > (int64_t)1 << 31)
+    return fail(PROGOT_ERR_INVALID_ARG, "n and m must be below 2^31");
+  if (precision != PROGOT_FP32 && precision != PROGOT_BF16X3 && precision != PROGOT_BF16)
+    return fail(PROGOT_ERR_INVALID_ARG, "unknown precision %d", precision);
+  return PROGOT_OK;
+}
+
+// One sweep description for "update the potential of A from the potential of B".
+static SweepParams make_sweep(const float* A, int64_t nA, const float* B, int64_t nB, int32_t d, const float* An,
+                              const float* Bn, double eps, const Workspace& ws) {
+  SweepParams p;
+  memset(&p, 0, sizeof(p));
+  p.A = A;
+  p.B = B;
+  p.An = An;
+  p.Bn = Bn;
+  p.nA = nA;
+  p.nB = nB;
+  p.d = d;
+  p.splits = plan_splits(nA, nB, 2);
+  const int64_t ct = cdiv(nB, fp32_tile_cols());
+  p.tiles_per_split = (int)cdiv(ct, p.splits);
+  p.splits = (int)cdiv(ct, p.tiles_per_split);  // drop empty splits
+  p.scale = (float)(2.0 * kLog2e / eps);
+  p.bscale = (float)(kLog2e / eps);
+  p.eps = eps;
+  p.inv_nA = 1.0 / (double)nA;
+  p.partial = ws.partial;
+  p.errpart = ws.errpart;
+  p.cnt = ws.cnt;
+  p.stall_window = g_stall_window.load();
+  return p;
+}
+
+static int lse_sweep(const SweepParams& p, int32_t precision, cudaStream_t s) {
+  (void)precision;
+  ProfRec r;
+  if (t_prof.on) prof_begin(r, s);
+  CK(launch_lse_sweep_fp32(p, s));
+  if (t_prof.on) prof_end(r, s, kProfLse, (double)p.nA * (double)p.nB);
+  return PROGOT_OK;
+}
+
+// Sinkhorn loop (Alg. 1) on device-resident state. f lives in {f_a, f_b} (ping-pong);
+// on return the current f is copied into f_a. Norms xn, yn must be ready.
+static int sinkhorn_core(const float* x, const float* a, int64_t n, const float* y, const float* b, int64_t m,
+                         int32_t d, double eps, double tau, int32_t max_iter, int32_t precision, float* f_a, float* f_b,
+                         float* g, const float* xn, const float* yn, const Workspace& ws, int32_t* iters_out,
+                         double* err_out, cudaStream_t s) {
+  int rc = t_host.init();
+  if (rc) return rc;
+  CK(launch_init_state(ws.state, s));
+  SweepParams pf = make_sweep(x, n, y, m, d, xn, yn, eps, ws);
+  pf.wA = a;
+  pf.potB = g;
+  pf.out = f_a;
+  pf.out_alt = f_b;
+  pf.mode = kModePotential;
+  pf.role = 1;
+  pf.state = ws.state;
+  pf.tau = tau;
+  pf.max_iter = max_iter;
+  SweepParams pg = make_sweep(y, m, x, n, d, yn, xn, eps, ws);
+  pg.wA = b;
+  pg.potB = f_a;
+  pg.potB_alt = f_b;
+  pg.out = g;
+  pg.mode = kModePotential;
+  pg.role = 2;
+  pg.state = ws.state;
+  pg.tau = tau;
+  pg.max_iter = max_iter;
+
+  auto enqueue = [&](int iters) -> int {
+    for (int i = 0; i < iters; ++i) {
+      int r = lse_sweep(pf, precision, s);
+      if (r) return r;
+      r = lse_sweep(pg, precision, s);
+      if (r) return r;
+    }
+    return PROGOT_OK;
+  };
+  const size_t prof_first = t_prof.recs.size();
+  const int64_t need = (int64_t)max_iter + 1;  // f-sweeps that guarantee a stop
+  int64_t launched = 0;
+  int chunk = 2;
+  int cur = 0;
+  auto issue = [&](int slot, int iters) -> int {
+    int r = enqueue(iters);
+    if (r) return r;
+    launched += iters;
+    CK(cudaMemcpyAsync(&t_host.hs[slot], ws.state, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(t_host.ev[slot], s));
+    return PROGOT_OK;
+  };
+  rc = issue(cur, (int)std::min<int64_t>(chunk, need));
+  if (rc) return rc;
+  SolverState fin;
+  for (;;) {
+    bool pending = false;
+    if (launched < need) {
+      chunk = std::min(chunk * 2, 64);
+      rc = issue(cur ^ 1, (int)std::min<int64_t>(chunk, need - launched));
+      if (rc) return rc;
+      pending = true;
+    }
+    CK(cudaEventSynchronize(t_host.ev[cur]));
+    if (t_host.hs[cur].done) {
+      fin = t_host.hs[cur];
+      if (pending) CK(cudaEventSynchronize(t_host.ev[cur ^ 1]));
+      break;
+    }
+    if (!pending) return fail(PROGOT_ERR_CUDA, "Sinkhorn loop did not stop after max_iter + 1 sweeps");
+    cur ^= 1;
+  }
+  if (t_prof.on) {
+    // sweeps f_0, g_0, ..., g_{it-1}, f_it did work; later launches returned at entry
+    const size_t working = 2 * (size_t)fin.it + 1;
+    for (size_t i = prof_first; i < t_prof.recs.size(); ++i) t_prof.recs[i].counted = (i - prof_first) < working;
+  }
+  if (fin.fcur == 1) CK(cudaMemcpyAsync(f_a, f_b, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+  if (iters_out) *iters_out = fin.it;
+  if (err_out) *err_out = fin.err;
+  switch (fin.status) {
+    case kConverged:
+      return PROGOT_OK;
+    case kNumeric:
+      return fail(PROGOT_ERR_NUMERIC, "non-finite marginal error after %d iterations", fin.it);
+    case kStalled:
+      return fail(PROGOT_ERR_NOT_CONVERGED, "marginal error %.3e stalled above tau %.3e after %d iterations", fin.err,
+                  tau, fin.it);
+    default:
+      return fail(PROGOT_ERR_NOT_CONVERGED, "marginal error %.3e above tau %.3e after %d iterations", fin.err, tau,
+                  fin.it);
+  }
+}
+
+// One barycentric displacement X <- X + alpha (T(X) - X) (Alg. 2 / Alg. 3), in place on X.
+static int map_step(float* X, int64_t n, const float* y, int64_t m, int32_t d, const float* g, const float* yn,
+                    double eps, double alpha, int32_t precision, const Workspace& ws, cudaStream_t s) {
+  SweepParams pl = make_sweep(X, n, y, m, d, nullptr, yn, eps, ws);
+  pl.potB = g;
+  pl.out = ws.L;
+  pl.mode = kModeLse;
+  int rc = lse_sweep(pl, precision, s);
+  if (rc) return rc;
+  MapParams mp;
+  memset(&mp, 0, sizeof(mp));
+  mp.A = X;
+  mp.B = y;
+  mp.Bn = yn;
+  mp.potB = g;
+  mp.L = ws.L;
+  mp.out = X;
+  mp.Opart = ws.Opart;
+  mp.Rpart = ws.Rpart;
+  mp.cnt = ws.mcnt;
+  mp.nA = n;
+  mp.nB = m;
+  mp.d = d;
+  mp.dchunks = (int)cdiv(d, map_dchunk());
+  mp.splits = plan_splits(n, m, 1, mp.dchunks);
+  const int64_t ct = cdiv(m, fp32_tile_cols());
+  mp.tiles_per_split = (int)cdiv(ct, mp.splits);
+  mp.splits = (int)cdiv(ct, mp.tiles_per_split);
+  mp.scale = (float)(2.0 * kLog2e / eps);
+  mp.bscale = (float)(kLog2e / eps);
+  mp.alpha = (float)alpha;
+  ProfRec r;
+  if (t_prof.on) prof_begin(r, s);
+  CK(launch_map_sweep_fp32(mp, s));
+  if (t_prof.on) prof_end(r, s, kProfMap, (double)n * (double)m);
+  return PROGOT_OK;
+}
+
+static int zero_counters(const Workspace& ws, int64_t rbmax, cudaStream_t s) {
+  CK(cudaMemsetAsync(ws.cnt, 0, sizeof(unsigned) * (rbmax + 2), s));
+  CK(cudaMemsetAsync(ws.mcnt, 0, sizeof(unsigned) * (rbmax + 2), s));
+  return PROGOT_OK;
+}
+
+}  // namespace progot
+
+using namespace progot;
+
+extern "C" {
+
+const char* progot_last_error_string(void) { return t_last_error.c_str(); }
+
+const char* progot_version(void) { return "0.1.0"; }
+
+size_t progot_workspace_size(int64_t n, int64_t m, int32_t d, int32_t precision) {
+  (void)precision;
+  if (n <= 0 || m <= 0 || d <= 0) return 0;
+  return ws_layout(ws_dims(n, m, d), nullptr, nullptr);
+}
+
+int progot_set_stall_window(int32_t iters) {
+  if (iters < 0) return fail(PROGOT_ERR_INVALID_ARG, "stall window must be >= 0");
+  g_stall_window.store(iters);
+  return PROGOT_OK;
+}
+
+int64_t progot_launch_count(int32_t reset) {
+  return reset ? g_launches.exchange(0) : g_launches.load();
+}
+
+int progot_profile(int32_t enable) {
+  prof_collect();
+  t_prof.on = enable != 0;
+  for (int k = 0; k < kProfKinds; ++k) {
+    t_prof.ms[k] = 0.0;
+    t_prof.pairs[k] = 0.0;
+    t_prof.launches[k] = 0;
+  }
+  return PROGOT_OK;
+}
+
+int progot_profile_read(int32_t kernel, int64_t* launches, double* total_ms, double* pairs) {
+  if (kernel < 0 || kernel >= kProfKinds) return fail(PROGOT_ERR_INVALID_ARG, "unknown kernel id %d", kernel);
+  prof_collect();
+  if (launches) *launches = t_prof.launches[kernel];
+  if (total_ms) *total_ms = t_prof.ms[kernel];
+  if (pairs) *pairs = t_prof.pairs[kernel];
+  return PROGOT_OK;
+}
+
+int sinkhorn_potentials(const float* x, const float* a, int64_t n, const float* y, const float* b, int64_t m,
+                        int32_t d, double eps, double tau, int32_t max_iter, int32_t precision, float* f, float* g,
+                        int32_t init_zero, int32_t* iters_out, double* err_out, void* workspace, size_t ws_bytes,
+                        progot_stream_t stream) {
+  t_last_error.clear();
+  int rc = check_common(x, n, y, m, d, precision);
+  if (rc) return rc;
+  if (f == nullptr || g == nullptr) return fail(PROGOT_ERR_INVALID_ARG, "f and g must not be NULL");
+  if (!(eps > 0.0) || !std::isfinite(eps)) return fail(PROGOT_ERR_INVALID_ARG, "eps must be positive and finite");
+  if (!(tau >= 0.0)) return fail(PROGOT_ERR_INVALID_ARG, "tau must be >= 0");
+  if (max_iter < 0) return fail(PROGOT_ERR_INVALID_ARG, "max_iter must be >= 0");
+  Workspace ws;
+  rc = carve(n, m, d, workspace, ws_bytes, &ws);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  rc = zero_counters(ws, ws_dims(n, m, d).rbmax, s);
+  if (rc) return rc;
+  if (init_zero) {
+    CK(cudaMemsetAsync(f, 0, sizeof(float) * n, s));
+    CK(cudaMemsetAsync(g, 0, sizeof(float) * m, s));
+  }
+  CK(launch_row_sqnorm(x, n, d, ws.xn, s));
+  CK(launch_row_sqnorm(y, m, d, ws.yn, s));
+  return sinkhorn_core(x, a, n, y, b, m, d, eps, tau, max_iter, precision, f, ws.f1, g, ws.xn, ws.yn, ws, iters_out,
+                       err_out, s);
+}
+
+int entropic_map_apply(const float* xq, int64_t nq, const float* y, int64_t m, int32_t d, int32_t K,
+                       const float* g_all, const double* eps, const double* alpha, int32_t precision, float* out,
+                       void* workspace, size_t ws_bytes, progot_stream_t stream) {
+  t_last_error.clear();
+  int rc = check_common(xq, nq, y, m, d, precision);
+  if (rc) return rc;
+  if (K <= 0 || g_all == nullptr || eps == nullptr || alpha == nullptr || out == nullptr)
+    return fail(PROGOT_ERR_INVALID_ARG, "K > 0 and non-NULL g_all, eps, alpha, out are required");
+  for (int k = 0; k < K; ++k) {
+    if (!(eps[k] > 0.0) || !std::isfinite(eps[k])) return fail(PROGOT_ERR_INVALID_ARG, "eps[%d] must be positive", k);
+    if (k < K - 1 && !(alpha[k] > 0.0 && alpha[k] <= 1.0))
+      return fail(PROGOT_ERR_INVALID_ARG, "alpha[%d] must lie in (0, 1]", k);
+  }
+  Workspace ws;
+  rc = carve(nq, m, d, workspace, ws_bytes, &ws);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  rc = zero_counters(ws, ws_dims(nq, m, d).rbmax, s);
+  if (rc) return rc;
+  if (out != xq) CK(cudaMemcpyAsync(out, xq, sizeof(float) * nq * d, cudaMemcpyDeviceToDevice, s));
+  CK(launch_row_sqnorm(y, m, d, ws.yn, s));
+  for (int k = 0; k < K; ++k) {
+    const double al = (k == K - 1) ? 1.0 : alpha[k];
+    rc = map_step(out, nq, y, m, d, g_all + (int64_t)k * m, ws.yn, eps[k], al, precision, ws, s);
+    if (rc) return rc;
+  }
+  return PROGOT_OK;
+}
+
+int coupling_marginals(const float* x, int64_t n, const float* y, int64_t m, int32_t d, const float* f,
+                       const float* g, double eps, int32_t precision, float* row, float* col, const float* a,
+                       const float* b, double* err_l1_out, void* workspace, size_t ws_bytes, progot_stream_t stream) {
+  t_last_error.clear();
+  int rc = check_common(x, n, y, m, d, precision);
+  if (rc) return rc;
+  if (f == nullptr || g == nullptr) return fail(PROGOT_ERR_INVALID_ARG, "f and g must not be NULL");
+  if (!(eps > 0.0) || !std::isfinite(eps)) return fail(PROGOT_ERR_INVALID_ARG, "eps must be positive and finite");
+  Workspace ws;
+  rc = carve(n, m, d, workspace, ws_bytes, &ws);
+  if (rc) return rc;
+  rc = t_host.init();
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const WsDims w = ws_dims(n, m, d);
+  rc = zero_counters(ws, w.rbmax, s);
+  if (rc) return rc;
+  CK(launch_row_sqnorm(x, n, d, ws.xn, s));
+  CK(launch_row_sqnorm(y, m, d, ws.yn, s));
+  SweepParams pr = make_sweep(x, n, y, m, d, ws.xn, ws.yn, eps, ws);
+  pr.wA = a;
+  pr.potB = g;
+  pr.potA_old = f;
+  pr.out = row;
+  pr.mode = kModeMarginal;
+  rc = lse_sweep(pr, precision, s);
+  if (rc) return rc;
+  const int64_t rbr = cdiv(n, fp32_tile_rows());
+  CK(cudaMemcpyAsync(&t_host.hd[0], ws.errpart + rbr, sizeof(double), cudaMemcpyDeviceToHost, s));
+  SweepParams pc = make_sweep(y, m, x, n, d, ws.yn, ws.xn, eps, ws);
+  pc.wA = b;
+  pc.potB = f;
+  pc.potA_old = g;
+  pc.out = col;
+  pc.mode = kModeMarginal;
+  rc = lse_sweep(pc, precision, s);
+  if (rc) return rc;
+  const int64_t rbc = cdiv(m, fp32_tile_rows());
+  CK(cudaMemcpyAsync(&t_host.hd[1], ws.errpart + rbc, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (err_l1_out) *err_l1_out = t_host.hd[0] + t_host.hd[1];
+  return PROGOT_OK;
+}
+
+int progot_solve(const float* x, const float* a, int64_t n, const float* y, const float* b, int64_t m, int32_t d,
+                 int32_t K, const double* alpha, const double* eps, const double* tau, int32_t max_iter,
+                 int32_t precision, float* x_out, float* g_all, float* f_last, float* x_last, int32_t* iters,
+                 double* errs, void* workspace, size_t ws_bytes, progot_stream_t stream) {
+  t_last_error.clear();
+  int rc = check_common(x, n, y, m, d, precision);
+  if (rc) return rc;
+  if (K <= 0 || alpha == nullptr || eps == nullptr || tau == nullptr || x_out == nullptr || g_all == nullptr)
+    return fail(PROGOT_ERR_INVALID_ARG, "K > 0 and non-NULL alpha, eps, tau, x_out, g_all are required");
+  if (max_iter < 0) return fail(PROGOT_ERR_INVALID_ARG, "max_iter must be >= 0");
+  for (int k = 0; k < K; ++k) {
+    if (!(eps[k] > 0.0) || !std::isfinite(eps[k])) return fail(PROGOT_ERR_INVALID_ARG, "eps[%d] must be positive", k);
+    if (!(alpha[k] > 0.0 && alpha[k] <= 1.0)) return fail(PROGOT_ERR_INVALID_ARG, "alpha[%d] must lie in (0, 1]", k);
+    if (!(tau[k] >= 0.0)) return fail(PROGOT_ERR_INVALID_ARG, "tau[%d] must be >= 0", k);
+  }
+  Workspace ws;
+  rc = carve(n, m, d, workspace, ws_bytes, &ws);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  rc = zero_counters(ws, ws_dims(n, m, d).rbmax, s);
+  if (rc) return rc;
+  if (x_out != x) CK(cudaMemcpyAsync(x_out, x, sizeof(float) * n * d, cudaMemcpyDeviceToDevice, s));
+  CK(launch_row_sqnorm(y, m, d, ws.yn, s));
+  CK(cudaMemsetAsync(ws.f0, 0, sizeof(float) * n, s));
+  int worst = PROGOT_OK;
+  std::string worst_msg;
+  for (int k = 0; k < K; ++k) {
+    float* gk = g_all + (int64_t)k * m;
+    if (k == 0) {
+      CK(cudaMemsetAsync(gk, 0, sizeof(float) * m, s));
+    } else {
+      // warm start of Alg. 2: (1 - alpha_k) f, (1 - alpha_k) g^(k-1)
+      const float c = (float)(1.0 - alpha[k]);
+      CK(cudaMemcpyAsync(gk, gk - m, sizeof(float) * m, cudaMemcpyDeviceToDevice, s));
+      CK(launch_scale(gk, m, c, s));
+      CK(launch_scale(ws.f0, n, c, s));
+    }
+    if (x_last != nullptr && k == K - 1)
+      CK(cudaMemcpyAsync(x_last, x_out, sizeof(float) * n * d, cudaMemcpyDeviceToDevice, s));
+    CK(launch_row_sqnorm(x_out, n, d, ws.xn, s));
+    int32_t it = 0;
+    double err = 0.0;
+    rc = sinkhorn_core(x_out, a, n, y, b, m, d, eps[k], tau[k], max_iter, precision, ws.f0, ws.f1, gk, ws.xn, ws.yn,
+                       ws, &it, &err, s);
+    if (iters) iters[k] = it;
+    if (errs) errs[k] = err;
+    if (rc == PROGOT_ERR_NOT_CONVERGED) {
+      if (worst == PROGOT_OK) {
+        worst = rc;
+        worst_msg = "step " + std::to_string(k + 1) + ": " + t_last_error;
+      }
+    } else if (rc) {
+      return rc;
+    }
+    rc = map_step(x_out, n, y, m, d, gk, ws.yn, eps[k], alpha[k], precision, ws, s);
+    if (rc) return rc;
+  }
+  if (f_last) CK(cudaMemcpyAsync(f_last, ws.f0, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  if (worst) {
+    t_last_error = worst_msg;
+    return worst;
+  }
+  t_last_error.clear();
+  return PROGOT_OK;
+}
+
+int progot_schedule_alpha(int32_t K, int32_t kind, double* out) {
+  t_last_error.clear();
+  if (K <= 0 || out == nullptr) return fail(PROGOT_ERR_INVALID_ARG, "K > 0 and out required");
+  if (kind == PROGOT_ALPHA_DECELERATED) {
+    for (int k = 0; k < K; ++k) out[k] = 1.0 / std::exp(1.0);
+  } else if (kind == PROGOT_ALPHA_CONSTANT || kind == PROGOT_ALPHA_ACCELERATED) {
+    auto t = [&](int k) {
+      const double r = (double)k / (double)K;
+      return kind == PROGOT_ALPHA_CONSTANT ? r : r * r;
+    };
+    for (int k = 1; k <= K; ++k) out[k - 1] = (t(k) - t(k - 1)) / (1.0 - t(k - 1));
+  } else {
+    return fail(PROGOT_ERR_INVALID_ARG, "unknown alpha schedule %d", kind);
+  }
+  out[K - 1] = 1.0;
+  return PROGOT_OK;
+}
+
+int progot_mean_cost(const float* x, int64_t n, const float* y, int64_t m, int32_t d, double* out, void* workspace,
+                     size_t ws_bytes, progot_stream_t stream) {
+  t_last_error.clear();
+  int rc = check_common(x, n, y, m, d, PROGOT_FP32);
+  if (rc) return rc;
+  if (out == nullptr) return fail(PROGOT_ERR_INVALID_ARG, "out must not be NULL");
+  Workspace ws;
+  rc = carve(n, m, d, workspace, ws_bytes, &ws);
+  if (rc) return rc;
+  rc = t_host.init();
+  if (rc) return rc;
+  if (2 * (d + 1) > 1024) return fail(PROGOT_ERR_INVALID_ARG, "d too large for the mean-cost reduction");
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(launch_moments(x, n, d, ws.rpart, reduce_parts(), ws.rout, s));
+  CK(launch_moments(y, m, d, ws.rpart, reduce_parts(), ws.rout + (d + 1), s));
+  CK(cudaMemcpyAsync(t_host.hd, ws.rout, sizeof(double) * 2 * (d + 1), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const double* mx = t_host.hd;
+  const double* my = t_host.hd + (d + 1);
+  double dot = 0.0;
+  for (int k = 0; k < d; ++k) dot += (mx[1 + k] / (double)n) * (my[1 + k] / (double)m);
+  *out = mx[0] / (double)n + my[0] / (double)m - 2.0 * dot;
+  return PROGOT_OK;
+}
+
+int progot_schedule_eps(const float* x, int64_t n, const float* y, const float* b, int64_t m, const float* y_test,
+                        int64_t mt, int32_t d, int32_t K, const double* alpha, const double* s_grid, int32_t P,
+                        double beta0, double tau, int32_t max_iter, int32_t precision, double* eps_out,
+                        double* errors_out, int32_t* p_star_out, void* workspace, size_t ws_bytes,
+                        progot_stream_t stream) {
+  t_last_error.clear();
+  int rc = check_common(x, n, y, m, d, precision);
+  if (rc) return rc;
+  if (y_test == nullptr || mt <= 0 || K <= 0 || alpha == nullptr || s_grid == nullptr || P <= 0 ||
+      eps_out == nullptr)
+    return fail(PROGOT_ERR_INVALID_ARG, "y_test, mt > 0, K > 0, alpha, s_grid, P > 0 and eps_out are required");
+  const int64_t nmax = std::max<int64_t>(std::max<int64_t>(n, m), mt);
+  Workspace ws;
+  rc = carve(nmax, nmax, d, workspace, ws_bytes, &ws);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  double mc_xy = 0.0, mc_yy = 0.0;
+  rc = progot_mean_cost(x, n, y, m, d, &mc_xy, workspace, ws_bytes, stream);
+  if (rc) return rc;
+  rc = progot_mean_cost(y, m, y, m, d, &mc_yy, workspace, ws_bytes, stream);
+  if (rc) return rc;
+  const double eps0 = mc_xy / 20.0, sigma = mc_yy / 20.0;
+  rc = zero_counters(ws, ws_dims(nmax, nmax, d).rbmax, s);
+  if (rc) return rc;
+  CK(launch_row_sqnorm(y, m, d, ws.yn, s));
+  std::vector<double> errors(P);
+  for (int p = 0; p < P; ++p) {
+    const double eps = s_grid[p] * sigma;
+    CK(cudaMemsetAsync(ws.f0, 0, sizeof(float) * m, s));
+    CK(cudaMemsetAsync(ws.gaux, 0, sizeof(float) * m, s));
+    rc = sinkhorn_core(y, b, m, y, b, m, d, eps, tau, max_iter, precision, ws.f0, ws.f1, ws.gaux, ws.yn, ws.yn, ws,
+                       nullptr, nullptr, s);
+    if (rc && rc != PROGOT_ERR_NOT_CONVERGED) return rc;
+    CK(cudaMemcpyAsync(ws.T, y_test, sizeof(float) * mt * d, cudaMemcpyDeviceToDevice, s));
+    rc = map_step(ws.T, mt, y, m, d, ws.gaux, ws.yn, eps, 1.0, precision, ws, s);
+    if (rc) return rc;
+    CK(launch_sq_error(y_test, ws.T, mt, d, ws.rpart, reduce_parts(), ws.rout, s));
+    rc = t_host.init();
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(t_host.hd, ws.rout, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    errors[p] = t_host.hd[0];
+  }
+  int pstar = 0;
+  for (int p = 1; p < P; ++p)
+    if (errors[p] < errors[pstar]) pstar = p;
+  const double epsK = s_grid[pstar] * sigma;
+  double prod = 1.0;
+  for (int k = 0; k < K; ++k) {
+    prod *= (1.0 - alpha[k]);
+    const double t = 1.0 - prod;
+    eps_out[k] = (1.0 - t) * beta0 * eps0 + t * epsK;
+  }
+  if (errors_out)
+    for (int p = 0; p < P; ++p) errors_out[p] = errors[p];
+  if (p_star_out) *p_star_out = pstar;
+  t_last_error.clear();
+  return PROGOT_OK;
+}
+
+}  // extern "C"

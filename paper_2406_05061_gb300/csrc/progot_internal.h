@@ -1,0 +1,51 @@
+// Internal (C++) interfaces between the host orchestration and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "progot_common.cuh"
+
+namespace progot {
+
+// Parameters of the barycentric-projection sweep (map step of Alg. 2 / Alg. 3).
+struct MapParams {
+  const float* A;      // nA x d current points (may alias out)
+  const float* B;      // nB x d target points
+  const float* Bn;     // |b_j|^2
+  const float* potB;   // g
+  const float* L;      // per-row log2-sum-exp of t_ij (from an LSE sweep)
+  float* out;          // nA x d: x + alpha (T(x) - x)
+  float* Opart;        // [splits][nA][d] partial numerators
+  float* Rpart;        // [splits][nA] partial row sums of P
+  unsigned int* cnt;   // [row blocks] arrival counters (zero between launches)
+  int64_t nA, nB;
+  int32_t d;
+  int32_t splits, tiles_per_split, dchunks;
+  float scale, bscale;
+  float alpha;
+};
+
+void count_launch();
+
+// float32 CUDA-core sweeps (sweep_fp32.cu)
+cudaError_t launch_lse_sweep_fp32(const SweepParams& p, cudaStream_t stream);
+cudaError_t launch_map_sweep_fp32(const MapParams& p, cudaStream_t stream);
+int fp32_tile_rows();
+int fp32_tile_cols();
+int map_dchunk();
+
+// small kernels (prep.cu)
+cudaError_t launch_row_sqnorm(const float* X, int64_t n, int32_t d, float* out, cudaStream_t s);
+cudaError_t launch_scale(float* v, int64_t n, float factor, cudaStream_t s);
+cudaError_t launch_init_state(SolverState* st, cudaStream_t s);
+// out[0] = sum_i |x_i|^2, out[1 + k] = sum_i x_ik (float64; partial buffer of
+// `parts` x (d + 1) doubles, deterministic two-pass reduction)
+cudaError_t launch_moments(const float* X, int64_t n, int32_t d, double* partial, int parts, double* out,
+                           cudaStream_t s);
+// out[0] = sum_i ||a_i - b_i||^2 (float64, deterministic)
+cudaError_t launch_sq_error(const float* A, const float* B, int64_t n, int32_t d, double* partial, int parts,
+                            double* out, cudaStream_t s);
+int reduce_parts();
+
+}  // namespace progot

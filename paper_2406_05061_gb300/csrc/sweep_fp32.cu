@@ -1,0 +1,469 @@
+// CUDA-core (float32 FMA) sweeps of the ProgOT hot path.
+//
+// lse_sweep_fp32: for every row a_i of A, L_i = log2 sum_j 2^{t_ij} with
+//   t_ij = (2 a_i . b_j + potB_j - |b_j|^2) * log2(e) / eps,
+// i.e. the soft-min of Sec. 2 over the squared Euclidean cost with the row constant
+// |a_i|^2 factored out. The cost matrix is never stored: each CTA owns BM = 128 rows
+// and streams BN = 128 columns at a time through shared memory, computing the 128 x 128
+// tile of dot products with a register-blocked (8 x 8 per thread) float32 FMA loop and
+// folding it into an online (max, sum) per row. Columns are split over gridDim.y; the
+// last CTA to finish a row block combines the splits in split order (deterministic)
+// and applies the epilogue (Sinkhorn update with the fused marginal-error term of
+// Alg. 1, raw L, or the coupling marginal).
+//
+// map_sweep_fp32: the barycentric projection of Alg. 2 / Alg. 3: with L_i known,
+//   T_i = sum_j 2^{t_ij - L_i} y_j / sum_j 2^{t_ij - L_i},
+//   x_i <- x_i + alpha (T_i - x_i).
+#include "progot_common.cuh"
+#include "progot_internal.h"
+
+namespace progot {
+
+constexpr int BM = 128, BN = 128, BK = 16, NT = 256;
+constexpr int DCH = 64;  // columns of d handled per CTA by the map sweep
+
+// Load one BK-wide chunk of `rows` rows (starting at r0) of a row-major (nrows x d)
+// matrix into registers; zero outside [0, nrows) x [0, d).
+struct ChunkLoader {
+  float4 v[2];
+  __device__ __forceinline__ void load(const float* __restrict__ M, int64_t nrows, int d, int64_t r0, int k0,
+                                       bool vec_ok) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      int e = threadIdx.x + NT * q;  // 0..511: (row, kq)
+      int r = e >> 2, kq = e & 3;
+      int64_t gr = r0 + r;
+      int k = k0 + kq * 4;
+      float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (gr < nrows) {
+        const float* src = M + gr * (int64_t)d + k;
+        if (vec_ok) {
+          if (k < d) val = __ldg(reinterpret_cast<const float4*>(src));
+        } else {
+          if (k + 0 < d) val.x = __ldg(src + 0);
+          if (k + 1 < d) val.y = __ldg(src + 1);
+          if (k + 2 < d) val.z = __ldg(src + 2);
+          if (k + 3 < d) val.w = __ldg(src + 3);
+        }
+      }
+      v[q] = val;
+    }
+  }
+  // store transposed: S[k][row]
+  __device__ __forceinline__ void store(float (*S)[BM]) const {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      int e = threadIdx.x + NT * q;
+      int r = e >> 2, kq = e & 3;
+      S[kq * 4 + 0][r] = v[q].x;
+      S[kq * 4 + 1][r] = v[q].y;
+      S[kq * 4 + 2][r] = v[q].z;
+      S[kq * 4 + 3][r] = v[q].w;
+    }
+  }
+};
+
+struct GemmSmem {
+  float As[2][BK][BM];
+  float Bs[2][BK][BN];
+};
+
+// acc[r][c] = a_row(r) . b_col(c) for the thread's 8 x 8 block of a 128 x 128 tile.
+// Rows of the thread: ty*4 + {0..3} and 64 + ty*4 + {0..3}; columns likewise with tx.
+__device__ __forceinline__ void tile_dots(GemmSmem& sm, const float* __restrict__ A, int64_t nA,
+                                          const float* __restrict__ B, int64_t nB, int d, int64_t row0,
+                                          int64_t col0, bool vec_ok, float (&acc)[8][8]) {
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
+  const int nk = (d + BK - 1) / BK;
+  ChunkLoader la, lb;
+  la.load(A, nA, d, row0, 0, vec_ok);
+  lb.load(B, nB, d, col0, 0, vec_ok);
+  __syncthreads();  // previous users of buffer 0 are done
+  la.store(sm.As[0]);
+  lb.store(sm.Bs[0]);
+  __syncthreads();
+  for (int kc = 0; kc < nk; ++kc) {
+    const int buf = kc & 1;
+    if (kc + 1 < nk) {
+      la.load(A, nA, d, row0, (kc + 1) * BK, vec_ok);
+      lb.load(B, nB, d, col0, (kc + 1) * BK, vec_ok);
+    }
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      float4 a0 = *reinterpret_cast<const float4*>(&sm.As[buf][kk][ty * 4]);
+      float4 a1 = *reinterpret_cast<const float4*>(&sm.As[buf][kk][64 + ty * 4]);
+      float4 b0 = *reinterpret_cast<const float4*>(&sm.Bs[buf][kk][tx * 4]);
+      float4 b1 = *reinterpret_cast<const float4*>(&sm.Bs[buf][kk][64 + tx * 4]);
+      float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
+    }
+    if (kc + 1 < nk) {
+      la.store(sm.As[buf ^ 1]);
+      lb.store(sm.Bs[buf ^ 1]);
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ int thread_row(int r) {  // 0..127
+  const int ty = threadIdx.x >> 4;
+  return (r < 4) ? ty * 4 + r : 64 + ty * 4 + (r - 4);
+}
+__device__ __forceinline__ int thread_col(int c) {
+  const int tx = threadIdx.x & 15;
+  return (c < 4) ? tx * 4 + c : 64 + tx * 4 + (c - 4);
+}
+
+// Block-wide float64 sum (deterministic order). Returns the total in thread 0.
+__device__ double block_sum_f64(double v, double* red) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double tot = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < NT / 32; ++w) tot += red[w];
+  return tot;
+}
+
+// Called by the last CTA of the whole sweep (thread 0): sum the per-row-block error
+// partials in order and advance the device-side Sinkhorn state.
+__device__ void finish_sweep(const SweepParams& p, int nblocks) {
+  double err = 0.0;
+  for (int b = 0; b < nblocks; ++b) err += __ldcg(p.errpart + b);
+  p.errpart[nblocks] = err;
+  SolverState* st = p.state;
+  if (st == nullptr) return;
+  if (p.role == 1) {
+    st->err = err;
+    const int it = st->it;
+    if (!isfinite(err)) {
+      st->status = kNumeric;
+      st->done = 1;
+    } else if (err <= p.tau) {
+      st->status = kConverged;
+      st->done = 1;
+    } else if (it >= p.max_iter) {
+      st->status = kMaxIter;
+      st->done = 1;
+    } else {
+      if (err < 0.99 * st->best_err) {
+        st->best_err = err;
+        st->best_it = it;
+      } else if (p.stall_window > 0 && it - st->best_it >= p.stall_window) {
+        st->status = kStalled;
+        st->done = 1;
+      }
+      if (!st->done) st->fcur ^= 1;  // the new f becomes current
+    }
+  } else if (p.role == 2) {
+    st->it += 1;
+  }
+}
+
+// Epilogue for one row given L (log2 units). Returns the row's error term.
+__device__ __forceinline__ double row_epilogue(const SweepParams& p, int64_t i, float L, const float* potA_cur,
+                                               float* out_target) {
+  const double w = p.wA ? (double)p.wA[i] : p.inv_nA;
+  if (p.mode == kModePotential) {
+    const float fnew = (float)(p.eps * log(w) + (double)p.An[i] - p.eps * kLn2 * (double)L);
+    out_target[i] = fnew;
+    if (p.role == 1) {
+      const double fold = (double)potA_cur[i];
+      return w * fabs(exp((fold - (double)fnew) / p.eps) - 1.0);
+    }
+    return 0.0;
+  }
+  if (p.mode == kModeLse) {
+    out_target[i] = L;
+    return 0.0;
+  }
+  // marginal
+  const double r = exp(((double)potA_cur[i] - (double)p.An[i]) / p.eps + kLn2 * (double)L);
+  if (out_target) out_target[i] = (float)r;
+  return fabs(r - w);
+}
+
+__global__ void __launch_bounds__(NT, 2) lse_sweep_fp32(SweepParams p) {
+  if (p.state != nullptr && p.state->done) return;
+  __shared__ GemmSmem sm;
+  __shared__ float beta_s[BN];
+  __shared__ double red[NT / 32];
+  __shared__ int s_last;
+
+  const int fcur = p.state ? p.state->fcur : 0;
+  const float* potB = (p.potB_alt && fcur == 1) ? p.potB_alt : p.potB;
+  const int tx = threadIdx.x & 15;
+  const int64_t row0 = (int64_t)blockIdx.x * BM;
+  const int ntiles = (int)((p.nB + BN - 1) / BN);
+  const int t_begin = blockIdx.y * p.tiles_per_split;
+  const int t_end = min(ntiles, t_begin + p.tiles_per_split);
+  const bool vec_ok = ((p.d & 3) == 0) && ((reinterpret_cast<uintptr_t>(p.A) & 15) == 0) &&
+                      ((reinterpret_cast<uintptr_t>(p.B) & 15) == 0);
+
+  float m_run[8], s_run[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    m_run[r] = -INFINITY;
+    s_run[r] = 0.f;
+  }
+  float acc[8][8];
+  for (int tile = t_begin; tile < t_end; ++tile) {
+    const int64_t col0 = (int64_t)tile * BN;
+    __syncthreads();  // beta_s of the previous tile is no longer read
+    if (threadIdx.x < BN) {
+      const int64_t j = col0 + threadIdx.x;
+      beta_s[threadIdx.x] = (j < p.nB) ? (potB[j] - p.Bn[j]) * p.bscale : -INFINITY;
+    }
+    tile_dots(sm, p.A, p.nA, p.B, p.nB, p.d, row0, col0, vec_ok, acc);  // ends with __syncthreads
+    float bcol[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) bcol[c] = beta_s[thread_col(c)];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      float t[8];
+      float tmax = -INFINITY;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        t[c] = fmaf(acc[r][c], p.scale, bcol[c]);
+        tmax = fmaxf(tmax, t[c]);
+      }
+      const float mnew = fmaxf(m_run[r], tmax);
+      if (mnew != -INFINITY) {
+        float s = s_run[r] * fast_exp2(m_run[r] - mnew);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) s += fast_exp2(t[c] - mnew);
+        s_run[r] = s;
+        m_run[r] = mnew;
+      }
+    }
+  }
+  // reduce over the 16 threads that share rows (lanes tx = 0..15 of a half warp)
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    float2 v = make_float2(m_run[r], s_run[r]);
+#pragma unroll
+    for (int off = 8; off > 0; off >>= 1) {
+      float2 o;
+      o.x = __shfl_xor_sync(0xffffffffu, v.x, off);
+      o.y = __shfl_xor_sync(0xffffffffu, v.y, off);
+      v = lse_combine(v, o);
+    }
+    if (tx == 0) {
+      const int64_t i = row0 + thread_row(r);
+      if (i < p.nA) p.partial[(int64_t)blockIdx.y * p.nA + i] = v;
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(&p.cnt[blockIdx.x], 1u);
+    s_last = (prev == (unsigned)(p.splits - 1));
+  }
+  __syncthreads();
+  if (!s_last) return;
+
+  // ---- last CTA of this row block: combine splits in order, epilogue
+  const float* potA_cur = p.potA_old;
+  float* out_target = p.out;
+  if (p.role == 1) {
+    potA_cur = (fcur == 0) ? p.out : p.out_alt;
+    out_target = (fcur == 0) ? p.out_alt : p.out;
+  }
+  double e = 0.0;
+  if (threadIdx.x < BM) {
+    const int64_t i = row0 + threadIdx.x;
+    if (i < p.nA) {
+      float2 v = make_float2(-INFINITY, 0.f);
+      for (int s = 0; s < p.splits; ++s) v = lse_combine(v, __ldcg(&p.partial[(int64_t)s * p.nA + i]));
+      const float L = v.x + __log2f(v.y);
+      e = row_epilogue(p, i, L, potA_cur, out_target);
+    }
+  }
+  const double tot = block_sum_f64(e, red);
+  if (threadIdx.x == 0) {
+    p.errpart[blockIdx.x] = tot;
+    p.cnt[blockIdx.x] = 0;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(&p.cnt[gridDim.x], 1u);
+    if (prev == gridDim.x - 1) {
+      __threadfence();
+      finish_sweep(p, gridDim.x);
+      p.cnt[gridDim.x] = 0;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- map sweep
+struct MapSmem {
+  GemmSmem g;
+  float Ps[BN][BM];   // P tile stored transposed: Ps[c][r]
+  float Ys[BN][DCH];  // d-chunk of the B tile for the P . Y product
+};
+
+size_t map_sweep_fp32_smem() { return sizeof(MapSmem); }
+
+__global__ void __launch_bounds__(NT, 1) map_sweep_fp32(MapParams p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  MapSmem& sm = *reinterpret_cast<MapSmem*>(smem_raw);
+  __shared__ float beta_s[BN];
+  __shared__ float Lrow[BM];
+  __shared__ float den[BM];
+  __shared__ int s_last;
+
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t row0 = (int64_t)blockIdx.x * BM;
+  const int dch0 = blockIdx.z * DCH;
+  const int ntiles = (int)((p.nB + BN - 1) / BN);
+  const int t_begin = blockIdx.y * p.tiles_per_split;
+  const int t_end = min(ntiles, t_begin + p.tiles_per_split);
+  const bool vec_ok = ((p.d & 3) == 0) && ((reinterpret_cast<uintptr_t>(p.A) & 15) == 0) &&
+                      ((reinterpret_cast<uintptr_t>(p.B) & 15) == 0);
+  if (threadIdx.x < BM) {
+    const int64_t i = row0 + threadIdx.x;
+    Lrow[threadIdx.x] = (i < p.nA) ? p.L[i] : 0.f;
+  }
+  float o[8][4];
+  float rs[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    rs[r] = 0.f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) o[r][c] = 0.f;
+  }
+  float acc[8][8];
+  for (int tile = t_begin; tile < t_end; ++tile) {
+    const int64_t col0 = (int64_t)tile * BN;
+    __syncthreads();  // the previous tile's Ps / Ys / beta_s are no longer read
+    if (threadIdx.x < BN) {
+      const int64_t j = col0 + threadIdx.x;
+      beta_s[threadIdx.x] = (j < p.nB) ? (p.potB[j] - p.Bn[j]) * p.bscale : -INFINITY;
+    }
+    for (int e = threadIdx.x; e < BN * DCH; e += NT) {
+      const int c = e / DCH, k = e % DCH;
+      const int64_t j = col0 + c;
+      const int kk = dch0 + k;
+      sm.Ys[c][k] = (j < p.nB && kk < p.d) ? __ldg(p.B + j * (int64_t)p.d + kk) : 0.f;
+    }
+    tile_dots(sm.g, p.A, p.nA, p.B, p.nB, p.d, row0, col0, vec_ok, acc);  // syncs at entry and exit
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int rr = thread_row(r);
+      const float Lr = Lrow[rr];
+      float part = 0.f;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int cc = thread_col(c);
+        const float pv = fast_exp2(fmaf(acc[r][c], p.scale, beta_s[cc]) - Lr);
+        sm.Ps[cc][rr] = pv;
+        part += pv;
+      }
+      rs[r] += part;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int c = 0; c < BN; ++c) {
+      const float4 p0 = *reinterpret_cast<const float4*>(&sm.Ps[c][ty * 4]);
+      const float4 p1 = *reinterpret_cast<const float4*>(&sm.Ps[c][64 + ty * 4]);
+      const float4 yv = *reinterpret_cast<const float4*>(&sm.Ys[c][tx * 4]);
+      const float pr[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+      const float yk[4] = {yv.x, yv.y, yv.z, yv.w};
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) o[r][k] = fmaf(pr[r], yk[k], o[r][k]);
+    }
+  }
+  // row sums of P over this split: sum the 16 column groups of a half warp
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    float v = rs[r];
+#pragma unroll
+    for (int off = 8; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    rs[r] = v;
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int64_t i = row0 + thread_row(r);
+    if (i >= p.nA) continue;
+    float* dst = p.Opart + ((int64_t)blockIdx.y * p.nA + i) * p.d;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int kk = dch0 + tx * 4 + k;
+      if (kk < p.d) dst[kk] = o[r][k];
+    }
+    if (blockIdx.z == 0 && tx == 0) p.Rpart[(int64_t)blockIdx.y * p.nA + i] = rs[r];
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(&p.cnt[blockIdx.x], 1u);
+    s_last = (prev == (unsigned)(p.splits * p.dchunks - 1));
+  }
+  __syncthreads();
+  if (!s_last) return;
+  // ---- last CTA of this row block: T_i = sum_s O_s / sum_s R_s, x <- x + alpha (T - x)
+  if (threadIdx.x < BM) {
+    const int64_t i = row0 + threadIdx.x;
+    float dsum = 0.f;
+    if (i < p.nA)
+      for (int s = 0; s < p.splits; ++s) dsum += __ldcg(p.Rpart + (int64_t)s * p.nA + i);
+    den[threadIdx.x] = dsum;
+  }
+  __syncthreads();
+  const int64_t rem = p.nA - row0;
+  const int rows = rem < BM ? (int)rem : BM;
+  for (int e = threadIdx.x; e < rows * p.d; e += NT) {
+    const int r = e / p.d, k = e % p.d;
+    const int64_t i = row0 + r;
+    float num = 0.f;
+    for (int s = 0; s < p.splits; ++s) num += __ldcg(p.Opart + ((int64_t)s * p.nA + i) * p.d + k);
+    const float T = num / den[r];
+    const float x = p.A[i * (int64_t)p.d + k];
+    p.out[i * (int64_t)p.d + k] = fmaf(p.alpha, T - x, x);
+  }
+  if (threadIdx.x == 0) p.cnt[blockIdx.x] = 0;
+}
+
+// ---------------------------------------------------------------- launchers
+cudaError_t launch_lse_sweep_fp32(const SweepParams& p, cudaStream_t stream) {
+  const int rb = (int)((p.nA + BM - 1) / BM);
+  dim3 grid(rb, p.splits);
+  lse_sweep_fp32<<<grid, NT, 0, stream>>>(p);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_map_sweep_fp32(const MapParams& p, cudaStream_t stream) {
+  static bool attr_set = false;
+  const size_t smem = sizeof(MapSmem);
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(map_sweep_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int rb = (int)((p.nA + BM - 1) / BM);
+  dim3 grid(rb, p.splits, p.dchunks);
+  map_sweep_fp32<<<grid, NT, smem, stream>>>(p);
+  count_launch();
+  return cudaGetLastError();
+}
+
+int fp32_tile_rows() { return BM; }
+int fp32_tile_cols() { return BN; }
+int map_dchunk() { return DCH; }
+
+}  // namespace progot

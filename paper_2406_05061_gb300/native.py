@@ -1,0 +1,333 @@
+"""Thin ctypes binding of libprogot.so (include/progot.h).
+
+Argument marshalling only: every step of the computation runs in the library's CUDA
+kernels. Device arrays are torch CUDA tensors (float32, contiguous); their raw
+pointers and torch's current stream are handed to the C ABI. There is no CPU
+fallback: if the library is not built or no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libprogot.so")
+
+PROGOT_OK = 0
+PROGOT_ERR_INVALID_ARG = 1
+PROGOT_ERR_NOT_CONVERGED = 2
+PROGOT_ERR_NUMERIC = 3
+PROGOT_ERR_OOM = 4
+PROGOT_ERR_CUDA = 5
+PROGOT_ERR_TIMEOUT = 6
+PROGOT_ERR_WORKSPACE = 7
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "NOT_CONVERGED", 3: "NUMERIC", 4: "OOM", 5: "CUDA", 6: "TIMEOUT",
+                7: "WORKSPACE"}
+
+PRECISIONS = {"fp32": 0, "bf16x3": 1, "bf16": 2}
+ALPHA_KINDS = {"constant": 0, "accelerated": 1, "decelerated": 2}
+
+# (name, restype, argtypes) of every exported symbol of include/progot.h
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+_D = ctypes.c_double
+_SZ = ctypes.c_size_t
+SIGNATURES = [
+    ("progot_last_error_string", ctypes.c_char_p, []),
+    ("progot_version", ctypes.c_char_p, []),
+    ("progot_workspace_size", _SZ, [_I64, _I64, _I32, _I32]),
+    ("sinkhorn_potentials", ctypes.c_int,
+     [_P, _P, _I64, _P, _P, _I64, _I32, _D, _D, _I32, _I32, _P, _P, _I32, _P, _P, _P, _SZ, _P]),
+    ("entropic_map_apply", ctypes.c_int, [_P, _I64, _P, _I64, _I32, _I32, _P, _P, _P, _I32, _P, _P, _SZ, _P]),
+    ("coupling_marginals", ctypes.c_int,
+     [_P, _I64, _P, _I64, _I32, _P, _P, _D, _I32, _P, _P, _P, _P, _P, _P, _SZ, _P]),
+    ("progot_solve", ctypes.c_int,
+     [_P, _P, _I64, _P, _P, _I64, _I32, _I32, _P, _P, _P, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
+    ("progot_schedule_alpha", ctypes.c_int, [_I32, _I32, _P]),
+    ("progot_mean_cost", ctypes.c_int, [_P, _I64, _P, _I64, _I32, _P, _P, _SZ, _P]),
+    ("progot_schedule_eps", ctypes.c_int,
+     [_P, _I64, _P, _P, _I64, _P, _I64, _I32, _I32, _P, _P, _I32, _D, _D, _I32, _I32, _P, _P, _P, _P, _SZ, _P]),
+    ("progot_set_stall_window", ctypes.c_int, [_I32]),
+    ("progot_launch_count", ctypes.c_int64, [_I32]),
+    ("progot_profile", ctypes.c_int, [_I32]),
+    ("progot_profile_read", ctypes.c_int, [_I32, _P, _P, _P]),
+]
+
+_lib = None
+
+
+class ProgOTError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def lib() -> ctypes.CDLL:
+    """Load libprogot.so (built in-tree by paper_2406_05061_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run paper_2406_05061_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().progot_last_error_string().decode()
+
+
+def _check(rc: int, allow_not_converged: bool = True) -> int:
+    if rc == PROGOT_OK or (allow_not_converged and rc == PROGOT_ERR_NOT_CONVERGED):
+        return rc
+    raise ProgOTError(rc, last_error())
+
+
+# ------------------------------------------------------------------ helpers
+def _torch():
+    import torch  # noqa: PLC0415  (imported lazily: the CPU tests only load the library)
+    return torch
+
+
+def _dev(t, name, shape=None):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError(f"{name} must be contiguous float32")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _opt(t, name, shape=None):
+    return None if t is None else _dev(t, name, shape)
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _prec(precision) -> int:
+    if isinstance(precision, int):
+        return precision
+    return PRECISIONS[precision]
+
+
+def workspace_size(n: int, m: int, d: int, precision="fp32") -> int:
+    return int(lib().progot_workspace_size(n, m, d, _prec(precision)))
+
+
+class Workspace:
+    """A reusable device workspace (torch uint8 buffer, 256-byte aligned)."""
+
+    def __init__(self, n: int, m: int, d: int, precision="fp32", device=None):
+        torch = _torch()
+        self.bytes = workspace_size(n, m, d, precision)
+        self.buf = torch.empty(self.bytes + 256, dtype=torch.uint8, device=device or "cuda")
+        base = self.buf.data_ptr()
+        self.ptr = (base + 255) & ~255
+        self.dims = (n, m, d, _prec(precision))
+
+    def covers(self, n, m, d, precision) -> bool:
+        return workspace_size(n, m, d, precision) <= self.bytes
+
+
+def _ws(ws, n, m, d, precision):
+    if ws is None or not ws.covers(n, m, d, precision):
+        ws = Workspace(n, m, d, precision)
+    return ws
+
+
+def _host_f64(v, k=None):
+    arr = np.ascontiguousarray(np.asarray(v, dtype=np.float64))
+    if k is not None and arr.shape != (k,):
+        raise ValueError(f"expected {k} values, got shape {arr.shape}")
+    return arr
+
+
+def _hp(arr):
+    return arr.ctypes.data_as(ctypes.c_void_p)
+
+
+# ------------------------------------------------------------------ API
+@dataclass
+class SinkhornOut:
+    f: object
+    g: object
+    iters: int
+    err: float
+    status: int
+
+
+def sinkhorn_potentials(x, y, eps, tau, max_iter=10000, a=None, b=None, f=None, g=None, precision="fp32",
+                        workspace=None, stream=None) -> SinkhornOut:
+    """Alg. 1 on the GPU. f, g (CUDA float32) are used as the initial potentials when
+    given (and overwritten), else zero-initialised tensors are returned."""
+    torch = _torch()
+    _dev(x, "x"), _dev(y, "y")
+    n, d = x.shape
+    m = y.shape[0]
+    init_zero = 1 if (f is None and g is None) else 0
+    if f is None:
+        f = torch.zeros(n, dtype=torch.float32, device=x.device)
+    if g is None:
+        g = torch.zeros(m, dtype=torch.float32, device=x.device)
+    ws = _ws(workspace, n, m, d, precision)
+    it = ctypes.c_int32(0)
+    err = ctypes.c_double(0.0)
+    rc = lib().sinkhorn_potentials(_dev(x, "x"), _opt(a, "a", (n,)), n, _dev(y, "y"), _opt(b, "b", (m,)), m, d,
+                                   float(eps), float(tau), int(max_iter), _prec(precision), _dev(f, "f", (n,)),
+                                   _dev(g, "g", (m,)), init_zero, ctypes.byref(it), ctypes.byref(err),
+                                   ctypes.c_void_p(ws.ptr), ws.bytes, _stream(stream))
+    _check(rc)
+    return SinkhornOut(f, g, it.value, err.value, rc)
+
+
+def entropic_map_apply(xq, y, g_all, eps, alpha, precision="fp32", out=None, workspace=None, stream=None):
+    """Alg. 3 (the progressive map) on nq query points; returns out (nq x d)."""
+    torch = _torch()
+    _dev(xq, "xq"), _dev(y, "y")
+    nq, d = xq.shape
+    m = y.shape[0]
+    K = g_all.shape[0] if g_all.dim() == 2 else 1
+    eps_h = _host_f64(eps, K)
+    al_h = _host_f64(alpha, K)
+    if out is None:
+        out = torch.empty_like(xq)
+    ws = _ws(workspace, nq, m, d, precision)
+    rc = lib().entropic_map_apply(_dev(xq, "xq"), nq, _dev(y, "y"), m, d, K, _dev(g_all.contiguous(), "g_all"),
+                                  _hp(eps_h), _hp(al_h), _prec(precision), _dev(out, "out", (nq, d)),
+                                  ctypes.c_void_p(ws.ptr), ws.bytes, _stream(stream))
+    _check(rc, allow_not_converged=False)
+    return out
+
+
+def coupling_marginals(x, y, f, g, eps, a=None, b=None, precision="fp32", workspace=None, stream=None):
+    """Row and column sums of P = exp((f (+) g - C)/eps) and ||r - a||_1 + ||c - b||_1."""
+    torch = _torch()
+    _dev(x, "x"), _dev(y, "y")
+    n, d = x.shape
+    m = y.shape[0]
+    row = torch.empty(n, dtype=torch.float32, device=x.device)
+    col = torch.empty(m, dtype=torch.float32, device=x.device)
+    err = ctypes.c_double(0.0)
+    ws = _ws(workspace, n, m, d, precision)
+    rc = lib().coupling_marginals(_dev(x, "x"), n, _dev(y, "y"), m, d, _dev(f, "f", (n,)), _dev(g, "g", (m,)),
+                                  float(eps), _prec(precision), _dev(row, "row"), _dev(col, "col"),
+                                  _opt(a, "a", (n,)), _opt(b, "b", (m,)), ctypes.byref(err),
+                                  ctypes.c_void_p(ws.ptr), ws.bytes, _stream(stream))
+    _check(rc, allow_not_converged=False)
+    return row, col, err.value
+
+
+@dataclass
+class ProgOTOut:
+    x_out: object
+    g_all: object
+    f_last: object
+    x_last: object
+    iters: list
+    errs: list
+    status: int
+
+
+def progot_solve(x, y, alpha, eps, tau, max_iter=10000, a=None, b=None, precision="fp32", workspace=None,
+                 stream=None, out=None) -> ProgOTOut:
+    """Alg. 2 on the GPU: K = len(eps) warm-started Sinkhorn solves and displacements."""
+    torch = _torch()
+    _dev(x, "x"), _dev(y, "y")
+    n, d = x.shape
+    m = y.shape[0]
+    K = len(eps)
+    al_h, eps_h, tau_h = _host_f64(alpha, K), _host_f64(eps, K), _host_f64(tau, K)
+    if out is None:
+        out = dict(x_out=torch.empty_like(x), g_all=torch.empty((K, m), dtype=torch.float32, device=x.device),
+                   f_last=torch.empty(n, dtype=torch.float32, device=x.device), x_last=torch.empty_like(x))
+    iters = np.zeros(K, dtype=np.int32)
+    errs = np.zeros(K, dtype=np.float64)
+    ws = _ws(workspace, n, m, d, precision)
+    rc = lib().progot_solve(_dev(x, "x"), _opt(a, "a", (n,)), n, _dev(y, "y"), _opt(b, "b", (m,)), m, d, K,
+                            _hp(al_h), _hp(eps_h), _hp(tau_h), int(max_iter), _prec(precision),
+                            _dev(out["x_out"], "x_out", (n, d)), _dev(out["g_all"], "g_all", (K, m)),
+                            _opt(out.get("f_last"), "f_last", (n,)), _opt(out.get("x_last"), "x_last", (n, d)),
+                            _hp(iters), _hp(errs), ctypes.c_void_p(ws.ptr), ws.bytes, _stream(stream))
+    _check(rc)
+    return ProgOTOut(out["x_out"], out["g_all"], out.get("f_last"), out.get("x_last"), iters.tolist(),
+                     errs.tolist(), rc)
+
+
+def progot_schedule_alpha(K: int, kind="constant") -> np.ndarray:
+    out = np.zeros(K, dtype=np.float64)
+    _check(lib().progot_schedule_alpha(int(K), ALPHA_KINDS[kind] if isinstance(kind, str) else int(kind), _hp(out)),
+           allow_not_converged=False)
+    return out
+
+
+def progot_mean_cost(x, y, workspace=None, stream=None) -> float:
+    n, d = x.shape
+    m = y.shape[0]
+    ws = _ws(workspace, n, m, d, "fp32")
+    out = ctypes.c_double(0.0)
+    _check(lib().progot_mean_cost(_dev(x, "x"), n, _dev(y, "y"), m, d, ctypes.byref(out), ctypes.c_void_p(ws.ptr),
+                                  ws.bytes, _stream(stream)), allow_not_converged=False)
+    return out.value
+
+
+def progot_schedule_eps(x, y, y_test, alpha, s_grid=None, beta0=5.0, tau=1e-6, max_iter=10000, b=None,
+                        precision="fp32", workspace=None, stream=None):
+    """Alg. 4 on the GPU; returns (eps_k array, scores per s_p, p_star)."""
+    n, d = x.shape
+    m = y.shape[0]
+    mt = y_test.shape[0]
+    if s_grid is None:
+        s_grid = [2.0 ** e for e in range(-3, 4)]
+    K = len(alpha)
+    al_h, sg_h = _host_f64(alpha, K), _host_f64(s_grid)
+    P = sg_h.shape[0]
+    eps_out = np.zeros(K)
+    errors = np.zeros(P)
+    pstar = ctypes.c_int32(0)
+    nmax = max(n, m, mt)
+    ws = _ws(workspace, nmax, nmax, d, precision)
+    _check(lib().progot_schedule_eps(_dev(x, "x"), n, _dev(y, "y"), _opt(b, "b", (m,)), m,
+                                     _dev(y_test, "y_test", (mt, d)), mt, d, K, _hp(al_h), _hp(sg_h), P,
+                                     float(beta0), float(tau), int(max_iter), _prec(precision), _hp(eps_out),
+                                     _hp(errors), ctypes.byref(pstar), ctypes.c_void_p(ws.ptr), ws.bytes,
+                                     _stream(stream)), allow_not_converged=False)
+    return eps_out, errors, pstar.value
+
+
+def set_stall_window(iters: int) -> None:
+    _check(lib().progot_set_stall_window(int(iters)), allow_not_converged=False)
+
+
+def launch_count(reset: bool = False) -> int:
+    return int(lib().progot_launch_count(1 if reset else 0))
+
+
+KERNEL_IDS = {"lse_sweep": 0, "map_sweep": 1}
+
+
+def profile(enable: bool) -> None:
+    """Start (True) or stop (False) per-kernel CUDA-event timing inside the library."""
+    _check(lib().progot_profile(1 if enable else 0), allow_not_converged=False)
+
+
+def profile_read(kernel: str) -> dict:
+    n = ctypes.c_int64(0)
+    ms = ctypes.c_double(0.0)
+    pairs = ctypes.c_double(0.0)
+    _check(lib().progot_profile_read(KERNEL_IDS[kernel], ctypes.byref(n), ctypes.byref(ms), ctypes.byref(pairs)),
+           allow_not_converged=False)
+    return dict(launches=n.value, ms=ms.value, pairs=pairs.value)
