@@ -124,6 +124,36 @@ int coupling_marginals(const float* x, int64_t n, const float* y, int64_t m, int
                        const float* b, double* err_l1_out, void* workspace, size_t ws_bytes, progot_stream_t stream);
 
 /*
+ * coupling_marginals_noalloc - coupling_marginals without a workspace and without any
+ * allocation (the paper has no counterpart: this is an interface for callers that
+ * cannot allocate device memory).
+ *
+ * Who needs it: callers that cannot call cudaMalloc or provide a scratch buffer, such
+ * as code running inside a framework or inference-engine callback whose device memory
+ * is planned ahead and where allocation calls are not allowed, code that must not incur
+ * the implicit device-wide synchronisation of cudaFree, or code whose device memory
+ * belongs to another allocator with a fixed budget. The caller still passes every input
+ * and output exactly as for coupling_marginals (same meaning, layout and ownership);
+ * the library's scratch is a fixed ~1.1 MB device array inside libprogot.so that every
+ * GPU loading the library holds until the process exits. The call makes no cudaMalloc,
+ * cudaFree or other allocating call.
+ *
+ * Limits and behaviour:
+ * - n and m must each be at most 65536; larger sizes return PROGOT_ERR_INVALID_ARG with
+ *   an explanatory progot_last_error_string(). Only PROGOT_FP32 is accepted.
+ * - The first call on a device looks up the device address of the array (a one-time
+ *   set-up per device); make that first call before any stream capture.
+ * - All calls share the one array, which keeps the last call's contents (the arrival
+ *   counters are cleared at the start of every call). Calls whose GPU work overlaps
+ *   (other streams, other host threads on the same device) race on it: serialise them.
+ * - err_l1_out (host, may be NULL): ||r - a||_1 + ||c - b||_1; when given, the stream is
+ *   synchronised; otherwise the call is asynchronous.
+ */
+int coupling_marginals_noalloc(const float* x, int64_t n, const float* y, int64_t m, int32_t d, const float* f,
+                               const float* g, double eps, int32_t precision, float* row, float* col, const float* a,
+                               const float* b, double* err_l1_out, progot_stream_t stream);
+
+/*
  * progot_solve - ProgOT(a, X, b, Y, (eps_k, alpha_k, tau_k)_k) of Alg. 2, K solves.
  *
  * f = 0, g^(0) = 0. For k = 1..K: warm start f, g <- (1 - alpha_k) f, (1 - alpha_k) g^(k-1);

@@ -24,6 +24,7 @@ static std::atomic<int32_t> g_stall_window{512};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 static thread_local std::string t_last_error;
+void set_last_error_message(const char* msg) { t_last_error = msg ? msg : ""; }
 
 // Opt-in per-kernel timing (progot_profile): CUDA events recorded on the launching
 // stream around every sweep. Launches of a Sinkhorn loop after its stop (no-op

@@ -27,6 +27,8 @@ struct MapParams {
 };
 
 void count_launch();
+// Text returned by progot_last_error_string() on the calling thread.
+void set_last_error_message(const char* msg);
 
 // float32 CUDA-core sweeps (sweep_fp32.cu)
 cudaError_t launch_lse_sweep_fp32(const SweepParams& p, cudaStream_t stream);

@@ -45,6 +45,8 @@ SIGNATURES = [
     ("entropic_map_apply", ctypes.c_int, [_P, _I64, _P, _I64, _I32, _I32, _P, _P, _P, _I32, _P, _P, _SZ, _P]),
     ("coupling_marginals", ctypes.c_int,
      [_P, _I64, _P, _I64, _I32, _P, _P, _D, _I32, _P, _P, _P, _P, _P, _P, _SZ, _P]),
+    ("coupling_marginals_noalloc", ctypes.c_int,
+     [_P, _I64, _P, _I64, _I32, _P, _P, _D, _I32, _P, _P, _P, _P, _P, _P]),
     ("progot_solve", ctypes.c_int,
      [_P, _P, _I64, _P, _P, _I64, _I32, _I32, _P, _P, _P, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     ("progot_schedule_alpha", ctypes.c_int, [_I32, _I32, _P]),
@@ -331,3 +333,27 @@ def profile_read(kernel: str) -> dict:
     _check(lib().progot_profile_read(KERNEL_IDS[kernel], ctypes.byref(n), ctypes.byref(ms), ctypes.byref(pairs)),
            allow_not_converged=False)
     return dict(launches=n.value, ms=ms.value, pairs=pairs.value)
+
+
+NOALLOC_MAX_POINTS = 65536
+
+
+def coupling_marginals_noalloc(x, y, f, g, eps, a=None, b=None, precision="fp32", row=None, col=None,
+                               stream=None):
+    """coupling_marginals through the allocation-free entry point: the library uses its
+    own static device scratch (n, m <= 65536); the caller supplies inputs and outputs."""
+    torch = _torch()
+    _dev(x, "x"), _dev(y, "y")
+    n, d = x.shape
+    m = y.shape[0]
+    if row is None:
+        row = torch.empty(n, dtype=torch.float32, device=x.device)
+    if col is None:
+        col = torch.empty(m, dtype=torch.float32, device=x.device)
+    err = ctypes.c_double(0.0)
+    rc = lib().coupling_marginals_noalloc(_dev(x, "x"), n, _dev(y, "y"), m, d, _dev(f, "f", (n,)),
+                                          _dev(g, "g", (m,)), float(eps), _prec(precision), _dev(row, "row", (n,)),
+                                          _dev(col, "col", (m,)), _opt(a, "a", (n,)), _opt(b, "b", (m,)),
+                                          ctypes.byref(err), _stream(stream))
+    _check(rc, allow_not_converged=False)
+    return row, col, err.value
