@@ -6,6 +6,9 @@
 // stopped loop return at entry, so the host enqueues iterations in growing chunks and
 // reads the state back (pinned memory, one event per chunk) while the next chunk is
 // already queued.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -116,16 +119,19 @@ static int num_sms() {
 static int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 static size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
-// Column splits of a sweep of nA rows against nB columns: enough CTAs to fill the GPU
-// (ctas_per_sm resident CTAs on every SM), never more splits than column tiles.
+// Column splits of a sweep of nA rows against nB columns. Each CTA covers one 128-row
+// block and `tiles_per_split` 128-column tiles; about kWaves waves of CTAs on the GPU's
+// resident slots (ctas_per_sm per SM) let the hardware scheduler balance the SMs, and
+// a CTA never gets fewer than one tile. Returns the split count.
+constexpr int64_t kWaves = 6;
 static int plan_splits(int64_t nA, int64_t nB, int ctas_per_sm, int extra_mult = 1) {
   const int64_t rb = cdiv(nA, fp32_tile_rows()) * extra_mult;
   const int64_t ct = cdiv(nB, fp32_tile_cols());
-  const int64_t target = (int64_t)num_sms() * ctas_per_sm;
-  int64_t s = target / rb;
-  if (s < 1) s = 1;
-  if (s > ct) s = ct;
-  return (int)s;
+  const int64_t slots = (int64_t)num_sms() * ctas_per_sm;
+  int64_t tps = (rb * ct) / (slots * kWaves);
+  if (tps < 1) tps = 1;
+  if (tps > ct) tps = ct;
+  return (int)cdiv(ct, tps);
 }
 
 // Device workspace carved from the caller's buffer.
@@ -146,30 +152,41 @@ struct Workspace {
   double* rout;     // 2 * (d + 1)
   float* Opart;     // opart_elems
   float* Rpart;     // rpart_elems
+  void* xh;         // bf16 hi/lo operands of the tensor-core sweeps: nmax x dp each
+  void* xl;
+  void* yh;
+  void* yl;
+  int32_t* fault;   // set by a tensor-core CTA whose bounded wait expired
   size_t bytes;
 };
 
 struct WsDims {
   int64_t nmax, rbmax, partial_elems, opart_elems, rpart_elems;
-  int32_t d;
+  int32_t d, dp;
+  bool tc;
 };
 
-static WsDims ws_dims(int64_t n, int64_t m, int32_t d) {
+static int32_t pad64(int32_t d) { return (d + 63) / 64 * 64; }
+
+static WsDims ws_dims(int64_t n, int64_t m, int32_t d, int32_t precision = PROGOT_FP32) {
   WsDims w;
+  w.tc = precision != PROGOT_FP32;
+  w.dp = pad64(d);
   w.nmax = std::max<int64_t>(std::max<int64_t>(n, m), 1);
   w.d = d;
   w.rbmax = cdiv(w.nmax, fp32_tile_rows());
-  // lse sweep: splits * nA over both directions and every (nA, nB) <= (nmax, nmax)
-  const int64_t s_lse = plan_splits(1, w.nmax, 2);  // largest split count for the smallest nA
-  (void)s_lse;
-  // splits * nA <= max(nA, (target / rb) * rb * BM) <= max(nmax, target * BM)
-  const int64_t target = (int64_t)num_sms() * 2;
-  w.partial_elems = std::max<int64_t>(w.nmax, target * fp32_tile_rows()) + fp32_tile_rows();
+  // Bound on splits * nA for both sweep directions. With X = rb ct / (slots W):
+  // X < 1 gives tps = 1 and splits = ct, so splits * nA <= rb ct BM < slots W BM;
+  // X >= 1 gives tps = floor(X) >= X / 2 and splits <= ct / tps + 1 <= 2 slots W / rb + 1,
+  // so splits * nA <= (2 slots W + rb) BM.
+  const int64_t BMr = fp32_tile_rows();
+  const int64_t slots = (int64_t)num_sms() * 2;
+  w.partial_elems = (2 * slots * kWaves + w.rbmax + 1) * BMr + w.nmax;
   const int64_t dch = cdiv(d, map_dchunk());
-  const int64_t mtarget = (int64_t)num_sms();
-  const int64_t rows_cap = std::max<int64_t>(w.nmax, (mtarget / dch + 1) * fp32_tile_rows());
-  w.opart_elems = rows_cap * d + fp32_tile_rows() * (int64_t)d;
-  w.rpart_elems = rows_cap + fp32_tile_rows();
+  const int64_t mslots = (int64_t)num_sms();
+  const int64_t rows_cap = (2 * mslots * kWaves / dch + w.rbmax + 1) * BMr + w.nmax;
+  w.opart_elems = rows_cap * d;
+  w.rpart_elems = rows_cap;
   return w;
 }
 
@@ -197,16 +214,23 @@ static size_t ws_layout(const WsDims& w, Workspace* out, char* base) {
   ws.rout = (double*)take(sizeof(double) * 2 * (size_t)(w.d + 1));
   ws.Opart = (float*)take(sizeof(float) * w.opart_elems);
   ws.Rpart = (float*)take(sizeof(float) * w.rpart_elems);
+  const size_t opb = w.tc ? 2 * (size_t)w.nmax * (size_t)w.dp : 0;
+  ws.xh = take(opb);
+  ws.xl = take(opb);
+  ws.yh = take(opb);
+  ws.yl = take(opb);
+  ws.fault = (int32_t*)take(sizeof(int32_t));
   ws.bytes = off;
   if (out) *out = ws;
   return off;
 }
 
-static int carve(int64_t n, int64_t m, int32_t d, void* workspace, size_t ws_bytes, Workspace* ws) {
+static int carve(int64_t n, int64_t m, int32_t d, void* workspace, size_t ws_bytes, Workspace* ws,
+                 int32_t precision = PROGOT_FP32) {
   if (workspace == nullptr) return fail(PROGOT_ERR_WORKSPACE, "workspace is NULL");
   if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
     return fail(PROGOT_ERR_WORKSPACE, "workspace is not 256-byte aligned");
-  const WsDims w = ws_dims(n, m, d);
+  const WsDims w = ws_dims(n, m, d, precision);
   const size_t need = ws_layout(w, ws, (char*)workspace);
   if (ws_bytes < need)
     return fail(PROGOT_ERR_WORKSPACE, "workspace has %zu bytes, %zu needed", ws_bytes, need);
@@ -242,9 +266,69 @@ static int check_common(const float* x, int64_t n, const float* y, int64_t m, in
   return PROGOT_OK;
 }
 
+// ---------------------------------------------------------------- tensor-core operands
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (fn == nullptr) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(ptr);
+  }
+  return fn;
+}
+
+// 2-D bf16 tensor map over a (rows x dp) row-major buffer, 64 x 128 boxes, 128-byte swizzle.
+static int make_map(CUtensorMap* map, void* base, int64_t rows, int32_t dp) {
+  EncodeTiledFn enc = encode_fn();
+  if (enc == nullptr) return fail(PROGOT_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+  cuuint64_t dims[2] = {(cuuint64_t)dp, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)dp * 2};
+  cuuint32_t box[2] = {64, 128};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(PROGOT_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return PROGOT_OK;
+}
+
+struct TcOps {
+  alignas(64) CUtensorMap xh, xl, yh, yl;
+  int nkb = 0;
+  int split3 = 0;
+  bool on = false;
+};
+
+// Split sqrt(2 log2(e) / eps) X and Y into bf16 hi/lo and describe them for TMA.
+static int prep_tc(const float* x, int64_t n, const float* y, int64_t m, int32_t d, double eps, int32_t precision,
+                   const Workspace& ws, TcOps* ops, cudaStream_t s) {
+  ops->on = precision != PROGOT_FP32;
+  if (!ops->on) return PROGOT_OK;
+  const int32_t dp = pad64(d);
+  ops->nkb = dp / 64;
+  ops->split3 = precision == PROGOT_BF16X3 ? 1 : 0;
+  if (tc_stages(ops->nkb, ops->split3) < 2)
+    return fail(PROGOT_ERR_INVALID_ARG, "d = %d is too large for the tensor-core sweep", d);
+  const float sc = (float)std::sqrt(2.0 * kLog2e / eps);
+  CK(launch_split_bf16(x, n, d, dp, sc, ws.xh, ops->split3 ? ws.xl : nullptr, s));
+  CK(launch_split_bf16(y, m, d, dp, sc, ws.yh, ops->split3 ? ws.yl : nullptr, s));
+  int rc = make_map(&ops->xh, ws.xh, n, dp);
+  if (!rc) rc = make_map(&ops->xl, ops->split3 ? ws.xl : ws.xh, n, dp);
+  if (!rc) rc = make_map(&ops->yh, ws.yh, m, dp);
+  if (!rc) rc = make_map(&ops->yl, ops->split3 ? ws.yl : ws.yh, m, dp);
+  return rc;
+}
+
 // One sweep description for "update the potential of A from the potential of B".
 static SweepParams make_sweep(const float* A, int64_t nA, const float* B, int64_t nB, int32_t d, const float* An,
-                              const float* Bn, double eps, const Workspace& ws) {
+                              const float* Bn, double eps, const Workspace& ws, int ctas_per_sm = 2) {
   SweepParams p;
   memset(&p, 0, sizeof(p));
   p.A = A;
@@ -254,7 +338,7 @@ static SweepParams make_sweep(const float* A, int64_t nA, const float* B, int64_
   p.nA = nA;
   p.nB = nB;
   p.d = d;
-  p.splits = plan_splits(nA, nB, 2);
+  p.splits = plan_splits(nA, nB, ctas_per_sm);
   const int64_t ct = cdiv(nB, fp32_tile_cols());
   p.tiles_per_split = (int)cdiv(ct, p.splits);
   p.splits = (int)cdiv(ct, p.tiles_per_split);  // drop empty splits
@@ -269,11 +353,21 @@ static SweepParams make_sweep(const float* A, int64_t nA, const float* B, int64_
   return p;
 }
 
-static int lse_sweep(const SweepParams& p, int32_t precision, cudaStream_t s) {
-  (void)precision;
+// Launch one log-sum-exp sweep: float32 CUDA cores, or tcgen05 on the prepared split
+// operands (a_is_x: rows of the sweep are the x cloud).
+static int lse_sweep(const SweepParams& p, int32_t precision, cudaStream_t s, const TcOps* ops = nullptr,
+                     bool a_is_x = true, const Workspace* ws = nullptr) {
   ProfRec r;
   if (t_prof.on) prof_begin(r, s);
-  CK(launch_lse_sweep_fp32(p, s));
+  if (precision != PROGOT_FP32 && ops != nullptr && ops->on) {
+    const CUtensorMap* ah = a_is_x ? &ops->xh : &ops->yh;
+    const CUtensorMap* al = a_is_x ? &ops->xl : &ops->yl;
+    const CUtensorMap* bh = a_is_x ? &ops->yh : &ops->xh;
+    const CUtensorMap* bl = a_is_x ? &ops->yl : &ops->xl;
+    CK(launch_lse_sweep_tc(p, ah, al, bh, bl, ops->nkb, ops->split3, ws ? ws->fault : nullptr, s));
+  } else {
+    CK(launch_lse_sweep_fp32(p, s));
+  }
   if (t_prof.on) prof_end(r, s, kProfLse, (double)p.nA * (double)p.nB);
   return PROGOT_OK;
 }
@@ -286,8 +380,13 @@ static int sinkhorn_core(const float* x, const float* a, int64_t n, const float*
                          double* err_out, cudaStream_t s) {
   int rc = t_host.init();
   if (rc) return rc;
+  TcOps ops;
+  rc = prep_tc(x, n, y, m, d, eps, precision, ws, &ops, s);
+  if (rc) return rc;
+  const int cps = ops.on ? 1 : 2;
+  if (ops.on) CK(cudaMemsetAsync(ws.fault, 0, sizeof(int32_t), s));
   CK(launch_init_state(ws.state, s));
-  SweepParams pf = make_sweep(x, n, y, m, d, xn, yn, eps, ws);
+  SweepParams pf = make_sweep(x, n, y, m, d, xn, yn, eps, ws, cps);
   pf.wA = a;
   pf.potB = g;
   pf.out = f_a;
@@ -297,7 +396,7 @@ static int sinkhorn_core(const float* x, const float* a, int64_t n, const float*
   pf.state = ws.state;
   pf.tau = tau;
   pf.max_iter = max_iter;
-  SweepParams pg = make_sweep(y, m, x, n, d, yn, xn, eps, ws);
+  SweepParams pg = make_sweep(y, m, x, n, d, yn, xn, eps, ws, cps);
   pg.wA = b;
   pg.potB = f_a;
   pg.potB_alt = f_b;
@@ -310,9 +409,9 @@ static int sinkhorn_core(const float* x, const float* a, int64_t n, const float*
 
   auto enqueue = [&](int iters) -> int {
     for (int i = 0; i < iters; ++i) {
-      int r = lse_sweep(pf, precision, s);
+      int r = lse_sweep(pf, precision, s, &ops, true, &ws);
       if (r) return r;
-      r = lse_sweep(pg, precision, s);
+      r = lse_sweep(pg, precision, s, &ops, false, &ws);
       if (r) return r;
     }
     return PROGOT_OK;
@@ -358,6 +457,12 @@ static int sinkhorn_core(const float* x, const float* a, int64_t n, const float*
   if (fin.fcur == 1) CK(cudaMemcpyAsync(f_a, f_b, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
   if (iters_out) *iters_out = fin.it;
   if (err_out) *err_out = fin.err;
+  if (ops.on) {
+    int32_t fault = 0;
+    CK(cudaMemcpyAsync(&fault, ws.fault, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (fault) return fail(PROGOT_ERR_TIMEOUT, "a tensor-core sweep hit its bounded wait (2 s) and aborted");
+  }
   switch (fin.status) {
     case kConverged:
       return PROGOT_OK;
@@ -427,9 +532,8 @@ const char* progot_last_error_string(void) { return t_last_error.c_str(); }
 const char* progot_version(void) { return "0.1.0"; }
 
 size_t progot_workspace_size(int64_t n, int64_t m, int32_t d, int32_t precision) {
-  (void)precision;
   if (n <= 0 || m <= 0 || d <= 0) return 0;
-  return ws_layout(ws_dims(n, m, d), nullptr, nullptr);
+  return ws_layout(ws_dims(n, m, d, precision), nullptr, nullptr);
 }
 
 int progot_set_stall_window(int32_t iters) {
@@ -474,7 +578,7 @@ int sinkhorn_potentials(const float* x, const float* a, int64_t n, const float* 
   if (!(tau >= 0.0)) return fail(PROGOT_ERR_INVALID_ARG, "tau must be >= 0");
   if (max_iter < 0) return fail(PROGOT_ERR_INVALID_ARG, "max_iter must be >= 0");
   Workspace ws;
-  rc = carve(n, m, d, workspace, ws_bytes, &ws);
+  rc = carve(n, m, d, workspace, ws_bytes, &ws, precision);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   rc = zero_counters(ws, ws_dims(n, m, d).rbmax, s);
@@ -578,7 +682,7 @@ int progot_solve(const float* x, const float* a, int64_t n, const float* y, cons
     if (!(tau[k] >= 0.0)) return fail(PROGOT_ERR_INVALID_ARG, "tau[%d] must be >= 0", k);
   }
   Workspace ws;
-  rc = carve(n, m, d, workspace, ws_bytes, &ws);
+  rc = carve(n, m, d, workspace, ws_bytes, &ws, precision);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   rc = zero_counters(ws, ws_dims(n, m, d).rbmax, s);
@@ -685,7 +789,7 @@ int progot_schedule_eps(const float* x, int64_t n, const float* y, const float* 
     return fail(PROGOT_ERR_INVALID_ARG, "y_test, mt > 0, K > 0, alpha, s_grid, P > 0 and eps_out are required");
   const int64_t nmax = std::max<int64_t>(std::max<int64_t>(n, m), mt);
   Workspace ws;
-  rc = carve(nmax, nmax, d, workspace, ws_bytes, &ws);
+  rc = carve(nmax, nmax, d, workspace, ws_bytes, &ws, precision);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   double mc_xy = 0.0, mc_yy = 0.0;

@@ -50,4 +50,12 @@ cudaError_t launch_sq_error(const float* A, const float* B, int64_t n, int32_t d
                             double* out, cudaStream_t s);
 int reduce_parts();
 
+// tcgen05 sweeps (sweep_tc.cu): operands pre-scaled by sqrt(2 log2(e) / eps), split into
+// bf16 hi/lo with K padded to a multiple of 64; map* point at CUtensorMap objects.
+cudaError_t launch_split_bf16(const float* X, int64_t n, int32_t d, int32_t dp, float scale, void* hi, void* lo,
+                              cudaStream_t s);
+cudaError_t launch_lse_sweep_tc(const SweepParams& p, const void* mapAh, const void* mapAl, const void* mapBh,
+                                const void* mapBl, int nkb, int split3, int32_t* fault, cudaStream_t stream);
+int tc_stages(int nkb, int split3);
+
 }  // namespace progot

@@ -16,6 +16,7 @@
 //   x_i <- x_i + alpha (T_i - x_i).
 #include "progot_common.cuh"
 #include "progot_internal.h"
+#include "sweep_epilogue.cuh"
 
 namespace progot {
 
@@ -26,14 +27,17 @@ constexpr int DCH = 64;  // columns of d handled per CTA by the map sweep
 // matrix into registers; zero outside [0, nrows) x [0, d).
 struct ChunkLoader {
   float4 v[2];
+  // Element e = threadIdx.x + NT * q maps to row r = e % BM and 4-wide k group
+  // kq = e / BM, so that consecutive threads store consecutive rows of the transposed
+  // shared tile (conflict-free stores).
   __device__ __forceinline__ void load(const float* __restrict__ M, int64_t nrows, int d, int64_t r0, int k0,
                                        bool vec_ok) {
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
-      int e = threadIdx.x + NT * q;  // 0..511: (row, kq)
-      int r = e >> 2, kq = e & 3;
-      int64_t gr = r0 + r;
-      int k = k0 + kq * 4;
+      const int e = threadIdx.x + NT * q;  // 0..511
+      const int r = e & (BM - 1), kq = e / BM;
+      const int64_t gr = r0 + r;
+      const int k = k0 + kq * 4;
       float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
       if (gr < nrows) {
         const float* src = M + gr * (int64_t)d + k;
@@ -53,8 +57,8 @@ struct ChunkLoader {
   __device__ __forceinline__ void store(float (*S)[BM]) const {
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
-      int e = threadIdx.x + NT * q;
-      int r = e >> 2, kq = e & 3;
+      const int e = threadIdx.x + NT * q;
+      const int r = e & (BM - 1), kq = e / BM;
       S[kq * 4 + 0][r] = v[q].x;
       S[kq * 4 + 1][r] = v[q].y;
       S[kq * 4 + 2][r] = v[q].z;
@@ -120,78 +124,6 @@ __device__ __forceinline__ int thread_row(int r) {  // 0..127
 __device__ __forceinline__ int thread_col(int c) {
   const int tx = threadIdx.x & 15;
   return (c < 4) ? tx * 4 + c : 64 + tx * 4 + (c - 4);
-}
-
-// Block-wide float64 sum (deterministic order). Returns the total in thread 0.
-__device__ double block_sum_f64(double v, double* red) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  double tot = 0.0;
-  if (threadIdx.x == 0)
-    for (int w = 0; w < NT / 32; ++w) tot += red[w];
-  return tot;
-}
-
-// Called by the last CTA of the whole sweep (thread 0): sum the per-row-block error
-// partials in order and advance the device-side Sinkhorn state.
-__device__ void finish_sweep(const SweepParams& p, int nblocks) {
-  double err = 0.0;
-  for (int b = 0; b < nblocks; ++b) err += __ldcg(p.errpart + b);
-  p.errpart[nblocks] = err;
-  SolverState* st = p.state;
-  if (st == nullptr) return;
-  if (p.role == 1) {
-    st->err = err;
-    const int it = st->it;
-    if (!isfinite(err)) {
-      st->status = kNumeric;
-      st->done = 1;
-    } else if (err <= p.tau) {
-      st->status = kConverged;
-      st->done = 1;
-    } else if (it >= p.max_iter) {
-      st->status = kMaxIter;
-      st->done = 1;
-    } else {
-      if (err < 0.99 * st->best_err) {
-        st->best_err = err;
-        st->best_it = it;
-      } else if (p.stall_window > 0 && it - st->best_it >= p.stall_window) {
-        st->status = kStalled;
-        st->done = 1;
-      }
-      if (!st->done) st->fcur ^= 1;  // the new f becomes current
-    }
-  } else if (p.role == 2) {
-    st->it += 1;
-  }
-}
-
-// Epilogue for one row given L (log2 units). Returns the row's error term.
-__device__ __forceinline__ double row_epilogue(const SweepParams& p, int64_t i, float L, const float* potA_cur,
-                                               float* out_target) {
-  const double w = p.wA ? (double)p.wA[i] : p.inv_nA;
-  if (p.mode == kModePotential) {
-    const float fnew = (float)(p.eps * log(w) + (double)p.An[i] - p.eps * kLn2 * (double)L);
-    out_target[i] = fnew;
-    if (p.role == 1) {
-      const double fold = (double)potA_cur[i];
-      return w * fabs(exp((fold - (double)fnew) / p.eps) - 1.0);
-    }
-    return 0.0;
-  }
-  if (p.mode == kModeLse) {
-    out_target[i] = L;
-    return 0.0;
-  }
-  // marginal
-  const double r = exp(((double)potA_cur[i] - (double)p.An[i]) / p.eps + kLn2 * (double)L);
-  if (out_target) out_target[i] = (float)r;
-  return fabs(r - w);
 }
 
 __global__ void __launch_bounds__(NT, 2) lse_sweep_fp32(SweepParams p) {
@@ -290,7 +222,7 @@ __global__ void __launch_bounds__(NT, 2) lse_sweep_fp32(SweepParams p) {
       e = row_epilogue(p, i, L, potA_cur, out_target);
     }
   }
-  const double tot = block_sum_f64(e, red);
+  const double tot = block_sum_f64<NT>(e, red);
   if (threadIdx.x == 0) {
     p.errpart[blockIdx.x] = tot;
     p.cnt[blockIdx.x] = 0;

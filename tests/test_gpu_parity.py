@@ -258,3 +258,72 @@ def test_full_size_gmm64_sampled_parity(nat):
     T_ref = O.entropic_map(X64[rows], Y64, g, eps)
     assert map_rms_rel(host(out)[rows], T_ref, p.y) <= TOL_FP32
     assert err <= 1e-5 + TOL_FP32
+
+
+# ---------------------------------------------------- tensor-core (bf16 split) path
+TOL_MIXED = 1e-3
+TC_SHAPES = [(300, 260, 16), (1000, 700, 64), (257, 129, 17), (129, 517, 3), (640, 384, 128), (333, 200, 256)]
+
+
+@pytest.mark.parametrize("n,m,d", TC_SHAPES)
+def test_sinkhorn_potentials_parity_bf16x3(nat, n, m, d):
+    p = W.gmm_pair(n, m, d, seed=n + m + d, k=4)
+    eps = eps_for(p)
+    tau = 1e-4
+    res = nat.sinkhorn_potentials(dev(p.x), dev(p.y), eps, tau, max_iter=5000, precision="bf16x3")
+    assert res.status == nat.PROGOT_OK, nat.last_error()
+    ref = O.sinkhorn(None, p.x, None, p.y, eps, 1e-6, max_iter=5000)
+    f, g = host(res.f), host(res.g)
+    assert marginal_l1(p.x, p.y, f, g, eps) <= TOL_MIXED
+    assert map_rms_rel(O.entropic_map(p.x, p.y, g, eps), O.entropic_map(p.x, p.y, ref.g, eps), p.y) <= TOL_MIXED
+
+
+def test_bf16_single_product_runs_and_is_coarser(nat):
+    """The hi-only product is a speed option without the mixed-precision accuracy
+    claim: it must run and stay within 1e-2 here, and bf16x3 must be at least as
+    accurate."""
+    p = W.gmm_pair(600, 500, 64, seed=77, k=4)
+    eps = eps_for(p)
+    ref = O.sinkhorn(None, p.x, None, p.y, eps, 1e-6)
+    T_ref = O.entropic_map(p.x, p.y, ref.g, eps)
+    errs = {}
+    for prec in ("bf16", "bf16x3"):
+        res = nat.sinkhorn_potentials(dev(p.x), dev(p.y), eps, 1e-4, precision=prec)
+        errs[prec] = map_rms_rel(O.entropic_map(p.x, p.y, host(res.g), eps), T_ref, p.y)
+    assert errs["bf16"] <= 1e-2
+    assert errs["bf16x3"] <= errs["bf16"] + 1e-6
+
+
+def test_progot_solve_parity_bf16x3(nat):
+    p = W.gmm_pair(700, 600, 64, seed=23, k=4)
+    K = 4
+    alpha = O.alpha_schedule(K)
+    e0 = O.mean_cost(p.x, p.y) / 20
+    eps = [5 * e0, 3 * e0, 2 * e0, e0]
+    res = nat.progot_solve(dev(p.x), dev(p.y), alpha, eps, [1e-4] * K, max_iter=5000, precision="bf16x3")
+    assert res.status == nat.PROGOT_OK, nat.last_error()
+    ref = O.progot(None, p.x, None, p.y, eps, alpha, [1e-6] * K)
+    assert map_rms_rel(host(res.x_out), ref.x_out, p.y) <= TOL_MIXED
+    assert marginal_l1(host(res.x_last), p.y, host(res.f_last), host(res.g_all[K - 1]), eps[-1]) <= TOL_MIXED
+
+
+def test_full_size_gmm64_sampled_parity_bf16x3(nat):
+    """n = m = 8192, d = 64 in the benchmark's launch configuration, bf16x3 sweeps:
+    marginals and map on 48 sampled rows computed one by one by the oracle from the
+    GPU's potentials, and the map against the oracle's map from the same g."""
+    p = W.gmm_pair(8192, 8192, 64, seed=1)
+    eps = 5 * O.mean_cost(p.x[:2048], p.y[:2048]) / 20
+    x, y = dev(p.x), dev(p.y)
+    res = nat.sinkhorn_potentials(x, y, eps, 1e-4, max_iter=2000, precision="bf16x3")
+    assert res.status == nat.PROGOT_OK, nat.last_error()
+    f, g = host(res.f), host(res.g)
+    rows = np.random.default_rng(1).choice(8192, 48, replace=False)
+    X64, Y64 = p.x.astype(np.float64), p.y.astype(np.float64)
+    Cs = O.cost_matrix_rows(X64[rows], Y64)
+    r_ref = np.exp((f[rows, None] + g[None, :] - Cs) / eps).sum(1)
+    # the sampled rows' share of the FP64 row-marginal error, scaled to all rows
+    assert np.abs(r_ref - 1.0 / 8192).sum() * 8192 / 48 <= 2 * TOL_MIXED
+    fp = nat.sinkhorn_potentials(x, y, eps, 1e-5, max_iter=2000, precision="fp32")
+    T_gpu = O.entropic_map(X64[rows], Y64, g, eps)
+    T_ref = O.entropic_map(X64[rows], Y64, host(fp.g), eps)
+    assert map_rms_rel(T_gpu, T_ref, p.y) <= TOL_MIXED
