@@ -156,6 +156,8 @@ struct Workspace {
   void* xl;
   void* yh;
   void* yl;
+  void* xb;         // bf16 bias rows (x side, rows padded to 128) x 16
+  void* yb;
   int32_t* fault;   // set by a tensor-core CTA whose bounded wait expired
   size_t bytes;
 };
@@ -219,6 +221,9 @@ static size_t ws_layout(const WsDims& w, Workspace* out, char* base) {
   ws.xl = take(opb);
   ws.yh = take(opb);
   ws.yl = take(opb);
+  const size_t bb = w.tc ? 32 * (size_t)(cdiv(w.nmax, 128) * 128) : 0;
+  ws.xb = take(bb);
+  ws.yb = take(bb);
   ws.fault = (int32_t*)take(sizeof(int32_t));
   ws.bytes = off;
   if (out) *out = ws;
@@ -284,31 +289,37 @@ static EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 2-D bf16 tensor map over a (rows x dp) row-major buffer, 64 x 128 boxes, 128-byte swizzle.
+// 2-D bf16 tensor map over a (rows x dp) row-major buffer: 64 x 128 boxes with
+// 128-byte swizzle for operands (dp a multiple of 64), or 16 x 128 boxes with
+// 32-byte swizzle for bias rows (dp = 16).
 static int make_map(CUtensorMap* map, void* base, int64_t rows, int32_t dp) {
   EncodeTiledFn enc = encode_fn();
   if (enc == nullptr) return fail(PROGOT_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+  const bool bias = dp == 16;
   cuuint64_t dims[2] = {(cuuint64_t)dp, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)dp * 2};
-  cuuint32_t box[2] = {64, 128};
+  cuuint32_t box[2] = {bias ? 16u : 64u, 128};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, bias ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(PROGOT_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return PROGOT_OK;
 }
 
 struct TcOps {
-  alignas(64) CUtensorMap xh, xl, yh, yl;
+  CUtensorMap xh, xl, yh, yl, xb, yb;  // 64-byte aligned by the type itself
   int nkb = 0;
   int split3 = 0;
   bool on = false;
 };
 
-// Split sqrt(2 log2(e) / eps) X and Y into bf16 hi/lo and describe them for TMA.
+// Split sqrt(2 log2(e) / eps) X and Y into bf16 hi/lo and describe them for TMA; write
+// the bias rows of both sides from the current potentials (f on x, g on y) and the
+// squared norms.
 static int prep_tc(const float* x, int64_t n, const float* y, int64_t m, int32_t d, double eps, int32_t precision,
-                   const Workspace& ws, TcOps* ops, cudaStream_t s) {
+                   const Workspace& ws, TcOps* ops, cudaStream_t s, const float* f_cur = nullptr,
+                   const float* g_cur = nullptr, const float* xn = nullptr, const float* yn = nullptr) {
   ops->on = precision != PROGOT_FP32;
   if (!ops->on) return PROGOT_OK;
   const int32_t dp = pad64(d);
@@ -323,7 +334,13 @@ static int prep_tc(const float* x, int64_t n, const float* y, int64_t m, int32_t
   if (!rc) rc = make_map(&ops->xl, ops->split3 ? ws.xl : ws.xh, n, dp);
   if (!rc) rc = make_map(&ops->yh, ws.yh, m, dp);
   if (!rc) rc = make_map(&ops->yl, ops->split3 ? ws.yl : ws.yh, m, dp);
-  return rc;
+  if (!rc) rc = make_map(&ops->xb, ws.xb, cdiv(n, 128) * 128, 16);
+  if (!rc) rc = make_map(&ops->yb, ws.yb, cdiv(m, 128) * 128, 16);
+  if (rc) return rc;
+  const float bscale = (float)(kLog2e / eps);
+  if (g_cur != nullptr) CK(launch_bias_prep(g_cur, yn, m, cdiv(m, 128) * 128, bscale, ws.yb, s));
+  if (f_cur != nullptr) CK(launch_bias_prep(f_cur, xn, n, cdiv(n, 128) * 128, bscale, ws.xb, s));
+  return PROGOT_OK;
 }
 
 // One sweep description for "update the potential of A from the potential of B".
@@ -364,7 +381,14 @@ static int lse_sweep(const SweepParams& p, int32_t precision, cudaStream_t s, co
     const CUtensorMap* al = a_is_x ? &ops->xl : &ops->yl;
     const CUtensorMap* bh = a_is_x ? &ops->yh : &ops->xh;
     const CUtensorMap* bl = a_is_x ? &ops->yl : &ops->xl;
-    CK(launch_lse_sweep_tc(p, ah, al, bh, bl, ops->nkb, ops->split3, ws ? ws->fault : nullptr, s));
+    const CUtensorMap* bb = a_is_x ? &ops->yb : &ops->xb;
+    void* bias_out = (p.mode == kModePotential && ws) ? (a_is_x ? ws->xb : ws->yb) : nullptr;
+    int G = 0, maxseg = 0;
+    tc_plan(p.nA, p.nB, num_sms(), &G, &maxseg);
+    SweepParams q = p;
+    q.splits = G;  // not used by the persistent kernel beyond bookkeeping
+    CK(launch_lse_sweep_tc(q, ah, al, bh, bl, bb, ops->nkb, ops->split3, G, maxseg, ws ? ws->fault : nullptr,
+                           bias_out, s));
   } else {
     CK(launch_lse_sweep_fp32(p, s));
   }
@@ -381,7 +405,7 @@ static int sinkhorn_core(const float* x, const float* a, int64_t n, const float*
   int rc = t_host.init();
   if (rc) return rc;
   TcOps ops;
-  rc = prep_tc(x, n, y, m, d, eps, precision, ws, &ops, s);
+  rc = prep_tc(x, n, y, m, d, eps, precision, ws, &ops, s, f_a, g, xn, yn);
   if (rc) return rc;
   const int cps = ops.on ? 1 : 2;
   if (ops.on) CK(cudaMemsetAsync(ws.fault, 0, sizeof(int32_t), s));

@@ -54,8 +54,15 @@ int reduce_parts();
 // bf16 hi/lo with K padded to a multiple of 64; map* point at CUtensorMap objects.
 cudaError_t launch_split_bf16(const float* X, int64_t n, int32_t d, int32_t dp, float scale, void* hi, void* lo,
                               cudaStream_t s);
+// mapBbias: (nB padded to 128) x 16 bf16 rows [beta_hi, beta_mid, beta_lo, 0...] of the
+// B side; bias_out (optional): the same rows for the A side, written from the updated
+// potential in potential mode (the next sweep's B bias).
 cudaError_t launch_lse_sweep_tc(const SweepParams& p, const void* mapAh, const void* mapAl, const void* mapBh,
-                                const void* mapBl, int nkb, int split3, int32_t* fault, cudaStream_t stream);
+                                const void* mapBl, const void* mapBbias, int nkb, int split3, int G, int maxseg,
+                                int32_t* fault, void* bias_out, cudaStream_t stream);
+cudaError_t launch_bias_prep(const float* potB, const float* Bn, int64_t nB, int64_t nB_pad, float bscale, void* out,
+                             cudaStream_t s);
+void tc_plan(int64_t nA, int64_t nB, int sms, int* G, int* maxseg);
 int tc_stages(int nkb, int split3);
 
 }  // namespace progot

@@ -27,6 +27,8 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "progot_internal.h"
 #include "sweep_epilogue.cuh"
 
@@ -47,13 +49,14 @@ struct TcShared {
   uint64_t empty[8];
   uint64_t tmem_full[2];
   uint64_t tmem_empty[2];
-  uint64_t a_full;
+  uint64_t a_full[2];
+  uint64_t a_empty[2];
   uint64_t drain;
   uint32_t tmem_base;
   int32_t abort_flag;
   int32_t s_last;
   int32_t pad_;
-  double red[NTHREADS / 32];
+  double red[4];
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -167,29 +170,37 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Parameters beyond SweepParams: tensor maps of the split operands and the layout.
+// Parameters beyond SweepParams. The CTAs are persistent: CTA c of G owns the work
+// units [c W / G, (c + 1) W / G) of the row-major (row block, column tile) space,
+// W = R T, cut at row-block boundaries into segments; a segment's (max, sum) partial
+// goes to slot (c * maxseg + k), k = its index within the CTA.
 struct TcParams {
   SweepParams p;
-  int32_t nkb;       // K blocks of 64
-  int32_t split3;    // 1: bf16x3 (hi and lo operands), 0: bf16 (hi only)
-  int32_t stages;    // B pipeline depth (units of one K block of one tile)
-  int32_t* fault;    // set to 1 by a CTA whose bounded wait expired
+  int32_t nkb;        // K blocks of 64
+  int32_t split3;     // 1: bf16x3 (hi and lo operands), 0: bf16 (hi only)
+  int32_t stages;     // B pipeline depth (units of one K block of one tile)
+  int32_t a_bufs;     // 1 or 2 A-operand buffers
+  int32_t G;          // CTAs
+  int32_t T;          // column tiles per row block
+  int32_t R;          // row blocks
+  int32_t maxseg;     // partial slots per CTA
+  int32_t* fault;     // set to 1 by a CTA whose bounded wait expired
+  __nv_bfloat16* bias_out;  // potential mode: beta rows of the updated side (rows x 16), or nullptr
 };
 
 struct SmemLayout {
-  uint32_t a_hi, a_lo, a_bias, stage0, stage_bytes, b_lo_off, bias_off, ctrl, total;
+  uint32_t a0, a_stride, a_lo_off, a_bias, stage0, stage_bytes, b_lo_off, bias_off, ctrl, total;
 };
 
-__host__ __device__ inline SmemLayout smem_layout(int nkb, int split3, int stages) {
+__host__ __device__ inline SmemLayout smem_layout(int nkb, int split3, int stages, int a_bufs) {
   SmemLayout L;
   uint32_t off = 0;
-  L.a_hi = off;
-  off += nkb * OP_TILE_BYTES;
-  L.a_lo = off;
-  if (split3) off += nkb * OP_TILE_BYTES;
+  L.a0 = off;
+  L.a_lo_off = nkb * OP_TILE_BYTES;
+  L.a_stride = nkb * OP_TILE_BYTES * (split3 ? 2 : 1);
+  off += a_bufs * L.a_stride;
   L.a_bias = off;
-  off += 1024;  // 128 rows x 32 B = 4 KB, but keep the next region 1024-aligned
-  off += BIAS_TILE_BYTES - 1024;
+  off += BIAS_TILE_BYTES;
   L.stage0 = off;
   L.b_lo_off = OP_TILE_BYTES;
   L.bias_off = OP_TILE_BYTES * (split3 ? 2 : 1);
@@ -201,27 +212,70 @@ __host__ __device__ inline SmemLayout smem_layout(int nkb, int split3, int stage
   return L;
 }
 
+struct Seg {
+  int r, t0, t1;
+};
+__device__ __forceinline__ int64_t work_begin(int c, int64_t W, int G) { return (int64_t)c * W / G; }
+// CTA owning work unit w: the largest c with floor(c W / G) <= w.
+__device__ __forceinline__ int cta_of(int64_t w, int64_t W, int G) { return (int)(((w + 1) * G - 1) / W); }
+__device__ __forceinline__ Seg segment(int c, int k, int64_t W, int G, int T) {
+  const int64_t w0 = work_begin(c, W, G), w1 = work_begin(c + 1, W, G);
+  Seg sg;
+  sg.r = (int)(w0 / T) + k;
+  const int64_t rb0 = (int64_t)sg.r * T;
+  sg.t0 = (int)(max(w0, rb0) - rb0);
+  sg.t1 = (int)(min(w1, rb0 + T) - rb0);
+  return sg;
+}
+__device__ __forceinline__ int num_segments(int c, int64_t W, int G, int T) {
+  const int64_t w0 = work_begin(c, W, G), w1 = work_begin(c + 1, W, G);
+  if (w1 <= w0) return 0;
+  return (int)((w1 - 1) / T - w0 / T + 1);
+}
+
+__device__ __forceinline__ void lse_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// beta_j split into three bf16 terms (hi, mid, lo) in the first three of 16 slots.
+__device__ __forceinline__ void write_bias_row(__nv_bfloat16* row16, float beta) {
+  __nv_bfloat16 h1, h2, h3;
+  if (isfinite(beta)) {
+    h1 = __float2bfloat16_rn(beta);
+    const float r1 = beta - __bfloat162float(h1);
+    h2 = __float2bfloat16_rn(r1);
+    h3 = __float2bfloat16_rn(r1 - __bfloat162float(h2));
+  } else {
+    h1 = __float2bfloat16_rn(-INFINITY);
+    h2 = __float2bfloat16_rn(0.f);
+    h3 = __float2bfloat16_rn(0.f);
+  }
+  uint4 lo4;
+  lo4.x = (uint32_t)__bfloat16_as_ushort(h1) | ((uint32_t)__bfloat16_as_ushort(h2) << 16);
+  lo4.y = (uint32_t)__bfloat16_as_ushort(h3);
+  lo4.z = 0u;
+  lo4.w = 0u;
+  uint4* dst = reinterpret_cast<uint4*>(row16);
+  dst[0] = lo4;
+  dst[1] = make_uint4(0u, 0u, 0u, 0u);
+}
+
 __global__ void __launch_bounds__(NTHREADS, 1)
     lse_sweep_tc(const __grid_constant__ CUtensorMap mapAh, const __grid_constant__ CUtensorMap mapAl,
-                 const __grid_constant__ CUtensorMap mapBh, const __grid_constant__ CUtensorMap mapBl, TcParams tp) {
+                 const __grid_constant__ CUtensorMap mapBh, const __grid_constant__ CUtensorMap mapBl,
+                 const __grid_constant__ CUtensorMap mapBbias, TcParams tp) {
   const SweepParams& p = tp.p;
   if (p.state != nullptr && p.state->done) return;
   extern __shared__ unsigned char smem_raw[];
-  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const SmemLayout L = smem_layout(tp.nkb, tp.split3, tp.stages);
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const SmemLayout L = smem_layout(tp.nkb, tp.split3, tp.stages, tp.a_bufs);
   TcShared& sh = *reinterpret_cast<TcShared*>(smem + L.ctrl);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t row0 = (int64_t)blockIdx.x * BM;
-  const int ntiles_total = (int)((p.nB + BN - 1) / BN);
-  const int t_begin = blockIdx.y * p.tiles_per_split;
-  const int t_end = min(ntiles_total, t_begin + p.tiles_per_split);
-  const int ntiles = max(0, t_end - t_begin);
-  const int nkb = tp.nkb, S = tp.stages;
-  const int units = ntiles * nkb;
+  const int c = blockIdx.x, G = tp.G, T = tp.T;
+  const int64_t W = (int64_t)tp.R * T;
+  const int nseg = num_segments(c, W, G, T);
+  const int nkb = tp.nkb, S = tp.stages, NA = tp.a_bufs;
   volatile int32_t* abort_flag = &sh.abort_flag;
-
   const int fcur = p.state ? p.state->fcur : 0;
-  const float* potB = (p.potB_alt && fcur == 1) ? p.potB_alt : p.potB;
 
   // ---------------------------------------------------------------- set-up
   if (threadIdx.x == 0) {
@@ -232,8 +286,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int b = 0; b < 2; ++b) {
       mbar_init(&sh.tmem_full[b], 1);
       mbar_init(&sh.tmem_empty[b], 4);
+      mbar_init(&sh.a_full[b], 1);
+      mbar_init(&sh.a_empty[b], 1);
     }
-    mbar_init(&sh.a_full, 1);
     mbar_init(&sh.drain, 1);
     sh.abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -256,115 +311,93 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   tc_fence_after();
   const uint32_t tmem_base = sh.tmem_base;
 
-  float m_run = -INFINITY, s_run = 0.f;
-
   if (warp == 0) {
-    // ------------------------------------------------------------ producer
-    int issued = 0;
-    bool ok = true;
-    if (lane == 0 && units > 0) {
-      const uint32_t abytes = (uint32_t)(nkb * OP_TILE_BYTES * (tp.split3 ? 2 : 1));
-      mbar_arrive_expect_tx(&sh.a_full, abytes);
-      for (int kb = 0; kb < nkb; ++kb) {
-        tma_load_2d(smem + L.a_hi + kb * OP_TILE_BYTES, &mapAh, &sh.a_full, kb * KB, (int)row0);
-        if (tp.split3) tma_load_2d(smem + L.a_lo + kb * OP_TILE_BYTES, &mapAl, &sh.a_full, kb * KB, (int)row0);
-      }
-    }
-    for (int u = 0; u < units && ok; ++u) {
-      const int s = u % S;
-      const uint32_t ph = (uint32_t)((u / S) & 1);
-      int okv = 0;
-      if (lane == 0) okv = mbar_wait(&sh.empty[s], ph ^ 1u, abort_flag) ? 1 : 0;
-      ok = __shfl_sync(0xffffffffu, okv, 0) != 0;  // warp-uniform decision
-      __syncwarp();
-      if (!ok) break;
-      const int tl = u / nkb, kb = u % nkb;
-      const int64_t col0 = (int64_t)(t_begin + tl) * BN;
-      unsigned char* st = smem + L.stage0 + s * L.stage_bytes;
-      if (kb == 0) {
-        // beta rows of this tile: [beta_hi, beta_mid, beta_lo, 0 x 13] as bf16
-        for (int r = lane; r < BN; r += 32) {
-          const int64_t j = col0 + r;
-          __nv_bfloat16 h1, h2, h3;
-          if (j < p.nB) {
-            const float beta = (potB[j] - p.Bn[j]) * p.bscale;
-            h1 = __float2bfloat16_rn(beta);
-            const float r1 = beta - __bfloat162float(h1);
-            h2 = __float2bfloat16_rn(r1);
-            const float r2 = r1 - __bfloat162float(h2);
-            h3 = __float2bfloat16_rn(r2);
-          } else {
-            h1 = __float2bfloat16_rn(-INFINITY);
-            h2 = __float2bfloat16_rn(0.f);
-            h3 = __float2bfloat16_rn(0.f);
-          }
-          uint4 lo4, hi4;
-          lo4.x = (uint32_t)__bfloat16_as_ushort(h1) | ((uint32_t)__bfloat16_as_ushort(h2) << 16);
-          lo4.y = (uint32_t)__bfloat16_as_ushort(h3);
-          lo4.z = 0u;
-          lo4.w = 0u;
-          hi4 = make_uint4(0u, 0u, 0u, 0u);
-          uint4* dst = reinterpret_cast<uint4*>(st + L.bias_off + r * 32);
-          dst[0] = lo4;
-          dst[1] = hi4;
+    // ------------------------------------------------------------ producer (lane 0)
+    if (lane == 0) {
+      int u = 0;  // B stage units issued
+      bool ok = true;
+      const uint32_t abytes = (uint32_t)L.a_stride;
+      const uint32_t bbytes = (uint32_t)(OP_TILE_BYTES * (tp.split3 ? 2 : 1));
+      int a_issued = 0;
+      for (int k = 0; k < nseg && ok; ++k) {
+        const Seg sg = segment(c, k, W, G, T);
+        const int ai = k % NA;
+        ok = mbar_wait(&sh.a_empty[ai], (uint32_t)(((k / NA) & 1) ^ 1), abort_flag);
+        if (!ok) break;
+        unsigned char* abuf = smem + L.a0 + ai * L.a_stride;
+        mbar_arrive_expect_tx(&sh.a_full[ai], abytes);
+        for (int kb = 0; kb < nkb; ++kb) {
+          tma_load_2d(abuf + kb * OP_TILE_BYTES, &mapAh, &sh.a_full[ai], kb * KB, sg.r * BM);
+          if (tp.split3) tma_load_2d(abuf + L.a_lo_off + kb * OP_TILE_BYTES, &mapAl, &sh.a_full[ai], kb * KB, sg.r * BM);
         }
-        fence_async_smem();
-        __syncwarp();
+        a_issued = k + 1;
+        for (int t = sg.t0; t < sg.t1 && ok; ++t) {
+          for (int kb = 0; kb < nkb; ++kb, ++u) {
+            const int s = u % S;
+            ok = mbar_wait(&sh.empty[s], (uint32_t)(((u / S) & 1) ^ 1), abort_flag);
+            if (!ok) break;
+            unsigned char* st = smem + L.stage0 + s * L.stage_bytes;
+            mbar_arrive_expect_tx(&sh.full[s], bbytes + (kb == 0 ? (uint32_t)BIAS_TILE_BYTES : 0u));
+            tma_load_2d(st, &mapBh, &sh.full[s], kb * KB, t * BN);
+            if (tp.split3) tma_load_2d(st + L.b_lo_off, &mapBl, &sh.full[s], kb * KB, t * BN);
+            if (kb == 0) tma_load_2d(st + L.bias_off, &mapBbias, &sh.full[s], 0, t * BN);
+          }
+        }
       }
-      if (lane == 0) {
-        const uint32_t bytes = (uint32_t)(OP_TILE_BYTES * (tp.split3 ? 2 : 1));
-        mbar_arrive_expect_tx(&sh.full[s], bytes);
-        tma_load_2d(st, &mapBh, &sh.full[s], kb * KB, (int)col0);
-        if (tp.split3) tma_load_2d(st + L.b_lo_off, &mapBl, &sh.full[s], kb * KB, (int)col0);
+      if (!ok) {
+        // drain this CTA's own copies still in flight before shared memory is released
+        for (int k = max(0, a_issued - NA); k < a_issued; ++k)
+          mbar_wait(&sh.a_full[k % NA], (uint32_t)((k / NA) & 1), abort_flag, true);
+        for (int v = max(0, u - S); v < u; ++v) mbar_wait(&sh.full[v % S], (uint32_t)((v / S) & 1), abort_flag, true);
       }
-      __syncwarp();
-      issued = u + 1;
-    }
-    if (!ok && lane == 0) {
-      // drain this CTA's own copies still in flight before shared memory is released
-      mbar_wait(&sh.a_full, 0, abort_flag, true);
-      for (int u = max(0, issued - S); u < issued; ++u) mbar_wait(&sh.full[u % S], (uint32_t)((u / S) & 1), abort_flag, true);
     }
   } else if (warp == 1) {
-    // ------------------------------------------------------------ MMA issuer
-    if (lane == 0 && units > 0) {
-      bool ok = mbar_wait(&sh.a_full, 0, abort_flag);
-      tc_fence_after();
-      const uint32_t a_hi = smem_u32(smem + L.a_hi), a_lo = smem_u32(smem + L.a_lo);
+    // ------------------------------------------------------------ MMA issuer (lane 0)
+    if (lane == 0) {
       const uint64_t abias = desc_sw32(smem_u32(smem + L.a_bias));
-      int committed = 0;
-      for (int tl = 0; tl < ntiles && ok; ++tl) {
-        const int b = tl & 1;
-        ok = mbar_wait(&sh.tmem_empty[b], (uint32_t)(((tl >> 1) & 1) ^ 1), abort_flag);
+      bool ok = true;
+      int u = 0, tl = 0;
+      for (int k = 0; k < nseg && ok; ++k) {
+        const Seg sg = segment(c, k, W, G, T);
+        const int ai = k % NA;
+        ok = mbar_wait(&sh.a_full[ai], (uint32_t)((k / NA) & 1), abort_flag);
         if (!ok) break;
         tc_fence_after();
-        const uint32_t d_tmem = tmem_base + (uint32_t)(b * BN);
-        for (int kb = 0; kb < nkb && ok; ++kb) {
-          const int u = tl * nkb + kb, s = u % S;
-          ok = mbar_wait(&sh.full[s], (uint32_t)((u / S) & 1), abort_flag);
+        const uint32_t a_hi = smem_u32(smem + L.a0 + ai * L.a_stride);
+        const uint32_t a_lo = a_hi + L.a_lo_off;
+        for (int t = sg.t0; t < sg.t1 && ok; ++t, ++tl) {
+          const int b = tl & 1;
+          ok = mbar_wait(&sh.tmem_empty[b], (uint32_t)(((tl >> 1) & 1) ^ 1), abort_flag);
           if (!ok) break;
           tc_fence_after();
-          const uint32_t st = smem_u32(smem + L.stage0 + s * L.stage_bytes);
-          const uint64_t bh = desc_sw128(st), bl = desc_sw128(st + L.b_lo_off);
-          const uint64_t ah = desc_sw128(a_hi + kb * OP_TILE_BYTES), al = desc_sw128(a_lo + kb * OP_TILE_BYTES);
+          const uint32_t d_tmem = tmem_base + (uint32_t)(b * BN);
+          for (int kb = 0; kb < nkb; ++kb, ++u) {
+            const int s = u % S;
+            ok = mbar_wait(&sh.full[s], (uint32_t)((u / S) & 1), abort_flag);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t st = smem_u32(smem + L.stage0 + s * L.stage_bytes);
+            const uint64_t bh = desc_sw128(st), bl = desc_sw128(st + L.b_lo_off);
+            const uint64_t ah = desc_sw128(a_hi + kb * OP_TILE_BYTES), al = desc_sw128(a_lo + kb * OP_TILE_BYTES);
 #pragma unroll
-          for (int k = 0; k < KB / 16; ++k) {
-            // +32 bytes per K = 16 step inside the 128-byte swizzle atom (encoded >> 4)
-            const uint64_t adv = (uint64_t)(k * 2);
-            umma(d_tmem, ah + adv, bh + adv, (kb > 0 || k > 0) ? 1u : 0u);
-            if (tp.split3) {
-              umma(d_tmem, ah + adv, bl + adv, 1u);
-              umma(d_tmem, al + adv, bh + adv, 1u);
+            for (int kk = 0; kk < KB / 16; ++kk) {
+              // +32 bytes per K = 16 step inside the 128-byte swizzle atom (encoded >> 4)
+              const uint64_t adv = (uint64_t)(kk * 2);
+              umma(d_tmem, ah + adv, bh + adv, (kb > 0 || kk > 0) ? 1u : 0u);
+              if (tp.split3) {
+                umma(d_tmem, ah + adv, bl + adv, 1u);
+                umma(d_tmem, al + adv, bh + adv, 1u);
+              }
             }
+            if (kb == 0) umma(d_tmem, abias, desc_sw32(st + L.bias_off), 1u);
+            umma_commit(&sh.empty[s]);
           }
-          if (kb == 0) umma(d_tmem, abias, desc_sw32(st + L.bias_off), 1u);
-          umma_commit(&sh.empty[s]);
+          if (!ok) break;
+          umma_commit(&sh.tmem_full[b]);
         }
         if (!ok) break;
-        umma_commit(&sh.tmem_full[b]);
-        committed = tl + 1;
+        umma_commit(&sh.a_empty[ai]);
       }
-      (void)committed;
       // make sure no MMA is still writing TMEM when the CTA moves on
       umma_commit(&sh.drain);
       mbar_wait(&sh.drain, 0, abort_flag, true);
@@ -372,102 +405,136 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   } else {
     // ------------------------------------------------------------ LSE warps
     const int quarter = warp & 3;  // TMEM lane quarter this warp may access
-    for (int tl = 0; tl < ntiles; ++tl) {
-      const int b = tl & 1;
-      int okv = 0;
-      if (lane == 0) okv = mbar_wait(&sh.tmem_full[b], (uint32_t)((tl >> 1) & 1), abort_flag) ? 1 : 0;
-      if (__shfl_sync(0xffffffffu, okv, 0) == 0) break;  // warp-uniform: the TMEM loads below are .sync.aligned
-      __syncwarp();
-      tc_fence_after();
-      const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN);
-      float v[4][32];
-      PROGOT_TMEM_LD32(taddr + 0, v[0]);
-      PROGOT_TMEM_LD32(taddr + 32, v[1]);
-      PROGOT_TMEM_LD32(taddr + 64, v[2]);
-      PROGOT_TMEM_LD32(taddr + 96, v[3]);
-      tmem_wait_ld();
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&sh.tmem_empty[b]);
-      float tmax = v[0][0];
-#pragma unroll
-      for (int c = 0; c < 4; ++c)
-#pragma unroll
-        for (int i = 0; i < 32; ++i) tmax = fmaxf(tmax, v[c][i]);
-      const float mnew = fmaxf(m_run, tmax);
-      if (mnew != -INFINITY) {
-        float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          acc0 += fast_exp2(v[0][i] - mnew);
-          acc1 += fast_exp2(v[1][i] - mnew);
-          acc2 += fast_exp2(v[2][i] - mnew);
-          acc3 += fast_exp2(v[3][i] - mnew);
+    const int row_local = quarter * 32 + lane;
+    const int ltid = threadIdx.x - 64;  // 0..127
+    int tl = 0;
+    // A warp whose bounded wait failed turns "dead": it skips tile work but keeps
+    // executing every named barrier below, so the other LSE warps never block on it.
+    bool dead = false;
+    for (int k = 0; k < nseg; ++k) {
+      const Seg sg = segment(c, k, W, G, T);
+      float m_run = -INFINITY, s_run = 0.f;
+      for (int t = sg.t0; t < sg.t1; ++t, ++tl) {
+        if (dead) continue;
+        const int b = tl & 1;
+        int okv = 0;
+        if (lane == 0) okv = mbar_wait(&sh.tmem_full[b], (uint32_t)((tl >> 1) & 1), abort_flag) ? 1 : 0;
+        if (__shfl_sync(0xffffffffu, okv, 0) == 0) {  // warp-uniform: the TMEM loads are .sync.aligned
+          dead = true;
+          continue;
         }
-        s_run = s_run * fast_exp2(m_run - mnew) + ((acc0 + acc1) + (acc2 + acc3));
-        m_run = mnew;
+        __syncwarp();
+        tc_fence_after();
+        const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN);
+        float v[4][32];
+        PROGOT_TMEM_LD32(taddr + 0, v[0]);
+        PROGOT_TMEM_LD32(taddr + 32, v[1]);
+        PROGOT_TMEM_LD32(taddr + 64, v[2]);
+        PROGOT_TMEM_LD32(taddr + 96, v[3]);
+        tmem_wait_ld();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sh.tmem_empty[b]);
+        float mx[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) mx[q] = v[q >> 1][(q & 1) * 16];
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc)
+#pragma unroll
+          for (int i = 0; i < 32; ++i) mx[cc * 2 + (i >> 4)] = fmaxf(mx[cc * 2 + (i >> 4)], v[cc][i]);
+        const float tmax = fmaxf(fmaxf(fmaxf(mx[0], mx[1]), fmaxf(mx[2], mx[3])),
+                                 fmaxf(fmaxf(mx[4], mx[5]), fmaxf(mx[6], mx[7])));
+        const float mnew = fmaxf(m_run, tmax);
+        if (mnew != -INFINITY) {
+          float acc[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) acc[q] = 0.f;
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc)
+#pragma unroll
+            for (int i = 0; i < 32; ++i) acc[cc * 2 + (i & 1)] += fast_exp2(v[cc][i] - mnew);
+          s_run = s_run * fast_exp2(m_run - mnew) +
+                  (((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7])));
+          m_run = mnew;
+        }
+      }
+      if (dead) {
+        m_run = NAN;
+        s_run = NAN;
+      }
+      // ---- segment done: publish the partial, last arrival combines the row block
+      const int64_t i = (int64_t)sg.r * BM + row_local;
+      if (i < p.nA) p.partial[((int64_t)c * tp.maxseg + k) * BM + row_local] = make_float2(m_run, s_run);
+      __threadfence();
+      lse_bar();
+      if (ltid == 0) {
+        const int c_first = cta_of((int64_t)sg.r * T, W, G);
+        const int c_last = cta_of((int64_t)sg.r * T + T - 1, W, G);
+        const unsigned prev = atomicAdd(&p.cnt[sg.r], 1u);
+        sh.s_last = (prev == (unsigned)(c_last - c_first));
+      }
+      lse_bar();
+      if (sh.s_last) {
+        __threadfence();
+        const int c_first = cta_of((int64_t)sg.r * T, W, G);
+        const int c_last = cta_of((int64_t)sg.r * T + T - 1, W, G);
+        const float* potA_cur = p.potA_old;
+        float* out_target = p.out;
+        if (p.role == 1) {
+          potA_cur = (fcur == 0) ? p.out : p.out_alt;
+          out_target = (fcur == 0) ? p.out_alt : p.out;
+        }
+        double e = 0.0;
+        if (i < p.nA) {
+          float2 acc = make_float2(-INFINITY, 0.f);
+          for (int cc = c_first; cc <= c_last; ++cc) {
+            const int kk = sg.r - (int)(work_begin(cc, W, G) / T);
+            acc = lse_combine(acc, __ldcg(&p.partial[((int64_t)cc * tp.maxseg + kk) * BM + row_local]));
+          }
+          const float Lr = acc.x + __log2f(acc.y);
+          e = row_epilogue(p, i, Lr, potA_cur, out_target);
+          if (tp.bias_out != nullptr && p.mode == kModePotential)
+            write_bias_row(tp.bias_out + i * 16, (out_target[i] - p.An[i]) * p.bscale);
+        }
+        // block sum of the error terms over the 128 LSE threads, in a fixed order
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
+        if (lane == 0) sh.red[quarter] = e;
+        lse_bar();
+        if (ltid == 0) {
+          const double tot = (sh.red[0] + sh.red[1]) + (sh.red[2] + sh.red[3]);
+          p.errpart[sg.r] = tot;
+          p.cnt[sg.r] = 0;
+          __threadfence();
+          const unsigned prev = atomicAdd(&p.cnt[tp.R], 1u);
+          if (prev == (unsigned)(tp.R - 1)) {
+            __threadfence();
+            finish_sweep(p, tp.R);
+            p.cnt[tp.R] = 0;
+          }
+        }
+        lse_bar();
       }
     }
   }
 
-  // ---------------------------------------------------------------- partials
+  // ---------------------------------------------------------------- teardown
   tc_fence_before();
   __syncthreads();
-  const bool aborted = sh.abort_flag != 0;
-  if (aborted && threadIdx.x == 0 && tp.fault) atomicExch(tp.fault, 1);
-  if (warp >= 2) {
-    const int64_t i = row0 + (warp & 3) * 32 + lane;
-    if (i < p.nA) {
-      float2 v = make_float2(m_run, s_run);
-      if (aborted) v = make_float2(NAN, NAN);
-      p.partial[(int64_t)blockIdx.y * p.nA + i] = v;
-    }
-  }
-  __threadfence();
-  __syncthreads();
+  if (sh.abort_flag != 0 && threadIdx.x == 0 && tp.fault) atomicExch(tp.fault, 1);
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
   }
-  if (threadIdx.x == 0) {
-    const unsigned prev = atomicAdd(&p.cnt[blockIdx.x], 1u);
-    sh.s_last = (prev == (unsigned)(p.splits - 1));
-  }
-  __syncthreads();
-  if (!sh.s_last) return;
+}
 
-  // ---- last CTA of this row block: combine the splits in order, epilogue
-  const float* potA_cur = p.potA_old;
-  float* out_target = p.out;
-  if (p.role == 1) {
-    potA_cur = (fcur == 0) ? p.out : p.out_alt;
-    out_target = (fcur == 0) ? p.out_alt : p.out;
-  }
-  double e = 0.0;
-  if (threadIdx.x < BM) {
-    const int64_t i = row0 + threadIdx.x;
-    if (i < p.nA) {
-      float2 v = make_float2(-INFINITY, 0.f);
-      for (int s = 0; s < p.splits; ++s) v = lse_combine(v, __ldcg(&p.partial[(int64_t)s * p.nA + i]));
-      const float Lr = v.x + __log2f(v.y);
-      e = row_epilogue(p, i, Lr, potA_cur, out_target);
-    }
-  }
-  const double tot = block_sum_f64<NTHREADS>(e, sh.red);
-  if (threadIdx.x == 0) {
-    p.errpart[blockIdx.x] = tot;
-    p.cnt[blockIdx.x] = 0;
-  }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned prev = atomicAdd(&p.cnt[gridDim.x], 1u);
-    if (prev == gridDim.x - 1) {
-      __threadfence();
-      finish_sweep(p, gridDim.x);
-      p.cnt[gridDim.x] = 0;
-    }
-  }
+// beta_j = (potB_j - |b_j|^2) log2(e)/eps for j < nB, -inf for nB <= j < nB_pad.
+__global__ void bias_prep_kernel(const float* __restrict__ potB, const float* __restrict__ Bn, int64_t nB,
+                                 int64_t nB_pad, float bscale, __nv_bfloat16* __restrict__ out) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nB_pad) return;
+  const float beta = (j < nB) ? (potB[j] - Bn[j]) * bscale : -INFINITY;
+  write_bias_row(out + j * 16, beta);
 }
 
 // ---------------------------------------------------------------- operand prep
@@ -488,14 +555,28 @@ __global__ void split_bf16_kernel(const float* __restrict__ X, int64_t n, int32_
 }  // namespace tc
 
 // ---------------------------------------------------------------- host side
-int tc_stages(int nkb, int split3) {
-  int best = 0;
-  for (int s = 2; s <= 8; ++s)
-    if (tc::smem_layout(nkb, split3, s).total <= 227 * 1024) best = s;
-  return best;
+// Pipeline shape for a K depth of nkb blocks: two A buffers when at least three B
+// stages still fit in 227 KB, else one; as many B stages (<= 8) as fit.
+static void tc_shape(int nkb, int split3, int* stages, int* a_bufs) {
+  *stages = 0;
+  *a_bufs = 1;
+  for (int na = 2; na >= 1; --na) {
+    int best = 0;
+    for (int s = 2; s <= 8; ++s)
+      if (tc::smem_layout(nkb, split3, s, na).total <= 227 * 1024) best = s;
+    if (best >= (na == 2 ? 3 : 2)) {
+      *stages = best;
+      *a_bufs = na;
+      return;
+    }
+  }
 }
 
-size_t tc_smem_bytes(int nkb, int split3, int stages) { return tc::smem_layout(nkb, split3, stages).total; }
+int tc_stages(int nkb, int split3) {
+  int s, na;
+  tc_shape(nkb, split3, &s, &na);
+  return s;
+}
 
 cudaError_t launch_split_bf16(const float* X, int64_t n, int32_t d, int32_t dp, float scale, void* hi, void* lo,
                               cudaStream_t s) {
@@ -507,11 +588,35 @@ cudaError_t launch_split_bf16(const float* X, int64_t n, int32_t d, int32_t dp, 
   return cudaGetLastError();
 }
 
+cudaError_t launch_bias_prep(const float* potB, const float* Bn, int64_t nB, int64_t nB_pad, float bscale, void* out,
+                             cudaStream_t s) {
+  tc::bias_prep_kernel<<<(unsigned)((nB_pad + 255) / 256), 256, 0, s>>>(potB, Bn, nB, nB_pad, bscale,
+                                                                        (__nv_bfloat16*)out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// Number of persistent CTAs and partial slots per CTA for a sweep of nA x nB.
+void tc_plan(int64_t nA, int64_t nB, int sms, int* G, int* maxseg) {
+  const int64_t R = (nA + tc::BM - 1) / tc::BM, T = (nB + tc::BN - 1) / tc::BN;
+  const int64_t W = R * T;
+  const int g = (int)std::min<int64_t>(W, sms);
+  int ms = 1;
+  for (int c = 0; c < g; ++c) {
+    const int64_t w0 = (int64_t)c * W / g, w1 = (int64_t)(c + 1) * W / g;
+    if (w1 > w0) ms = std::max<int>(ms, (int)((w1 - 1) / T - w0 / T + 1));
+  }
+  *G = g;
+  *maxseg = ms;
+}
+
 cudaError_t launch_lse_sweep_tc(const SweepParams& p, const void* mapAh, const void* mapAl, const void* mapBh,
-                                const void* mapBl, int nkb, int split3, int32_t* fault, cudaStream_t stream) {
-  const int stages = tc_stages(nkb, split3);
+                                const void* mapBl, const void* mapBbias, int nkb, int split3, int G, int maxseg,
+                                int32_t* fault, void* bias_out, cudaStream_t stream) {
+  int stages, a_bufs;
+  tc_shape(nkb, split3, &stages, &a_bufs);
   if (stages < 2) return cudaErrorInvalidValue;
-  const size_t smem = tc_smem_bytes(nkb, split3, stages);
+  const size_t smem = tc::smem_layout(nkb, split3, stages, a_bufs).total;
   static size_t attr_bytes = 0;
   if (smem > attr_bytes) {
     cudaError_t e = cudaFuncSetAttribute(tc::lse_sweep_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -523,13 +628,17 @@ cudaError_t launch_lse_sweep_tc(const SweepParams& p, const void* mapAh, const v
   tp.nkb = nkb;
   tp.split3 = split3;
   tp.stages = stages;
+  tp.a_bufs = a_bufs;
+  tp.G = G;
+  tp.R = (int)((p.nA + tc::BM - 1) / tc::BM);
+  tp.T = (int)((p.nB + tc::BN - 1) / tc::BN);
+  tp.maxseg = maxseg;
   tp.fault = fault;
-  const int rb = (int)((p.nA + tc::BM - 1) / tc::BM);
-  dim3 grid(rb, p.splits);
-  tc::lse_sweep_tc<<<grid, tc::NTHREADS, smem, stream>>>(*reinterpret_cast<const CUtensorMap*>(mapAh),
-                                                        *reinterpret_cast<const CUtensorMap*>(mapAl),
-                                                        *reinterpret_cast<const CUtensorMap*>(mapBh),
-                                                        *reinterpret_cast<const CUtensorMap*>(mapBl), tp);
+  tp.bias_out = (__nv_bfloat16*)bias_out;
+  tc::lse_sweep_tc<<<G, tc::NTHREADS, smem, stream>>>(
+      *reinterpret_cast<const CUtensorMap*>(mapAh), *reinterpret_cast<const CUtensorMap*>(mapAl),
+      *reinterpret_cast<const CUtensorMap*>(mapBh), *reinterpret_cast<const CUtensorMap*>(mapBl),
+      *reinterpret_cast<const CUtensorMap*>(mapBbias), tp);
   count_launch();
   return cudaGetLastError();
 }
