@@ -221,7 +221,7 @@ static size_t ws_layout(const WsDims& w, Workspace* out, char* base) {
   ws.xl = take(opb);
   ws.yh = take(opb);
   ws.yl = take(opb);
-  const size_t bb = w.tc ? 32 * (size_t)(cdiv(w.nmax, 128) * 128) : 0;
+  const size_t bb = w.tc ? 32 * (size_t)(cdiv(w.nmax, 256) * 256) : 0;
   ws.xb = take(bb);
   ws.yb = take(bb);
   ws.fault = (int32_t*)take(sizeof(int32_t));
@@ -289,16 +289,16 @@ static EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 2-D bf16 tensor map over a (rows x dp) row-major buffer: 64 x 128 boxes with
-// 128-byte swizzle for operands (dp a multiple of 64), or 16 x 128 boxes with
-// 32-byte swizzle for bias rows (dp = 16).
-static int make_map(CUtensorMap* map, void* base, int64_t rows, int32_t dp) {
+// 2-D bf16 tensor map over a (rows x dp) row-major buffer with boxes of box_rows rows:
+// 64-wide boxes with 128-byte swizzle for operands (dp a multiple of 64), or 16-wide
+// boxes with 32-byte swizzle for bias rows (dp = 16).
+static int make_map(CUtensorMap* map, void* base, int64_t rows, int32_t dp, int box_rows) {
   EncodeTiledFn enc = encode_fn();
   if (enc == nullptr) return fail(PROGOT_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
   const bool bias = dp == 16;
   cuuint64_t dims[2] = {(cuuint64_t)dp, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)dp * 2};
-  cuuint32_t box[2] = {bias ? 16u : 64u, 128};
+  cuuint32_t box[2] = {bias ? 16u : 64u, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, bias ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_128B,
@@ -308,9 +308,12 @@ static int make_map(CUtensorMap* map, void* base, int64_t rows, int32_t dp) {
 }
 
 struct TcOps {
-  CUtensorMap xh, xl, yh, yl, xb, yb;  // 64-byte aligned by the type itself
+  // operand maps in the A role (128-row boxes) and the B role (bn-row boxes), bias maps
+  // (bn-row boxes); CUtensorMap is 64-byte aligned by its own declaration
+  CUtensorMap xh_a, xl_a, yh_a, yl_a, xh_b, xl_b, yh_b, yl_b, xb, yb;
   int nkb = 0;
   int split3 = 0;
+  int bn = 128;
   bool on = false;
 };
 
@@ -330,16 +333,23 @@ static int prep_tc(const float* x, int64_t n, const float* y, int64_t m, int32_t
   const float sc = (float)std::sqrt(2.0 * kLog2e / eps);
   CK(launch_split_bf16(x, n, d, dp, sc, ws.xh, ops->split3 ? ws.xl : nullptr, s));
   CK(launch_split_bf16(y, m, d, dp, sc, ws.yh, ops->split3 ? ws.yl : nullptr, s));
-  int rc = make_map(&ops->xh, ws.xh, n, dp);
-  if (!rc) rc = make_map(&ops->xl, ops->split3 ? ws.xl : ws.xh, n, dp);
-  if (!rc) rc = make_map(&ops->yh, ws.yh, m, dp);
-  if (!rc) rc = make_map(&ops->yl, ops->split3 ? ws.yl : ws.yh, m, dp);
-  if (!rc) rc = make_map(&ops->xb, ws.xb, cdiv(n, 128) * 128, 16);
-  if (!rc) rc = make_map(&ops->yb, ws.yb, cdiv(m, 128) * 128, 16);
+  ops->bn = tc_tile_cols(ops->nkb, ops->split3);
+  void* xl = ops->split3 ? ws.xl : ws.xh;
+  void* yl = ops->split3 ? ws.yl : ws.yh;
+  int rc = make_map(&ops->xh_a, ws.xh, n, dp, 128);
+  if (!rc) rc = make_map(&ops->xl_a, xl, n, dp, 128);
+  if (!rc) rc = make_map(&ops->yh_a, ws.yh, m, dp, 128);
+  if (!rc) rc = make_map(&ops->yl_a, yl, m, dp, 128);
+  if (!rc) rc = make_map(&ops->xh_b, ws.xh, n, dp, ops->bn);
+  if (!rc) rc = make_map(&ops->xl_b, xl, n, dp, ops->bn);
+  if (!rc) rc = make_map(&ops->yh_b, ws.yh, m, dp, ops->bn);
+  if (!rc) rc = make_map(&ops->yl_b, yl, m, dp, ops->bn);
+  if (!rc) rc = make_map(&ops->xb, ws.xb, cdiv(n, 256) * 256, 16, ops->bn);
+  if (!rc) rc = make_map(&ops->yb, ws.yb, cdiv(m, 256) * 256, 16, ops->bn);
   if (rc) return rc;
   const float bscale = (float)(kLog2e / eps);
-  if (g_cur != nullptr) CK(launch_bias_prep(g_cur, yn, m, cdiv(m, 128) * 128, bscale, ws.yb, s));
-  if (f_cur != nullptr) CK(launch_bias_prep(f_cur, xn, n, cdiv(n, 128) * 128, bscale, ws.xb, s));
+  if (g_cur != nullptr) CK(launch_bias_prep(g_cur, yn, m, cdiv(m, 256) * 256, bscale, ws.yb, s));
+  if (f_cur != nullptr) CK(launch_bias_prep(f_cur, xn, n, cdiv(n, 256) * 256, bscale, ws.xb, s));
   return PROGOT_OK;
 }
 
@@ -377,18 +387,18 @@ static int lse_sweep(const SweepParams& p, int32_t precision, cudaStream_t s, co
   ProfRec r;
   if (t_prof.on) prof_begin(r, s);
   if (precision != PROGOT_FP32 && ops != nullptr && ops->on) {
-    const CUtensorMap* ah = a_is_x ? &ops->xh : &ops->yh;
-    const CUtensorMap* al = a_is_x ? &ops->xl : &ops->yl;
-    const CUtensorMap* bh = a_is_x ? &ops->yh : &ops->xh;
-    const CUtensorMap* bl = a_is_x ? &ops->yl : &ops->xl;
+    const CUtensorMap* ah = a_is_x ? &ops->xh_a : &ops->yh_a;
+    const CUtensorMap* al = a_is_x ? &ops->xl_a : &ops->yl_a;
+    const CUtensorMap* bh = a_is_x ? &ops->yh_b : &ops->xh_b;
+    const CUtensorMap* bl = a_is_x ? &ops->yl_b : &ops->xl_b;
     const CUtensorMap* bb = a_is_x ? &ops->yb : &ops->xb;
     void* bias_out = (p.mode == kModePotential && ws) ? (a_is_x ? ws->xb : ws->yb) : nullptr;
     int G = 0, maxseg = 0;
-    tc_plan(p.nA, p.nB, num_sms(), &G, &maxseg);
+    tc_plan(p.nA, p.nB, ops->bn, num_sms(), &G, &maxseg);
     SweepParams q = p;
     q.splits = G;  // not used by the persistent kernel beyond bookkeeping
-    CK(launch_lse_sweep_tc(q, ah, al, bh, bl, bb, ops->nkb, ops->split3, G, maxseg, ws ? ws->fault : nullptr,
-                           bias_out, s));
+    CK(launch_lse_sweep_tc(q, ah, al, bh, bl, bb, ops->nkb, ops->split3, ops->bn, G, maxseg,
+                           ws ? ws->fault : nullptr, bias_out, s));
   } else {
     CK(launch_lse_sweep_fp32(p, s));
   }

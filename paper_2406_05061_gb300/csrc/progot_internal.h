@@ -58,11 +58,12 @@ cudaError_t launch_split_bf16(const float* X, int64_t n, int32_t d, int32_t dp, 
 // B side; bias_out (optional): the same rows for the A side, written from the updated
 // potential in potential mode (the next sweep's B bias).
 cudaError_t launch_lse_sweep_tc(const SweepParams& p, const void* mapAh, const void* mapAl, const void* mapBh,
-                                const void* mapBl, const void* mapBbias, int nkb, int split3, int G, int maxseg,
-                                int32_t* fault, void* bias_out, cudaStream_t stream);
+                                const void* mapBl, const void* mapBbias, int nkb, int split3, int bn, int G,
+                                int maxseg, int32_t* fault, void* bias_out, cudaStream_t stream);
 cudaError_t launch_bias_prep(const float* potB, const float* Bn, int64_t nB, int64_t nB_pad, float bscale, void* out,
                              cudaStream_t s);
-void tc_plan(int64_t nA, int64_t nB, int sms, int* G, int* maxseg);
+void tc_plan(int64_t nA, int64_t nB, int bn, int sms, int* G, int* maxseg);
 int tc_stages(int nkb, int split3);
+int tc_tile_cols(int nkb, int split3);  // 128 or 256
 
 }  // namespace progot

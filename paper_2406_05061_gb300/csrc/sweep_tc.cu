@@ -36,12 +36,13 @@ namespace progot {
 namespace tc {
 
 constexpr int BM = 128;          // rows per CTA (TMEM lanes)
-constexpr int BN = 128;          // columns per tile (TMEM columns per accumulator)
 constexpr int KB = 64;           // bf16 K elements per 128-byte swizzle atom
-constexpr int NTHREADS = 192;    // 6 warps
-constexpr int TMEM_COLS = 256;   // two accumulators
-constexpr int OP_TILE_BYTES = BM * KB * 2;   // 16 KB: 128 rows x 64 bf16
-constexpr int BIAS_TILE_BYTES = BN * 32;     // 4 KB: 128 rows x 16 bf16 (32-byte swizzle)
+constexpr int NTHREADS = 320;    // 10 warps: producer, MMA, two LSE warpgroups
+constexpr int TMEM_COLS = 512;   // two accumulators of up to 256 columns
+constexpr int A_TILE_BYTES = BM * KB * 2;    // 16 KB: 128 rows x 64 bf16
+constexpr int A_BIAS_BYTES = BM * 32;        // 4 KB: 128 rows x 16 bf16 (32-byte swizzle)
+// Per column-tile width BN (128 or 256, a template parameter of the kernel):
+//   B operand tile BN rows x 64 bf16, bias tile BN rows x 16 bf16.
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded-wait limit per CTA
 
 struct TcShared {
@@ -57,6 +58,7 @@ struct TcShared {
   int32_t s_last;
   int32_t pad_;
   double red[4];
+  float2 ms[2][128];  // (max, sum) of LSE warpgroup 1 by segment parity, merged by warpgroup 0
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -90,7 +92,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 
 // Wait for the phase with the given parity; false when the CTA aborted or the wait
 // ran past kWaitNs (then the abort flag is raised for the whole CTA).
-__device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int32_t* abort_flag,
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int32_t* abort_flag,
                                        bool ignore_abort = false) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
@@ -104,6 +106,26 @@ __device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile 
       }
     }
   }
+}
+
+// One lane of a converged warp (the lowest), chosen by elect.sync: issuing TMA and
+// tcgen05 instructions from warp-uniform code keeps their operands in uniform
+// registers.
+__device__ __forceinline__ bool elect_one() {
+  uint32_t pred = 0;
+  asm volatile(
+      "{\n\t.reg .pred P;\n\t"
+      "elect.sync _|P, 0xffffffff;\n\t"
+      "selp.b32 %0, 1, 0, P;\n\t}"
+      : "=r"(pred));
+  return pred != 0;
+}
+
+// Bounded wait by every lane of a warp; the warp proceeds only if all lanes saw the phase.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int32_t* abort_flag,
+                                          bool ignore_abort = false) {
+  const bool ok = mbar_wait(bar, parity, abort_flag, ignore_abort);
+  return __all_sync(0xffffffffu, ok) != 0;
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
@@ -143,9 +165,9 @@ __device__ __forceinline__ uint64_t desc_sw32(uint32_t saddr) {
 constexpr uint32_t make_idesc(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
-constexpr uint32_t kIdesc = make_idesc(BM, BN);
-
+template <int BN>
 __device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  constexpr uint32_t kIdesc = make_idesc(BM, BN);
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
@@ -192,19 +214,20 @@ struct SmemLayout {
   uint32_t a0, a_stride, a_lo_off, a_bias, stage0, stage_bytes, b_lo_off, bias_off, ctrl, total;
 };
 
-__host__ __device__ inline SmemLayout smem_layout(int nkb, int split3, int stages, int a_bufs) {
+__host__ __device__ inline SmemLayout smem_layout(int bn, int nkb, int split3, int stages, int a_bufs) {
   SmemLayout L;
+  const uint32_t b_tile = (uint32_t)bn * KB * 2, bias_tile = (uint32_t)bn * 32;
   uint32_t off = 0;
   L.a0 = off;
-  L.a_lo_off = nkb * OP_TILE_BYTES;
-  L.a_stride = nkb * OP_TILE_BYTES * (split3 ? 2 : 1);
+  L.a_lo_off = nkb * A_TILE_BYTES;
+  L.a_stride = nkb * A_TILE_BYTES * (split3 ? 2 : 1);
   off += a_bufs * L.a_stride;
   L.a_bias = off;
-  off += BIAS_TILE_BYTES;
+  off += A_BIAS_BYTES;
   L.stage0 = off;
-  L.b_lo_off = OP_TILE_BYTES;
-  L.bias_off = OP_TILE_BYTES * (split3 ? 2 : 1);
-  L.stage_bytes = L.bias_off + BIAS_TILE_BYTES;
+  L.b_lo_off = b_tile;
+  L.bias_off = b_tile * (split3 ? 2 : 1);
+  L.stage_bytes = L.bias_off + bias_tile;
   off += stages * L.stage_bytes;
   L.ctrl = off;
   off += sizeof(TcShared);
@@ -233,7 +256,28 @@ __device__ __forceinline__ int num_segments(int c, int64_t W, int G, int T) {
   return (int)((w1 - 1) / T - w0 / T + 1);
 }
 
-__device__ __forceinline__ void lse_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+// Named barriers: 1 = both LSE warpgroups (256 threads), 2 = LSE warpgroup 0 (128).
+__device__ __forceinline__ void lse_bar_all() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ void lse_bar() { asm volatile("bar.sync 2, 128;" ::: "memory"); }
+
+__device__ __forceinline__ float max3(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ uint64_t pack2(float a, float b) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void unpack2(uint64_t v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
 
 // beta_j split into three bf16 terms (hi, mid, lo) in the first three of 16 slots.
 __device__ __forceinline__ void write_bias_row(__nv_bfloat16* row16, float beta) {
@@ -258,6 +302,7 @@ __device__ __forceinline__ void write_bias_row(__nv_bfloat16* row16, float beta)
   dst[1] = make_uint4(0u, 0u, 0u, 0u);
 }
 
+template <int BN>
 __global__ void __launch_bounds__(NTHREADS, 1)
     lse_sweep_tc(const __grid_constant__ CUtensorMap mapAh, const __grid_constant__ CUtensorMap mapAl,
                  const __grid_constant__ CUtensorMap mapBh, const __grid_constant__ CUtensorMap mapBl,
@@ -267,7 +312,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const SmemLayout L = smem_layout(tp.nkb, tp.split3, tp.stages, tp.a_bufs);
+  const SmemLayout L = smem_layout(BN, tp.nkb, tp.split3, tp.stages, tp.a_bufs);
+  constexpr uint32_t B_TILE_BYTES = (uint32_t)BN * KB * 2, BIAS_TILE_BYTES = (uint32_t)BN * 32;
   TcShared& sh = *reinterpret_cast<TcShared*>(smem + L.ctrl);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = blockIdx.x, G = tp.G, T = tp.T;
@@ -297,7 +343,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   // beta_hi + beta_mid + beta_lo whatever the order of the 16-byte chunks in a row.
   {
     uint32_t* ab = reinterpret_cast<uint32_t*>(smem + L.a_bias);
-    for (int i = threadIdx.x; i < BIAS_TILE_BYTES / 4; i += NTHREADS) ab[i] = 0x3F803F80u;
+    for (int i = threadIdx.x; i < A_BIAS_BYTES / 4; i += NTHREADS) ab[i] = 0x3F803F80u;
     fence_async_smem();
   }
   if (warp == 1) {
@@ -312,102 +358,114 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint32_t tmem_base = sh.tmem_base;
 
   if (warp == 0) {
-    // ------------------------------------------------------------ producer (lane 0)
-    if (lane == 0) {
-      int u = 0;  // B stage units issued
-      bool ok = true;
-      const uint32_t abytes = (uint32_t)L.a_stride;
-      const uint32_t bbytes = (uint32_t)(OP_TILE_BYTES * (tp.split3 ? 2 : 1));
-      int a_issued = 0;
-      for (int k = 0; k < nseg && ok; ++k) {
-        const Seg sg = segment(c, k, W, G, T);
-        const int ai = k % NA;
-        ok = mbar_wait(&sh.a_empty[ai], (uint32_t)(((k / NA) & 1) ^ 1), abort_flag);
-        if (!ok) break;
-        unsigned char* abuf = smem + L.a0 + ai * L.a_stride;
+    // ------------------------------------------------------------ producer (whole warp, one lane issues)
+    int u = 0;  // B stage units issued
+    bool ok = true;
+    const uint32_t abytes = (uint32_t)L.a_stride;
+    const uint32_t bbytes = B_TILE_BYTES * (tp.split3 ? 2u : 1u);
+    int a_issued = 0;
+    for (int k = 0; k < nseg && ok; ++k) {
+      const Seg sg = segment(c, k, W, G, T);
+      const int ai = k % NA;
+      ok = warp_wait(&sh.a_empty[ai], (uint32_t)(((k / NA) & 1) ^ 1), abort_flag);
+      if (!ok) break;
+      unsigned char* abuf = smem + L.a0 + ai * L.a_stride;
+      if (elect_one()) {
         mbar_arrive_expect_tx(&sh.a_full[ai], abytes);
         for (int kb = 0; kb < nkb; ++kb) {
-          tma_load_2d(abuf + kb * OP_TILE_BYTES, &mapAh, &sh.a_full[ai], kb * KB, sg.r * BM);
-          if (tp.split3) tma_load_2d(abuf + L.a_lo_off + kb * OP_TILE_BYTES, &mapAl, &sh.a_full[ai], kb * KB, sg.r * BM);
+          tma_load_2d(abuf + kb * A_TILE_BYTES, &mapAh, &sh.a_full[ai], kb * KB, sg.r * BM);
+          if (tp.split3) tma_load_2d(abuf + L.a_lo_off + kb * A_TILE_BYTES, &mapAl, &sh.a_full[ai], kb * KB, sg.r * BM);
         }
-        a_issued = k + 1;
-        for (int t = sg.t0; t < sg.t1 && ok; ++t) {
-          for (int kb = 0; kb < nkb; ++kb, ++u) {
-            const int s = u % S;
-            ok = mbar_wait(&sh.empty[s], (uint32_t)(((u / S) & 1) ^ 1), abort_flag);
-            if (!ok) break;
-            unsigned char* st = smem + L.stage0 + s * L.stage_bytes;
-            mbar_arrive_expect_tx(&sh.full[s], bbytes + (kb == 0 ? (uint32_t)BIAS_TILE_BYTES : 0u));
+      }
+      __syncwarp();
+      a_issued = k + 1;
+      for (int t = sg.t0; t < sg.t1 && ok; ++t) {
+        for (int kb = 0; kb < nkb; ++kb, ++u) {
+          const int s = u % S;
+          ok = warp_wait(&sh.empty[s], (uint32_t)(((u / S) & 1) ^ 1), abort_flag);
+          if (!ok) break;
+          unsigned char* st = smem + L.stage0 + s * L.stage_bytes;
+          if (elect_one()) {
+            mbar_arrive_expect_tx(&sh.full[s], bbytes + (kb == 0 ? BIAS_TILE_BYTES : 0u));
             tma_load_2d(st, &mapBh, &sh.full[s], kb * KB, t * BN);
             if (tp.split3) tma_load_2d(st + L.b_lo_off, &mapBl, &sh.full[s], kb * KB, t * BN);
             if (kb == 0) tma_load_2d(st + L.bias_off, &mapBbias, &sh.full[s], 0, t * BN);
           }
+          __syncwarp();
         }
       }
-      if (!ok) {
-        // drain this CTA's own copies still in flight before shared memory is released
-        for (int k = max(0, a_issued - NA); k < a_issued; ++k)
-          mbar_wait(&sh.a_full[k % NA], (uint32_t)((k / NA) & 1), abort_flag, true);
-        for (int v = max(0, u - S); v < u; ++v) mbar_wait(&sh.full[v % S], (uint32_t)((v / S) & 1), abort_flag, true);
-      }
+    }
+    if (!ok) {
+      // drain this CTA's own copies still in flight before shared memory is released
+      for (int k = max(0, a_issued - NA); k < a_issued; ++k)
+        warp_wait(&sh.a_full[k % NA], (uint32_t)((k / NA) & 1), abort_flag, true);
+      for (int v = max(0, u - S); v < u; ++v) warp_wait(&sh.full[v % S], (uint32_t)((v / S) & 1), abort_flag, true);
     }
   } else if (warp == 1) {
-    // ------------------------------------------------------------ MMA issuer (lane 0)
-    if (lane == 0) {
-      const uint64_t abias = desc_sw32(smem_u32(smem + L.a_bias));
-      bool ok = true;
-      int u = 0, tl = 0;
-      for (int k = 0; k < nseg && ok; ++k) {
-        const Seg sg = segment(c, k, W, G, T);
-        const int ai = k % NA;
-        ok = mbar_wait(&sh.a_full[ai], (uint32_t)((k / NA) & 1), abort_flag);
+    // ------------------------------------------------------------ MMA issuer (whole warp, one lane issues)
+    const uint64_t abias = desc_sw32(smem_u32(smem + L.a_bias));
+    bool ok = true;
+    int u = 0, tl = 0;
+    for (int k = 0; k < nseg && ok; ++k) {
+      const Seg sg = segment(c, k, W, G, T);
+      const int ai = k % NA;
+      ok = warp_wait(&sh.a_full[ai], (uint32_t)((k / NA) & 1), abort_flag);
+      if (!ok) break;
+      tc_fence_after();
+      const uint32_t a_hi = smem_u32(smem + L.a0 + ai * L.a_stride);
+      const uint32_t a_lo = a_hi + L.a_lo_off;
+      for (int t = sg.t0; t < sg.t1 && ok; ++t, ++tl) {
+        const int b = tl & 1;
+        ok = warp_wait(&sh.tmem_empty[b], (uint32_t)(((tl >> 1) & 1) ^ 1), abort_flag);
         if (!ok) break;
         tc_fence_after();
-        const uint32_t a_hi = smem_u32(smem + L.a0 + ai * L.a_stride);
-        const uint32_t a_lo = a_hi + L.a_lo_off;
-        for (int t = sg.t0; t < sg.t1 && ok; ++t, ++tl) {
-          const int b = tl & 1;
-          ok = mbar_wait(&sh.tmem_empty[b], (uint32_t)(((tl >> 1) & 1) ^ 1), abort_flag);
+        const uint32_t d_tmem = tmem_base + (uint32_t)(b * BN);
+        for (int kb = 0; kb < nkb; ++kb, ++u) {
+          const int s = u % S;
+          ok = warp_wait(&sh.full[s], (uint32_t)((u / S) & 1), abort_flag);
           if (!ok) break;
           tc_fence_after();
-          const uint32_t d_tmem = tmem_base + (uint32_t)(b * BN);
-          for (int kb = 0; kb < nkb; ++kb, ++u) {
-            const int s = u % S;
-            ok = mbar_wait(&sh.full[s], (uint32_t)((u / S) & 1), abort_flag);
-            if (!ok) break;
-            tc_fence_after();
-            const uint32_t st = smem_u32(smem + L.stage0 + s * L.stage_bytes);
-            const uint64_t bh = desc_sw128(st), bl = desc_sw128(st + L.b_lo_off);
-            const uint64_t ah = desc_sw128(a_hi + kb * OP_TILE_BYTES), al = desc_sw128(a_lo + kb * OP_TILE_BYTES);
+          const uint32_t st = smem_u32(smem + L.stage0 + s * L.stage_bytes);
+          const uint64_t bh = desc_sw128(st), bl = desc_sw128(st + L.b_lo_off);
+          const uint64_t ah = desc_sw128(a_hi + kb * A_TILE_BYTES), al = desc_sw128(a_lo + kb * A_TILE_BYTES);
+          const uint64_t bb = desc_sw32(st + L.bias_off);
+          if (elect_one()) {
 #pragma unroll
             for (int kk = 0; kk < KB / 16; ++kk) {
               // +32 bytes per K = 16 step inside the 128-byte swizzle atom (encoded >> 4)
               const uint64_t adv = (uint64_t)(kk * 2);
-              umma(d_tmem, ah + adv, bh + adv, (kb > 0 || kk > 0) ? 1u : 0u);
+              umma<BN>(d_tmem, ah + adv, bh + adv, (kb > 0 || kk > 0) ? 1u : 0u);
               if (tp.split3) {
-                umma(d_tmem, ah + adv, bl + adv, 1u);
-                umma(d_tmem, al + adv, bh + adv, 1u);
+                umma<BN>(d_tmem, ah + adv, bl + adv, 1u);
+                umma<BN>(d_tmem, al + adv, bh + adv, 1u);
               }
             }
-            if (kb == 0) umma(d_tmem, abias, desc_sw32(st + L.bias_off), 1u);
+            if (kb == 0) umma<BN>(d_tmem, abias, bb, 1u);
             umma_commit(&sh.empty[s]);
           }
-          if (!ok) break;
-          umma_commit(&sh.tmem_full[b]);
+          __syncwarp();
         }
         if (!ok) break;
-        umma_commit(&sh.a_empty[ai]);
+        if (elect_one()) umma_commit(&sh.tmem_full[b]);
+        __syncwarp();
       }
-      // make sure no MMA is still writing TMEM when the CTA moves on
-      umma_commit(&sh.drain);
-      mbar_wait(&sh.drain, 0, abort_flag, true);
+      if (!ok) break;
+      if (elect_one()) umma_commit(&sh.a_empty[ai]);
+      __syncwarp();
     }
+    // make sure no MMA is still writing TMEM when the CTA moves on
+    if (elect_one()) umma_commit(&sh.drain);
+    __syncwarp();
+    warp_wait(&sh.drain, 0, abort_flag, true);
   } else {
     // ------------------------------------------------------------ LSE warps
+    // Two warpgroups: warpgroup wg reads TMEM buffer wg, i.e. the tiles with
+    // (tile counter & 1) == wg, so two tiles are folded at once.
+    const int wg = (warp - 2) >> 2;
     const int quarter = warp & 3;  // TMEM lane quarter this warp may access
     const int row_local = quarter * 32 + lane;
-    const int ltid = threadIdx.x - 64;  // 0..127
-    int tl = 0;
+    const int ltid = threadIdx.x - 64;  // 0..127 in warpgroup 0
+    int tl = 0, jt = 0;
     // A warp whose bounded wait failed turns "dead": it skips tile work but keeps
     // executing every named barrier below, so the other LSE warps never block on it.
     bool dead = false;
@@ -415,52 +473,85 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const Seg sg = segment(c, k, W, G, T);
       float m_run = -INFINITY, s_run = 0.f;
       for (int t = sg.t0; t < sg.t1; ++t, ++tl) {
+        if ((tl & 1) != wg) continue;
+        const uint32_t ph = (uint32_t)(jt & 1);
+        ++jt;
         if (dead) continue;
-        const int b = tl & 1;
         int okv = 0;
-        if (lane == 0) okv = mbar_wait(&sh.tmem_full[b], (uint32_t)((tl >> 1) & 1), abort_flag) ? 1 : 0;
+        if (lane == 0) okv = mbar_wait(&sh.tmem_full[wg], ph, abort_flag) ? 1 : 0;
         if (__shfl_sync(0xffffffffu, okv, 0) == 0) {  // warp-uniform: the TMEM loads are .sync.aligned
           dead = true;
           continue;
         }
         __syncwarp();
         tc_fence_after();
-        const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * BN);
-        float v[4][32];
-        PROGOT_TMEM_LD32(taddr + 0, v[0]);
-        PROGOT_TMEM_LD32(taddr + 32, v[1]);
-        PROGOT_TMEM_LD32(taddr + 64, v[2]);
-        PROGOT_TMEM_LD32(taddr + 96, v[3]);
-        tmem_wait_ld();
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&sh.tmem_empty[b]);
-        float mx[8];
+        const uint32_t taddr0 = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(wg * BN);
+#pragma unroll 1
+        for (int half = 0; half < BN / 128; ++half) {
+          const uint32_t taddr = taddr0 + (uint32_t)(half * 128);
+          float v[4][32];
+          PROGOT_TMEM_LD32(taddr + 0, v[0]);
+          PROGOT_TMEM_LD32(taddr + 32, v[1]);
+          PROGOT_TMEM_LD32(taddr + 64, v[2]);
+          PROGOT_TMEM_LD32(taddr + 96, v[3]);
+          tmem_wait_ld();
+          if (half == BN / 128 - 1) {
+            // the whole accumulator is in registers: hand the TMEM buffer back to the MMA warp
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh.tmem_empty[wg]);
+          }
+          // maximum: 8 independent chains of three-input max
+          float mx[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) mx[q] = v[q >> 1][(q & 1) * 16];
-#pragma unroll
-        for (int cc = 0; cc < 4; ++cc)
-#pragma unroll
-          for (int i = 0; i < 32; ++i) mx[cc * 2 + (i >> 4)] = fmaxf(mx[cc * 2 + (i >> 4)], v[cc][i]);
-        const float tmax = fmaxf(fmaxf(fmaxf(mx[0], mx[1]), fmaxf(mx[2], mx[3])),
-                                 fmaxf(fmaxf(mx[4], mx[5]), fmaxf(mx[6], mx[7])));
-        const float mnew = fmaxf(m_run, tmax);
-        if (mnew != -INFINITY) {
-          float acc[8];
-#pragma unroll
-          for (int q = 0; q < 8; ++q) acc[q] = 0.f;
+          for (int q = 0; q < 8; ++q) mx[q] = v[q >> 1][(q & 1) * 16];
 #pragma unroll
           for (int cc = 0; cc < 4; ++cc)
 #pragma unroll
-            for (int i = 0; i < 32; ++i) acc[cc * 2 + (i & 1)] += fast_exp2(v[cc][i] - mnew);
-          s_run = s_run * fast_exp2(m_run - mnew) +
-                  (((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7])));
-          m_run = mnew;
+            for (int i = 1; i < 16; i += 2) {
+              mx[cc * 2] = max3(mx[cc * 2], v[cc][i], v[cc][i + 1 < 16 ? i + 1 : i]);
+              mx[cc * 2 + 1] = max3(mx[cc * 2 + 1], v[cc][16 + i], v[cc][16 + (i + 1 < 16 ? i + 1 : i)]);
+            }
+          const float tmax = max3(max3(mx[0], mx[1], mx[2]), max3(mx[3], mx[4], mx[5]), fmaxf(mx[6], mx[7]));
+          const float mnew = fmaxf(m_run, tmax);
+          if (mnew != -INFINITY) {
+            const uint64_t negm = pack2(-mnew, -mnew);
+            uint64_t acc[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] = 0ull;
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc)
+#pragma unroll
+              for (int i = 0; i < 32; i += 2) {
+                float a0, a1;
+                unpack2(add2(pack2(v[cc][i], v[cc][i + 1]), negm), a0, a1);
+                acc[(i >> 1) & 3] = add2(acc[(i >> 1) & 3], pack2(fast_exp2(a0), fast_exp2(a1)));
+              }
+            float s0, s1, s2, s3, s4, s5, s6, s7;
+            unpack2(acc[0], s0, s1);
+            unpack2(acc[1], s2, s3);
+            unpack2(acc[2], s4, s5);
+            unpack2(acc[3], s6, s7);
+            s_run = s_run * fast_exp2(m_run - mnew) + (((s0 + s1) + (s2 + s3)) + ((s4 + s5) + (s6 + s7)));
+            m_run = mnew;
+          }
         }
       }
       if (dead) {
         m_run = NAN;
         s_run = NAN;
+      }
+      // merge warpgroup 1's (max, sum) into warpgroup 0
+      // (slots alternate by segment parity: warpgroup 1 can only reuse slot k & 1 after
+      // the next 256-thread barrier, which warpgroup 0 reaches after reading it)
+      if (wg == 1) sh.ms[k & 1][row_local] = make_float2(m_run, s_run);
+      lse_bar_all();
+      if (wg == 1) continue;
+      {
+        const float2 o = sh.ms[k & 1][row_local];
+        const float2 mrg = lse_combine(make_float2(m_run, s_run), o);
+        m_run = (isnan(o.y) || isnan(s_run)) ? NAN : mrg.x;
+        s_run = (isnan(o.y) || isnan(s_run)) ? NAN : mrg.y;
       }
       // ---- segment done: publish the partial, last arrival combines the row block
       const int64_t i = (int64_t)sg.r * BM + row_local;
@@ -555,15 +646,15 @@ __global__ void split_bf16_kernel(const float* __restrict__ X, int64_t n, int32_
 }  // namespace tc
 
 // ---------------------------------------------------------------- host side
-// Pipeline shape for a K depth of nkb blocks: two A buffers when at least three B
-// stages still fit in 227 KB, else one; as many B stages (<= 8) as fit.
-static void tc_shape(int nkb, int split3, int* stages, int* a_bufs) {
+// Pipeline shape for a tile width bn and a K depth of nkb blocks: two A buffers when
+// at least three B stages still fit in 227 KB, else one; as many B stages (<= 8) as fit.
+static void tc_shape(int bn, int nkb, int split3, int* stages, int* a_bufs) {
   *stages = 0;
   *a_bufs = 1;
   for (int na = 2; na >= 1; --na) {
     int best = 0;
     for (int s = 2; s <= 8; ++s)
-      if (tc::smem_layout(nkb, split3, s, na).total <= 227 * 1024) best = s;
+      if (tc::smem_layout(bn, nkb, split3, s, na).total <= 227 * 1024) best = s;
     if (best >= (na == 2 ? 3 : 2)) {
       *stages = best;
       *a_bufs = na;
@@ -572,9 +663,16 @@ static void tc_shape(int nkb, int split3, int* stages, int* a_bufs) {
   }
 }
 
+// Column-tile width: 256 (one N = 256 MMA per K step) when two B stages fit, else 128.
+int tc_tile_cols(int nkb, int split3) {
+  int s, na;
+  tc_shape(256, nkb, split3, &s, &na);
+  return s >= 2 ? 256 : 128;
+}
+
 int tc_stages(int nkb, int split3) {
   int s, na;
-  tc_shape(nkb, split3, &s, &na);
+  tc_shape(tc_tile_cols(nkb, split3), nkb, split3, &s, &na);
   return s;
 }
 
@@ -596,9 +694,10 @@ cudaError_t launch_bias_prep(const float* potB, const float* Bn, int64_t nB, int
   return cudaGetLastError();
 }
 
-// Number of persistent CTAs and partial slots per CTA for a sweep of nA x nB.
-void tc_plan(int64_t nA, int64_t nB, int sms, int* G, int* maxseg) {
-  const int64_t R = (nA + tc::BM - 1) / tc::BM, T = (nB + tc::BN - 1) / tc::BN;
+// Number of persistent CTAs and partial slots per CTA for a sweep of nA x nB with
+// column tiles of width bn.
+void tc_plan(int64_t nA, int64_t nB, int bn, int sms, int* G, int* maxseg) {
+  const int64_t R = (nA + tc::BM - 1) / tc::BM, T = (nB + bn - 1) / bn;
   const int64_t W = R * T;
   const int g = (int)std::min<int64_t>(W, sms);
   int ms = 1;
@@ -610,19 +709,29 @@ void tc_plan(int64_t nA, int64_t nB, int sms, int* G, int* maxseg) {
   *maxseg = ms;
 }
 
-cudaError_t launch_lse_sweep_tc(const SweepParams& p, const void* mapAh, const void* mapAl, const void* mapBh,
-                                const void* mapBl, const void* mapBbias, int nkb, int split3, int G, int maxseg,
-                                int32_t* fault, void* bias_out, cudaStream_t stream) {
-  int stages, a_bufs;
-  tc_shape(nkb, split3, &stages, &a_bufs);
-  if (stages < 2) return cudaErrorInvalidValue;
-  const size_t smem = tc::smem_layout(nkb, split3, stages, a_bufs).total;
+template <int BN>
+static cudaError_t launch_tc(const tc::TcParams& tp, size_t smem, const void* mapAh, const void* mapAl,
+                             const void* mapBh, const void* mapBl, const void* mapBbias, cudaStream_t stream) {
   static size_t attr_bytes = 0;
   if (smem > attr_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(tc::lse_sweep_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(tc::lse_sweep_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_bytes = smem;
   }
+  tc::lse_sweep_tc<BN><<<tp.G, tc::NTHREADS, smem, stream>>>(
+      *reinterpret_cast<const CUtensorMap*>(mapAh), *reinterpret_cast<const CUtensorMap*>(mapAl),
+      *reinterpret_cast<const CUtensorMap*>(mapBh), *reinterpret_cast<const CUtensorMap*>(mapBl),
+      *reinterpret_cast<const CUtensorMap*>(mapBbias), tp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lse_sweep_tc(const SweepParams& p, const void* mapAh, const void* mapAl, const void* mapBh,
+                                const void* mapBl, const void* mapBbias, int nkb, int split3, int bn, int G,
+                                int maxseg, int32_t* fault, void* bias_out, cudaStream_t stream) {
+  int stages, a_bufs;
+  tc_shape(bn, nkb, split3, &stages, &a_bufs);
+  if (stages < 2 || (bn != 128 && bn != 256)) return cudaErrorInvalidValue;
+  const size_t smem = tc::smem_layout(bn, nkb, split3, stages, a_bufs).total;
   tc::TcParams tp;
   tp.p = p;
   tp.nkb = nkb;
@@ -631,16 +740,14 @@ cudaError_t launch_lse_sweep_tc(const SweepParams& p, const void* mapAh, const v
   tp.a_bufs = a_bufs;
   tp.G = G;
   tp.R = (int)((p.nA + tc::BM - 1) / tc::BM);
-  tp.T = (int)((p.nB + tc::BN - 1) / tc::BN);
+  tp.T = (int)((p.nB + bn - 1) / bn);
   tp.maxseg = maxseg;
   tp.fault = fault;
   tp.bias_out = (__nv_bfloat16*)bias_out;
-  tc::lse_sweep_tc<<<G, tc::NTHREADS, smem, stream>>>(
-      *reinterpret_cast<const CUtensorMap*>(mapAh), *reinterpret_cast<const CUtensorMap*>(mapAl),
-      *reinterpret_cast<const CUtensorMap*>(mapBh), *reinterpret_cast<const CUtensorMap*>(mapBl),
-      *reinterpret_cast<const CUtensorMap*>(mapBbias), tp);
+  cudaError_t e = (bn == 256) ? launch_tc<256>(tp, smem, mapAh, mapAl, mapBh, mapBl, mapBbias, stream)
+                              : launch_tc<128>(tp, smem, mapAh, mapAl, mapBh, mapBl, mapBbias, stream);
   count_launch();
-  return cudaGetLastError();
+  return e;
 }
 
 }  // namespace progot
