@@ -16,6 +16,7 @@
 // the start of each call; two calls whose work overlaps on the GPU (different streams,
 // or different host threads on one device) race on the array and must be serialised by
 // the caller.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -109,6 +110,7 @@ static SweepParams noalloc_sweep(const float* A, int64_t nA, const float* B, int
   p.bscale = (float)(kLog2e / eps);
   p.eps = eps;
   p.inv_nA = 1.0 / (double)nA;
+  p.log_w_uniform = std::log(1.0 / (double)nA);
   p.partial = partial;
   p.errpart = errpart;
   p.cnt = cnt;

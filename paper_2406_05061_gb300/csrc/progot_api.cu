@@ -373,6 +373,7 @@ static SweepParams make_sweep(const float* A, int64_t nA, const float* B, int64_
   p.bscale = (float)(kLog2e / eps);
   p.eps = eps;
   p.inv_nA = 1.0 / (double)nA;
+  p.log_w_uniform = std::log(1.0 / (double)nA);
   p.partial = ws.partial;
   p.errpart = ws.errpart;
   p.cnt = ws.cnt;

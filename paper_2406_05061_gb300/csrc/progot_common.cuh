@@ -62,6 +62,7 @@ struct SweepParams {
   double eps;
   double tau;
   double inv_nA;       // uniform weight 1/nA
+  double log_w_uniform;  // log(1/nA)
 };
 
 // Combine two partial log-sum-exps (max, sum) in log2 units.

@@ -22,11 +22,16 @@ __device__ __forceinline__ double block_sum_f64(double v, double* red) {
   return tot;
 }
 
-// Called by the last CTA of the whole sweep (thread 0): sum the per-row-block error
-// partials in order and advance the device-side Sinkhorn state.
-__device__ __forceinline__ void finish_sweep(const SweepParams& p, int nblocks) {
+// Called by one full warp of the last CTA of the whole sweep: sum the per-row-block
+// error partials in a fixed order (lane l takes blocks l, l + 32, ... in order, then a
+// fixed shuffle tree) and advance the device-side Sinkhorn state (lane 0).
+__device__ __forceinline__ void finish_sweep_warp(const SweepParams& p, int nblocks) {
+  const int lane = threadIdx.x & 31;
   double err = 0.0;
-  for (int b = 0; b < nblocks; ++b) err += __ldcg(p.errpart + b);
+  for (int b = lane; b < nblocks; b += 32) err += __ldcg(p.errpart + b);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) err += __shfl_xor_sync(0xffffffffu, err, off);
+  if (lane != 0) return;
   p.errpart[nblocks] = err;
   SolverState* st = p.state;
   if (st == nullptr) return;
@@ -57,27 +62,53 @@ __device__ __forceinline__ void finish_sweep(const SweepParams& p, int nblocks) 
   }
 }
 
-// Epilogue for one row given L (log2 units). Returns the row's error term.
-__device__ __forceinline__ double row_epilogue(const SweepParams& p, int64_t i, float L, const float* potA_cur,
-                                               float* out_target) {
-  const double w = p.wA ? (double)p.wA[i] : p.inv_nA;
+// Per-row inputs of the epilogue, loaded before the split combine so that their
+// latency overlaps it.
+struct RowIn {
+  float an;    // |a_i|^2 (potential and marginal modes)
+  float pot;   // current potential of row i (f-update error, marginal mode)
+  float w;     // weight a_i
+};
+
+__device__ __forceinline__ RowIn row_inputs(const SweepParams& p, int64_t i, const float* potA_cur) {
+  RowIn r;
+  r.an = (p.mode != kModeLse && p.An) ? p.An[i] : 0.f;
+  r.pot = (potA_cur != nullptr && (p.mode == kModeMarginal || p.role == 1)) ? potA_cur[i] : 0.f;
+  r.w = p.wA ? p.wA[i] : (float)p.inv_nA;
+  return r;
+}
+
+// Epilogue for one row given L = log2 sum_j 2^{t_ij}. Writes the row's output, returns
+// its error term (float64) and the written value in *val.
+//   potential: f_i = eps log w_i + |a_i|^2 - eps ln2 L, assembled in float64 adds and
+//              multiplies; error a_i |exp((f_old - f_new)/eps) - 1| with expm1 of the
+//              small float32 difference;
+//   marginal:  r_i = exp((pot_i - |a_i|^2)/eps + ln2 L), the exponent formed in float64
+//              (it is a difference of large terms) and exponentiated in float32.
+__device__ __forceinline__ double row_epilogue(const SweepParams& p, int64_t i, float L, const RowIn& in,
+                                               float* out_target, float* val) {
   if (p.mode == kModePotential) {
-    const float fnew = (float)(p.eps * log(w) + (double)p.An[i] - p.eps * kLn2 * (double)L);
+    const double logw = p.wA ? (double)__logf(in.w) : p.log_w_uniform;
+    const float fnew = (float)(p.eps * logw + (double)in.an - p.eps * kLn2 * (double)L);
     out_target[i] = fnew;
+    *val = fnew;
     if (p.role == 1) {
-      const double fold = (double)potA_cur[i];
-      return w * fabs(exp((fold - (double)fnew) / p.eps) - 1.0);
+      const float d = (in.pot - fnew) * (float)(1.0 / p.eps);
+      return (double)in.w * (double)fabsf(expm1f(d));
     }
     return 0.0;
   }
   if (p.mode == kModeLse) {
     out_target[i] = L;
+    *val = L;
     return 0.0;
   }
   // marginal
-  const double r = exp(((double)potA_cur[i] - (double)p.An[i]) / p.eps + kLn2 * (double)L);
-  if (out_target) out_target[i] = (float)r;
-  return fabs(r - w);
+  const double arg = ((double)in.pot - (double)in.an) / p.eps + kLn2 * (double)L;
+  const float r = expf((float)arg);
+  if (out_target) out_target[i] = r;
+  *val = r;
+  return fabs((double)r - (double)in.w);
 }
 
 }  // namespace progot

@@ -216,10 +216,12 @@ __global__ void __launch_bounds__(NT, 2) lse_sweep_fp32(SweepParams p) {
   if (threadIdx.x < BM) {
     const int64_t i = row0 + threadIdx.x;
     if (i < p.nA) {
+      const RowIn in = row_inputs(p, i, potA_cur);
       float2 v = make_float2(-INFINITY, 0.f);
       for (int s = 0; s < p.splits; ++s) v = lse_combine(v, __ldcg(&p.partial[(int64_t)s * p.nA + i]));
       const float L = v.x + __log2f(v.y);
-      e = row_epilogue(p, i, L, potA_cur, out_target);
+      float val;
+      e = row_epilogue(p, i, L, in, out_target, &val);
     }
   }
   const double tot = block_sum_f64<NT>(e, red);
@@ -231,11 +233,13 @@ __global__ void __launch_bounds__(NT, 2) lse_sweep_fp32(SweepParams p) {
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned prev = atomicAdd(&p.cnt[gridDim.x], 1u);
-    if (prev == gridDim.x - 1) {
-      __threadfence();
-      finish_sweep(p, gridDim.x);
-      p.cnt[gridDim.x] = 0;
-    }
+    s_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x < 32) {
+    __threadfence();
+    finish_sweep_warp(p, gridDim.x);
+    if (threadIdx.x == 0) p.cnt[gridDim.x] = 0;
   }
 }
 

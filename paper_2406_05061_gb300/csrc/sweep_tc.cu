@@ -56,7 +56,7 @@ struct TcShared {
   uint32_t tmem_base;
   int32_t abort_flag;
   int32_t s_last;
-  int32_t pad_;
+  int32_t s_fin;
   double red[4];
   float2 ms[2][128];  // (max, sum) of LSE warpgroup 1 by segment parity, merged by warpgroup 0
 };
@@ -162,7 +162,7 @@ __device__ __forceinline__ uint64_t desc_sw32(uint32_t saddr) {
 }
 
 // kind::f16 instruction descriptor: bf16 x bf16 -> fp32, K-major A and B, M x N.
-constexpr uint32_t make_idesc(int M, int N) {
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 template <int BN>
@@ -556,6 +556,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       // ---- segment done: publish the partial, last arrival combines the row block
       const int64_t i = (int64_t)sg.r * BM + row_local;
       if (i < p.nA) p.partial[((int64_t)c * tp.maxseg + k) * BM + row_local] = make_float2(m_run, s_run);
+      const float* potA_cur = p.potA_old;
+      float* out_target = p.out;
+      if (p.role == 1) {
+        potA_cur = (fcur == 0) ? p.out : p.out_alt;
+        out_target = (fcur == 0) ? p.out_alt : p.out;
+      }
+      // the row's epilogue inputs are loaded now, overlapping the arrival below
+      RowIn rin;
+      rin.an = 0.f;
+      rin.pot = 0.f;
+      rin.w = 0.f;
+      if (i < p.nA) rin = row_inputs(p, i, potA_cur);
       __threadfence();
       lse_bar();
       if (ltid == 0) {
@@ -569,23 +581,33 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         __threadfence();
         const int c_first = cta_of((int64_t)sg.r * T, W, G);
         const int c_last = cta_of((int64_t)sg.r * T + T - 1, W, G);
-        const float* potA_cur = p.potA_old;
-        float* out_target = p.out;
-        if (p.role == 1) {
-          potA_cur = (fcur == 0) ? p.out : p.out_alt;
-          out_target = (fcur == 0) ? p.out_alt : p.out;
-        }
         double e = 0.0;
         if (i < p.nA) {
+          // issue the partial loads back to back, then combine them in CTA order
+          constexpr int kMaxC = 8;
+          const int nc = c_last - c_first + 1;
+          float2 pv[kMaxC];
+#pragma unroll
+          for (int q = 0; q < kMaxC; ++q) {
+            if (q < nc) {
+              const int cc = c_first + q;
+              const int kk = sg.r - (int)(work_begin(cc, W, G) / T);
+              pv[q] = __ldcg(&p.partial[((int64_t)cc * tp.maxseg + kk) * BM + row_local]);
+            }
+          }
           float2 acc = make_float2(-INFINITY, 0.f);
-          for (int cc = c_first; cc <= c_last; ++cc) {
+#pragma unroll
+          for (int q = 0; q < kMaxC; ++q)
+            if (q < nc) acc = lse_combine(acc, pv[q]);
+          for (int cc = c_first + kMaxC; cc <= c_last; ++cc) {
             const int kk = sg.r - (int)(work_begin(cc, W, G) / T);
             acc = lse_combine(acc, __ldcg(&p.partial[((int64_t)cc * tp.maxseg + kk) * BM + row_local]));
           }
           const float Lr = acc.x + __log2f(acc.y);
-          e = row_epilogue(p, i, Lr, potA_cur, out_target);
+          float val;
+          e = row_epilogue(p, i, Lr, rin, out_target, &val);
           if (tp.bias_out != nullptr && p.mode == kModePotential)
-            write_bias_row(tp.bias_out + i * 16, (out_target[i] - p.An[i]) * p.bscale);
+            write_bias_row(tp.bias_out + i * 16, (val - rin.an) * p.bscale);
         }
         // block sum of the error terms over the 128 LSE threads, in a fixed order
 #pragma unroll
@@ -598,11 +620,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           p.cnt[sg.r] = 0;
           __threadfence();
           const unsigned prev = atomicAdd(&p.cnt[tp.R], 1u);
-          if (prev == (unsigned)(tp.R - 1)) {
-            __threadfence();
-            finish_sweep(p, tp.R);
-            p.cnt[tp.R] = 0;
-          }
+          sh.s_fin = (prev == (unsigned)(tp.R - 1));
+        }
+        lse_bar();
+        if (sh.s_fin && ltid < 32) {
+          __threadfence();
+          finish_sweep_warp(p, tp.R);
+          if (ltid == 0) p.cnt[tp.R] = 0;
         }
         lse_bar();
       }
