@@ -30,12 +30,12 @@ sys.path.insert(0, ROOT)
 from paper_2406_05061_gb300 import workloads as W  # noqa: E402
 
 WORKLOADS = {
-    # name: (generator kwargs, K, tau by precision, nominal sweeps per solve used only to
-    # convert the reference arm's oracle sweep rate into solves/s; measured on GB300
-    # with the float32 path)
+    # name: generator kwargs, K, tau by precision, and the n x m sweeps one GPU solve of
+    # this workload performs at the default precision (bf16x3, tau = 1e-4; 1062 on GB300),
+    # used only to convert the reference arm's oracle sweep rate into solves/s
     "gmm8_8192_d64": dict(gen=dict(n=8192, m=8192, d=64, seed=1, k=8), K=8, tau={"fp32": 1e-5, "bf16x3": 1e-4,
                                                                                "bf16": 1e-4},
-                          nominal_sweeps=None),
+                          nominal_sweeps=1062),
 }
 
 # Measured peaks (MEASURED_PEAKS.json when present) and the unit counts used for the
@@ -183,7 +183,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3", "bf16"])
+    ap.add_argument("--precision", default="bf16x3", choices=["fp32", "bf16x3", "bf16"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the float32 comparison solve")
     ap.add_argument("--workload", default="gmm8_8192_d64", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
@@ -238,7 +239,7 @@ def main():
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    native.profile(True)
+    native.profile(True, period=8)  # events around every 8th sweep launch
     native.launch_count(reset=True)
     if pg:
         pg.barrier()
@@ -292,6 +293,25 @@ def main():
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         e2e_total = float(t.item())
     e2e_value = args.steps * world / (e2e_total / 1e3)
+    # ------------------------------------------------ float32 path on the same workload
+    compare = None
+    if args.precision != "fp32" and not args.no_compare:
+        ws32 = native.Workspace(max(p.n, p.m, yt.shape[0]), max(p.n, p.m, yt.shape[0]), p.d, "fp32")
+        tau32 = [wl["tau"]["fp32"]] * K
+        r32 = native.progot_solve(x, y, alpha, eps, tau32, max_iter=10000, precision="fp32", workspace=ws32)
+        ms32 = []
+        for _ in range(2):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r32 = native.progot_solve(x, y, alpha, eps, tau32, max_iter=10000, precision="fp32", workspace=ws32)
+            e1.record(stream)
+            e1.synchronize()
+            ms32.append(e0.elapsed_time(e1))
+        compare = {"fp32": {"value": 1000.0 / statistics.mean(ms32), "unit": "solves/s", "tau": tau32[-1],
+                            "iters_per_step": list(r32.iters), "ms_per_step": statistics.mean(ms32)}}
+        del ws32
     # ------------------------------------------------ roofline of the dominant kernel
     peaks = load_peaks()
     sm_max_ghz = float(peaks.get("sm_max_mhz", 2070.0)) / 1e3
@@ -309,12 +329,13 @@ def main():
         peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
         bound, peak_src = "tensor", f"{peaks['source']} bf16_tflops_sustained"
     achieved = flops_pair * pairs_per_launch / (avg_ms / 1e3) / 1e12
-    sweeps_per_solve = (lse["launches"] + mp["launches"]) / args.steps
+    sweeps_per_solve = (lse["worked"] + mp["worked"]) / args.steps
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": None, "kernel": "lse_sweep_fp32" if args.precision == "fp32" else "lse_sweep_tc",
-                "launches": lse["launches"], "avg_launch_ms": avg_ms, "pairs_per_launch": pairs_per_launch,
+                "launches_timed": lse["launches"], "launches_worked": lse["worked"], "avg_launch_ms": avg_ms,
+                "pairs_per_launch": pairs_per_launch,
                 "pairs_per_sec": pairs_per_launch / (avg_ms / 1e3), "peak_source": peak_src,
-                "share_of_step": lse["ms"] / total_ms if total_ms else None}
+                "share_of_step": avg_ms * lse["worked"] / total_ms if total_ms else None}
     line = {
         "metric": "progot_solves_per_sec", "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -328,10 +349,11 @@ def main():
                 "d2h_bytes_per_step": int((p.n * p.d + K * p.m) * 4)},
         "gpu_launches": launches // args.steps * args.steps if launches else 0,
         "roofline": roofline,
-        "map_sweep": {"launches": mp["launches"], "avg_launch_ms": mp["ms"] / max(1, mp["launches"])},
+        "map_sweep": {"launches_worked": mp["worked"], "avg_launch_ms": mp["ms"] / max(1, mp["launches"])},
         "sweeps_per_solve": sweeps_per_solve,
         "clocks": clk,
         "status": res.status,
+        "other_precisions": compare,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, rows, el, thr = oracle_sweep_rate(p.x, p.y, float(eps[0]), budget_s=args.cpu_budget)

@@ -226,17 +226,20 @@ int progot_set_stall_window(int32_t iters);
 int64_t progot_launch_count(int32_t reset);
 
 /*
- * progot_profile - enable (1) or disable (0) per-kernel timing on the calling thread
- * and reset its totals. While enabled, every log-sum-exp sweep and map sweep the
- * library launches is bracketed by CUDA events recorded on the launching stream;
- * launches of a Sinkhorn loop after its stop (which return at entry) are not counted.
+ * progot_profile - enable (enable >= 1) or disable (0) per-kernel timing on the calling
+ * thread and reset its totals. While enabled, every enable-th log-sum-exp sweep and map
+ * sweep launch (all of them for enable = 1) is bracketed by CUDA events recorded on the
+ * launching stream; launches of a Sinkhorn loop after its stop (which return at entry)
+ * are not counted. Sampling keeps the events' own cost (a few microseconds per pair)
+ * out of most launches.
  * progot_profile_read - totals since the last progot_profile call for kernel 0 (the
- * row/column log-sum-exp sweep) or 1 (the map sweep): counted launches, summed
- * device time in ms, and summed point pairs (rows x columns) those launches covered.
- * Reading synchronises on the recorded events.
+ * row/column log-sum-exp sweep) or 1 (the map sweep): sampled launches, their summed
+ * device time in ms and summed point pairs (rows x columns), and the number of
+ * launches that did work (sampled or not). Reading synchronises on the recorded events.
+ * Any output pointer may be NULL.
  */
 int progot_profile(int32_t enable);
-int progot_profile_read(int32_t kernel, int64_t* launches, double* total_ms, double* pairs);
+int progot_profile_read(int32_t kernel, int64_t* sampled, double* total_ms, double* pairs, int64_t* worked);
 
 #ifdef __cplusplus
 }

@@ -38,14 +38,18 @@ struct ProfRec {
   int kind;
   double pairs;
   bool counted;
+  int64_t seq;  // sequence number of the launch among all profiled-kernel launches
 };
 struct Profiler {
   bool on = false;
+  int64_t period = 1;                   // events around every period-th launch of a kind
+  int64_t seq[kProfKinds] = {0, 0};     // launches of each kind seen while on
   std::vector<ProfRec> recs;
   std::vector<cudaEvent_t> pool;
   double ms[kProfKinds] = {0, 0};
   double pairs[kProfKinds] = {0, 0};
   int64_t launches[kProfKinds] = {0, 0};
+  int64_t worked[kProfKinds] = {0, 0};  // launches that did work, sampled or not
   cudaEvent_t get() {
     if (!pool.empty()) {
       cudaEvent_t e = pool.back();
@@ -59,10 +63,15 @@ struct Profiler {
 };
 static thread_local Profiler t_prof;
 
-static void prof_begin(ProfRec& r, cudaStream_t s) {
+// True when this launch is sampled (events recorded around it).
+static bool prof_begin(ProfRec& r, cudaStream_t s, int kind) {
+  if (!t_prof.on) return false;
+  r.seq = t_prof.seq[kind]++;
+  if (r.seq % t_prof.period != 0) return false;
   r.a = t_prof.get();
   r.b = t_prof.get();
   cudaEventRecord(r.a, s);
+  return true;
 }
 static void prof_end(ProfRec& r, cudaStream_t s, int kind, double pairs) {
   cudaEventRecord(r.b, s);
@@ -386,7 +395,7 @@ static SweepParams make_sweep(const float* A, int64_t nA, const float* B, int64_
 static int lse_sweep(const SweepParams& p, int32_t precision, cudaStream_t s, const TcOps* ops = nullptr,
                      bool a_is_x = true, const Workspace* ws = nullptr) {
   ProfRec r;
-  if (t_prof.on) prof_begin(r, s);
+  const bool rec = prof_begin(r, s, kProfLse);
   if (precision != PROGOT_FP32 && ops != nullptr && ops->on) {
     const CUtensorMap* ah = a_is_x ? &ops->xh_a : &ops->yh_a;
     const CUtensorMap* al = a_is_x ? &ops->xl_a : &ops->yl_a;
@@ -403,7 +412,8 @@ static int lse_sweep(const SweepParams& p, int32_t precision, cudaStream_t s, co
   } else {
     CK(launch_lse_sweep_fp32(p, s));
   }
-  if (t_prof.on) prof_end(r, s, kProfLse, (double)p.nA * (double)p.nB);
+  if (rec) prof_end(r, s, kProfLse, (double)p.nA * (double)p.nB);
+  if (t_prof.on && p.state == nullptr) t_prof.worked[kProfLse] += 1;
   return PROGOT_OK;
 }
 
@@ -451,7 +461,7 @@ static int sinkhorn_core(const float* x, const float* a, int64_t n, const float*
     }
     return PROGOT_OK;
   };
-  const size_t prof_first = t_prof.recs.size();
+  const int64_t prof_seq0 = t_prof.seq[kProfLse];
   const int64_t need = (int64_t)max_iter + 1;  // f-sweeps that guarantee a stop
   int64_t launched = 0;
   int chunk = 2;
@@ -486,8 +496,10 @@ static int sinkhorn_core(const float* x, const float* a, int64_t n, const float*
   }
   if (t_prof.on) {
     // sweeps f_0, g_0, ..., g_{it-1}, f_it did work; later launches returned at entry
-    const size_t working = 2 * (size_t)fin.it + 1;
-    for (size_t i = prof_first; i < t_prof.recs.size(); ++i) t_prof.recs[i].counted = (i - prof_first) < working;
+    const int64_t working = 2 * (int64_t)fin.it + 1;
+    for (ProfRec& rr : t_prof.recs)
+      if (rr.kind == kProfLse && rr.seq >= prof_seq0) rr.counted = (rr.seq - prof_seq0) < working;
+    t_prof.worked[kProfLse] += working;
   }
   if (fin.fcur == 1) CK(cudaMemcpyAsync(f_a, f_b, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
   if (iters_out) *iters_out = fin.it;
@@ -544,9 +556,10 @@ static int map_step(float* X, int64_t n, const float* y, int64_t m, int32_t d, c
   mp.bscale = (float)(kLog2e / eps);
   mp.alpha = (float)alpha;
   ProfRec r;
-  if (t_prof.on) prof_begin(r, s);
+  const bool rec = prof_begin(r, s, kProfMap);
   CK(launch_map_sweep_fp32(mp, s));
-  if (t_prof.on) prof_end(r, s, kProfMap, (double)n * (double)m);
+  if (rec) prof_end(r, s, kProfMap, (double)n * (double)m);
+  if (t_prof.on) t_prof.worked[kProfMap] += 1;
   return PROGOT_OK;
 }
 
@@ -584,20 +597,24 @@ int64_t progot_launch_count(int32_t reset) {
 int progot_profile(int32_t enable) {
   prof_collect();
   t_prof.on = enable != 0;
+  t_prof.period = enable > 1 ? enable : 1;
+  t_prof.seq[0] = t_prof.seq[1] = 0;
   for (int k = 0; k < kProfKinds; ++k) {
     t_prof.ms[k] = 0.0;
     t_prof.pairs[k] = 0.0;
     t_prof.launches[k] = 0;
+    t_prof.worked[k] = 0;
   }
   return PROGOT_OK;
 }
 
-int progot_profile_read(int32_t kernel, int64_t* launches, double* total_ms, double* pairs) {
+int progot_profile_read(int32_t kernel, int64_t* sampled, double* total_ms, double* pairs, int64_t* worked) {
   if (kernel < 0 || kernel >= kProfKinds) return fail(PROGOT_ERR_INVALID_ARG, "unknown kernel id %d", kernel);
   prof_collect();
-  if (launches) *launches = t_prof.launches[kernel];
+  if (sampled) *sampled = t_prof.launches[kernel];
   if (total_ms) *total_ms = t_prof.ms[kernel];
   if (pairs) *pairs = t_prof.pairs[kernel];
+  if (worked) *worked = t_prof.worked[kernel];
   return PROGOT_OK;
 }
 

@@ -56,7 +56,7 @@ SIGNATURES = [
     ("progot_set_stall_window", ctypes.c_int, [_I32]),
     ("progot_launch_count", ctypes.c_int64, [_I32]),
     ("progot_profile", ctypes.c_int, [_I32]),
-    ("progot_profile_read", ctypes.c_int, [_I32, _P, _P, _P]),
+    ("progot_profile_read", ctypes.c_int, [_I32, _P, _P, _P, _P]),
 ]
 
 _lib = None
@@ -321,18 +321,21 @@ def launch_count(reset: bool = False) -> int:
 KERNEL_IDS = {"lse_sweep": 0, "map_sweep": 1}
 
 
-def profile(enable: bool) -> None:
-    """Start (True) or stop (False) per-kernel CUDA-event timing inside the library."""
-    _check(lib().progot_profile(1 if enable else 0), allow_not_converged=False)
+def profile(enable, period: int = 1) -> None:
+    """Start (True; events around every period-th launch) or stop (False) per-kernel
+    CUDA-event timing inside the library."""
+    _check(lib().progot_profile(max(1, int(period)) if enable else 0), allow_not_converged=False)
 
 
 def profile_read(kernel: str) -> dict:
+    """launches/ms/pairs of the sampled launches, worked = launches that did work."""
     n = ctypes.c_int64(0)
     ms = ctypes.c_double(0.0)
     pairs = ctypes.c_double(0.0)
-    _check(lib().progot_profile_read(KERNEL_IDS[kernel], ctypes.byref(n), ctypes.byref(ms), ctypes.byref(pairs)),
-           allow_not_converged=False)
-    return dict(launches=n.value, ms=ms.value, pairs=pairs.value)
+    worked = ctypes.c_int64(0)
+    _check(lib().progot_profile_read(KERNEL_IDS[kernel], ctypes.byref(n), ctypes.byref(ms), ctypes.byref(pairs),
+                                     ctypes.byref(worked)), allow_not_converged=False)
+    return dict(launches=n.value, ms=ms.value, pairs=pairs.value, worked=worked.value)
 
 
 NOALLOC_MAX_POINTS = 65536
