@@ -419,13 +419,16 @@ static int lse_sweep(const SweepParams& p, int32_t precision, cudaStream_t s, co
 
 // Sinkhorn loop (Alg. 1) on device-resident state. f lives in {f_a, f_b} (ping-pong);
 // on return the current f is copied into f_a. Norms xn, yn must be ready.
+// ops_out (optional) receives the tensor-core operand descriptions, valid for a map
+// step on the same (x, y, eps) right after the loop (the y-side bias rows then hold g).
 static int sinkhorn_core(const float* x, const float* a, int64_t n, const float* y, const float* b, int64_t m,
                          int32_t d, double eps, double tau, int32_t max_iter, int32_t precision, float* f_a, float* f_b,
                          float* g, const float* xn, const float* yn, const Workspace& ws, int32_t* iters_out,
-                         double* err_out, cudaStream_t s) {
+                         double* err_out, cudaStream_t s, TcOps* ops_out = nullptr) {
   int rc = t_host.init();
   if (rc) return rc;
-  TcOps ops;
+  TcOps ops_local;
+  TcOps& ops = ops_out ? *ops_out : ops_local;
   rc = prep_tc(x, n, y, m, d, eps, precision, ws, &ops, s, f_a, g, xn, yn);
   if (rc) return rc;
   const int cps = ops.on ? 1 : 2;
@@ -525,13 +528,18 @@ static int sinkhorn_core(const float* x, const float* a, int64_t n, const float*
 }
 
 // One barycentric displacement X <- X + alpha (T(X) - X) (Alg. 2 / Alg. 3), in place on X.
+// The log-sum-exp pass runs on the tensor cores when `ops` describes X, Y and the y-side
+// bias rows of g at this eps; the map sweep itself normalises by its own row sums, so
+// L only has to be close to the row's log-sum-exp.
 static int map_step(float* X, int64_t n, const float* y, int64_t m, int32_t d, const float* g, const float* yn,
-                    double eps, double alpha, int32_t precision, const Workspace& ws, cudaStream_t s) {
-  SweepParams pl = make_sweep(X, n, y, m, d, nullptr, yn, eps, ws);
+                    double eps, double alpha, int32_t precision, const Workspace& ws, cudaStream_t s,
+                    const TcOps* ops = nullptr) {
+  const bool tc = ops != nullptr && ops->on;
+  SweepParams pl = make_sweep(X, n, y, m, d, nullptr, yn, eps, ws, tc ? 1 : 2);
   pl.potB = g;
   pl.out = ws.L;
   pl.mode = kModeLse;
-  int rc = lse_sweep(pl, precision, s);
+  int rc = tc ? lse_sweep(pl, precision, s, ops, true, &ws) : lse_sweep(pl, PROGOT_FP32, s);
   if (rc) return rc;
   MapParams mp;
   memset(&mp, 0, sizeof(mp));
@@ -659,7 +667,7 @@ int entropic_map_apply(const float* xq, int64_t nq, const float* y, int64_t m, i
       return fail(PROGOT_ERR_INVALID_ARG, "alpha[%d] must lie in (0, 1]", k);
   }
   Workspace ws;
-  rc = carve(nq, m, d, workspace, ws_bytes, &ws);
+  rc = carve(nq, m, d, workspace, ws_bytes, &ws, precision);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   rc = zero_counters(ws, ws_dims(nq, m, d).rbmax, s);
@@ -668,7 +676,11 @@ int entropic_map_apply(const float* xq, int64_t nq, const float* y, int64_t m, i
   CK(launch_row_sqnorm(y, m, d, ws.yn, s));
   for (int k = 0; k < K; ++k) {
     const double al = (k == K - 1) ? 1.0 : alpha[k];
-    rc = map_step(out, nq, y, m, d, g_all + (int64_t)k * m, ws.yn, eps[k], al, precision, ws, s);
+    const float* gk = g_all + (int64_t)k * m;
+    TcOps ops;
+    rc = prep_tc(out, nq, y, m, d, eps[k], precision, ws, &ops, s, nullptr, gk, nullptr, ws.yn);
+    if (rc) return rc;
+    rc = map_step(out, nq, y, m, d, gk, ws.yn, eps[k], al, precision, ws, s, &ops);
     if (rc) return rc;
   }
   return PROGOT_OK;
@@ -760,8 +772,9 @@ int progot_solve(const float* x, const float* a, int64_t n, const float* y, cons
     CK(launch_row_sqnorm(x_out, n, d, ws.xn, s));
     int32_t it = 0;
     double err = 0.0;
+    TcOps ops;
     rc = sinkhorn_core(x_out, a, n, y, b, m, d, eps[k], tau[k], max_iter, precision, ws.f0, ws.f1, gk, ws.xn, ws.yn,
-                       ws, &it, &err, s);
+                       ws, &it, &err, s, &ops);
     if (iters) iters[k] = it;
     if (errs) errs[k] = err;
     if (rc == PROGOT_ERR_NOT_CONVERGED) {
@@ -772,7 +785,7 @@ int progot_solve(const float* x, const float* a, int64_t n, const float* y, cons
     } else if (rc) {
       return rc;
     }
-    rc = map_step(x_out, n, y, m, d, gk, ws.yn, eps[k], alpha[k], precision, ws, s);
+    rc = map_step(x_out, n, y, m, d, gk, ws.yn, eps[k], alpha[k], precision, ws, s, &ops);
     if (rc) return rc;
   }
   if (f_last) CK(cudaMemcpyAsync(f_last, ws.f0, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
@@ -862,7 +875,11 @@ int progot_schedule_eps(const float* x, int64_t n, const float* y, const float* 
                        nullptr, nullptr, s);
     if (rc && rc != PROGOT_ERR_NOT_CONVERGED) return rc;
     CK(cudaMemcpyAsync(ws.T, y_test, sizeof(float) * mt * d, cudaMemcpyDeviceToDevice, s));
-    rc = map_step(ws.T, mt, y, m, d, ws.gaux, ws.yn, eps, 1.0, precision, ws, s);
+    // tensor-core operands of the held-out points against Y, with the y-side bias of g
+    TcOps ops;
+    rc = prep_tc(ws.T, mt, y, m, d, eps, precision, ws, &ops, s, nullptr, ws.gaux, nullptr, ws.yn);
+    if (rc) return rc;
+    rc = map_step(ws.T, mt, y, m, d, ws.gaux, ws.yn, eps, 1.0, precision, ws, s, &ops);
     if (rc) return rc;
     CK(launch_sq_error(y_test, ws.T, mt, d, ws.rpart, reduce_parts(), ws.rout, s));
     rc = t_host.init();

@@ -308,7 +308,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                  const __grid_constant__ CUtensorMap mapBh, const __grid_constant__ CUtensorMap mapBl,
                  const __grid_constant__ CUtensorMap mapBbias, TcParams tp) {
   const SweepParams& p = tp.p;
-  if (p.state != nullptr && p.state->done) return;
+  // Programmatic dependent launch: let the next sweep's CTAs be scheduled as soon as
+  // SMs free up; this kernel's own reads of the previous sweep's results wait below.
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -321,7 +323,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int nseg = num_segments(c, W, G, T);
   const int nkb = tp.nkb, S = tp.stages, NA = tp.a_bufs;
   volatile int32_t* abort_flag = &sh.abort_flag;
-  const int fcur = p.state ? p.state->fcur : 0;
 
   // ---------------------------------------------------------------- set-up
   if (threadIdx.x == 0) {
@@ -352,10 +353,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
+  // everything below may read results of the previous kernel in the stream
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = sh.tmem_base;
+  const bool stopped = p.state != nullptr && p.state->done;
+  const int fcur = p.state ? p.state->fcur : 0;
+  if (stopped) {
+    // the Sinkhorn loop already met its stop rule: release TMEM and leave
+    if (warp == 1) {
+      tc_fence_after();
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
+    }
+    return;
+  }
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer (whole warp, one lane issues)
@@ -742,11 +755,20 @@ static cudaError_t launch_tc(const tc::TcParams& tp, size_t smem, const void* ma
     if (e != cudaSuccess) return e;
     attr_bytes = smem;
   }
-  tc::lse_sweep_tc<BN><<<tp.G, tc::NTHREADS, smem, stream>>>(
-      *reinterpret_cast<const CUtensorMap*>(mapAh), *reinterpret_cast<const CUtensorMap*>(mapAl),
-      *reinterpret_cast<const CUtensorMap*>(mapBh), *reinterpret_cast<const CUtensorMap*>(mapBl),
-      *reinterpret_cast<const CUtensorMap*>(mapBbias), tp);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(tp.G);
+  cfg.blockDim = dim3(tc::NTHREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, tc::lse_sweep_tc<BN>, *reinterpret_cast<const CUtensorMap*>(mapAh),
+                            *reinterpret_cast<const CUtensorMap*>(mapAl), *reinterpret_cast<const CUtensorMap*>(mapBh),
+                            *reinterpret_cast<const CUtensorMap*>(mapBl),
+                            *reinterpret_cast<const CUtensorMap*>(mapBbias), tp);
 }
 
 cudaError_t launch_lse_sweep_tc(const SweepParams& p, const void* mapAh, const void* mapAl, const void* mapBh,
