@@ -257,6 +257,15 @@ __device__ __forceinline__ int num_segments(int c, int64_t W, int G, int T) {
 }
 
 // Named barriers: 1 = both LSE warpgroups (256 threads), 2 = LSE warpgroup 0 (128).
+// Arrival on a grid-wide counter with acquire-release semantics at GPU scope: orders
+// this CTA's prior writes (made visible to the calling thread by a CTA barrier) before
+// the increment, and the other arrivals' writes before this thread's later reads.
+__device__ __forceinline__ unsigned atomic_add_acq_rel_gpu(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
 __device__ __forceinline__ void lse_bar_all() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 __device__ __forceinline__ void lse_bar() { asm volatile("bar.sync 2, 128;" ::: "memory"); }
 
@@ -581,17 +590,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       rin.pot = 0.f;
       rin.w = 0.f;
       if (i < p.nA) rin = row_inputs(p, i, potA_cur);
-      __threadfence();
-      lse_bar();
+      lse_bar();  // the partial stores of all 128 rows happen before the arrival below
       if (ltid == 0) {
         const int c_first = cta_of((int64_t)sg.r * T, W, G);
         const int c_last = cta_of((int64_t)sg.r * T + T - 1, W, G);
-        const unsigned prev = atomicAdd(&p.cnt[sg.r], 1u);
+        const unsigned prev = atomic_add_acq_rel_gpu(&p.cnt[sg.r], 1u);
         sh.s_last = (prev == (unsigned)(c_last - c_first));
       }
-      lse_bar();
+      lse_bar();  // ... and the other CTAs' partials are visible after it
       if (sh.s_last) {
-        __threadfence();
         const int c_first = cta_of((int64_t)sg.r * T, W, G);
         const int c_last = cta_of((int64_t)sg.r * T + T - 1, W, G);
         double e = 0.0;
@@ -631,13 +638,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const double tot = (sh.red[0] + sh.red[1]) + (sh.red[2] + sh.red[3]);
           p.errpart[sg.r] = tot;
           p.cnt[sg.r] = 0;
-          __threadfence();
-          const unsigned prev = atomicAdd(&p.cnt[tp.R], 1u);
+          const unsigned prev = atomic_add_acq_rel_gpu(&p.cnt[tp.R], 1u);
           sh.s_fin = (prev == (unsigned)(tp.R - 1));
         }
         lse_bar();
         if (sh.s_fin && ltid < 32) {
-          __threadfence();
           finish_sweep_warp(p, tp.R);
           if (ltid == 0) p.cnt[tp.R] = 0;
         }
