@@ -179,6 +179,72 @@ int progot_solve(const float* x, const float* a, int64_t n, const float* y, cons
                  double* errs, void* workspace, size_t ws_bytes, progot_stream_t stream);
 
 /*
+ * progot_problem - one ProgOT problem for progot_solve_batched (device pointers) or
+ * for the server (host pointers). Meanings, layouts and lengths as in progot_solve;
+ * alpha, eps, tau (host, K); iters, errs (host, K, may be NULL); f_last may be NULL;
+ * status receives the problem's own return code.
+ */
+typedef struct progot_problem {
+  const float* x;
+  const float* a;
+  int64_t n;
+  const float* y;
+  const float* b;
+  int64_t m;
+  int32_t d;
+  int32_t K;
+  const double* alpha;
+  const double* eps;
+  const double* tau;
+  float* x_out;
+  float* g_all;
+  float* f_last;
+  int32_t* iters;
+  double* errs;
+  int32_t status;
+} progot_problem;
+
+/*
+ * progot_solve_batched - Alg. 2 on `count` independent problems of uneven sizes (the
+ * batched workload of many small ProgOT problems). The problems run through
+ * progot_solve on n_streams internal CUDA streams, each driven by a host worker
+ * thread, largest problems first; the internal streams wait for `stream` at entry and
+ * `stream` waits for them at exit; the call returns when every problem is done.
+ * Results are bit-identical to solving each problem alone (launch shapes depend only on
+ * a problem's sizes). workspace: at least progot_batched_workspace_size(...) bytes.
+ * Returns the first hard error of any problem, else PROGOT_ERR_NOT_CONVERGED if any
+ * problem did not reach its tau, else PROGOT_OK; per-problem codes in problems[i].status.
+ */
+size_t progot_batched_workspace_size(const progot_problem* problems, int32_t count, int32_t precision,
+                                     int32_t n_streams);
+int progot_solve_batched(progot_problem* problems, int32_t count, int32_t max_iter, int32_t precision,
+                         int32_t n_streams, void* workspace, size_t ws_bytes, progot_stream_t stream);
+
+/*
+ * Continuous-batching server. progot_server_create allocates one device arena of
+ * budget_bytes (the device-memory budget) and starts n_workers host threads, each with
+ * its own CUDA stream. progot_server_submit queues a request (host pointers, which must
+ * stay valid until progot_server_wait returns for it) and returns its id (>= 0) or a
+ * negated error code (-PROGOT_ERR_OOM when the request alone exceeds the budget).
+ * Requests are admitted in arrival order as soon as a worker is free and the request's
+ * memory (inputs, outputs, solve workspace) fits in the arena (first-fit sub-allocator);
+ * the worker copies the inputs in, runs progot_solve with the server's precision and
+ * max_iter, copies x_out, g_all (and f_last, iters, errs) back and releases the memory,
+ * so requests that arrive while others run are admitted as memory frees up and their
+ * work overlaps on the device. progot_server_wait blocks until a request finished and
+ * returns its status and its latency from submission (ms). progot_server_stats reports
+ * completed and in-flight requests and the arena's current and peak use.
+ * progot_server_destroy finishes the queued requests and frees the arena.
+ */
+typedef struct progot_server progot_server;
+progot_server* progot_server_create(size_t budget_bytes, int32_t n_workers, int32_t precision, int32_t max_iter);
+int64_t progot_server_submit(progot_server* server, const progot_problem* request);
+int progot_server_wait(progot_server* server, int64_t id, double* latency_ms);
+int progot_server_stats(progot_server* server, int64_t* completed, int64_t* in_flight, size_t* bytes_in_use,
+                        size_t* peak_bytes);
+void progot_server_destroy(progot_server* server);
+
+/*
  * progot_schedule_alpha - alpha_1..alpha_K of the step-length schedules of Sec. 4
  * (Table 7), with alpha_K = 1. Each alpha_k is the fraction of the remaining path that
  * step k covers: alpha_k = (t_k - t_{k-1}) / (1 - t_{k-1}) for the target progress

@@ -384,7 +384,9 @@ cudaError_t launch_lse_sweep_fp32(const SweepParams& p, cudaStream_t stream) {
 }
 
 cudaError_t launch_map_sweep_fp32(const MapParams& p, cudaStream_t stream) {
-  static bool attr_set = false;
+  // per-thread flag: the attribute call is cheap and idempotent, so each host thread
+  // sets it once without shared mutable state
+  static thread_local bool attr_set = false;
   const size_t smem = sizeof(MapSmem);
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(map_sweep_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -754,7 +754,7 @@ void tc_plan(int64_t nA, int64_t nB, int bn, int sms, int* G, int* maxseg) {
 template <int BN>
 static cudaError_t launch_tc(const tc::TcParams& tp, size_t smem, const void* mapAh, const void* mapAl,
                              const void* mapBh, const void* mapBl, const void* mapBbias, cudaStream_t stream) {
-  static size_t attr_bytes = 0;
+  static thread_local size_t attr_bytes = 0;  // per host thread, see launch_map_sweep_fp32
   if (smem > attr_bytes) {
     cudaError_t e = cudaFuncSetAttribute(tc::lse_sweep_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

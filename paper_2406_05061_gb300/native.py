@@ -55,6 +55,13 @@ SIGNATURES = [
      [_P, _I64, _P, _P, _I64, _P, _I64, _I32, _I32, _P, _P, _I32, _D, _D, _I32, _I32, _P, _P, _P, _P, _SZ, _P]),
     ("progot_set_stall_window", ctypes.c_int, [_I32]),
     ("progot_launch_count", ctypes.c_int64, [_I32]),
+    ("progot_batched_workspace_size", _SZ, [_P, _I32, _I32, _I32]),
+    ("progot_solve_batched", ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _P, _SZ, _P]),
+    ("progot_server_create", ctypes.c_void_p, [_SZ, _I32, _I32, _I32]),
+    ("progot_server_submit", ctypes.c_int64, [_P, _P]),
+    ("progot_server_wait", ctypes.c_int, [_P, _I64, _P]),
+    ("progot_server_stats", ctypes.c_int, [_P, _P, _P, _P, _P]),
+    ("progot_server_destroy", None, [_P]),
     ("progot_profile", ctypes.c_int, [_I32]),
     ("progot_profile_read", ctypes.c_int, [_I32, _P, _P, _P, _P]),
 ]
@@ -360,3 +367,116 @@ def coupling_marginals_noalloc(x, y, f, g, eps, a=None, b=None, precision="fp32"
                                           ctypes.byref(err), _stream(stream))
     _check(rc, allow_not_converged=False)
     return row, col, err.value
+
+
+class ProblemStruct(ctypes.Structure):
+    """ctypes mirror of progot_problem (include/progot.h)."""
+    _fields_ = [("x", _P), ("a", _P), ("n", _I64), ("y", _P), ("b", _P), ("m", _I64), ("d", _I32), ("K", _I32),
+                ("alpha", _P), ("eps", _P), ("tau", _P), ("x_out", _P), ("g_all", _P), ("f_last", _P),
+                ("iters", _P), ("errs", _P), ("status", _I32)]
+
+
+def _problem_struct(x, y, alpha, eps, tau, x_out, g_all, f_last=None, a=None, b=None, keep=None):
+    """Fill a ProblemStruct from torch CUDA tensors (batched) or numpy arrays (server)."""
+    def ptr(t):
+        if t is None:
+            return None
+        if isinstance(t, np.ndarray):
+            return t.ctypes.data_as(ctypes.c_void_p)
+        return ctypes.c_void_p(t.data_ptr())
+    K = len(eps)
+    al_h, eps_h, tau_h = _host_f64(alpha, K), _host_f64(eps, K), _host_f64(tau, K)
+    iters = np.zeros(K, dtype=np.int32)
+    errs = np.zeros(K, dtype=np.float64)
+    n, d = x.shape
+    m = y.shape[0]
+    s = ProblemStruct(ptr(x), ptr(a), n, ptr(y), ptr(b), m, d, K, _hp(al_h), _hp(eps_h), _hp(tau_h), ptr(x_out),
+                      ptr(g_all), ptr(f_last), _hp(iters), _hp(errs), 0)
+    holder = dict(al=al_h, eps=eps_h, tau=tau_h, iters=iters, errs=errs, x=x, y=y, x_out=x_out, g_all=g_all,
+                  f_last=f_last, a=a, b=b)
+    if keep is not None:
+        keep.append(holder)
+    return s, holder
+
+
+def progot_solve_batched(problems, max_iter=10000, precision="bf16x3", n_streams=8, stream=None):
+    """Solve a list of problems (dicts with x, y CUDA tensors and alpha, eps, tau) together.
+
+    Returns a list of dicts with x_out, g_all, f_last, iters, errs, status per problem."""
+    torch = _torch()
+    keep = []
+    arr = (ProblemStruct * len(problems))()
+    outs = []
+    for i, pr in enumerate(problems):
+        x, y = pr["x"], pr["y"]
+        _dev(x, "x"), _dev(y, "y")
+        K = len(pr["eps"])
+        x_out = torch.empty_like(x)
+        g_all = torch.empty((K, y.shape[0]), dtype=torch.float32, device=x.device)
+        f_last = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+        arr[i], holder = _problem_struct(x, y, pr["alpha"], pr["eps"], pr["tau"], x_out, g_all, f_last,
+                                         pr.get("a"), pr.get("b"), keep)
+        outs.append(holder)
+    L = lib()
+    pc = _prec(precision)
+    ws_bytes = int(L.progot_batched_workspace_size(arr, len(problems), pc, n_streams))
+    ws = torch.empty(ws_bytes + 256, dtype=torch.uint8, device="cuda")
+    rc = L.progot_solve_batched(arr, len(problems), int(max_iter), pc, int(n_streams), ctypes.c_void_p(ws.data_ptr()),
+                                ws_bytes + 256, _stream(stream))
+    _check(rc)
+    return [dict(x_out=h["x_out"], g_all=h["g_all"], f_last=h["f_last"], iters=h["iters"].tolist(),
+                 errs=h["errs"].tolist(), status=int(arr[i].status)) for i, h in enumerate(outs)]
+
+
+class Server:
+    """Continuous-batching ProgOT server (progot_server_* in include/progot.h)."""
+
+    def __init__(self, budget_bytes: int, n_workers: int = 8, precision="bf16x3", max_iter: int = 10000):
+        L = lib()
+        h = L.progot_server_create(int(budget_bytes), int(n_workers), _prec(precision), int(max_iter))
+        if not h:
+            raise ProgOTError(PROGOT_ERR_CUDA, last_error())
+        self._h = ctypes.c_void_p(h)
+        self._pending = {}
+
+    def submit(self, x, y, alpha, eps, tau, a=None, b=None) -> int:
+        """Queue one request on host arrays (float32, C-contiguous); returns its id."""
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        K = len(eps)
+        x_out = np.empty_like(x)
+        g_all = np.empty((K, y.shape[0]), dtype=np.float32)
+        f_last = np.empty(x.shape[0], dtype=np.float32)
+        st, holder = _problem_struct(x, y, alpha, eps, tau, x_out, g_all, f_last,
+                                     None if a is None else np.ascontiguousarray(a, dtype=np.float32),
+                                     None if b is None else np.ascontiguousarray(b, dtype=np.float32))
+        holder["struct"] = st
+        rid = int(lib().progot_server_submit(self._h, ctypes.byref(st)))
+        if rid < 0:
+            raise ProgOTError(-rid, last_error())
+        self._pending[rid] = holder
+        return rid
+
+    def wait(self, rid: int) -> dict:
+        lat = ctypes.c_double(0.0)
+        rc = int(lib().progot_server_wait(self._h, int(rid), ctypes.byref(lat)))
+        h = self._pending.pop(rid)
+        return dict(status=rc, latency_ms=lat.value, x_out=h["x_out"], g_all=h["g_all"], f_last=h["f_last"],
+                    iters=h["iters"].tolist(), errs=h["errs"].tolist())
+
+    def stats(self) -> dict:
+        c, f = ctypes.c_int64(0), ctypes.c_int64(0)
+        u, pk = ctypes.c_size_t(0), ctypes.c_size_t(0)
+        lib().progot_server_stats(self._h, ctypes.byref(c), ctypes.byref(f), ctypes.byref(u), ctypes.byref(pk))
+        return dict(completed=c.value, in_flight=f.value, bytes_in_use=u.value, peak_bytes=pk.value)
+
+    def close(self):
+        if self._h:
+            lib().progot_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

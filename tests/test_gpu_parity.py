@@ -327,3 +327,24 @@ def test_full_size_gmm64_sampled_parity_bf16x3(nat):
     T_gpu = O.entropic_map(X64[rows], Y64, g, eps)
     T_ref = O.entropic_map(X64[rows], Y64, host(fp.g), eps)
     assert map_rms_rel(T_gpu, T_ref, p.y) <= TOL_MIXED
+
+
+def test_full_size_sphere_65536_d256_sampled_parity(nat):
+    """n = m = 65536 points on the sphere in d = 256 (the large coupling workload; the
+    cost matrix would be 17 GB): one bf16x3 Sinkhorn solve, then row marginals and the
+    map on 32 sampled rows computed one by one by the oracle from the GPU's potentials."""
+    p = W.sphere_mixture_pair(65536, 65536, 256, seed=2)
+    X64, Y64 = p.x.astype(np.float64), p.y.astype(np.float64)
+    sub = np.random.default_rng(0).choice(65536, 1024, replace=False)
+    eps = O.mean_cost(X64[sub], Y64[sub]) / 20
+    x, y = dev(p.x), dev(p.y)
+    res = nat.sinkhorn_potentials(x, y, eps, 1e-4, max_iter=3000, precision="bf16x3")
+    assert res.status == nat.PROGOT_OK, nat.last_error()
+    f, g = host(res.f), host(res.g)
+    rows = np.random.default_rng(3).choice(65536, 32, replace=False)
+    Cs = O.cost_matrix_rows(X64[rows], Y64)
+    r_ref = np.exp((f[rows, None] + g[None, :] - Cs) / eps).sum(1)
+    assert np.abs(r_ref - 1.0 / 65536).sum() * 65536 / 32 <= 2 * TOL_MIXED
+    out = nat.entropic_map_apply(x, y, res.g.reshape(1, -1), [eps], [1.0], precision="bf16x3")
+    T_ref = O.entropic_map(X64[rows], Y64, g, eps)
+    assert map_rms_rel(host(out)[rows], T_ref, p.y) <= TOL_MIXED
