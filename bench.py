@@ -177,6 +177,101 @@ def run_reference(args, rank, world):
     return 0
 
 
+def closed_form_schedule(x, y, K):
+    """eps_k from 5 eps0 to sigma along t_k (Alg. 4's end points without its grid search),
+    eps0 = mean cost(X, Y)/20, sigma = mean cost(Y, Y)/20 in closed form (host float64)."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    mc = lambda u, v: float(np.mean(np.sum(u * u, 1)) + np.mean(np.sum(v * v, 1)) - 2 * u.mean(0) @ v.mean(0))
+    t = np.arange(1, K + 1) / K  # constant speed
+    return (1 - t) * 5 * mc(x, y) / 20 + t * mc(y, y) / 20
+
+
+def run_batched(args, rank, world, local):
+    """256 independent problems (n, m log-uniform in [128, 4096], d in {16, 64}), K = 8,
+    solved by one progot_solve_batched call per step."""
+    import torch
+    from paper_2406_05061_gb300 import native
+    torch.cuda.set_device(local)
+    probs = W.batched_problems(256, 128, 4096, (16, 64), seed=3)
+    K = 8
+    alpha = native.progot_schedule_alpha(K, "constant")
+    tau = [1e-4 if args.precision != "fp32" else 1e-5] * K
+    specs = [dict(x=torch.from_numpy(p.x).cuda(), y=torch.from_numpy(p.y).cuda(), alpha=alpha,
+                  eps=closed_form_schedule(p.x, p.y, K), tau=tau) for p in probs]
+    for _ in range(args.warmup):
+        native.progot_solve_batched(specs, precision=args.precision, n_streams=16)
+    torch.cuda.synchronize()
+    native.launch_count(reset=True)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        res = native.progot_solve_batched(specs, precision=args.precision, n_streams=16)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / args.steps
+    pairs = sum(p.n * p.m for p in probs)
+    line = {"metric": "batched_problems_per_sec", "value": len(probs) / dt, "unit": "problems/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": "batched256", "problems": len(probs), "K": K, "tau": tau[-1],
+                       "n_m_range": [128, 4096], "d": [16, 64], "eps": "closed-form 5 eps0 -> sigma",
+                       "streams": 16, "sum_nm": pairs},
+            "statuses": sorted(set(r["status"] for r in res)),
+            "total_iters": int(sum(sum(r["iters"]) for r in res)), "gpu_launches": native.launch_count()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serving(args, rank, world, local):
+    """Poisson request stream (mean args.rate req/s) of ProgOT solves with n, m
+    log-uniform in [256, 32768], d in {16, 64, 256}, K = 8, replayed through the server
+    with a 40 GB device budget; bf16x3 and float32 serving on the same stream."""
+    import torch
+    from paper_2406_05061_gb300 import native
+    torch.cuda.set_device(local)
+    reqs = W.poisson_requests(args.requests, args.rate, 256, 32768, (16, 64, 256), seed=4)
+    K = 8
+    alpha = native.progot_schedule_alpha(K, "constant")
+    # one point pool per dimension; request i takes its first n (resp. m) rows of a
+    # per-request rotation of the pool, so requests differ without regenerating clouds
+    pools = {d: W.gmm_pair(32768, 32768, d, seed=40 + d, k=8) for d in (16, 64, 256)}
+    data = []
+    for (t_arr, n, m, d, sub) in reqs:
+        pool = pools[d]
+        shift = sub % 32768
+        x = np.roll(pool.x, -shift, axis=0)[:n].copy()
+        y = np.roll(pool.y, -(sub // 7) % 32768, axis=0)[:m].copy()
+        data.append((t_arr, x, y, closed_form_schedule(x[:2048], y[:2048], K)))
+    out = {}
+    for prec in ("bf16x3", "fp32"):
+        tau = [1e-4 if prec != "fp32" else 1e-5] * K
+        srv = native.Server(40 << 30, n_workers=8, precision=prec, max_iter=10000)
+        t0 = time.perf_counter()
+        ids = []
+        for (t_arr, x, y, eps) in data:
+            now = time.perf_counter() - t0
+            if t_arr > now:
+                time.sleep(t_arr - now)
+            ids.append(srv.submit(x, y, alpha, eps, tau))
+        res = [srv.wait(i) for i in ids]
+        dt = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        lat = np.array([r["latency_ms"] for r in res])
+        out[prec] = {"solves_per_sec": len(res) / dt, "p50_ms": float(np.percentile(lat, 50)),
+                     "p99_ms": float(np.percentile(lat, 99)), "wall_s": dt, "peak_arena_bytes": st["peak_bytes"],
+                     "statuses": sorted(set(r["status"] for r in res)),
+                     "mean_iters": float(np.mean([sum(r["iters"]) for r in res]))}
+    line = {"metric": "served_solves_per_sec", "value": out["bf16x3"]["solves_per_sec"], "unit": "solves/s",
+            "n_gpus": 1, "higher_is_better": True, "dtype": "bf16x3", "data": "synthetic",
+            "config": {"workload": "serving", "requests": len(data), "rate_per_s": args.rate, "K": K,
+                       "n_m_range": [256, 32768], "d": [16, 64, 256], "budget_bytes": 40 << 30, "workers": 8,
+                       "eps": "closed-form 5 eps0 -> sigma"},
+            "latency_ms": {"p50": out["bf16x3"]["p50_ms"], "p99": out["bf16x3"]["p99_ms"]},
+            "by_precision": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -185,7 +280,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16x3", choices=["fp32", "bf16x3", "bf16"])
     ap.add_argument("--no-compare", action="store_true", help="skip the float32 comparison solve")
-    ap.add_argument("--workload", default="gmm8_8192_d64", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="gmm8_8192_d64", choices=sorted(WORKLOADS) + ["batched256", "serving"])
+    ap.add_argument("--requests", type=int, default=240, help="serving: requests replayed from the stream")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrival rate (requests/s)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--ref-budget", type=float, default=10.0)
@@ -193,6 +290,10 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "batched256":
+        return run_batched(args, rank, world, local)
+    if args.workload == "serving":
+        return run_serving(args, rank, world, local)
 
     import torch
     from paper_2406_05061_gb300 import native
