@@ -480,21 +480,38 @@ static int sinkhorn_core(const float* x, const float* a, int64_t n, const float*
   rc = issue(cur, (int)std::min<int64_t>(chunk, need));
   if (rc) return rc;
   SolverState fin;
+  // Chunk sizing: double until a completed chunk's state is known, then aim at the
+  // iteration count predicted from the observed linear convergence rate of the error,
+  // so that few launches after the stop return at entry.
+  bool have_prev = false;
+  SolverState prev_state;
+  int next_chunk = chunk * 2;
   for (;;) {
     bool pending = false;
     if (launched < need) {
-      chunk = std::min(chunk * 2, 64);
-      rc = issue(cur ^ 1, (int)std::min<int64_t>(chunk, need - launched));
+      rc = issue(cur ^ 1, (int)std::min<int64_t>(std::min(next_chunk, 64), need - launched));
       if (rc) return rc;
       pending = true;
     }
     CK(cudaEventSynchronize(t_host.ev[cur]));
-    if (t_host.hs[cur].done) {
-      fin = t_host.hs[cur];
+    const SolverState now = t_host.hs[cur];
+    if (now.done) {
+      fin = now;
       if (pending) CK(cudaEventSynchronize(t_host.ev[cur ^ 1]));
       break;
     }
     if (!pending) return fail(PROGOT_ERR_CUDA, "Sinkhorn loop did not stop after max_iter + 1 sweeps");
+    // iterations already queued beyond the state just read
+    const int64_t queued = launched - (int64_t)now.it - 1;
+    int64_t want = 2 * (int64_t)next_chunk;
+    if (have_prev && now.it > prev_state.it && now.err > 0.0 && prev_state.err > now.err && tau > 0.0) {
+      const double rate = std::pow(now.err / prev_state.err, 1.0 / (double)(now.it - prev_state.it));
+      const double left = std::log(tau / now.err) / std::log(rate);  // iterations still needed
+      want = (int64_t)std::ceil(left * 1.1) + 1 - queued;
+    }
+    next_chunk = (int)std::max<int64_t>(1, std::min<int64_t>(want, 64));
+    prev_state = now;
+    have_prev = true;
     cur ^= 1;
   }
   if (t_prof.on) {
