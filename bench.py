@@ -110,6 +110,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """Largest value over all ranks (the whole-job time of replicas run in lockstep);
+    identity without a process group. Uses a tensor on `device` (CUDA under NCCL,
+    CPU under gloo)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device or "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, world: int, slowest_ms: float) -> float:
+    """Units processed by all ranks per second of the slowest rank (weak scaling)."""
+    return units_per_rank * world / (slowest_ms / 1e3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -365,12 +382,8 @@ def main():
     mp = native.profile_read("map_sweep")
     native.profile(False)
     clk = clocks.stop()
-    total_ms = sum(step_ms)
-    if pg:
-        t = torch.tensor([total_ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = args.steps * world / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(step_ms), pg, dev)
+    value = whole_job_rate(args.steps, world, total_ms)
     # ------------------------------------------------ end to end from host buffers
     x_back = torch.empty((p.n, p.d), dtype=torch.float32).pin_memory()
     g_back = torch.empty((K, p.m), dtype=torch.float32).pin_memory()
@@ -388,12 +401,8 @@ def main():
         e1.record(stream)
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
-    e2e_total = sum(e2e_ms)
-    if pg:
-        t = torch.tensor([e2e_total], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = args.steps * world / (e2e_total / 1e3)
+    e2e_total = max_over_ranks(sum(e2e_ms), pg, dev)
+    e2e_value = whole_job_rate(args.steps, world, e2e_total)
     # ------------------------------------------------ float32 path on the same workload
     compare = None
     if args.precision != "fp32" and not args.no_compare:
