@@ -16,7 +16,11 @@ What it computes, in float64, step by step in the paper's order and notation:
 * Alg. 3: the progressive map applied to new points from the stored g^(k).
 * Sec. 4 "Setting step lengths" and Table 7: alpha schedules and t_k.
 * Alg. 4: the epsilon scheduler.
-* Sec. 5.2: coupling cost <P, C>, entropy E(P), marginal L1 error.
+* Sec. 5.2: coupling cost <P, C>, entropy E(P), marginal L1 error; the
+  iterate-dependent rule eps_k = theta cbar_k of the coupling experiments and the
+  linear threshold schedule tau_k of Sec. 4.
+* eq. (8): the Sinkhorn divergence D_eps(X, Y) built from the eq. (5) objective.
+* Sec. 5.3 / Prop. 3: trace and KL of the coupling diagonal against Id / n.
 
 Readings where the paper's printed formulas are garbled or silent (each one is
 also listed in the design notes):
@@ -42,6 +46,14 @@ also listed in the design notes):
 * Alg. 4: the value returned as "eps_1" is eps_K; eps_k = (1 - t_k) beta0 eps0 +
   t_k eps_K. Grid s_p = 2^-3 .. 2^3, beta0 = 5, ties broken by the smallest p.
 * eps0 and sigma: unweighted means of the cost matrices over all pairs.
+* theta rule: cbar_k is the unweighted mean of h(x_i^(k) - y_j) over all pairs,
+  divided by 20, on the cloud X^(k) that solve k transports (the input of its
+  Sinkhorn call); eps_k = theta cbar_k.
+* tau schedule: tau_k falls linearly in k from tau_1 to tau_K.
+* eq. (8) objective: OT_eps is the eq. (5) dual value at the Sinkhorn potentials;
+  eps_D = 5% of the unweighted mean of the target's intra cost C_YY.
+* Blur benchmark KL: KL(P* || P) = -log n - (1/n) sum_i log P_ii (the printed
+  "n sum_i" would not vanish at P = P* = Id / n).
 """
 from __future__ import annotations
 
@@ -57,6 +69,8 @@ __all__ = [
     "barycentric_displacement", "progot", "ProgOTResult", "progot_map",
     "alpha_schedule", "progress_times", "mean_cost", "eps_schedule",
     "coupling_cost", "coupling_entropy", "dual_objective",
+    "eps_theta_rule", "tau_schedule", "eps_divergence", "ot_value",
+    "sinkhorn_divergence", "coupling_diagonal", "diagonal_metrics",
 ]
 
 # Rows per block: the oracle never holds more than BLOCK_ELEMS doubles of an
@@ -316,36 +330,42 @@ class ProgOTResult:
     errs: list
     converged: list
     x_steps: list              # X^(1) .. X^(K) (inputs of each solve)
+    eps_used: list = field(default_factory=list)  # eps_k of each solve
 
 
 def progot(a, X, b, Y, eps_sched, alpha_sched, tau_sched, max_iter: int = 10000) -> ProgOTResult:
-    """ProgOT(a, X, b, Y, (eps_k, alpha_k, tau_k)_k) of Alg. 2, K = len(eps_sched) solves.
+    """ProgOT(a, X, b, Y, (eps_k, alpha_k, tau_k)_k) of Alg. 2, K = len(alpha_sched) solves.
 
     f = 0, g^(0) = 0; for k = 1..K: warm start (1 - alpha_k) f, (1 - alpha_k) g^(k-1);
     Sinkhorn at (eps_k, tau_k); displace X <- X - alpha_k Z. Returns the coupling
-    potentials of the last solve and the map-estimator state (g^(k), eps_k, alpha_k)."""
+    potentials of the last solve and the map-estimator state (g^(k), eps_k, alpha_k).
+
+    eps_sched is a sequence of K values, or a function (k, X^(k)) -> eps_k (k = 0..K-1)
+    evaluated on the cloud that solve k transports (the theta rule of Sec. 5.2)."""
     X = np.array(X, dtype=np.float64)
     Y = np.asarray(Y, dtype=np.float64)
-    K = len(eps_sched)
+    K = len(alpha_sched)
     n, m = X.shape[0], Y.shape[0]
     f = np.zeros(n)
     g_prev = np.zeros(m)
     g_all = np.zeros((K, m))
-    iters, errs, conv, steps = [], [], [], []
+    iters, errs, conv, steps, used = [], [], [], [], []
     x_last = X.copy()
     for k in range(K):
         alpha = float(alpha_sched[k])
+        eps = float(eps_sched(k, X) if callable(eps_sched) else eps_sched[k])
         f_init, g_init = (1.0 - alpha) * f, (1.0 - alpha) * g_prev
         steps.append(X.copy())
+        used.append(eps)
         x_last = X.copy()
-        res = sinkhorn(a, X, b, Y, float(eps_sched[k]), float(tau_sched[k]), f_init, g_init, max_iter)
+        res = sinkhorn(a, X, b, Y, eps, float(tau_sched[k]), f_init, g_init, max_iter)
         f, g_prev = res.f, res.g
         g_all[k] = res.g
         iters.append(res.iters)
         errs.append(res.err)
         conv.append(res.converged)
-        X = barycentric_displacement(X, Y, f, g_prev, float(eps_sched[k]), alpha)
-    return ProgOTResult(X, g_all, f, x_last, iters, errs, conv, steps)
+        X = barycentric_displacement(X, Y, f, g_prev, eps, alpha)
+    return ProgOTResult(X, g_all, f, x_last, iters, errs, conv, steps, used)
 
 
 # --------------------------------------------------------------------------
@@ -476,3 +496,69 @@ def dual_objective(a, X, b, Y, f, g, eps: float) -> float:
     for i0, Cb in C.row_blocks():
         mass += float(np.sum(np.exp((tensor_sum(f[i0:i0 + Cb.shape[0]], g) - Cb) / eps)))
     return float(f @ a + g @ b - eps * mass)
+
+
+# --------------------------------------------------------------------------
+# Sec. 5.2 (coupling experiments): eps_k = theta cbar_k; Sec. 4: tau_k schedule.
+# --------------------------------------------------------------------------
+def eps_theta_rule(theta: float, Y):
+    """The rule (k, X^(k)) -> theta cbar_k, cbar_k = sum_ij h(x^(k)_i - y_j) / (20 n m),
+    for ``progot``'s eps_sched."""
+    Yd = np.asarray(Y, dtype=np.float64)
+
+    def rule(k, Xk):
+        return float(theta) * mean_cost(Xk, Yd) / 20.0
+    return rule
+
+
+def tau_schedule(K: int, tau_first: float, tau_last: float) -> np.ndarray:
+    """tau_1..tau_K decreasing linearly in k from tau_first to tau_last (Sec. 4)."""
+    if K < 1:
+        raise ValueError("K >= 1")
+    if K == 1:
+        return np.array([float(tau_last)])
+    k = np.arange(K, dtype=np.float64)
+    return tau_first + (tau_last - tau_first) * k / (K - 1)
+
+
+# --------------------------------------------------------------------------
+# eq. (8): Sinkhorn divergence.
+# --------------------------------------------------------------------------
+def eps_divergence(Y) -> float:
+    """eps_D: 5% of the unweighted mean intra cost of the target cloud."""
+    return 0.05 * mean_cost(Y, Y)
+
+
+def ot_value(a, X, b, Y, eps: float, tau: float, max_iter: int = 10000):
+    """OT_eps(X, Y): the eq. (5) objective at the potentials Alg. 1 returns.
+    Returns (value, SinkhornResult)."""
+    res = sinkhorn(a, X, b, Y, eps, tau, max_iter=max_iter)
+    return dual_objective(a, X, b, Y, res.f, res.g, eps), res
+
+
+def sinkhorn_divergence(a, X, b, Y, eps: float, tau: float, max_iter: int = 10000):
+    """D_eps(X, Y) = OT_eps(X, Y) - (OT_eps(X, X) + OT_eps(Y, Y)) / 2   (eq. (8)).
+    Returns (D, (OT_xy, OT_xx, OT_yy), (iters_xy, iters_xx, iters_yy))."""
+    oxy, rxy = ot_value(a, X, b, Y, eps, tau, max_iter)
+    oxx, rxx = ot_value(a, X, a, X, eps, tau, max_iter)
+    oyy, ryy = ot_value(b, Y, b, Y, eps, tau, max_iter)
+    return oxy - 0.5 * (oxx + oyy), (oxy, oxx, oyy), (rxy.iters, rxx.iters, ryy.iters)
+
+
+# --------------------------------------------------------------------------
+# Sec. 5.3 / Prop. 3: the coupling diagonal against the identity coupling.
+# --------------------------------------------------------------------------
+def coupling_diagonal(X, Y, f, g, eps: float) -> np.ndarray:
+    """log P_ii = (f_i + g_i - h(x_i - y_i)) / eps for n = m."""
+    X = np.asarray(X, dtype=np.float64)
+    Y = np.asarray(Y, dtype=np.float64)
+    if X.shape != Y.shape:
+        raise ValueError("the diagonal needs n = m")
+    return (np.asarray(f, dtype=np.float64) + np.asarray(g, dtype=np.float64) - h(X - Y)) / eps
+
+
+def diagonal_metrics(X, Y, f, g, eps: float):
+    """(Tr(P), KL(Id/n || P)) with KL = -log n - (1/n) sum_i log P_ii."""
+    logd = coupling_diagonal(X, Y, f, g, eps)
+    n = logd.shape[0]
+    return float(np.sum(np.exp(logd))), float(-math.log(n) - np.mean(logd))
