@@ -51,7 +51,9 @@ also listed in the design notes):
   Sinkhorn call); eps_k = theta cbar_k.
 * tau schedule: tau_k falls linearly in k from tau_1 to tau_K.
 * eq. (8) objective: OT_eps is the eq. (5) dual value at the Sinkhorn potentials;
-  eps_D = 5% of the unweighted mean of the target's intra cost C_YY.
+  eps_D = 5% of the unweighted mean of the target's intra cost C_YY. The self terms
+  OT(X, X), OT(Y, Y) are solved by the symmetric (averaged) fixed point, whose
+  maximiser is the same and which converges much faster than alternating updates.
 * Blur benchmark KL: KL(P* || P) = -log n - (1/n) sum_i log P_ii (the printed
   "n sum_i" would not vanish at P = P* = Id / n).
 """
@@ -69,7 +71,7 @@ __all__ = [
     "barycentric_displacement", "progot", "ProgOTResult", "progot_map",
     "alpha_schedule", "progress_times", "mean_cost", "eps_schedule",
     "coupling_cost", "coupling_entropy", "dual_objective",
-    "eps_theta_rule", "tau_schedule", "eps_divergence", "ot_value",
+    "eps_theta_rule", "tau_schedule", "eps_divergence", "ot_value", "sinkhorn_symmetric",
     "sinkhorn_divergence", "coupling_diagonal", "diagonal_metrics",
 ]
 
@@ -529,19 +531,51 @@ def eps_divergence(Y) -> float:
     return 0.05 * mean_cost(Y, Y)
 
 
-def ot_value(a, X, b, Y, eps: float, tau: float, max_iter: int = 10000):
-    """OT_eps(X, Y): the eq. (5) objective at the potentials Alg. 1 returns.
-    Returns (value, SinkhornResult)."""
-    res = sinkhorn(a, X, b, Y, eps, tau, max_iter=max_iter)
+def sinkhorn_symmetric(a, X, eps: float, tau: float, max_iter: int = 10000) -> SinkhornResult:
+    """Self-transport Sink(a, X, a, X, eps, tau) by the symmetric fixed point: with
+    f_new = eps log a + min_eps(C - f (+) f) + f (the Alg. 1 f-update with g = f), stop
+    when ||P 1 - a||_1 <= tau for P = exp((f (+) f - C)/eps), else f <- (f + f_new) / 2.
+    The maximiser of eq. (5) for (a, X, a, X) is symmetric (f = g), so this reaches the
+    same OT value as alternating updates, in far fewer iterations. Returns g = f."""
+    X = np.asarray(X, dtype=np.float64)
+    n = X.shape[0]
+    a = _weights(a, n)
+    C = CostOperator(X, X)
+    f = np.zeros(n)
+    it = 0
+    errs = []
+    while True:
+        f_new = _update_f(C, f, f, eps, a)
+        # row sums of P at the current f: a_i exp((f_i - f_new_i) / eps)
+        err = float(np.sum(np.abs(a * np.expm1((f - f_new) / eps))))
+        errs.append(err)
+        if not math.isfinite(err):
+            return SinkhornResult(f, f.copy(), it, err, False, errs)
+        if err <= tau:
+            return SinkhornResult(f, f.copy(), it, err, True, errs)
+        if it >= max_iter:
+            return SinkhornResult(f, f.copy(), it, err, False, errs)
+        f = 0.5 * (f + f_new)
+        it += 1
+
+
+def ot_value(a, X, b, Y, eps: float, tau: float, max_iter: int = 10000, symmetric: bool = False):
+    """OT_eps(X, Y): the eq. (5) objective at the potentials Alg. 1 returns (or the
+    symmetric fixed point for a self term, Y = X, b = a). Returns (value, result)."""
+    if symmetric:
+        res = sinkhorn_symmetric(a, X, eps, tau, max_iter=max_iter)
+    else:
+        res = sinkhorn(a, X, b, Y, eps, tau, max_iter=max_iter)
     return dual_objective(a, X, b, Y, res.f, res.g, eps), res
 
 
 def sinkhorn_divergence(a, X, b, Y, eps: float, tau: float, max_iter: int = 10000):
-    """D_eps(X, Y) = OT_eps(X, Y) - (OT_eps(X, X) + OT_eps(Y, Y)) / 2   (eq. (8)).
+    """D_eps(X, Y) = OT_eps(X, Y) - (OT_eps(X, X) + OT_eps(Y, Y)) / 2   (eq. (8)), the
+    self terms by the symmetric fixed point.
     Returns (D, (OT_xy, OT_xx, OT_yy), (iters_xy, iters_xx, iters_yy))."""
     oxy, rxy = ot_value(a, X, b, Y, eps, tau, max_iter)
-    oxx, rxx = ot_value(a, X, a, X, eps, tau, max_iter)
-    oyy, ryy = ot_value(b, Y, b, Y, eps, tau, max_iter)
+    oxx, rxx = ot_value(a, X, a, X, eps, tau, max_iter, symmetric=True)
+    oyy, ryy = ot_value(b, Y, b, Y, eps, tau, max_iter, symmetric=True)
     return oxy - 0.5 * (oxx + oyy), (oxy, oxx, oyy), (rxy.iters, rxx.iters, ryy.iters)
 
 

@@ -169,3 +169,26 @@ def test_coupling_diagonal_matches_rows_of_p():
     for i in range(n):
         c = sum((X[i, k] - Y[i, k]) ** 2 for k in range(2))
         assert logd[i] == pytest.approx((f[i] + g[i] - c) / eps, rel=1e-13)
+
+
+def test_symmetric_self_transport_matches_alternating_sinkhorn():
+    # the symmetric fixed point and plain Alg. 1 reach the same maximiser of eq. (5):
+    # equal OT values, symmetric potentials satisfying the f-update, marginals = a
+    rng = _rng(25)
+    X = rng.normal(size=(14, 3))
+    a = rng.uniform(0.5, 1.5, 14)
+    a /= a.sum()
+    eps = 0.8
+    sym = O.sinkhorn_symmetric(a, X, eps, 1e-12)
+    alt = O.sinkhorn(a, X, a, X, eps, 1e-12, max_iter=200000)
+    assert sym.converged and alt.converged and sym.iters < alt.iters
+    v_sym = O.dual_objective(a, X, a, X, sym.f, sym.g, eps)
+    v_alt = O.dual_objective(a, X, a, X, alt.f, alt.g, eps)
+    assert v_sym == pytest.approx(v_alt, rel=1e-10)
+    C = O.CostOperator(X, X)
+    np.testing.assert_allclose(O.row_marginal(C, sym.f, sym.f, eps), a, atol=1e-12)
+    np.testing.assert_allclose(O.col_marginal(C, sym.f, sym.f, eps), a, atol=1e-12)
+    # potentials are unique up to (f + k, g - k); the symmetric one has k = 0
+    kappa = np.mean(alt.f - sym.f)
+    np.testing.assert_allclose(alt.f - kappa, sym.f, atol=1e-9)
+    np.testing.assert_allclose(alt.g + kappa, sym.f, atol=1e-9)
