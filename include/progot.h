@@ -280,6 +280,88 @@ int progot_schedule_eps(const float* x, int64_t n, const float* y, const float* 
                         progot_stream_t stream);
 
 /*
+ * progot_schedule_tau - the Sinkhorn threshold schedule of Sec. 4 ("Setting threshold
+ * schedule"): tau_k falls linearly in k from tau_first (k = 1) to tau_last (k = K), so
+ * early solves stop loose and the last one meets tau_last. K = 1 gives tau_last.
+ * tau_first, tau_last >= 0. out (host, K).
+ */
+int progot_schedule_tau(int32_t K, double tau_first, double tau_last, double* out);
+
+/*
+ * progot_solve_theta - Alg. 2 with the iterate-dependent regularisation of the coupling
+ * experiments (Sec. 5.2 and the experiment details of the appendix): solve k uses
+ * eps_k = theta cbar_k, where cbar_k = sum_ij ||x^(k)_i - y_j||^2 / (20 n m) is the mean
+ * cost of the cloud X^(k) that solve k transports (X^(1) = X), divided by 20. cbar_k is
+ * computed on the device in closed form from float64 first moments before each solve.
+ * theta > 0 (the paper's default 2^-4). eps_out (host, K, required) receives eps_k (the
+ * map estimator of Alg. 3 needs them). Every other argument, output and return code is
+ * that of progot_solve. Synchronises the stream once per step (eps_k is a host scalar
+ * of the sweeps).
+ */
+int progot_solve_theta(const float* x, const float* a, int64_t n, const float* y, const float* b, int64_t m,
+                       int32_t d, int32_t K, const double* alpha, double theta, const double* tau, int32_t max_iter,
+                       int32_t precision, float* x_out, float* g_all, float* f_last, float* x_last, int32_t* iters,
+                       double* errs, double* eps_out, void* workspace, size_t ws_bytes, progot_stream_t stream);
+
+/*
+ * Coupling metrics of Sec. 5.2 for P_ij = exp((f_i + g_j - ||x_i - y_j||^2) / eps):
+ *   transport_cost = <P, C> = sum_ij P_ij ||x_i - y_j||^2
+ *   entropy        = E(P) = -sum_ij P_ij (log P_ij - 1)
+ *   dual           = <f, a> + <g, b> - eps sum_ij P_ij   (the objective of eq. (5))
+ *   mass           = sum_ij P_ij
+ *   err_row        = ||P 1 - a||_1,  err_col = ||P^T 1 - b||_1
+ */
+typedef struct progot_coupling_metrics {
+  double transport_cost;
+  double entropy;
+  double dual;
+  double mass;
+  double err_row;
+  double err_col;
+} progot_coupling_metrics;
+
+/*
+ * coupling_metrics - the metrics above from two float32 CUDA-core sweeps (one over rows,
+ * one over columns) that never store P. The row sweep carries, besides the row
+ * log-sum-exp, the 2^t-weighted mean of t_ij (t_ij = log2 of the row's terms), which
+ * gives sum_j P_ij log P_ij per row; then <P, C> = <f, P 1> + <g, P^T 1> - eps
+ * sum P log P. All reductions are float64 in a fixed order (deterministic).
+ * x (device, n x d), y (device, m x d), f (device, n), g (device, m), a, b (device or
+ * NULL = uniform). out (host). workspace: progot_workspace_size(n, m, d, PROGOT_FP32).
+ * Synchronises the stream.
+ */
+int coupling_metrics(const float* x, const float* a, int64_t n, const float* y, const float* b, int64_t m, int32_t d,
+                     const float* f, const float* g, double eps, progot_coupling_metrics* out, void* workspace,
+                     size_t ws_bytes, progot_stream_t stream);
+
+/*
+ * sinkhorn_divergence - the Sinkhorn divergence of eq. (8):
+ *   D_eps(X, Y) = OT_eps(X, Y) - (OT_eps(X, X) + OT_eps(Y, Y)) / 2,
+ * where OT_eps is the eq. (5) objective at the potentials of a Sinkhorn solve (Alg. 1,
+ * zero start, threshold tau, at most max_iter iterations, given precision) and is
+ * evaluated by coupling_metrics. The paper takes eps = 5% of the target's mean intra cost
+ * (0.05 x progot_mean_cost(y, y)). value (host); ot_parts (host, 3, may be NULL):
+ * OT(X, Y), OT(X, X), OT(Y, Y); iters (host, 3, may be NULL). workspace:
+ * progot_workspace_size(max(n, m), max(n, m), d, precision). Returns
+ * PROGOT_ERR_NOT_CONVERGED if a solve missed tau (value still written).
+ */
+int sinkhorn_divergence(const float* x, const float* a, int64_t n, const float* y, const float* b, int64_t m,
+                        int32_t d, double eps, double tau, int32_t max_iter, int32_t precision, double* value,
+                        double* ot_parts, int32_t* iters, void* workspace, size_t ws_bytes, progot_stream_t stream);
+
+/*
+ * coupling_diagonal - the identity-coupling check of Sec. 5.3 / Prop. 3 for n = m
+ * (point i of Y is the image of point i of X): log P_ii = (f_i + g_i - ||x_i - y_i||^2)
+ * / eps, trace = sum_i P_ii and kl = KL(Id/n || P) = -log n - (1/n) sum_i log P_ii
+ * (float64 sums, fixed order). log_diag (device, n, may be NULL) receives log P_ii.
+ * trace, kl (host, may be NULL). workspace: progot_workspace_size(n, n, d, PROGOT_FP32).
+ * Synchronises the stream.
+ */
+int coupling_diagonal(const float* x, const float* y, int64_t n, int32_t d, const float* f, const float* g, double eps,
+                      float* log_diag, double* trace, double* kl, void* workspace, size_t ws_bytes,
+                      progot_stream_t stream);
+
+/*
  * progot_set_stall_window - Sinkhorn stops with PROGOT_ERR_NOT_CONVERGED when its
  * marginal error has not fallen below 0.99 x its best value for `iters` consecutive
  * iterations (float32 potentials reach a rounding floor). 0 disables the check.

@@ -1,7 +1,7 @@
 // Small O((n + m) d) kernels: squared norms (float64 accumulation), potential scaling
 // for the warm start of Alg. 2, state initialisation, and deterministic float64
-// reductions (first moments for the closed-form mean cost of Alg. 4, squared error
-// for the Alg. 4 score).
+// reductions (first moments for the closed-form mean cost of Alg. 4 and of the theta
+// rule, squared error for the Alg. 4 score, the coupling diagonal of Prop. 3).
 #include "progot_internal.h"
 
 namespace progot {
@@ -96,6 +96,62 @@ __global__ void sq_error_pass1(const float* __restrict__ A, const float* __restr
   }
 }
 
+// Pass 1 of the coupling diagonal (n = m): log P_ii = (f_i + g_i - |x_i - y_i|^2) / eps
+// with the squared distance summed in float64 from the differences; block b sums
+// P_ii and log P_ii over rows b, b + parts, ... (one warp per row).
+__global__ void diag_pass1(const float* __restrict__ X, const float* __restrict__ Y, const float* __restrict__ f,
+                           const float* __restrict__ g, int64_t n, int32_t d, double inv_eps,
+                           float* __restrict__ logd, double* __restrict__ partial) {
+  __shared__ double red[2][32];
+  const int warps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double sp = 0.0, sl = 0.0;
+  for (int64_t row = (int64_t)blockIdx.x * warps + warp; row < n; row += (int64_t)gridDim.x * warps) {
+    const float* x = X + row * (int64_t)d;
+    const float* y = Y + row * (int64_t)d;
+    double c = 0.0;
+    for (int k = lane; k < d; k += 32) {
+      const double v = (double)x[k] - (double)y[k];
+      c += v * v;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+    if (lane == 0) {
+      const double lp = ((double)f[row] + (double)g[row] - c) * inv_eps;
+      if (logd) logd[row] = (float)lp;
+      sp += exp(lp);
+      sl += lp;
+    }
+  }
+  if (lane == 0) {
+    red[0][warp] = sp;
+    red[1][warp] = sl;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    double t = 0.0;
+    for (int w = 0; w < warps; ++w) t += red[threadIdx.x][w];
+    partial[(int64_t)blockIdx.x * 2 + threadIdx.x] = t;
+  }
+}
+
+// Closed-form mean cost over all pairs from first moments (exact for h = |.|^2):
+// mean |x|^2 + mean |y|^2 - 2 xbar . ybar, with mx = (sum |x_i|^2, sum x_i), my likewise.
+__global__ void mean_cost_closed(const double* __restrict__ mx, const double* __restrict__ my, int64_t n, int64_t m,
+                                 int32_t d, double* __restrict__ out) {
+  __shared__ double red[32];
+  double dot = 0.0;
+  for (int k = threadIdx.x; k < d; k += blockDim.x) dot += (mx[1 + k] / (double)n) * (my[1 + k] / (double)m);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dot;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    *out = mx[0] / (double)n + my[0] / (double)m - 2.0 * t;
+  }
+}
+
 cudaError_t launch_row_sqnorm(const float* X, int64_t n, int32_t d, float* out, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int rows_per_block = 8;
@@ -138,6 +194,28 @@ cudaError_t launch_sq_error(const float* A, const float* B, int64_t n, int32_t d
   sq_error_pass1<<<parts, 256, 0, s>>>(A, B, n, d, partial);
   count_launch();
   sum_parts<<<1, 32, 0, s>>>(partial, parts, 1, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag(const float* X, const float* Y, const float* f, const float* g, int64_t n, int32_t d, double eps,
+                        float* logd, double* partial, int parts, double* out, cudaStream_t s) {
+  diag_pass1<<<parts, 256, 0, s>>>(X, Y, f, g, n, d, 1.0 / eps, logd, partial);
+  count_launch();
+  sum_parts<<<1, 32, 0, s>>>(partial, parts, 2, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mean_cost_closed(const double* mx, const double* my, int64_t n, int64_t m, int32_t d, double* out,
+                                    cudaStream_t s) {
+  mean_cost_closed<<<1, 256, 0, s>>>(mx, my, n, m, d, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum_parts(const double* partial, int parts, int width, double* out, cudaStream_t s) {
+  sum_parts<<<1, 32, 0, s>>>(partial, parts, width, out);
   count_launch();
   return cudaGetLastError();
 }

@@ -153,6 +153,9 @@ struct Workspace {
   float* L;         // nmax
   float* T;         // nmax * d
   float2* partial;  // partial_elems
+  float* wpart;     // partial_elems (tilted sums of the coupling-metrics sweep)
+  double* metpart;  // kMetricSums * (rbmax + 2)
+  double* metout;   // 2 * kMetricSums + 2: reduced metric sums (row sweep, column sweep), mean cost
   double* errpart;  // rbmax + 2
   unsigned* cnt;    // rbmax + 2
   unsigned* mcnt;   // rbmax + 2
@@ -217,6 +220,9 @@ static size_t ws_layout(const WsDims& w, Workspace* out, char* base) {
   ws.L = (float*)take(sizeof(float) * w.nmax);
   ws.T = (float*)take(sizeof(float) * w.nmax * (size_t)w.d);
   ws.partial = (float2*)take(sizeof(float2) * w.partial_elems);
+  ws.wpart = (float*)take(sizeof(float) * w.partial_elems);
+  ws.metpart = (double*)take(sizeof(double) * kMetricSums * (w.rbmax + 2));
+  ws.metout = (double*)take(sizeof(double) * (2 * kMetricSums + 2));
   ws.errpart = (double*)take(sizeof(double) * (w.rbmax + 2));
   ws.cnt = (unsigned*)take(sizeof(unsigned) * (w.rbmax + 2));
   ws.mcnt = (unsigned*)take(sizeof(unsigned) * (w.rbmax + 2));
@@ -384,6 +390,8 @@ static SweepParams make_sweep(const float* A, int64_t nA, const float* B, int64_
   p.inv_nA = 1.0 / (double)nA;
   p.log_w_uniform = std::log(1.0 / (double)nA);
   p.partial = ws.partial;
+  p.wpart = ws.wpart;
+  p.metpart = ws.metpart;
   p.errpart = ws.errpart;
   p.cnt = ws.cnt;
   p.stall_window = g_stall_window.load();
@@ -421,26 +429,31 @@ static int lse_sweep(const SweepParams& p, int32_t precision, cudaStream_t s, co
 // on return the current f is copied into f_a. Norms xn, yn must be ready.
 // ops_out (optional) receives the tensor-core operand descriptions, valid for a map
 // step on the same (x, y, eps) right after the loop (the y-side bias rows then hold g).
+// symmetric: self-transport (y = x, b = a) by the averaged fixed point
+// f <- (f + f_new) / 2 with one sweep per iteration (potB = f); the symmetric coupling
+// P_ij = exp((f_i + f_j - C_ij)/eps) then has both marginals equal, and on return g
+// (when not NULL) receives f.
 static int sinkhorn_core(const float* x, const float* a, int64_t n, const float* y, const float* b, int64_t m,
                          int32_t d, double eps, double tau, int32_t max_iter, int32_t precision, float* f_a, float* f_b,
                          float* g, const float* xn, const float* yn, const Workspace& ws, int32_t* iters_out,
-                         double* err_out, cudaStream_t s, TcOps* ops_out = nullptr) {
+                         double* err_out, cudaStream_t s, TcOps* ops_out = nullptr, bool symmetric = false) {
   int rc = t_host.init();
   if (rc) return rc;
   TcOps ops_local;
   TcOps& ops = ops_out ? *ops_out : ops_local;
-  rc = prep_tc(x, n, y, m, d, eps, precision, ws, &ops, s, f_a, g, xn, yn);
+  rc = prep_tc(x, n, y, m, d, eps, precision, ws, &ops, s, f_a, symmetric ? f_a : g, xn, yn);
   if (rc) return rc;
   const int cps = ops.on ? 1 : 2;
   if (ops.on) CK(cudaMemsetAsync(ws.fault, 0, sizeof(int32_t), s));
   CK(launch_init_state(ws.state, s));
   SweepParams pf = make_sweep(x, n, y, m, d, xn, yn, eps, ws, cps);
   pf.wA = a;
-  pf.potB = g;
+  pf.potB = symmetric ? f_a : g;
+  pf.potB_alt = symmetric ? f_b : nullptr;
   pf.out = f_a;
   pf.out_alt = f_b;
   pf.mode = kModePotential;
-  pf.role = 1;
+  pf.role = symmetric ? 3 : 1;
   pf.state = ws.state;
   pf.tau = tau;
   pf.max_iter = max_iter;
@@ -455,8 +468,18 @@ static int sinkhorn_core(const float* x, const float* a, int64_t n, const float*
   pg.tau = tau;
   pg.max_iter = max_iter;
 
+  int64_t sym_sweeps = 0;
   auto enqueue = [&](int iters) -> int {
     for (int i = 0; i < iters; ++i) {
+      if (symmetric) {
+        // alternate the operand roles so that the tensor-core sweep reads the bias rows
+        // of the current f from one side's buffer while it writes the next f's rows
+        // into the other side's buffer (x and y are the same cloud)
+        int r = lse_sweep(pf, precision, s, &ops, (sym_sweeps & 1) == 0, &ws);
+        if (r) return r;
+        ++sym_sweeps;
+        continue;
+      }
       int r = lse_sweep(pf, precision, s, &ops, true, &ws);
       if (r) return r;
       r = lse_sweep(pg, precision, s, &ops, false, &ws);
@@ -515,13 +538,15 @@ static int sinkhorn_core(const float* x, const float* a, int64_t n, const float*
     cur ^= 1;
   }
   if (t_prof.on) {
-    // sweeps f_0, g_0, ..., g_{it-1}, f_it did work; later launches returned at entry
-    const int64_t working = 2 * (int64_t)fin.it + 1;
+    // sweeps f_0, g_0, ..., g_{it-1}, f_it did work (f_0 .. f_it when symmetric); later
+    // launches returned at entry
+    const int64_t working = (symmetric ? 1 : 2) * (int64_t)fin.it + 1;
     for (ProfRec& rr : t_prof.recs)
       if (rr.kind == kProfLse && rr.seq >= prof_seq0) rr.counted = (rr.seq - prof_seq0) < working;
     t_prof.worked[kProfLse] += working;
   }
   if (fin.fcur == 1) CK(cudaMemcpyAsync(f_a, f_b, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+  if (symmetric && g != nullptr) CK(cudaMemcpyAsync(g, f_a, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
   if (iters_out) *iters_out = fin.it;
   if (err_out) *err_out = fin.err;
   if (ops.on) {
@@ -591,6 +616,132 @@ static int map_step(float* X, int64_t n, const float* y, int64_t m, int32_t d, c
 static int zero_counters(const Workspace& ws, int64_t rbmax, cudaStream_t s) {
   CK(cudaMemsetAsync(ws.cnt, 0, sizeof(unsigned) * (rbmax + 2), s));
   CK(cudaMemsetAsync(ws.mcnt, 0, sizeof(unsigned) * (rbmax + 2), s));
+  return PROGOT_OK;
+}
+
+// Coupling metrics (Sec. 5.2) of P = exp((f (+) g - C)/eps): a row sweep and a column
+// sweep in kModeMetrics, each followed by a fixed-order float64 reduction of its
+// per-row-block sums into ws.metout. ws.xn, ws.yn must hold |x|^2 and |y|^2 and the
+// arrival counters must be zero.
+static int metrics_core(const float* x, const float* a, int64_t n, const float* y, const float* b, int64_t m,
+                        int32_t d, const float* f, const float* g, double eps, const Workspace& ws, cudaStream_t s,
+                        progot_coupling_metrics* out) {
+  int rc = t_host.init();
+  if (rc) return rc;
+  SweepParams pr = make_sweep(x, n, y, m, d, ws.xn, ws.yn, eps, ws);
+  pr.wA = a;
+  pr.potB = g;
+  pr.potA_old = f;
+  pr.mode = kModeMetrics;
+  CK(launch_lse_sweep_fp32(pr, s));
+  CK(launch_sum_parts(ws.metpart, (int)cdiv(n, fp32_tile_rows()), kMetricSums, ws.metout, s));
+  SweepParams pc = make_sweep(y, m, x, n, d, ws.yn, ws.xn, eps, ws);
+  pc.wA = b;
+  pc.potB = f;
+  pc.potA_old = g;
+  pc.mode = kModeMetrics;
+  CK(launch_lse_sweep_fp32(pc, s));
+  CK(launch_sum_parts(ws.metpart, (int)cdiv(m, fp32_tile_rows()), kMetricSums, ws.metout + kMetricSums, s));
+  CK(cudaMemcpyAsync(t_host.hd, ws.metout, sizeof(double) * 2 * kMetricSums, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const double* R = t_host.hd;                // row sweep: pot = f, w = a
+  const double* Cs = t_host.hd + kMetricSums;  // column sweep: pot = g, w = b
+  out->mass = R[kSumMass];
+  out->err_row = R[kSumErr];
+  out->err_col = Cs[kSumErr];
+  out->entropy = R[kSumMass] - R[kSumPlogP];
+  out->transport_cost = R[kSumPotR] + Cs[kSumPotR] - eps * R[kSumPlogP];
+  out->dual = R[kSumPotW] + Cs[kSumPotW] - eps * R[kSumMass];
+  if (!std::isfinite(out->transport_cost) || !std::isfinite(out->entropy) || !std::isfinite(out->dual))
+    return fail(PROGOT_ERR_NUMERIC, "non-finite coupling metric");
+  return PROGOT_OK;
+}
+
+// Mean cost of (x, y) in closed form from float64 first moments, computed on the device;
+// the y moments must already sit at ws.rout + (d + 1) when y_ready.
+static int mean_cost_dev(const float* x, int64_t n, const float* y, int64_t m, int32_t d, const Workspace& ws,
+                         bool y_ready, cudaStream_t s, double* out) {
+  int rc = t_host.init();
+  if (rc) return rc;
+  CK(launch_moments(x, n, d, ws.rpart, reduce_parts(), ws.rout, s));
+  if (!y_ready) CK(launch_moments(y, m, d, ws.rpart, reduce_parts(), ws.rout + (d + 1), s));
+  double* dst = ws.metout + 2 * kMetricSums;
+  CK(launch_mean_cost_closed(ws.rout, ws.rout + (d + 1), n, m, d, dst, s));
+  CK(cudaMemcpyAsync(t_host.hd, dst, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  *out = t_host.hd[0];
+  return PROGOT_OK;
+}
+
+// Alg. 2 with eps_k from `eps` (host, K) or, when eps is NULL, from the theta rule
+// eps_k = theta mean cost(X^(k), Y) / 20 on the cloud each solve transports.
+static int solve_impl(const float* x, const float* a, int64_t n, const float* y, const float* b, int64_t m, int32_t d,
+                      int32_t K, const double* alpha, const double* eps, double theta, const double* tau,
+                      int32_t max_iter, int32_t precision, float* x_out, float* g_all, float* f_last, float* x_last,
+                      int32_t* iters, double* errs, double* eps_out, void* workspace, size_t ws_bytes,
+                      cudaStream_t s) {
+  Workspace ws;
+  int rc = carve(n, m, d, workspace, ws_bytes, &ws, precision);
+  if (rc) return rc;
+  rc = zero_counters(ws, ws_dims(n, m, d).rbmax, s);
+  if (rc) return rc;
+  if (x_out != x) CK(cudaMemcpyAsync(x_out, x, sizeof(float) * n * d, cudaMemcpyDeviceToDevice, s));
+  CK(launch_row_sqnorm(y, m, d, ws.yn, s));
+  CK(cudaMemsetAsync(ws.f0, 0, sizeof(float) * n, s));
+  if (eps == nullptr) CK(launch_moments(y, m, d, ws.rpart, reduce_parts(), ws.rout + (d + 1), s));
+  int worst = PROGOT_OK;
+  std::string worst_msg;
+  for (int k = 0; k < K; ++k) {
+    float* gk = g_all + (int64_t)k * m;
+    if (k == 0) {
+      CK(cudaMemsetAsync(gk, 0, sizeof(float) * m, s));
+    } else {
+      // warm start of Alg. 2: (1 - alpha_k) f, (1 - alpha_k) g^(k-1)
+      const float c = (float)(1.0 - alpha[k]);
+      CK(cudaMemcpyAsync(gk, gk - m, sizeof(float) * m, cudaMemcpyDeviceToDevice, s));
+      CK(launch_scale(gk, m, c, s));
+      CK(launch_scale(ws.f0, n, c, s));
+    }
+    if (x_last != nullptr && k == K - 1)
+      CK(cudaMemcpyAsync(x_last, x_out, sizeof(float) * n * d, cudaMemcpyDeviceToDevice, s));
+    double eps_k = 0.0;
+    if (eps != nullptr) {
+      eps_k = eps[k];
+    } else {
+      double cbar = 0.0;
+      rc = mean_cost_dev(x_out, n, y, m, d, ws, true, s, &cbar);
+      if (rc) return rc;
+      eps_k = theta * cbar / 20.0;
+      if (!(eps_k > 0.0) || !std::isfinite(eps_k))
+        return fail(PROGOT_ERR_NUMERIC, "step %d: theta rule gave eps = %g (mean cost %g)", k + 1, eps_k, cbar);
+    }
+    if (eps_out) eps_out[k] = eps_k;
+    CK(launch_row_sqnorm(x_out, n, d, ws.xn, s));
+    int32_t it = 0;
+    double err = 0.0;
+    TcOps ops;
+    rc = sinkhorn_core(x_out, a, n, y, b, m, d, eps_k, tau[k], max_iter, precision, ws.f0, ws.f1, gk, ws.xn, ws.yn,
+                       ws, &it, &err, s, &ops);
+    if (iters) iters[k] = it;
+    if (errs) errs[k] = err;
+    if (rc == PROGOT_ERR_NOT_CONVERGED) {
+      if (worst == PROGOT_OK) {
+        worst = rc;
+        worst_msg = "step " + std::to_string(k + 1) + ": " + t_last_error;
+      }
+    } else if (rc) {
+      return rc;
+    }
+    rc = map_step(x_out, n, y, m, d, gk, ws.yn, eps_k, alpha[k], precision, ws, s, &ops);
+    if (rc) return rc;
+  }
+  if (f_last) CK(cudaMemcpyAsync(f_last, ws.f0, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  if (worst) {
+    t_last_error = worst_msg;
+    return worst;
+  }
+  t_last_error.clear();
   return PROGOT_OK;
 }
 
@@ -762,56 +913,145 @@ int progot_solve(const float* x, const float* a, int64_t n, const float* y, cons
     if (!(alpha[k] > 0.0 && alpha[k] <= 1.0)) return fail(PROGOT_ERR_INVALID_ARG, "alpha[%d] must lie in (0, 1]", k);
     if (!(tau[k] >= 0.0)) return fail(PROGOT_ERR_INVALID_ARG, "tau[%d] must be >= 0", k);
   }
+  return solve_impl(x, a, n, y, b, m, d, K, alpha, eps, 0.0, tau, max_iter, precision, x_out, g_all, f_last, x_last,
+                    iters, errs, nullptr, workspace, ws_bytes, (cudaStream_t)stream);
+}
+
+int progot_solve_theta(const float* x, const float* a, int64_t n, const float* y, const float* b, int64_t m,
+                       int32_t d, int32_t K, const double* alpha, double theta, const double* tau, int32_t max_iter,
+                       int32_t precision, float* x_out, float* g_all, float* f_last, float* x_last, int32_t* iters,
+                       double* errs, double* eps_out, void* workspace, size_t ws_bytes, progot_stream_t stream) {
+  t_last_error.clear();
+  int rc = check_common(x, n, y, m, d, precision);
+  if (rc) return rc;
+  if (K <= 0 || alpha == nullptr || tau == nullptr || x_out == nullptr || g_all == nullptr || eps_out == nullptr)
+    return fail(PROGOT_ERR_INVALID_ARG, "K > 0 and non-NULL alpha, tau, x_out, g_all, eps_out are required");
+  if (!(theta > 0.0) || !std::isfinite(theta)) return fail(PROGOT_ERR_INVALID_ARG, "theta must be positive and finite");
+  if (max_iter < 0) return fail(PROGOT_ERR_INVALID_ARG, "max_iter must be >= 0");
+  for (int k = 0; k < K; ++k) {
+    if (!(alpha[k] > 0.0 && alpha[k] <= 1.0)) return fail(PROGOT_ERR_INVALID_ARG, "alpha[%d] must lie in (0, 1]", k);
+    if (!(tau[k] >= 0.0)) return fail(PROGOT_ERR_INVALID_ARG, "tau[%d] must be >= 0", k);
+  }
+  return solve_impl(x, a, n, y, b, m, d, K, alpha, nullptr, theta, tau, max_iter, precision, x_out, g_all, f_last,
+                    x_last, iters, errs, eps_out, workspace, ws_bytes, (cudaStream_t)stream);
+}
+
+int progot_schedule_tau(int32_t K, double tau_first, double tau_last, double* out) {
+  t_last_error.clear();
+  if (K <= 0 || out == nullptr) return fail(PROGOT_ERR_INVALID_ARG, "K > 0 and out required");
+  if (!(tau_first >= 0.0) || !(tau_last >= 0.0) || !std::isfinite(tau_first) || !std::isfinite(tau_last))
+    return fail(PROGOT_ERR_INVALID_ARG, "tau_first and tau_last must be finite and >= 0");
+  if (K == 1) {
+    out[0] = tau_last;
+    return PROGOT_OK;
+  }
+  for (int k = 0; k < K; ++k) out[k] = tau_first + (tau_last - tau_first) * (double)k / (double)(K - 1);
+  out[K - 1] = tau_last;
+  return PROGOT_OK;
+}
+
+int coupling_metrics(const float* x, const float* a, int64_t n, const float* y, const float* b, int64_t m, int32_t d,
+                     const float* f, const float* g, double eps, progot_coupling_metrics* out, void* workspace,
+                     size_t ws_bytes, progot_stream_t stream) {
+  t_last_error.clear();
+  int rc = check_common(x, n, y, m, d, PROGOT_FP32);
+  if (rc) return rc;
+  if (f == nullptr || g == nullptr || out == nullptr)
+    return fail(PROGOT_ERR_INVALID_ARG, "f, g and out must not be NULL");
+  if (!(eps > 0.0) || !std::isfinite(eps)) return fail(PROGOT_ERR_INVALID_ARG, "eps must be positive and finite");
   Workspace ws;
-  rc = carve(n, m, d, workspace, ws_bytes, &ws, precision);
+  rc = carve(n, m, d, workspace, ws_bytes, &ws);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   rc = zero_counters(ws, ws_dims(n, m, d).rbmax, s);
   if (rc) return rc;
-  if (x_out != x) CK(cudaMemcpyAsync(x_out, x, sizeof(float) * n * d, cudaMemcpyDeviceToDevice, s));
+  CK(launch_row_sqnorm(x, n, d, ws.xn, s));
   CK(launch_row_sqnorm(y, m, d, ws.yn, s));
-  CK(cudaMemsetAsync(ws.f0, 0, sizeof(float) * n, s));
+  return metrics_core(x, a, n, y, b, m, d, f, g, eps, ws, s, out);
+}
+
+int sinkhorn_divergence(const float* x, const float* a, int64_t n, const float* y, const float* b, int64_t m,
+                        int32_t d, double eps, double tau, int32_t max_iter, int32_t precision, double* value,
+                        double* ot_parts, int32_t* iters, void* workspace, size_t ws_bytes, progot_stream_t stream) {
+  t_last_error.clear();
+  int rc = check_common(x, n, y, m, d, precision);
+  if (rc) return rc;
+  if (value == nullptr) return fail(PROGOT_ERR_INVALID_ARG, "value must not be NULL");
+  if (!(eps > 0.0) || !std::isfinite(eps)) return fail(PROGOT_ERR_INVALID_ARG, "eps must be positive and finite");
+  if (!(tau >= 0.0)) return fail(PROGOT_ERR_INVALID_ARG, "tau must be >= 0");
+  if (max_iter < 0) return fail(PROGOT_ERR_INVALID_ARG, "max_iter must be >= 0");
+  const int64_t nmax = std::max<int64_t>(n, m);
+  Workspace ws;
+  rc = carve(nmax, nmax, d, workspace, ws_bytes, &ws, precision);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  struct Side {
+    const float* p;
+    const float* w;
+    int64_t k;
+  };
+  const Side pairs[3][2] = {{{x, a, n}, {y, b, m}}, {{x, a, n}, {x, a, n}}, {{y, b, m}, {y, b, m}}};
+  double ot[3] = {0.0, 0.0, 0.0};
   int worst = PROGOT_OK;
   std::string worst_msg;
-  for (int k = 0; k < K; ++k) {
-    float* gk = g_all + (int64_t)k * m;
-    if (k == 0) {
-      CK(cudaMemsetAsync(gk, 0, sizeof(float) * m, s));
-    } else {
-      // warm start of Alg. 2: (1 - alpha_k) f, (1 - alpha_k) g^(k-1)
-      const float c = (float)(1.0 - alpha[k]);
-      CK(cudaMemcpyAsync(gk, gk - m, sizeof(float) * m, cudaMemcpyDeviceToDevice, s));
-      CK(launch_scale(gk, m, c, s));
-      CK(launch_scale(ws.f0, n, c, s));
-    }
-    if (x_last != nullptr && k == K - 1)
-      CK(cudaMemcpyAsync(x_last, x_out, sizeof(float) * n * d, cudaMemcpyDeviceToDevice, s));
-    CK(launch_row_sqnorm(x_out, n, d, ws.xn, s));
+  for (int q = 0; q < 3; ++q) {
+    const Side& A = pairs[q][0];
+    const Side& B = pairs[q][1];
+    rc = zero_counters(ws, ws_dims(nmax, nmax, d).rbmax, s);
+    if (rc) return rc;
+    CK(launch_row_sqnorm(A.p, A.k, d, ws.xn, s));
+    CK(launch_row_sqnorm(B.p, B.k, d, ws.yn, s));
+    CK(cudaMemsetAsync(ws.f0, 0, sizeof(float) * A.k, s));
+    CK(cudaMemsetAsync(ws.gaux, 0, sizeof(float) * B.k, s));
     int32_t it = 0;
-    double err = 0.0;
-    TcOps ops;
-    rc = sinkhorn_core(x_out, a, n, y, b, m, d, eps[k], tau[k], max_iter, precision, ws.f0, ws.f1, gk, ws.xn, ws.yn,
-                       ws, &it, &err, s, &ops);
-    if (iters) iters[k] = it;
-    if (errs) errs[k] = err;
+    // the self terms OT(X, X), OT(Y, Y) use the symmetric fixed point, which reaches
+    // the same maximiser of eq. (5) in far fewer iterations than alternating updates
+    rc = sinkhorn_core(A.p, A.w, A.k, B.p, B.w, B.k, d, eps, tau, max_iter, precision, ws.f0, ws.f1, ws.gaux, ws.xn,
+                       ws.yn, ws, &it, nullptr, s, nullptr, q != 0);
+    if (iters) iters[q] = it;
     if (rc == PROGOT_ERR_NOT_CONVERGED) {
       if (worst == PROGOT_OK) {
         worst = rc;
-        worst_msg = "step " + std::to_string(k + 1) + ": " + t_last_error;
+        worst_msg = std::string(q == 0 ? "OT(X, Y)" : (q == 1 ? "OT(X, X)" : "OT(Y, Y)")) + ": " + t_last_error;
       }
     } else if (rc) {
       return rc;
     }
-    rc = map_step(x_out, n, y, m, d, gk, ws.yn, eps[k], alpha[k], precision, ws, s, &ops);
+    progot_coupling_metrics met;
+    rc = metrics_core(A.p, A.w, A.k, B.p, B.w, B.k, d, ws.f0, ws.gaux, eps, ws, s, &met);
     if (rc) return rc;
+    ot[q] = met.dual;
   }
-  if (f_last) CK(cudaMemcpyAsync(f_last, ws.f0, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
-  CK(cudaStreamSynchronize(s));
+  *value = ot[0] - 0.5 * (ot[1] + ot[2]);
+  if (ot_parts)
+    for (int q = 0; q < 3; ++q) ot_parts[q] = ot[q];
   if (worst) {
     t_last_error = worst_msg;
     return worst;
   }
   t_last_error.clear();
+  return PROGOT_OK;
+}
+
+int coupling_diagonal(const float* x, const float* y, int64_t n, int32_t d, const float* f, const float* g, double eps,
+                      float* log_diag, double* trace, double* kl, void* workspace, size_t ws_bytes,
+                      progot_stream_t stream) {
+  t_last_error.clear();
+  int rc = check_common(x, n, y, n, d, PROGOT_FP32);
+  if (rc) return rc;
+  if (f == nullptr || g == nullptr) return fail(PROGOT_ERR_INVALID_ARG, "f and g must not be NULL");
+  if (!(eps > 0.0) || !std::isfinite(eps)) return fail(PROGOT_ERR_INVALID_ARG, "eps must be positive and finite");
+  Workspace ws;
+  rc = carve(n, n, d, workspace, ws_bytes, &ws);
+  if (rc) return rc;
+  rc = t_host.init();
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(launch_diag(x, y, f, g, n, d, eps, log_diag, ws.rpart, reduce_parts(), ws.rout, s));
+  CK(cudaMemcpyAsync(t_host.hd, ws.rout, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (trace) *trace = t_host.hd[0];
+  if (kl) *kl = -std::log((double)n) - t_host.hd[1] / (double)n;
   return PROGOT_OK;
 }
 
@@ -842,20 +1082,7 @@ int progot_mean_cost(const float* x, int64_t n, const float* y, int64_t m, int32
   Workspace ws;
   rc = carve(n, m, d, workspace, ws_bytes, &ws);
   if (rc) return rc;
-  rc = t_host.init();
-  if (rc) return rc;
-  if (2 * (d + 1) > 1024) return fail(PROGOT_ERR_INVALID_ARG, "d too large for the mean-cost reduction");
-  cudaStream_t s = (cudaStream_t)stream;
-  CK(launch_moments(x, n, d, ws.rpart, reduce_parts(), ws.rout, s));
-  CK(launch_moments(y, m, d, ws.rpart, reduce_parts(), ws.rout + (d + 1), s));
-  CK(cudaMemcpyAsync(t_host.hd, ws.rout, sizeof(double) * 2 * (d + 1), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  const double* mx = t_host.hd;
-  const double* my = t_host.hd + (d + 1);
-  double dot = 0.0;
-  for (int k = 0; k < d; ++k) dot += (mx[1 + k] / (double)n) * (my[1 + k] / (double)m);
-  *out = mx[0] / (double)n + my[0] / (double)m - 2.0 * dot;
-  return PROGOT_OK;
+  return mean_cost_dev(x, n, y, m, d, ws, false, (cudaStream_t)stream, out);
 }
 
 int progot_schedule_eps(const float* x, int64_t n, const float* y, const float* b, int64_t m, const float* y_test,

@@ -15,6 +15,17 @@ enum SweepMode : int32_t {
   kModePotential = 0,  // out_i = eps log w_i + |a_i|^2 - eps ln2 L_i (Sinkhorn update)
   kModeLse = 1,        // out_i = L_i (log2 units)
   kModeMarginal = 2,   // out_i = exp((pot_i - |a_i|^2)/eps + ln2 L_i)  (row sums of P)
+  kModeMetrics = 3,    // marginal plus the per-row-block sums of the coupling metrics
+};
+
+// Per-row-block float64 sums written by a kModeMetrics sweep (metpart[block * kMetricSums + q]).
+enum MetricSum : int32_t {
+  kSumErr = 0,    // sum_i |r_i - w_i|
+  kSumMass = 1,   // sum_i r_i
+  kSumPotR = 2,   // sum_i pot_i r_i
+  kSumPlogP = 3,  // sum_i sum_j P_ij log P_ij
+  kSumPotW = 4,   // sum_i pot_i w_i
+  kMetricSums = 5,
 };
 
 // Solver state kept on the device so that the Sinkhorn loop runs without a host
@@ -46,6 +57,8 @@ struct SweepParams {
   float* out;          // nA outputs (see SweepMode)
   float* out_alt;      // second output buffer (state->fcur selects), or nullptr
   float2* partial;     // [splits][nA] (max, sum) in log2 units
+  float* wpart;        // [splits][nA] tilted sums sum_j 2^{t_ij - max} (t_ij - max) (kModeMetrics)
+  double* metpart;     // [row blocks][kMetricSums] (kModeMetrics)
   double* errpart;     // [row blocks] float64 error partials
   unsigned int* cnt;   // [row blocks + 1] arrival counters (zero between launches)
   SolverState* state;  // nullptr when the sweep is not part of a Sinkhorn loop
@@ -54,7 +67,9 @@ struct SweepParams {
   int32_t splits;      // column splits (gridDim.y)
   int32_t tiles_per_split;
   int32_t mode;        // SweepMode
-  int32_t role;        // 0 none, 1 f-update of a Sinkhorn loop (error + stop), 2 g-update (it++)
+  int32_t role;        // 0 none, 1 f-update of a Sinkhorn loop (error + stop), 2 g-update (it++),
+                       // 3 symmetric self-transport update (A = B, potB = f): error + stop,
+                       //   f <- (f + f_new) / 2 and it++
   int32_t max_iter;
   int32_t stall_window;
   float scale;         // 2 log2(e) / eps: multiplies x . y

@@ -49,6 +49,15 @@ cudaError_t launch_moments(const float* X, int64_t n, int32_t d, double* partial
 cudaError_t launch_sq_error(const float* A, const float* B, int64_t n, int32_t d, double* partial, int parts,
                             double* out, cudaStream_t s);
 int reduce_parts();
+// out[0] = sum_i P_ii, out[1] = sum_i log P_ii for n = m, log P_ii = (f_i + g_i - |x_i - y_i|^2)/eps;
+// logd (optional) receives log P_ii in float32; partial holds parts x 2 doubles
+cudaError_t launch_diag(const float* X, const float* Y, const float* f, const float* g, int64_t n, int32_t d, double eps,
+                        float* logd, double* partial, int parts, double* out, cudaStream_t s);
+// *out = mean_ij |x_i - y_j|^2 from launch_moments outputs mx (of X, n rows) and my (of Y, m rows)
+cudaError_t launch_mean_cost_closed(const double* mx, const double* my, int64_t n, int64_t m, int32_t d, double* out,
+                                    cudaStream_t s);
+// out[k] = sum_b partial[b * width + k], b = 0..parts-1 in order
+cudaError_t launch_sum_parts(const double* partial, int parts, int width, double* out, cudaStream_t s);
 
 // tcgen05 sweeps (sweep_tc.cu): operands pre-scaled by sqrt(2 log2(e) / eps), split into
 // bf16 hi/lo with K padded to a multiple of 64; map* point at CUtensorMap objects.

@@ -35,7 +35,7 @@ __device__ __forceinline__ void finish_sweep_warp(const SweepParams& p, int nblo
   p.errpart[nblocks] = err;
   SolverState* st = p.state;
   if (st == nullptr) return;
-  if (p.role == 1) {
+  if (p.role == 1 || p.role == 3) {
     st->err = err;
     const int it = st->it;
     if (!isfinite(err)) {
@@ -55,7 +55,10 @@ __device__ __forceinline__ void finish_sweep_warp(const SweepParams& p, int nblo
         st->status = kStalled;
         st->done = 1;
       }
-      if (!st->done) st->fcur ^= 1;  // the new f becomes current
+      if (!st->done) {
+        st->fcur ^= 1;  // the new f becomes current
+        if (p.role == 3) st->it += 1;
+      }
     }
   } else if (p.role == 2) {
     st->it += 1;
@@ -73,7 +76,9 @@ struct RowIn {
 __device__ __forceinline__ RowIn row_inputs(const SweepParams& p, int64_t i, const float* potA_cur) {
   RowIn r;
   r.an = (p.mode != kModeLse && p.An) ? p.An[i] : 0.f;
-  r.pot = (potA_cur != nullptr && (p.mode == kModeMarginal || p.role == 1)) ? potA_cur[i] : 0.f;
+  r.pot = (potA_cur != nullptr && (p.mode == kModeMarginal || p.mode == kModeMetrics || p.role == 1 || p.role == 3))
+              ? potA_cur[i]
+              : 0.f;
   r.w = p.wA ? p.wA[i] : (float)p.inv_nA;
   return r;
 }
@@ -82,7 +87,8 @@ __device__ __forceinline__ RowIn row_inputs(const SweepParams& p, int64_t i, con
 // its error term (float64) and the written value in *val.
 //   potential: f_i = eps log w_i + |a_i|^2 - eps ln2 L, assembled in float64 adds and
 //              multiplies; error a_i |exp((f_old - f_new)/eps) - 1| with expm1 of the
-//              small float32 difference;
+//              small float32 difference; the symmetric update (role 3) stores the
+//              average (f_old + f_new) / 2 and measures the error at f_old;
 //   marginal:  r_i = exp((pot_i - |a_i|^2)/eps + ln2 L), the exponent formed in float64
 //              (it is a difference of large terms) and exponentiated in float32.
 __device__ __forceinline__ double row_epilogue(const SweepParams& p, int64_t i, float L, const RowIn& in,
@@ -90,9 +96,10 @@ __device__ __forceinline__ double row_epilogue(const SweepParams& p, int64_t i, 
   if (p.mode == kModePotential) {
     const double logw = p.wA ? (double)__logf(in.w) : p.log_w_uniform;
     const float fnew = (float)(p.eps * logw + (double)in.an - p.eps * kLn2 * (double)L);
-    out_target[i] = fnew;
-    *val = fnew;
-    if (p.role == 1) {
+    const float fout = (p.role == 3) ? 0.5f * (in.pot + fnew) : fnew;
+    out_target[i] = fout;
+    *val = fout;
+    if (p.role == 1 || p.role == 3) {
       const float d = (in.pot - fnew) * (float)(1.0 / p.eps);
       return (double)in.w * (double)fabsf(expm1f(d));
     }

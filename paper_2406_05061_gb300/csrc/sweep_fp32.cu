@@ -126,6 +126,28 @@ __device__ __forceinline__ int thread_col(int c) {
   return (c < 4) ? tx * 4 + c : 64 + tx * 4 + (c - 4);
 }
 
+// (max, sum, tilted sum) of one row's exponentials in log2 units: with M the max,
+// S = sum_j 2^{t_j - M} and W = sum_j 2^{t_j - M} (t_j - M), so that the 2^t-weighted
+// mean of t is M + W / S. Combining two triples rescales both to the larger max.
+__device__ __forceinline__ float3 tilt_combine(float3 p, float3 q) {
+  const float M = fmaxf(p.x, q.x);
+  if (M == -INFINITY) return make_float3(-INFINITY, 0.f, 0.f);
+  float s = 0.f, w = 0.f;
+  if (p.x != -INFINITY) {
+    const float c = exp2f(p.x - M);
+    s += p.y * c;
+    w += c * fmaf(p.y, p.x - M, p.z);
+  }
+  if (q.x != -INFINITY) {
+    const float c = exp2f(q.x - M);
+    s += q.y * c;
+    w += c * fmaf(q.y, q.x - M, q.z);
+  }
+  return make_float3(M, s, w);
+}
+
+// kTilt adds the tilted sum W per row (coupling metrics); otherwise the plain sweep.
+template <bool kTilt>
 __global__ void __launch_bounds__(NT, 2) lse_sweep_fp32(SweepParams p) {
   if (p.state != nullptr && p.state->done) return;
   __shared__ GemmSmem sm;
@@ -143,11 +165,12 @@ __global__ void __launch_bounds__(NT, 2) lse_sweep_fp32(SweepParams p) {
   const bool vec_ok = ((p.d & 3) == 0) && ((reinterpret_cast<uintptr_t>(p.A) & 15) == 0) &&
                       ((reinterpret_cast<uintptr_t>(p.B) & 15) == 0);
 
-  float m_run[8], s_run[8];
+  float m_run[8], s_run[8], w_run[8];
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
     m_run[r] = -INFINITY;
     s_run[r] = 0.f;
+    w_run[r] = 0.f;
   }
   float acc[8][8];
   for (int tile = t_begin; tile < t_end; ++tile) {
@@ -172,9 +195,22 @@ __global__ void __launch_bounds__(NT, 2) lse_sweep_fp32(SweepParams p) {
       }
       const float mnew = fmaxf(m_run[r], tmax);
       if (mnew != -INFINITY) {
-        float s = s_run[r] * fast_exp2(m_run[r] - mnew);
+        const float resc = fast_exp2(m_run[r] - mnew);  // 0 while the row is still empty
+        float s = s_run[r] * resc;
+        if constexpr (kTilt) {
+          float w = (m_run[r] == -INFINITY) ? 0.f : resc * fmaf(s_run[r], m_run[r] - mnew, w_run[r]);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) s += fast_exp2(t[c] - mnew);
+          for (int c = 0; c < 8; ++c) {
+            const float e = fast_exp2(t[c] - mnew);
+            s += e;
+            // padded columns have t = -inf and e = 0; the clamp keeps 0 * (-inf) out
+            w = fmaf(e, fmaxf(t[c] - mnew, -256.f), w);
+          }
+          w_run[r] = w;
+        } else {
+#pragma unroll
+          for (int c = 0; c < 8; ++c) s += fast_exp2(t[c] - mnew);
+        }
         s_run[r] = s;
         m_run[r] = mnew;
       }
@@ -183,17 +219,36 @@ __global__ void __launch_bounds__(NT, 2) lse_sweep_fp32(SweepParams p) {
   // reduce over the 16 threads that share rows (lanes tx = 0..15 of a half warp)
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
-    float2 v = make_float2(m_run[r], s_run[r]);
+    if constexpr (kTilt) {
+      float3 v = make_float3(m_run[r], s_run[r], w_run[r]);
 #pragma unroll
-    for (int off = 8; off > 0; off >>= 1) {
-      float2 o;
-      o.x = __shfl_xor_sync(0xffffffffu, v.x, off);
-      o.y = __shfl_xor_sync(0xffffffffu, v.y, off);
-      v = lse_combine(v, o);
-    }
-    if (tx == 0) {
-      const int64_t i = row0 + thread_row(r);
-      if (i < p.nA) p.partial[(int64_t)blockIdx.y * p.nA + i] = v;
+      for (int off = 8; off > 0; off >>= 1) {
+        float3 o;
+        o.x = __shfl_xor_sync(0xffffffffu, v.x, off);
+        o.y = __shfl_xor_sync(0xffffffffu, v.y, off);
+        o.z = __shfl_xor_sync(0xffffffffu, v.z, off);
+        v = tilt_combine(v, o);
+      }
+      if (tx == 0) {
+        const int64_t i = row0 + thread_row(r);
+        if (i < p.nA) {
+          p.partial[(int64_t)blockIdx.y * p.nA + i] = make_float2(v.x, v.y);
+          p.wpart[(int64_t)blockIdx.y * p.nA + i] = v.z;
+        }
+      }
+    } else {
+      float2 v = make_float2(m_run[r], s_run[r]);
+#pragma unroll
+      for (int off = 8; off > 0; off >>= 1) {
+        float2 o;
+        o.x = __shfl_xor_sync(0xffffffffu, v.x, off);
+        o.y = __shfl_xor_sync(0xffffffffu, v.y, off);
+        v = lse_combine(v, o);
+      }
+      if (tx == 0) {
+        const int64_t i = row0 + thread_row(r);
+        if (i < p.nA) p.partial[(int64_t)blockIdx.y * p.nA + i] = v;
+      }
     }
   }
   __threadfence();
@@ -208,20 +263,58 @@ __global__ void __launch_bounds__(NT, 2) lse_sweep_fp32(SweepParams p) {
   // ---- last CTA of this row block: combine splits in order, epilogue
   const float* potA_cur = p.potA_old;
   float* out_target = p.out;
-  if (p.role == 1) {
+  if (p.role == 1 || p.role == 3) {
     potA_cur = (fcur == 0) ? p.out : p.out_alt;
     out_target = (fcur == 0) ? p.out_alt : p.out;
   }
   double e = 0.0;
-  if (threadIdx.x < BM) {
-    const int64_t i = row0 + threadIdx.x;
-    if (i < p.nA) {
-      const RowIn in = row_inputs(p, i, potA_cur);
-      float2 v = make_float2(-INFINITY, 0.f);
-      for (int s = 0; s < p.splits; ++s) v = lse_combine(v, __ldcg(&p.partial[(int64_t)s * p.nA + i]));
-      const float L = v.x + __log2f(v.y);
-      float val;
-      e = row_epilogue(p, i, L, in, out_target, &val);
+  if constexpr (kTilt) {
+    // coupling metrics of the rows of this block: with base_i = (pot_i - |a_i|^2) / eps,
+    // log P_ij = base_i + ln2 t_ij, so r_i = exp(base_i + ln2 L_i) and
+    // sum_j P_ij log P_ij = r_i (base_i + ln2 tbar_i), tbar_i = M + W / S
+    double q[kMetricSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (threadIdx.x < BM) {
+      const int64_t i = row0 + threadIdx.x;
+      if (i < p.nA) {
+        const RowIn in = row_inputs(p, i, potA_cur);
+        float3 v = make_float3(-INFINITY, 0.f, 0.f);
+        for (int s = 0; s < p.splits; ++s) {
+          const float2 ms = __ldcg(&p.partial[(int64_t)s * p.nA + i]);
+          v = tilt_combine(v, make_float3(ms.x, ms.y, __ldcg(&p.wpart[(int64_t)s * p.nA + i])));
+        }
+        double r = 0.0, plogp = 0.0;
+        if (v.y > 0.f) {
+          const double base = ((double)in.pot - (double)in.an) / p.eps;
+          const double L = (double)v.x + (double)__log2f(v.y);
+          r = (double)expf((float)(base + kLn2 * L));
+          const double tbar = (double)v.x + (double)v.z / (double)v.y;
+          plogp = r * (base + kLn2 * tbar);
+        }
+        if (out_target) out_target[i] = (float)r;
+        q[kSumErr] = fabs(r - (double)in.w);
+        q[kSumMass] = r;
+        q[kSumPotR] = (double)in.pot * r;
+        q[kSumPlogP] = plogp;
+        q[kSumPotW] = (double)in.pot * (double)in.w;
+      }
+    }
+    e = q[kSumErr];
+#pragma unroll
+    for (int k = 0; k < kMetricSums; ++k) {
+      const double t = block_sum_f64<NT>(q[k], red);
+      if (threadIdx.x == 0) p.metpart[(int64_t)blockIdx.x * kMetricSums + k] = t;
+    }
+  } else {
+    if (threadIdx.x < BM) {
+      const int64_t i = row0 + threadIdx.x;
+      if (i < p.nA) {
+        const RowIn in = row_inputs(p, i, potA_cur);
+        float2 v = make_float2(-INFINITY, 0.f);
+        for (int s = 0; s < p.splits; ++s) v = lse_combine(v, __ldcg(&p.partial[(int64_t)s * p.nA + i]));
+        const float L = v.x + __log2f(v.y);
+        float val;
+        e = row_epilogue(p, i, L, in, out_target, &val);
+      }
     }
   }
   const double tot = block_sum_f64<NT>(e, red);
@@ -378,7 +471,10 @@ __global__ void __launch_bounds__(NT, 1) map_sweep_fp32(MapParams p) {
 cudaError_t launch_lse_sweep_fp32(const SweepParams& p, cudaStream_t stream) {
   const int rb = (int)((p.nA + BM - 1) / BM);
   dim3 grid(rb, p.splits);
-  lse_sweep_fp32<<<grid, NT, 0, stream>>>(p);
+  if (p.mode == kModeMetrics)
+    lse_sweep_fp32<true><<<grid, NT, 0, stream>>>(p);
+  else
+    lse_sweep_fp32<false><<<grid, NT, 0, stream>>>(p);
   count_launch();
   return cudaGetLastError();
 }

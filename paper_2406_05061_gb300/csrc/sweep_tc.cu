@@ -580,7 +580,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (i < p.nA) p.partial[((int64_t)c * tp.maxseg + k) * BM + row_local] = make_float2(m_run, s_run);
       const float* potA_cur = p.potA_old;
       float* out_target = p.out;
-      if (p.role == 1) {
+      if (p.role == 1 || p.role == 3) {
         potA_cur = (fcur == 0) ? p.out : p.out_alt;
         out_target = (fcur == 0) ? p.out_alt : p.out;
       }

@@ -62,6 +62,13 @@ SIGNATURES = [
     ("progot_server_wait", ctypes.c_int, [_P, _I64, _P]),
     ("progot_server_stats", ctypes.c_int, [_P, _P, _P, _P, _P]),
     ("progot_server_destroy", None, [_P]),
+    ("progot_schedule_tau", ctypes.c_int, [_I32, _D, _D, _P]),
+    ("progot_solve_theta", ctypes.c_int,
+     [_P, _P, _I64, _P, _P, _I64, _I32, _I32, _P, _D, _P, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
+    ("coupling_metrics", ctypes.c_int, [_P, _P, _I64, _P, _P, _I64, _I32, _P, _P, _D, _P, _P, _SZ, _P]),
+    ("sinkhorn_divergence", ctypes.c_int,
+     [_P, _P, _I64, _P, _P, _I64, _I32, _D, _D, _I32, _I32, _P, _P, _P, _P, _SZ, _P]),
+    ("coupling_diagonal", ctypes.c_int, [_P, _P, _I64, _I32, _P, _P, _D, _P, _P, _P, _P, _SZ, _P]),
     ("progot_profile", ctypes.c_int, [_I32]),
     ("progot_profile_read", ctypes.c_int, [_I32, _P, _P, _P, _P]),
 ]
@@ -274,6 +281,93 @@ def progot_solve(x, y, alpha, eps, tau, max_iter=10000, a=None, b=None, precisio
     _check(rc)
     return ProgOTOut(out["x_out"], out["g_all"], out.get("f_last"), out.get("x_last"), iters.tolist(),
                      errs.tolist(), rc)
+
+
+def progot_solve_theta(x, y, alpha, theta, tau, max_iter=10000, a=None, b=None, precision="fp32", workspace=None,
+                       stream=None, out=None):
+    """Alg. 2 with eps_k = theta * mean cost(X^(k), Y) / 20 (Sec. 5.2); K = len(alpha).
+    Returns (ProgOTOut, eps_k array)."""
+    torch = _torch()
+    _dev(x, "x"), _dev(y, "y")
+    n, d = x.shape
+    m = y.shape[0]
+    K = len(alpha)
+    al_h, tau_h = _host_f64(alpha, K), _host_f64(tau, K)
+    if out is None:
+        out = dict(x_out=torch.empty_like(x), g_all=torch.empty((K, m), dtype=torch.float32, device=x.device),
+                   f_last=torch.empty(n, dtype=torch.float32, device=x.device), x_last=torch.empty_like(x))
+    iters = np.zeros(K, dtype=np.int32)
+    errs = np.zeros(K, dtype=np.float64)
+    eps_out = np.zeros(K, dtype=np.float64)
+    ws = _ws(workspace, n, m, d, precision)
+    rc = lib().progot_solve_theta(_dev(x, "x"), _opt(a, "a", (n,)), n, _dev(y, "y"), _opt(b, "b", (m,)), m, d, K,
+                                  _hp(al_h), float(theta), _hp(tau_h), int(max_iter), _prec(precision),
+                                  _dev(out["x_out"], "x_out", (n, d)), _dev(out["g_all"], "g_all", (K, m)),
+                                  _opt(out.get("f_last"), "f_last", (n,)), _opt(out.get("x_last"), "x_last", (n, d)),
+                                  _hp(iters), _hp(errs), _hp(eps_out), ctypes.c_void_p(ws.ptr), ws.bytes,
+                                  _stream(stream))
+    _check(rc)
+    return (ProgOTOut(out["x_out"], out["g_all"], out.get("f_last"), out.get("x_last"), iters.tolist(),
+                      errs.tolist(), rc), eps_out)
+
+
+def progot_schedule_tau(K: int, tau_first: float, tau_last: float) -> np.ndarray:
+    out = np.zeros(K, dtype=np.float64)
+    _check(lib().progot_schedule_tau(int(K), float(tau_first), float(tau_last), _hp(out)), allow_not_converged=False)
+    return out
+
+
+class CouplingMetricsStruct(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in
+                ("transport_cost", "entropy", "dual", "mass", "err_row", "err_col")]
+
+
+def coupling_metrics(x, y, f, g, eps, a=None, b=None, workspace=None, stream=None) -> dict:
+    """<P, C>, E(P), the eq. (5) objective, sum P and both marginal errors (Sec. 5.2)."""
+    _dev(x, "x"), _dev(y, "y")
+    n, d = x.shape
+    m = y.shape[0]
+    ws = _ws(workspace, n, m, d, "fp32")
+    res = CouplingMetricsStruct()
+    rc = lib().coupling_metrics(_dev(x, "x"), _opt(a, "a", (n,)), n, _dev(y, "y"), _opt(b, "b", (m,)), m, d,
+                                _dev(f, "f", (n,)), _dev(g, "g", (m,)), float(eps), ctypes.byref(res),
+                                ctypes.c_void_p(ws.ptr), ws.bytes, _stream(stream))
+    _check(rc, allow_not_converged=False)
+    return {k: getattr(res, k) for k, _ in CouplingMetricsStruct._fields_}
+
+
+def sinkhorn_divergence(x, y, eps, tau, max_iter=10000, a=None, b=None, precision="fp32", workspace=None,
+                        stream=None):
+    """D_eps(X, Y) of eq. (8). Returns (D, [OT_xy, OT_xx, OT_yy], [iters ...], status)."""
+    _dev(x, "x"), _dev(y, "y")
+    n, d = x.shape
+    m = y.shape[0]
+    k = max(n, m)
+    ws = _ws(workspace, k, k, d, precision)
+    val = ctypes.c_double(0.0)
+    parts = np.zeros(3, dtype=np.float64)
+    its = np.zeros(3, dtype=np.int32)
+    rc = lib().sinkhorn_divergence(_dev(x, "x"), _opt(a, "a", (n,)), n, _dev(y, "y"), _opt(b, "b", (m,)), m, d,
+                                   float(eps), float(tau), int(max_iter), _prec(precision), ctypes.byref(val),
+                                   _hp(parts), _hp(its), ctypes.c_void_p(ws.ptr), ws.bytes, _stream(stream))
+    _check(rc)
+    return val.value, parts.tolist(), its.tolist(), rc
+
+
+def coupling_diagonal(x, y, f, g, eps, log_diag=None, workspace=None, stream=None):
+    """Tr(P) and KL(Id/n || P) for n = m (Sec. 5.3, Prop. 3). Returns (trace, kl)."""
+    _dev(x, "x"), _dev(y, "y")
+    n, d = x.shape
+    if y.shape != x.shape:
+        raise ValueError("coupling_diagonal needs x and y of the same shape")
+    ws = _ws(workspace, n, n, d, "fp32")
+    tr = ctypes.c_double(0.0)
+    kl = ctypes.c_double(0.0)
+    rc = lib().coupling_diagonal(_dev(x, "x"), _dev(y, "y"), n, d, _dev(f, "f", (n,)), _dev(g, "g", (n,)),
+                                 float(eps), _opt(log_diag, "log_diag", (n,)), ctypes.byref(tr), ctypes.byref(kl),
+                                 ctypes.c_void_p(ws.ptr), ws.bytes, _stream(stream))
+    _check(rc, allow_not_converged=False)
+    return tr.value, kl.value
 
 
 def progot_schedule_alpha(K: int, kind="constant") -> np.ndarray:

@@ -28,6 +28,8 @@ __all__ = [
     "poisson_requests",
     "random_spd",
     "haar_orthogonal",
+    "synthetic_images",
+    "blur_pair",
 ]
 
 
@@ -197,3 +199,52 @@ def poisson_requests(count: int = 20000, rate: float = 200.0, lo: int = 256, hi:
         d = int(dims[rng.integers(0, len(dims))])
         reqs.append((float(t[i]), n, m, d, int(rng.integers(0, 2**31 - 1))))
     return reqs
+
+
+def synthetic_images(n: int, side: int = 32, seed: int = 5) -> np.ndarray:
+    """n grey-level images (side x side, values in [0, 1]) standing in for grey-scale
+    CIFAR-10 (Sec. 5.3): a random linear shading, two to four Gaussian blobs of random
+    position, width and sign, one random axis-aligned rectangle (a sharp edge) and
+    small pixel noise, clipped to [0, 1]. Returns (n, side * side) float32, row-major
+    pixels."""
+    rng = np.random.default_rng(seed)
+    out = np.empty((n, side * side), dtype=np.float32)
+    u = (np.arange(side) + 0.5) / side
+    gy, gx = np.meshgrid(u, u, indexing="ij")
+    chunk = 2048
+    for i0 in range(0, n, chunk):
+        c = min(chunk, n - i0)
+        img = 0.5 + 0.25 * (rng.uniform(-1, 1, (c, 1, 1)) * (gx - 0.5) + rng.uniform(-1, 1, (c, 1, 1)) * (gy - 0.5))
+        nb = rng.integers(2, 5, size=c)
+        for b in range(4):
+            on = (nb > b)[:, None, None]
+            cx, cy = rng.uniform(0, 1, (c, 1, 1)), rng.uniform(0, 1, (c, 1, 1))
+            w = rng.uniform(0.05, 0.3, (c, 1, 1))
+            amp = rng.uniform(-0.5, 0.5, (c, 1, 1))
+            img = img + on * amp * np.exp(-((gx - cx) ** 2 + (gy - cy) ** 2) / (2 * w * w))
+        x0, x1 = np.sort(rng.integers(0, side + 1, (2, c)), axis=0)
+        y0, y1 = np.sort(rng.integers(0, side + 1, (2, c)), axis=0)
+        idx = np.arange(side)
+        rect = ((idx[None, None, :] >= x0[:, None, None]) & (idx[None, None, :] < x1[:, None, None]) &
+                (idx[None, :, None] >= y0[:, None, None]) & (idx[None, :, None] < y1[:, None, None]))
+        img = img + rect * rng.uniform(-0.3, 0.3, (c, 1, 1))
+        img = img + 0.02 * rng.standard_normal((c, side, side))
+        out[i0:i0 + c] = np.clip(img, 0.0, 1.0).reshape(c, side * side)
+    return out
+
+
+def blur_pair(n: int = 60000, side: int = 32, sigma: float = 2.0, seed: int = 5) -> Problem:
+    """The de-blurring benchmark of Sec. 5.3 on synthetic images: x = images, y = G(x)
+    with G(U) = K U K and K_ij = exp(-(i - j)^2 / sigma) on the pixel grid (a Gaussian
+    blur whose width grows with sigma). G is linear, symmetric and positive definite on
+    vec(U), so by Prop. 3 the optimal coupling of (x, y) under the squared Euclidean
+    cost is the identity Id / n: point i of y is the image of point i of x."""
+    x = synthetic_images(n, side, seed)
+    idx = np.arange(side, dtype=np.float64)
+    K = np.exp(-((idx[:, None] - idx[None, :]) ** 2) / float(sigma))
+    y = np.empty_like(x)
+    chunk = 4096
+    for i0 in range(0, n, chunk):
+        U = x[i0:i0 + chunk].astype(np.float64).reshape(-1, side, side)
+        y[i0:i0 + chunk] = np.matmul(K, np.matmul(U, K)).reshape(-1, side * side).astype(np.float32)
+    return Problem(x, y, seed, f"blur_s{sigma:g}_{side}x{side}")

@@ -112,3 +112,39 @@ def test_binding_refuses_non_cuda_tensors(lib):
     x = torch.zeros(4, 2)
     with pytest.raises(TypeError):
         native.sinkhorn_potentials(x, x, 1.0, 1e-3)
+
+
+def test_tau_schedule_matches_oracle(lib):
+    for K in (1, 2, 5, 16):
+        np.testing.assert_allclose(native.progot_schedule_tau(K, 0.01, 1e-3), O.tau_schedule(K, 0.01, 1e-3),
+                                   rtol=1e-14)
+    out = np.zeros(3)
+    assert lib.progot_schedule_tau(3, -1.0, 1e-3, out.ctypes.data_as(ctypes.c_void_p)) == native.PROGOT_ERR_INVALID_ARG
+
+
+def test_widened_entry_points_check_arguments_on_the_host(lib):
+    fake = ctypes.c_void_p(0x100000)
+    ws = ctypes.c_void_p(0x200000)
+    h = np.ones(2, dtype=np.float64)
+    hp = h.ctypes.data_as(ctypes.c_void_p)
+    # theta <= 0, missing eps_out
+    rc = lib.progot_solve_theta(fake, None, 8, fake, None, 8, 2, 2, hp, 0.0, hp, 10, 0, fake, fake, None, None,
+                                None, None, hp, ws, 1 << 20, None)
+    assert rc == native.PROGOT_ERR_INVALID_ARG and "theta" in native.last_error()
+    rc = lib.progot_solve_theta(fake, None, 8, fake, None, 8, 2, 2, hp, 0.1, hp, 10, 0, fake, fake, None, None,
+                                None, None, None, ws, 1 << 20, None)
+    assert rc == native.PROGOT_ERR_INVALID_ARG
+    met = native.CouplingMetricsStruct()
+    rc = lib.coupling_metrics(fake, None, 8, fake, None, 8, 2, fake, fake, -1.0, ctypes.byref(met), ws, 1 << 20, None)
+    assert rc == native.PROGOT_ERR_INVALID_ARG and "eps" in native.last_error()
+    rc = lib.coupling_metrics(fake, None, 8, fake, None, 8, 2, None, fake, 1.0, ctypes.byref(met), ws, 1 << 20, None)
+    assert rc == native.PROGOT_ERR_INVALID_ARG
+    val = ctypes.c_double(0.0)
+    rc = lib.sinkhorn_divergence(fake, None, 8, fake, None, 8, 2, 1.0, -1.0, 10, 0, ctypes.byref(val), None, None,
+                                 ws, 1 << 20, None)
+    assert rc == native.PROGOT_ERR_INVALID_ARG and "tau" in native.last_error()
+    rc = lib.sinkhorn_divergence(fake, None, 8, fake, None, 8, 2, 1.0, 1e-3, 10, 0, ctypes.byref(val), None, None,
+                                 ws, 16, None)
+    assert rc == native.PROGOT_ERR_WORKSPACE
+    rc = lib.coupling_diagonal(fake, fake, 8, 2, fake, fake, 0.0, None, None, None, ws, 1 << 20, None)
+    assert rc == native.PROGOT_ERR_INVALID_ARG

@@ -1,0 +1,168 @@
+"""GPU parity of the widened entry points against the FP64 oracle: coupling metrics
+(Sec. 5.2), the Sinkhorn divergence (eq. (8)), the theta-scaled eps rule (Sec. 5.2),
+the linear tau schedule (Sec. 4) and the coupling diagonal of the blur benchmark
+(Sec. 5.3, Prop. 3). Sizes span several 128-row tiles with ragged tails."""
+import numpy as np
+import pytest
+
+from oracle import progot_oracle as O
+from paper_2406_05061_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_FP32 = 1e-4
+TOL_MIXED = 1e-3
+
+
+@pytest.fixture(scope="module")
+def nat():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2406_05061_gb300 import native
+    native.lib()
+    return native
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def map_rms_rel(T_gpu, T_ref, Y):
+    Y = np.asarray(Y, dtype=np.float64)
+    spread = np.sqrt(np.mean(np.sum((Y - Y.mean(0)) ** 2, 1)))
+    return float(np.sqrt(np.mean(np.sum((np.asarray(T_gpu) - np.asarray(T_ref)) ** 2, 1))) / spread)
+
+
+def _weights(rng, k):
+    w = rng.uniform(0.5, 1.5, k)
+    return (w / w.sum()).astype(np.float32)
+
+
+# ------------------------------------------------------------ coupling metrics
+@pytest.mark.parametrize("n,m,d,weighted", [(700, 530, 5, False), (300, 1000, 64, True), (129, 257, 2, True)])
+def test_coupling_metrics_parity(nat, n, m, d, weighted):
+    p = W.gmm_pair(n, m, d, seed=40 + d, k=3)
+    rng = np.random.default_rng(41)
+    a = _weights(rng, n) if weighted else None
+    b = _weights(rng, m) if weighted else None
+    eps = 0.05 * O.mean_cost(p.x, p.y)
+    sk = O.sinkhorn(a, p.x, b, p.y, eps, 1e-7)
+    # the GPU reads float32 potentials: give the oracle the very same values
+    f32, g32 = sk.f.astype(np.float32), sk.g.astype(np.float32)
+    f, g = f32.astype(np.float64), g32.astype(np.float64)
+    met = nat.coupling_metrics(dev(p.x), dev(p.y), dev(f32), dev(g32), eps,
+                               a=None if a is None else dev(a), b=None if b is None else dev(b))
+    cost = O.coupling_cost(p.x, p.y, f, g, eps)
+    ent = O.coupling_entropy(p.x, p.y, f, g, eps)
+    dual = O.dual_objective(a, p.x, b, p.y, f, g, eps)
+    C = O.CostOperator(p.x, p.y)
+    r, c = O.row_marginal(C, f, g, eps), O.col_marginal(C, f, g, eps)
+    aa = np.full(n, 1.0 / n) if a is None else a.astype(np.float64)
+    bb = np.full(m, 1.0 / m) if b is None else b.astype(np.float64)
+    assert met["transport_cost"] == pytest.approx(cost, rel=TOL_FP32)
+    assert met["entropy"] == pytest.approx(ent, rel=TOL_FP32)
+    assert met["dual"] == pytest.approx(dual, rel=TOL_FP32, abs=TOL_FP32 * cost)
+    assert met["mass"] == pytest.approx(float(r.sum()), rel=TOL_FP32)
+    assert met["err_row"] == pytest.approx(float(np.abs(r - aa).sum()), abs=TOL_FP32)
+    assert met["err_col"] == pytest.approx(float(np.abs(c - bb).sum()), abs=TOL_FP32)
+
+
+def test_coupling_metrics_at_scale(nat):
+    # 4096 x 4096 d = 64 mixture (32 x 32 tiles) against the blocked float64 definitions
+    p = W.gmm_pair(4096, 4096, 64, seed=42, k=8)
+    eps = 0.05 * O.mean_cost(p.x, p.y)
+    res = nat.sinkhorn_potentials(dev(p.x), dev(p.y), eps, 1e-5, max_iter=5000)
+    f, g = host(res.f), host(res.g)
+    met = nat.coupling_metrics(dev(p.x), dev(p.y), res.f, res.g, eps)
+    assert met["transport_cost"] == pytest.approx(O.coupling_cost(p.x, p.y, f, g, eps), rel=TOL_FP32)
+    assert met["entropy"] == pytest.approx(O.coupling_entropy(p.x, p.y, f, g, eps), rel=TOL_FP32)
+    assert met["err_row"] + met["err_col"] <= 1e-5 + TOL_FP32
+
+
+# ------------------------------------------------------- Sinkhorn divergence
+@pytest.mark.parametrize("precision,tol", [("fp32", TOL_FP32), ("bf16x3", TOL_MIXED)])
+def test_sinkhorn_divergence_parity(nat, precision, tol):
+    p = W.gmm_pair(700, 450, 16, seed=43, k=3)
+    eps = O.eps_divergence(p.y)
+    tau = 1e-5
+    D, parts, its, st = nat.sinkhorn_divergence(dev(p.x), dev(p.y), eps, tau, max_iter=20000, precision=precision)
+    assert st == nat.PROGOT_OK, nat.last_error()
+    Dr, pr, _ = O.sinkhorn_divergence(None, p.x, None, p.y, eps, 1e-9, max_iter=50000)
+    scale = max(abs(v) for v in pr)
+    for v, w in zip(parts, pr):
+        assert abs(v - w) <= tol * scale
+    assert abs(D - Dr) <= tol * scale
+    assert D > 0
+    # the self terms use the symmetric fixed point: tens of iterations, not thousands
+    assert max(its[1:]) < 200
+
+
+def test_sinkhorn_divergence_of_a_translate(nat):
+    # D(X, X + v) = |v|^2 for every eps (the linear cost terms go into the potentials)
+    rng = np.random.default_rng(44)
+    x = rng.standard_normal((500, 8)).astype(np.float32)
+    v = np.linspace(-0.5, 0.5, 8).astype(np.float32)
+    D, parts, _, st = nat.sinkhorn_divergence(dev(x), dev(x + v), 2.0, 1e-5, max_iter=20000)
+    assert st == nat.PROGOT_OK, nat.last_error()
+    assert D == pytest.approx(float(v.astype(np.float64) @ v), rel=1e-3)
+
+
+# ------------------------------------------------------------ theta rule
+@pytest.mark.parametrize("precision,tol", [("fp32", TOL_FP32), ("bf16x3", TOL_MIXED)])
+def test_progot_solve_theta_parity(nat, precision, tol):
+    # theta = 1 puts eps_k at the usual mean-cost / 20 level, where a solve stopped at
+    # tau = 1e-5 determines the map to the parity tolerance; smaller theta slows
+    # Sinkhorn down (thousands of iterations) and the float32 and float64 runs then stop
+    # at different points of a long, flat approach
+    p = W.gmm_pair(600, 450, 16, seed=45, k=4)
+    K, theta = 4, 1.0
+    alpha = O.alpha_schedule(K)
+    # both sides run the same linear tau schedule (equal accuracy); the mixed path ends
+    # at 1e-4, the threshold its bf16 hi/lo products reach reliably
+    tau = O.tau_schedule(K, 1e-4, 1e-5) if precision == "fp32" else O.tau_schedule(K, 1e-3, 1e-4)
+    res, eps = nat.progot_solve_theta(dev(p.x), dev(p.y), alpha, theta, tau, max_iter=20000, precision=precision)
+    assert res.status == nat.PROGOT_OK, nat.last_error()
+    ref = O.progot(None, p.x, None, p.y, O.eps_theta_rule(theta, p.y), alpha, tau)
+    # eps_1 comes from the input cloud itself: float64 closed form vs the definition
+    assert eps[0] == pytest.approx(ref.eps_used[0], rel=1e-9)
+    np.testing.assert_allclose(eps, ref.eps_used, rtol=10 * tol)
+    assert map_rms_rel(host(res.x_out), ref.x_out, p.y) <= tol
+    # teacher forcing: the rule on the GPU's own X^(K) gives the GPU's eps_K
+    assert eps[-1] == pytest.approx(theta * O.mean_cost(host(res.x_last), p.y) / 20, rel=1e-6)
+
+
+def test_progot_solve_theta_matches_progot_solve_with_its_eps(nat):
+    # the theta path and the explicit-eps path run the same kernels: with the eps the
+    # rule produced, progot_solve must give the same result bit for bit
+    p = W.gmm_pair(500, 380, 24, seed=46, k=3)
+    K = 3
+    alpha = O.alpha_schedule(K, "accelerated")
+    tau = [1e-5] * K
+    r1, eps = nat.progot_solve_theta(dev(p.x), dev(p.y), alpha, 2.0 ** -4, tau, max_iter=20000)
+    r2 = nat.progot_solve(dev(p.x), dev(p.y), alpha, eps, tau, max_iter=20000)
+    assert torch.equal(r1.x_out, r2.x_out) and torch.equal(r1.g_all, r2.g_all)
+    assert r1.iters == r2.iters
+
+
+# ------------------------------------------------------------ coupling diagonal
+def test_coupling_diagonal_parity_and_identity_recovery(nat):
+    # Prop. 3: images and their blurs are optimally coupled by Id / n
+    p = W.blur_pair(1500, side=8, sigma=2.0, seed=47)
+    eps = 2.0 ** -6 * O.mean_cost(p.x, p.y) / 20
+    res = nat.sinkhorn_potentials(dev(p.x), dev(p.y), eps, 1e-4, max_iter=30000)
+    assert res.status in (nat.PROGOT_OK, nat.PROGOT_ERR_NOT_CONVERGED), nat.last_error()
+    logd = torch.empty(p.n, dtype=torch.float32, device="cuda")
+    tr, kl = nat.coupling_diagonal(dev(p.x), dev(p.y), res.f, res.g, eps, log_diag=logd)
+    tr_r, kl_r = O.diagonal_metrics(p.x, p.y, host(res.f), host(res.g), eps)
+    ld_r = O.coupling_diagonal(p.x, p.y, host(res.f), host(res.g), eps)
+    np.testing.assert_allclose(host(logd), ld_r, rtol=1e-5, atol=1e-4)
+    assert tr == pytest.approx(tr_r, rel=1e-6)
+    assert kl == pytest.approx(kl_r, rel=1e-6, abs=1e-7)
+    # a valid coupling: KL(Id/n || P) >= 0 (Gibbs) and Tr(P) <= 1, and at this small eps
+    # the diagonal carries most of the mass (the independent coupling has Tr = 1/n)
+    assert 0.5 < tr <= 1.0 + 1e-4 and 0 <= kl
