@@ -201,7 +201,7 @@ struct TcParams {
   int32_t nkb;        // K blocks of 64
   int32_t split3;     // 1: bf16x3 (hi and lo operands), 0: bf16 (hi only)
   int32_t stages;     // B pipeline depth (units of one K block of one tile)
-  int32_t a_bufs;     // 1 or 2 A-operand buffers
+  int32_t a_bufs;     // 1 or 2 resident A-operand buffers, or 0: A K blocks stream with B
   int32_t G;          // CTAs
   int32_t T;          // column tiles per row block
   int32_t R;          // row blocks
@@ -211,7 +211,7 @@ struct TcParams {
 };
 
 struct SmemLayout {
-  uint32_t a0, a_stride, a_lo_off, a_bias, stage0, stage_bytes, b_lo_off, bias_off, ctrl, total;
+  uint32_t a0, a_stride, a_lo_off, a_bias, stage0, stage_bytes, b_lo_off, bias_off, a_stage_off, ctrl, total;
 };
 
 __host__ __device__ inline SmemLayout smem_layout(int bn, int nkb, int split3, int stages, int a_bufs) {
@@ -227,7 +227,9 @@ __host__ __device__ inline SmemLayout smem_layout(int bn, int nkb, int split3, i
   L.stage0 = off;
   L.b_lo_off = b_tile;
   L.bias_off = b_tile * (split3 ? 2 : 1);
-  L.stage_bytes = L.bias_off + bias_tile;
+  // streamed A (a_bufs = 0): the A K block (hi, then lo) follows the bias rows in the stage
+  L.a_stage_off = L.bias_off + bias_tile;
+  L.stage_bytes = L.a_stage_off + (a_bufs == 0 ? A_TILE_BYTES * (split3 ? 2u : 1u) : 0u);
   off += stages * L.stage_bytes;
   L.ctrl = off;
   off += sizeof(TcShared);
@@ -385,22 +387,27 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     bool ok = true;
     const uint32_t abytes = (uint32_t)L.a_stride;
     const uint32_t bbytes = B_TILE_BYTES * (tp.split3 ? 2u : 1u);
+    // streamed A: each stage also carries the A K block (hi and lo) of its tile
+    const uint32_t sabytes = NA == 0 ? A_TILE_BYTES * (tp.split3 ? 2u : 1u) : 0u;
     int a_issued = 0;
     for (int k = 0; k < nseg && ok; ++k) {
       const Seg sg = segment(c, k, W, G, T);
-      const int ai = k % NA;
-      ok = warp_wait(&sh.a_empty[ai], (uint32_t)(((k / NA) & 1) ^ 1), abort_flag);
-      if (!ok) break;
-      unsigned char* abuf = smem + L.a0 + ai * L.a_stride;
-      if (elect_one()) {
-        mbar_arrive_expect_tx(&sh.a_full[ai], abytes);
-        for (int kb = 0; kb < nkb; ++kb) {
-          tma_load_2d(abuf + kb * A_TILE_BYTES, &mapAh, &sh.a_full[ai], kb * KB, sg.r * BM);
-          if (tp.split3) tma_load_2d(abuf + L.a_lo_off + kb * A_TILE_BYTES, &mapAl, &sh.a_full[ai], kb * KB, sg.r * BM);
+      if (NA > 0) {
+        const int ai = k % NA;
+        ok = warp_wait(&sh.a_empty[ai], (uint32_t)(((k / NA) & 1) ^ 1), abort_flag);
+        if (!ok) break;
+        unsigned char* abuf = smem + L.a0 + ai * L.a_stride;
+        if (elect_one()) {
+          mbar_arrive_expect_tx(&sh.a_full[ai], abytes);
+          for (int kb = 0; kb < nkb; ++kb) {
+            tma_load_2d(abuf + kb * A_TILE_BYTES, &mapAh, &sh.a_full[ai], kb * KB, sg.r * BM);
+            if (tp.split3)
+              tma_load_2d(abuf + L.a_lo_off + kb * A_TILE_BYTES, &mapAl, &sh.a_full[ai], kb * KB, sg.r * BM);
+          }
         }
+        __syncwarp();
+        a_issued = k + 1;
       }
-      __syncwarp();
-      a_issued = k + 1;
       for (int t = sg.t0; t < sg.t1 && ok; ++t) {
         for (int kb = 0; kb < nkb; ++kb, ++u) {
           const int s = u % S;
@@ -408,10 +415,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           if (!ok) break;
           unsigned char* st = smem + L.stage0 + s * L.stage_bytes;
           if (elect_one()) {
-            mbar_arrive_expect_tx(&sh.full[s], bbytes + (kb == 0 ? BIAS_TILE_BYTES : 0u));
+            mbar_arrive_expect_tx(&sh.full[s], bbytes + sabytes + (kb == 0 ? BIAS_TILE_BYTES : 0u));
             tma_load_2d(st, &mapBh, &sh.full[s], kb * KB, t * BN);
             if (tp.split3) tma_load_2d(st + L.b_lo_off, &mapBl, &sh.full[s], kb * KB, t * BN);
             if (kb == 0) tma_load_2d(st + L.bias_off, &mapBbias, &sh.full[s], 0, t * BN);
+            if (NA == 0) {
+              tma_load_2d(st + L.a_stage_off, &mapAh, &sh.full[s], kb * KB, sg.r * BM);
+              if (tp.split3) tma_load_2d(st + L.a_stage_off + A_TILE_BYTES, &mapAl, &sh.full[s], kb * KB, sg.r * BM);
+            }
           }
           __syncwarp();
         }
@@ -419,8 +430,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     if (!ok) {
       // drain this CTA's own copies still in flight before shared memory is released
-      for (int k = max(0, a_issued - NA); k < a_issued; ++k)
-        warp_wait(&sh.a_full[k % NA], (uint32_t)((k / NA) & 1), abort_flag, true);
+      if (NA > 0)
+        for (int k = max(0, a_issued - NA); k < a_issued; ++k)
+          warp_wait(&sh.a_full[k % NA], (uint32_t)((k / NA) & 1), abort_flag, true);
       for (int v = max(0, u - S); v < u; ++v) warp_wait(&sh.full[v % S], (uint32_t)((v / S) & 1), abort_flag, true);
     }
   } else if (warp == 1) {
@@ -430,10 +442,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     int u = 0, tl = 0;
     for (int k = 0; k < nseg && ok; ++k) {
       const Seg sg = segment(c, k, W, G, T);
-      const int ai = k % NA;
-      ok = warp_wait(&sh.a_full[ai], (uint32_t)((k / NA) & 1), abort_flag);
-      if (!ok) break;
-      tc_fence_after();
+      const int ai = NA > 0 ? k % NA : 0;
+      if (NA > 0) {
+        ok = warp_wait(&sh.a_full[ai], (uint32_t)((k / NA) & 1), abort_flag);
+        if (!ok) break;
+        tc_fence_after();
+      }
       const uint32_t a_hi = smem_u32(smem + L.a0 + ai * L.a_stride);
       const uint32_t a_lo = a_hi + L.a_lo_off;
       for (int t = sg.t0; t < sg.t1 && ok; ++t, ++tl) {
@@ -449,7 +463,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           tc_fence_after();
           const uint32_t st = smem_u32(smem + L.stage0 + s * L.stage_bytes);
           const uint64_t bh = desc_sw128(st), bl = desc_sw128(st + L.b_lo_off);
-          const uint64_t ah = desc_sw128(a_hi + kb * A_TILE_BYTES), al = desc_sw128(a_lo + kb * A_TILE_BYTES);
+          const uint32_t sa = st + L.a_stage_off;  // streamed A block of this stage
+          const uint64_t ah = NA > 0 ? desc_sw128(a_hi + kb * A_TILE_BYTES) : desc_sw128(sa);
+          const uint64_t al = NA > 0 ? desc_sw128(a_lo + kb * A_TILE_BYTES) : desc_sw128(sa + A_TILE_BYTES);
           const uint64_t bb = desc_sw32(st + L.bias_off);
           if (elect_one()) {
 #pragma unroll
@@ -472,7 +488,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         __syncwarp();
       }
       if (!ok) break;
-      if (elect_one()) umma_commit(&sh.a_empty[ai]);
+      if (NA > 0 && elect_one()) umma_commit(&sh.a_empty[ai]);
       __syncwarp();
     }
     // make sure no MMA is still writing TMEM when the CTA moves on
@@ -688,12 +704,14 @@ __global__ void split_bf16_kernel(const float* __restrict__ X, int64_t n, int32_
 }  // namespace tc
 
 // ---------------------------------------------------------------- host side
-// Pipeline shape for a tile width bn and a K depth of nkb blocks: two A buffers when
-// at least three B stages still fit in 227 KB, else one; as many B stages (<= 8) as fit.
+// Pipeline shape for a tile width bn and a K depth of nkb blocks: the A operand of a row
+// block resident in shared memory (two buffers when at least three B stages still fit
+// in 227 KB, else one), or, when no resident A leaves room for two B stages (large d),
+// streamed with B one K block per stage (a_bufs = 0); as many stages (<= 8) as fit.
 static void tc_shape(int bn, int nkb, int split3, int* stages, int* a_bufs) {
   *stages = 0;
   *a_bufs = 1;
-  for (int na = 2; na >= 1; --na) {
+  for (int na = 2; na >= 0; --na) {
     int best = 0;
     for (int s = 2; s <= 8; ++s)
       if (tc::smem_layout(bn, nkb, split3, s, na).total <= 227 * 1024) best = s;
@@ -705,9 +723,15 @@ static void tc_shape(int bn, int nkb, int split3, int* stages, int* a_bufs) {
   }
 }
 
-// Column-tile width: 256 (one N = 256 MMA per K step) when two B stages fit, else 128.
+// Column-tile width: 256 (one N = 256 MMA per K step) when two B stages fit next to a
+// resident A, else 128 with a resident A; for K depths where neither fits, 256 with A
+// streamed (or 128 when even that does not fit).
 int tc_tile_cols(int nkb, int split3) {
   int s, na;
+  tc_shape(256, nkb, split3, &s, &na);
+  if (s >= 2 && na > 0) return 256;
+  tc_shape(128, nkb, split3, &s, &na);
+  if (s >= 2 && na > 0) return 128;
   tc_shape(256, nkb, split3, &s, &na);
   return s >= 2 ? 256 : 128;
 }

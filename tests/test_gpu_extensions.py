@@ -166,3 +166,33 @@ def test_coupling_diagonal_parity_and_identity_recovery(nat):
     # a valid coupling: KL(Id/n || P) >= 0 (Gibbs) and Tr(P) <= 1, and at this small eps
     # the diagonal carries most of the mass (the independent coupling has Tr = 1/n)
     assert 0.5 < tr <= 1.0 + 1e-4 and 0 <= kl
+
+
+# ------------------------------------------------- large d: A streamed with B
+@pytest.mark.parametrize("n,m,d", [(300, 520, 320), (700, 900, 1024), (257, 130, 1000)])
+def test_large_d_streamed_operand_parity_bf16x3(nat, n, m, d):
+    # above d = 256 the bf16 hi/lo A operand of a row block no longer fits next to two B
+    # stages, so the tensor-core sweep streams A one K block per stage
+    p = W.gmm_pair(n, m, d, seed=n + m + d, k=4)
+    eps = 0.05 * O.mean_cost(p.x, p.y)
+    res = nat.sinkhorn_potentials(dev(p.x), dev(p.y), eps, 1e-4, max_iter=5000, precision="bf16x3")
+    assert res.status == nat.PROGOT_OK, nat.last_error()
+    ref = O.sinkhorn(None, p.x, None, p.y, eps, 1e-6, max_iter=5000)
+    f, g = host(res.f), host(res.g)
+    C = O.CostOperator(p.x, p.y)
+    err = float(np.abs(O.row_marginal(C, f, g, eps) - 1.0 / n).sum() + np.abs(O.col_marginal(C, f, g, eps) - 1.0 / m).sum())
+    assert err <= TOL_MIXED
+    T_gpu = O.entropic_map(p.x, p.y, g, eps)
+    T_ref = O.entropic_map(p.x, p.y, ref.g, eps)
+    assert map_rms_rel(T_gpu, T_ref, p.y) <= TOL_MIXED
+
+
+def test_large_d_map_step_parity_bf16x3(nat):
+    # one ProgOT step at d = 1024: tensor-core LSE pass with streamed A, then the map
+    p = W.blur_pair(600, side=32, sigma=2.0, seed=48)
+    eps = 0.05 * O.mean_cost(p.x, p.y)
+    alpha = [0.5, 1.0]
+    res = nat.progot_solve(dev(p.x), dev(p.y), alpha, [eps, eps], [1e-4, 1e-4], max_iter=5000, precision="bf16x3")
+    assert res.status == nat.PROGOT_OK, nat.last_error()
+    ref = O.progot(None, p.x, None, p.y, [eps, eps], alpha, [1e-6, 1e-6])
+    assert map_rms_rel(host(res.x_out), ref.x_out, p.y) <= TOL_MIXED
