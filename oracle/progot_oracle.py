@@ -234,7 +234,9 @@ def sinkhorn(a, X, b, Y, eps: float, tau: float, f_init=None, g_init=None,
     L1 error of P = exp((f (+) g - C)/eps) exceeds tau, update f then g. The
     error is checked before every iteration (so a warm start that already meets
     tau does no work). ``iters`` counts completed (f, g) update pairs; after
-    ``max_iter`` of them the result is returned with converged = False."""
+    ``max_iter`` of them the result is returned with converged = False. An error that
+    overflows (a warm start far from feasible at small eps) is still above tau, so the
+    loop goes on; only a NaN error stops it."""
     X = np.asarray(X, dtype=np.float64)
     Y = np.asarray(Y, dtype=np.float64)
     n, m = X.shape[0], Y.shape[0]
@@ -248,7 +250,7 @@ def sinkhorn(a, X, b, Y, eps: float, tau: float, f_init=None, g_init=None,
     while True:
         err = marginal_error(C, f, g, eps, a)
         errs.append(err)
-        if not math.isfinite(err):
+        if math.isnan(err):
             return SinkhornResult(f, g, it, err, False, errs)
         if err <= tau:
             return SinkhornResult(f, g, it, err, True, errs)
@@ -549,7 +551,7 @@ def sinkhorn_symmetric(a, X, eps: float, tau: float, max_iter: int = 10000) -> S
         # row sums of P at the current f: a_i exp((f_i - f_new_i) / eps)
         err = float(np.sum(np.abs(a * np.expm1((f - f_new) / eps))))
         errs.append(err)
-        if not math.isfinite(err):
+        if math.isnan(err):
             return SinkhornResult(f, f.copy(), it, err, False, errs)
         if err <= tau:
             return SinkhornResult(f, f.copy(), it, err, True, errs)

@@ -386,3 +386,16 @@ def test_planted_mistakes_are_caught(monkeypatch):
     np.testing.assert_allclose(good, pr.x_out, atol=1e-8)
     bad = O.progot_map(X, Y, [gk + e * np.log(b) for gk, e in zip(pr.g_all, [0.8, 0.5])], [0.8, 0.5], al)
     assert np.max(np.abs(bad - pr.x_out)) > 1e-4
+
+
+def test_sinkhorn_continues_through_an_overflowing_error():
+    # a warm start far from feasible makes P overflow (error = inf > tau); Alg. 1 keeps
+    # iterating and reaches the same coupling as the zero start (f (+) g is unique)
+    a, X, b, Y = _small_problem(seed=9)
+    eps = 0.05
+    ref = O.sinkhorn(a, X, b, Y, eps, 1e-10, max_iter=100000)
+    with np.errstate(over="ignore"):
+        hot = O.sinkhorn(a, X, b, Y, eps, 1e-10, f_init=np.full(X.shape[0], 50.0),
+                         g_init=np.full(Y.shape[0], 50.0), max_iter=100000)
+    assert math.isinf(hot.errs[0]) and hot.converged
+    np.testing.assert_allclose(hot.f[:, None] + hot.g[None, :], ref.f[:, None] + ref.g[None, :], atol=1e-8)
