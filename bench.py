@@ -289,6 +289,86 @@ def run_serving(args, rank, world, local):
     return 0
 
 
+def run_blur(args, rank, world, local):
+    """The de-blurring benchmark of Sec. 5.3 on synthetic images: n grey 32 x 32 images
+    (d = 1024) against their Gaussian blurs; by Prop. 3 the optimal coupling is Id / n.
+    Sinkhorn at eps = beta eps0 and ProgOT (K = 4, constant speed, eps_k = theta cbar_k,
+    tau_k linear from 1e-2 to 1e-3) with beta = theta = 2^-4 and tau = 1e-3 as in the
+    coupling experiments; each reports Tr(P), KL(Id/n || P), iterations and time."""
+    import torch
+    from paper_2406_05061_gb300 import native
+    torch.cuda.set_device(local)
+    t_gen = time.perf_counter()
+    p = W.blur_pair(args.blur_n, 32, args.sigma, seed=5)
+    t_gen = time.perf_counter() - t_gen
+    x = torch.from_numpy(p.x).cuda()
+    y = torch.from_numpy(p.y).cuda()
+    n, d = p.n, p.d
+    prec = args.precision
+    ws = native.Workspace(n, n, d, prec)
+    beta = theta = 2.0 ** -4
+    K = 4
+    eps0 = native.progot_mean_cost(x, y, workspace=ws) / 20.0
+    alpha = native.progot_schedule_alpha(K, "constant")
+    tau_k = native.progot_schedule_tau(K, 1e-2, 1e-3)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def sinkhorn():
+        return native.sinkhorn_potentials(x, y, beta * eps0, 1e-3, max_iter=10000, precision=prec, workspace=ws)
+
+    def progot():
+        return native.progot_solve_theta(x, y, alpha, theta, tau_k, max_iter=10000, precision=prec, workspace=ws)
+
+    out = {}
+    for name, fn in (("sinkhorn", sinkhorn), ("progot", progot)):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        native.launch_count(reset=True)
+        native.profile(True, period=1)
+        ms = []
+        for _ in range(args.steps):
+            e0, e1 = ev(), ev()
+            e0.record()
+            r = fn()
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        lse, mp = native.profile_read("lse_sweep"), native.profile_read("map_sweep")
+        native.profile(False)
+        launches = native.launch_count()
+        if name == "sinkhorn":
+            tr, kl = native.coupling_diagonal(x, y, r.f, r.g, beta * eps0, workspace=ws)
+            iters, eps_used, status = r.iters, [beta * eps0], r.status
+        else:
+            res, eps_k = r
+            tr, kl = native.coupling_diagonal(res.x_last, y, res.f_last, res.g_all[K - 1], float(eps_k[-1]),
+                                              workspace=ws)
+            iters, eps_used, status = res.iters, [float(e) for e in eps_k], res.status
+        out[name] = {"trace": tr, "kl": kl, "iters": iters, "eps": eps_used, "status": status,
+                     "seconds_per_solve": sum(ms) / len(ms) / 1e3, "gpu_launches": launches,
+                     "lse_sweep_ms_avg": lse["ms"] / max(1, lse["launches"]),
+                     "map_sweep_ms_avg": mp["ms"] / max(1, mp["launches"]),
+                     "lse_sweeps": lse["worked"], "map_sweeps": mp["worked"]}
+    pairs = float(n) * n
+    lse_ms = out["progot"]["lse_sweep_ms_avg"]
+    flop = 6.0 * d * pairs if prec == "bf16x3" else (2.0 * d * pairs)
+    peaks = load_peaks()
+    line = {"metric": "blur_progot_seconds_per_solve", "value": out["progot"]["seconds_per_solve"], "unit": "s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+            "dtype": prec, "data": "synthetic",
+            "config": {"workload": f"blur_sigma{args.sigma:g}_{n}x{d}", "n": n, "d": d, "sigma": args.sigma,
+                       "K": K, "theta": theta, "beta": beta, "tau": 1e-3, "tau_schedule": [float(t) for t in tau_k],
+                       "eps0": eps0, "generate_s": t_gen, "l2": "inputs 2 x %d MB > L2" % (n * d * 4 >> 20)},
+            "progot": out["progot"], "sinkhorn": out["sinkhorn"],
+            "lse_sweep_tflops": flop / (lse_ms * 1e-3) / 1e12 if lse_ms > 0 else None,
+            "lse_sweep_frac_of_sustained_bf16": (flop / (lse_ms * 1e-3) / 1e12 / peaks["bf16_tflops_sustained"]
+                                                 if lse_ms > 0 and prec != "fp32" else None),
+            "gpu_launches": out["progot"]["gpu_launches"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -297,7 +377,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16x3", choices=["fp32", "bf16x3", "bf16"])
     ap.add_argument("--no-compare", action="store_true", help="skip the float32 comparison solve")
-    ap.add_argument("--workload", default="gmm8_8192_d64", choices=sorted(WORKLOADS) + ["batched256", "serving"])
+    ap.add_argument("--workload", default="gmm8_8192_d64",
+                    choices=sorted(WORKLOADS) + ["batched256", "serving", "blur"])
+    ap.add_argument("--blur-n", type=int, default=60000, help="blur: number of images (32 x 32)")
+    ap.add_argument("--sigma", type=float, default=2.0, help="blur: kernel width")
     ap.add_argument("--requests", type=int, default=240, help="serving: requests replayed from the stream")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean arrival rate (requests/s)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -309,6 +392,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "batched256":
         return run_batched(args, rank, world, local)
+    if args.workload == "blur":
+        return run_blur(args, rank, world, local) if rank == 0 else 0
     if args.workload == "serving":
         return run_serving(args, rank, world, local)
 

@@ -100,7 +100,11 @@ __device__ __forceinline__ double row_epilogue(const SweepParams& p, int64_t i, 
     out_target[i] = fout;
     *val = fout;
     if (p.role == 1 || p.role == 3) {
-      const float d = (in.pot - fnew) * (float)(1.0 / p.eps);
+      // a_i exp(d) is the row sum of P at the current f; far from feasibility (a warm
+      // start at small eps) it overflows float32. Such a term only has to exceed tau,
+      // so d is capped at 80 (the term stays below 1e35); a NaN stays NaN.
+      float d = (in.pot - fnew) * (float)(1.0 / p.eps);
+      if (d > 80.f) d = 80.f;
       return (double)in.w * (double)fabsf(expm1f(d));
     }
     return 0.0;

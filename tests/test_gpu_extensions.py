@@ -196,3 +196,18 @@ def test_large_d_map_step_parity_bf16x3(nat):
     assert res.status == nat.PROGOT_OK, nat.last_error()
     ref = O.progot(None, p.x, None, p.y, [eps, eps], alpha, [1e-6, 1e-6])
     assert map_rms_rel(host(res.x_out), ref.x_out, p.y) <= TOL_MIXED
+
+
+def test_overflowing_warm_start_keeps_iterating(nat):
+    # potentials far above feasibility make the first row sums overflow float32; the loop
+    # must treat that as "error above tau" and reach the zero-start coupling (oracle)
+    p = W.gmm_pair(400, 300, 16, seed=49, k=3)
+    eps = 0.05 * O.mean_cost(p.x, p.y)
+    cmax = float(O.cost_matrix_rows(p.x, p.y).max())
+    f0 = np.full(p.n, cmax, dtype=np.float32)
+    g0 = np.full(p.m, cmax, dtype=np.float32)
+    res = nat.sinkhorn_potentials(dev(p.x), dev(p.y), eps, 1e-5, max_iter=5000, f=dev(f0), g=dev(g0))
+    assert res.status == nat.PROGOT_OK, nat.last_error()
+    ref = O.sinkhorn(None, p.x, None, p.y, eps, 1e-7)
+    T = O.entropic_map(p.x, p.y, host(res.g), eps)
+    assert map_rms_rel(T, O.entropic_map(p.x, p.y, ref.g, eps), p.y) <= TOL_FP32
