@@ -54,6 +54,9 @@ also listed in the design notes):
   eps_D = 5% of the unweighted mean of the target's intra cost C_YY. The self terms
   OT(X, X), OT(Y, Y) are solved by the symmetric (averaged) fixed point, whose
   maximiser is the same and which converges much faster than alternating updates.
+* Costs: the squared Euclidean h = ||.||^2 everywhere by default; the coupling
+  experiments' h = (1/p) ||.||_p^p (p = 1.5) through the ``cost`` argument, with its
+  gradient and the gradient of its conjugate written coordinate by coordinate.
 * Blur benchmark KL: KL(P* || P) = -log n - (1/n) sum_i log P_ii (the printed
   "n sum_i" would not vanish at P = P* = Id / n).
 """
@@ -73,6 +76,7 @@ __all__ = [
     "coupling_cost", "coupling_entropy", "dual_objective",
     "eps_theta_rule", "tau_schedule", "eps_divergence", "ot_value", "sinkhorn_symmetric",
     "sinkhorn_divergence", "coupling_diagonal", "diagonal_metrics",
+    "SqEuclidean", "PNorm", "SQEUCLIDEAN",
 ]
 
 # Rows per block: the oracle never holds more than BLOCK_ELEMS doubles of an
@@ -99,15 +103,64 @@ def grad_h_star(w: np.ndarray) -> np.ndarray:
     return 0.5 * w
 
 
+class SqEuclidean:
+    """The workload cost h = ||.||^2 with grad h = 2z and grad h* = w/2."""
+
+    name = "sqeuclidean"
+
+    @staticmethod
+    def h(z):
+        return h(z)
+
+    @staticmethod
+    def grad_h(z):
+        return grad_h(z)
+
+    @staticmethod
+    def grad_h_star(w):
+        return grad_h_star(w)
+
+
+class PNorm:
+    """The non-quadratic cost of the coupling experiments (Sec. 5.2),
+    h(z) = (1/p) sum_k |z_k|^p with p > 1, coordinate by coordinate:
+    grad h(z)_k = sign(z_k) |z_k|^(p-1); its convex conjugate is
+    h*(w) = (1/q) sum_k |w_k|^q with 1/p + 1/q = 1, so
+    grad h*(w)_k = sign(w_k) |w_k|^(q-1) = sign(w_k) |w_k|^(1/(p-1))."""
+
+    def __init__(self, p: float):
+        if not p > 1.0:
+            raise ValueError("p > 1")
+        self.p = float(p)
+        self.name = f"pnorm{self.p:g}"
+
+    def h(self, z):
+        return np.sum(np.abs(z) ** self.p, axis=-1) / self.p
+
+    def grad_h(self, z):
+        return np.sign(z) * np.abs(z) ** (self.p - 1.0)
+
+    def grad_h_star(self, w):
+        return np.sign(w) * np.abs(w) ** (1.0 / (self.p - 1.0))
+
+
+SQEUCLIDEAN = SqEuclidean()
+
+
+def _cost(cost):
+    return SQEUCLIDEAN if cost is None else cost
+
+
 def _rows_per_block(m: int, d: int) -> int:
     return max(1, BLOCK_ELEMS // max(1, m * d))
 
 
-def cost_matrix_rows(X: np.ndarray, Y: np.ndarray) -> np.ndarray:
+def cost_matrix_rows(X: np.ndarray, Y: np.ndarray, cost=None) -> np.ndarray:
     """C_ij = h(x_i - y_j) for all rows of X against all rows of Y, computed from the
-    differences x_i - y_j themselves (the definition, no norm expansion)."""
+    differences x_i - y_j themselves (the definition, no norm expansion); h is the
+    squared Euclidean cost unless another cost is given."""
     diff = X[:, None, :] - Y[None, :, :]
-    return h(diff)
+    return _cost(cost).h(diff)
 
 
 def softmin(S: np.ndarray, eps: float) -> np.ndarray:
@@ -129,9 +182,10 @@ class CostOperator:
     Small problems keep C (computed once from the definition); larger ones
     recompute row blocks on demand, never holding more than one block."""
 
-    def __init__(self, X: np.ndarray, Y: np.ndarray, cache_limit: int = 1 << 24):
+    def __init__(self, X: np.ndarray, Y: np.ndarray, cache_limit: int = 1 << 24, cost=None):
         self.X = np.asarray(X, dtype=np.float64)
         self.Y = np.asarray(Y, dtype=np.float64)
+        self.cost = _cost(cost)
         self.n, self.m = self.X.shape[0], self.Y.shape[0]
         self._full = None
         if self.n * self.m <= cache_limit:
@@ -140,7 +194,7 @@ class CostOperator:
     def _compute_row_blocks(self):
         step = _rows_per_block(self.m, self.X.shape[1])
         for i0 in range(0, self.n, step):
-            yield cost_matrix_rows(self.X[i0:i0 + step], self.Y)
+            yield cost_matrix_rows(self.X[i0:i0 + step], self.Y, self.cost)
 
     def row_blocks(self):
         """Yield (i0, C[i0:i1, :])."""
@@ -149,7 +203,7 @@ class CostOperator:
             return
         step = _rows_per_block(self.m, self.X.shape[1])
         for i0 in range(0, self.n, step):
-            yield i0, cost_matrix_rows(self.X[i0:i0 + step], self.Y)
+            yield i0, cost_matrix_rows(self.X[i0:i0 + step], self.Y, self.cost)
 
     def col_blocks(self):
         """Yield (j0, C[:, j0:j1]^T), i.e. blocks of C^T."""
@@ -158,7 +212,8 @@ class CostOperator:
             return
         step = _rows_per_block(self.n, self.X.shape[1])
         for j0 in range(0, self.m, step):
-            yield j0, cost_matrix_rows(self.Y[j0:j0 + step], self.X)
+            # both costs are even (h(-z) = h(z)), so C^T rows are costs from y_j to X
+            yield j0, cost_matrix_rows(self.Y[j0:j0 + step], self.X, self.cost)
 
 
 def _uniform(k: int) -> np.ndarray:
@@ -227,7 +282,7 @@ class SinkhornResult:
 
 
 def sinkhorn(a, X, b, Y, eps: float, tau: float, f_init=None, g_init=None,
-             max_iter: int = 10000, C: CostOperator | None = None) -> SinkhornResult:
+             max_iter: int = 10000, C: CostOperator | None = None, cost=None) -> SinkhornResult:
     """Sink(a, X, b, Y, eps, tau, f_init, g_init) of Alg. 1.
 
     Potentials start at f_init, g_init (zero by default). While the row-marginal
@@ -242,7 +297,7 @@ def sinkhorn(a, X, b, Y, eps: float, tau: float, f_init=None, g_init=None,
     n, m = X.shape[0], Y.shape[0]
     a = _weights(a, n)
     b = _weights(b, m)
-    C = C if C is not None else CostOperator(X, Y)
+    C = C if C is not None else CostOperator(X, Y, cost=cost)
     f = np.zeros(n) if f_init is None else np.array(f_init, dtype=np.float64)
     g = np.zeros(m) if g_init is None else np.array(g_init, dtype=np.float64)
     it = 0
@@ -270,7 +325,7 @@ def _softmax_rows(L: np.ndarray) -> np.ndarray:
     return E / np.sum(E, axis=1, keepdims=True)
 
 
-def entropic_potential(xq, Y, g, eps: float) -> np.ndarray:
+def entropic_potential(xq, Y, g, eps: float, cost=None) -> np.ndarray:
     """f_hat(x) = min_eps([h(x - y_j) - g_j]_j)   (eq. (6), bracket sign as read)."""
     xq = np.atleast_2d(np.asarray(xq, dtype=np.float64))
     Y = np.asarray(Y, dtype=np.float64)
@@ -278,12 +333,12 @@ def entropic_potential(xq, Y, g, eps: float) -> np.ndarray:
     out = np.empty(xq.shape[0])
     step = _rows_per_block(Y.shape[0], Y.shape[1])
     for i0 in range(0, xq.shape[0], step):
-        S = cost_matrix_rows(xq[i0:i0 + step], Y) - g[None, :]
+        S = cost_matrix_rows(xq[i0:i0 + step], Y, cost) - g[None, :]
         out[i0:i0 + step] = softmin(S, eps)
     return out
 
 
-def entropic_map(xq, Y, g, eps: float) -> np.ndarray:
+def entropic_map(xq, Y, g, eps: float, cost=None) -> np.ndarray:
     """T_hat(x) = x - grad h*(grad f_hat(x))   (eq. (7)).
 
     grad f_hat(x) = sum_j p_j grad h(x - y_j) with p = softmax_j((g_j - h(x - y_j))/eps),
@@ -291,21 +346,22 @@ def entropic_map(xq, Y, g, eps: float) -> np.ndarray:
     xq = np.atleast_2d(np.asarray(xq, dtype=np.float64))
     Y = np.asarray(Y, dtype=np.float64)
     g = np.asarray(g, dtype=np.float64)
+    c = _cost(cost)
     out = np.empty_like(xq)
     step = _rows_per_block(Y.shape[0], Y.shape[1])
     for i0 in range(0, xq.shape[0], step):
         xb = xq[i0:i0 + step]
         diff = xb[:, None, :] - Y[None, :, :]
-        p = _softmax_rows((g[None, :] - h(diff)) / eps)
-        grad_f = np.einsum("ij,ijk->ik", p, grad_h(diff))
-        out[i0:i0 + step] = xb - grad_h_star(grad_f)
+        p = _softmax_rows((g[None, :] - c.h(diff)) / eps)
+        grad_f = np.einsum("ij,ijk->ik", p, c.grad_h(diff))
+        out[i0:i0 + step] = xb - c.grad_h_star(grad_f)
     return out
 
 
 # --------------------------------------------------------------------------
 # Alg. 2: ProgOT.
 # --------------------------------------------------------------------------
-def barycentric_displacement(X, Y, f, g, eps: float, alpha: float) -> np.ndarray:
+def barycentric_displacement(X, Y, f, g, eps: float, alpha: float, cost=None) -> np.ndarray:
     """Q <- diag(1/P 1) P; Z_i = grad h*(sum_j Q_ij grad h(x_i - y_j)); X <- X - alpha Z.
 
     P_ij = exp((f_i + g_j - C_ij)/eps). Row i of Q is P's row i divided by its sum;
@@ -313,13 +369,14 @@ def barycentric_displacement(X, Y, f, g, eps: float, alpha: float) -> np.ndarray
     (f_i + g_j - C_ij)/eps with its maximum factored out (same value, no overflow)."""
     X = np.asarray(X, dtype=np.float64)
     Y = np.asarray(Y, dtype=np.float64)
+    c = _cost(cost)
     out = np.empty_like(X)
     step = _rows_per_block(Y.shape[0], Y.shape[1])
     for i0 in range(0, X.shape[0], step):
         xb = X[i0:i0 + step]
         diff = xb[:, None, :] - Y[None, :, :]
-        Q = _softmax_rows((tensor_sum(f[i0:i0 + step], g) - h(diff)) / eps)
-        Z = grad_h_star(np.einsum("ij,ijk->ik", Q, grad_h(diff)))
+        Q = _softmax_rows((tensor_sum(f[i0:i0 + step], g) - c.h(diff)) / eps)
+        Z = c.grad_h_star(np.einsum("ij,ijk->ik", Q, c.grad_h(diff)))
         out[i0:i0 + step] = xb - alpha * Z
     return out
 
@@ -337,7 +394,7 @@ class ProgOTResult:
     eps_used: list = field(default_factory=list)  # eps_k of each solve
 
 
-def progot(a, X, b, Y, eps_sched, alpha_sched, tau_sched, max_iter: int = 10000) -> ProgOTResult:
+def progot(a, X, b, Y, eps_sched, alpha_sched, tau_sched, max_iter: int = 10000, cost=None) -> ProgOTResult:
     """ProgOT(a, X, b, Y, (eps_k, alpha_k, tau_k)_k) of Alg. 2, K = len(alpha_sched) solves.
 
     f = 0, g^(0) = 0; for k = 1..K: warm start (1 - alpha_k) f, (1 - alpha_k) g^(k-1);
@@ -362,26 +419,27 @@ def progot(a, X, b, Y, eps_sched, alpha_sched, tau_sched, max_iter: int = 10000)
         steps.append(X.copy())
         used.append(eps)
         x_last = X.copy()
-        res = sinkhorn(a, X, b, Y, eps, float(tau_sched[k]), f_init, g_init, max_iter)
+        res = sinkhorn(a, X, b, Y, eps, float(tau_sched[k]), f_init, g_init, max_iter, cost=cost)
         f, g_prev = res.f, res.g
         g_all[k] = res.g
         iters.append(res.iters)
         errs.append(res.err)
         conv.append(res.converged)
-        X = barycentric_displacement(X, Y, f, g_prev, eps, alpha)
+        X = barycentric_displacement(X, Y, f, g_prev, eps, alpha, cost)
     return ProgOTResult(X, g_all, f, x_last, iters, errs, conv, steps, used)
 
 
 # --------------------------------------------------------------------------
 # Alg. 3: the progressive map on new points.
 # --------------------------------------------------------------------------
-def progot_map(xq, Y, g_all, eps_sched, alpha_sched) -> np.ndarray:
+def progot_map(xq, Y, g_all, eps_sched, alpha_sched, cost=None) -> np.ndarray:
     """T_Prog[b, Y, (g^(k), eps_k, alpha_k)_k](x) of Alg. 3 with alpha_K reset to 1.
 
     For each step: p = softmax_j((g^(k)_j - h(y - y_j))/eps_k) (no b_j factor, see the
     module notes), Delta = [grad h(y - y_j)]_j, z = grad h*(p^T Delta), y <- y - alpha_k z."""
     Yt = np.asarray(Y, dtype=np.float64)
     yq = np.array(np.atleast_2d(xq), dtype=np.float64)
+    c = _cost(cost)
     K = len(eps_sched)
     alphas = [float(a) for a in alpha_sched]
     alphas[K - 1] = 1.0
@@ -391,8 +449,8 @@ def progot_map(xq, Y, g_all, eps_sched, alpha_sched) -> np.ndarray:
         for i0 in range(0, yq.shape[0], step):
             yb = yq[i0:i0 + step]
             diff = yb[:, None, :] - Yt[None, :, :]
-            p = _softmax_rows((g[None, :] - h(diff)) / float(eps_sched[k]))
-            z = grad_h_star(np.einsum("ij,ijk->ik", p, grad_h(diff)))
+            p = _softmax_rows((g[None, :] - c.h(diff)) / float(eps_sched[k]))
+            z = c.grad_h_star(np.einsum("ij,ijk->ik", p, c.grad_h(diff)))
             yq[i0:i0 + step] = yb - alphas[k] * z
     return yq
 
@@ -431,9 +489,9 @@ def progress_times(alphas) -> np.ndarray:
 # --------------------------------------------------------------------------
 # Alg. 4: epsilon scheduler.
 # --------------------------------------------------------------------------
-def mean_cost(X, Y) -> float:
+def mean_cost(X, Y, cost=None) -> float:
     """(1/(n m)) sum_ij h(x_i - y_j), summed block by block from the definition."""
-    C = CostOperator(X, Y, cache_limit=0)
+    C = CostOperator(X, Y, cache_limit=0, cost=cost)
     tot = 0.0
     for _, Cb in C.row_blocks():
         tot += float(np.sum(Cb))
@@ -469,9 +527,9 @@ def eps_schedule(X, b, Y, Y_test, alphas, s_grid=None, beta0: float = 5.0, tau: 
 # --------------------------------------------------------------------------
 # Sec. 5.2 coupling metrics and the eq. (5) dual objective.
 # --------------------------------------------------------------------------
-def coupling_cost(X, Y, f, g, eps: float) -> float:
+def coupling_cost(X, Y, f, g, eps: float, cost=None) -> float:
     """<P, C> for P = exp((f (+) g - C)/eps)."""
-    C = CostOperator(X, Y, cache_limit=0)
+    C = CostOperator(X, Y, cache_limit=0, cost=cost)
     tot = 0.0
     for i0, Cb in C.row_blocks():
         P = np.exp((tensor_sum(f[i0:i0 + Cb.shape[0]], g) - Cb) / eps)
@@ -479,9 +537,9 @@ def coupling_cost(X, Y, f, g, eps: float) -> float:
     return tot
 
 
-def coupling_entropy(X, Y, f, g, eps: float) -> float:
+def coupling_entropy(X, Y, f, g, eps: float, cost=None) -> float:
     """E(P) = -sum_ij P_ij (log P_ij - 1)."""
-    C = CostOperator(X, Y, cache_limit=0)
+    C = CostOperator(X, Y, cache_limit=0, cost=cost)
     tot = 0.0
     for i0, Cb in C.row_blocks():
         logP = (tensor_sum(f[i0:i0 + Cb.shape[0]], g) - Cb) / eps
@@ -489,13 +547,13 @@ def coupling_entropy(X, Y, f, g, eps: float) -> float:
     return tot
 
 
-def dual_objective(a, X, b, Y, f, g, eps: float) -> float:
+def dual_objective(a, X, b, Y, f, g, eps: float, cost=None) -> float:
     """<f, a> + <g, b> - eps <e^{f/eps}, K e^{g/eps}>, K_ij = exp(-C_ij/eps)   (eq. (5))."""
     X = np.asarray(X, dtype=np.float64)
     Y = np.asarray(Y, dtype=np.float64)
     a = _weights(a, X.shape[0])
     b = _weights(b, Y.shape[0])
-    C = CostOperator(X, Y, cache_limit=0)
+    C = CostOperator(X, Y, cache_limit=0, cost=cost)
     mass = 0.0
     for i0, Cb in C.row_blocks():
         mass += float(np.sum(np.exp((tensor_sum(f[i0:i0 + Cb.shape[0]], g) - Cb) / eps)))
@@ -505,13 +563,13 @@ def dual_objective(a, X, b, Y, f, g, eps: float) -> float:
 # --------------------------------------------------------------------------
 # Sec. 5.2 (coupling experiments): eps_k = theta cbar_k; Sec. 4: tau_k schedule.
 # --------------------------------------------------------------------------
-def eps_theta_rule(theta: float, Y):
+def eps_theta_rule(theta: float, Y, cost=None):
     """The rule (k, X^(k)) -> theta cbar_k, cbar_k = sum_ij h(x^(k)_i - y_j) / (20 n m),
     for ``progot``'s eps_sched."""
     Yd = np.asarray(Y, dtype=np.float64)
 
     def rule(k, Xk):
-        return float(theta) * mean_cost(Xk, Yd) / 20.0
+        return float(theta) * mean_cost(Xk, Yd, cost) / 20.0
     return rule
 
 
