@@ -362,6 +362,43 @@ int coupling_diagonal(const float* x, const float* y, int64_t n, int32_t d, cons
                       progot_stream_t stream);
 
 /*
+ * The p-norm cost of the coupling experiments (Sec. 5.2): c(x, y) = h(x - y) with
+ * h(z) = (1/p) sum_k |z_k|^p, 1 < p <= 8 (the paper uses p = 1.5, which has a
+ * specialised kernel; other p go through 2^(p log2 |z|)). There is no product form, so
+ * these entry points run on float32 CUDA cores: every pair term is summed coordinate by
+ * coordinate, and the map step evaluates grad h(z)_k = sign(z_k) |z_k|^(p-1) for every
+ * pair and coordinate and moves x by grad h*(w)_k = sign(w_k) |w_k|^(1/(p-1)):
+ *   Z_i = grad h*(sum_j Q_ij grad h(x_i - y_j)), x_i <- x_i - alpha_k Z_i   (Alg. 2, Alg. 3).
+ * The potentials follow the same eq. (5) convention, P_ij = exp((f_i + g_j - c_ij)/eps).
+ * Arguments, layouts, outputs and errors are those of the squared Euclidean entry
+ * points named in each comment, with p added and no precision argument; workspaces as
+ * progot_workspace_size(..., PROGOT_FP32). p outside (1, 8] gives PROGOT_ERR_INVALID_ARG.
+ */
+/* As sinkhorn_potentials. */
+int sinkhorn_potentials_pnorm(const float* x, const float* a, int64_t n, const float* y, const float* b, int64_t m,
+                              int32_t d, double p, double eps, double tau, int32_t max_iter, float* f, float* g,
+                              int32_t init_zero, int32_t* iters_out, double* err_out, void* workspace,
+                              size_t ws_bytes, progot_stream_t stream);
+/* As progot_solve with the eps schedule eps (host, K), or, when eps is NULL, as
+ * progot_solve_theta with eps_k = theta * mean_ij h(x^(k)_i - y_j) / 20, the mean taken
+ * over all n m pairs on the device; eps_out (host, K, may be NULL) receives eps_k. */
+int progot_solve_pnorm(const float* x, const float* a, int64_t n, const float* y, const float* b, int64_t m, int32_t d,
+                       double p, int32_t K, const double* alpha, const double* eps, double theta, const double* tau,
+                       int32_t max_iter, float* x_out, float* g_all, float* f_last, float* x_last, int32_t* iters,
+                       double* errs, double* eps_out, void* workspace, size_t ws_bytes, progot_stream_t stream);
+/* As entropic_map_apply (Alg. 3). */
+int entropic_map_apply_pnorm(const float* xq, int64_t nq, const float* y, int64_t m, int32_t d, double p, int32_t K,
+                             const float* g_all, const double* eps, const double* alpha, float* out, void* workspace,
+                             size_t ws_bytes, progot_stream_t stream);
+/* As coupling_metrics: <P, C> with C_ij = h(x_i - y_j), E(P), the eq. (5) objective. */
+int coupling_metrics_pnorm(const float* x, const float* a, int64_t n, const float* y, const float* b, int64_t m,
+                           int32_t d, double p, const float* f, const float* g, double eps,
+                           progot_coupling_metrics* out, void* workspace, size_t ws_bytes, progot_stream_t stream);
+/* (1/(n m)) sum_ij h(x_i - y_j), summed over all pairs (float64 per CTA, fixed order). out (host). */
+int progot_mean_cost_pnorm(const float* x, int64_t n, const float* y, int64_t m, int32_t d, double p, double* out,
+                           void* workspace, size_t ws_bytes, progot_stream_t stream);
+
+/*
  * progot_set_stall_window - Sinkhorn stops with PROGOT_ERR_NOT_CONVERGED when its
  * marginal error has not fallen below 0.99 x its best value for `iters` consecutive
  * iterations (float32 potentials reach a rounding floor). 0 disables the check.

@@ -398,6 +398,33 @@ static SweepParams make_sweep(const float* A, int64_t nA, const float* B, int64_
   return p;
 }
 
+// The ground cost of a sweep: the squared Euclidean cost (default) or the p-norm cost
+// h(z) = (1/p) sum_k |z_k|^p of the coupling experiments (Sec. 5.2), float32 CUDA cores.
+struct Cost {
+  int32_t kind = kCostSqEuclid;
+  float p = 2.f;
+  bool pnorm() const { return kind != kCostSqEuclid; }
+};
+
+static int pnorm_cost(double p, Cost* c) {
+  if (!(p > 1.0) || !(p <= 8.0))
+    return fail(PROGOT_ERR_INVALID_ARG, "the p-norm cost needs 1 < p <= 8 (got %g)", p);
+  c->kind = (p == 1.5) ? kCostP15 : kCostPGeneral;
+  c->p = (float)p;
+  return PROGOT_OK;
+}
+
+// Switch a sweep built by make_sweep to the p-norm cost: t_ij = (potB_j - h(a_i - b_j))
+// log2(e) / eps, i.e. scale = -log2(e) / (eps p) on sum_k |a_ik - b_jk|^p and no norms.
+static void apply_cost(SweepParams& sp, const Cost& c, double eps) {
+  if (!c.pnorm()) return;
+  sp.cost = c.kind;
+  sp.cost_p = c.p;
+  sp.scale = (float)(-kLog2e / (eps * (double)c.p));
+  sp.An = nullptr;
+  sp.Bn = nullptr;
+}
+
 // Launch one log-sum-exp sweep: float32 CUDA cores, or tcgen05 on the prepared split
 // operands (a_is_x: rows of the sweep are the x cloud).
 static int lse_sweep(const SweepParams& p, int32_t precision, cudaStream_t s, const TcOps* ops = nullptr,
@@ -436,13 +463,19 @@ static int lse_sweep(const SweepParams& p, int32_t precision, cudaStream_t s, co
 static int sinkhorn_core(const float* x, const float* a, int64_t n, const float* y, const float* b, int64_t m,
                          int32_t d, double eps, double tau, int32_t max_iter, int32_t precision, float* f_a, float* f_b,
                          float* g, const float* xn, const float* yn, const Workspace& ws, int32_t* iters_out,
-                         double* err_out, cudaStream_t s, TcOps* ops_out = nullptr, bool symmetric = false) {
+                         double* err_out, cudaStream_t s, TcOps* ops_out = nullptr, bool symmetric = false,
+                         const Cost& cost = Cost()) {
   int rc = t_host.init();
   if (rc) return rc;
   TcOps ops_local;
   TcOps& ops = ops_out ? *ops_out : ops_local;
-  rc = prep_tc(x, n, y, m, d, eps, precision, ws, &ops, s, f_a, symmetric ? f_a : g, xn, yn);
-  if (rc) return rc;
+  if (cost.pnorm()) {
+    ops.on = false;  // the p-norm cost runs on CUDA cores (float32)
+    precision = PROGOT_FP32;
+  } else {
+    rc = prep_tc(x, n, y, m, d, eps, precision, ws, &ops, s, f_a, symmetric ? f_a : g, xn, yn);
+    if (rc) return rc;
+  }
   const int cps = ops.on ? 1 : 2;
   if (ops.on) CK(cudaMemsetAsync(ws.fault, 0, sizeof(int32_t), s));
   CK(launch_init_state(ws.state, s));
@@ -457,6 +490,7 @@ static int sinkhorn_core(const float* x, const float* a, int64_t n, const float*
   pf.state = ws.state;
   pf.tau = tau;
   pf.max_iter = max_iter;
+  apply_cost(pf, cost, eps);
   SweepParams pg = make_sweep(y, m, x, n, d, yn, xn, eps, ws, cps);
   pg.wA = b;
   pg.potB = f_a;
@@ -467,6 +501,7 @@ static int sinkhorn_core(const float* x, const float* a, int64_t n, const float*
   pg.state = ws.state;
   pg.tau = tau;
   pg.max_iter = max_iter;
+  apply_cost(pg, cost, eps);
 
   int64_t sym_sweeps = 0;
   auto enqueue = [&](int iters) -> int {
@@ -575,12 +610,13 @@ static int sinkhorn_core(const float* x, const float* a, int64_t n, const float*
 // L only has to be close to the row's log-sum-exp.
 static int map_step(float* X, int64_t n, const float* y, int64_t m, int32_t d, const float* g, const float* yn,
                     double eps, double alpha, int32_t precision, const Workspace& ws, cudaStream_t s,
-                    const TcOps* ops = nullptr) {
-  const bool tc = ops != nullptr && ops->on;
+                    const TcOps* ops = nullptr, const Cost& cost = Cost()) {
+  const bool tc = !cost.pnorm() && ops != nullptr && ops->on;
   SweepParams pl = make_sweep(X, n, y, m, d, nullptr, yn, eps, ws, tc ? 1 : 2);
   pl.potB = g;
   pl.out = ws.L;
   pl.mode = kModeLse;
+  apply_cost(pl, cost, eps);
   int rc = tc ? lse_sweep(pl, precision, s, ops, true, &ws) : lse_sweep(pl, PROGOT_FP32, s);
   if (rc) return rc;
   MapParams mp;
@@ -605,9 +641,17 @@ static int map_step(float* X, int64_t n, const float* y, int64_t m, int32_t d, c
   mp.scale = (float)(2.0 * kLog2e / eps);
   mp.bscale = (float)(kLog2e / eps);
   mp.alpha = (float)alpha;
+  if (cost.pnorm()) {
+    mp.cost = cost.kind;
+    mp.cost_p = cost.p;
+    mp.scale = (float)(-kLog2e / (eps * (double)cost.p));
+  }
   ProfRec r;
   const bool rec = prof_begin(r, s, kProfMap);
-  CK(launch_map_sweep_fp32(mp, s));
+  if (cost.pnorm())
+    CK(launch_map_sweep_pnorm(mp, s));
+  else
+    CK(launch_map_sweep_fp32(mp, s));
   if (rec) prof_end(r, s, kProfMap, (double)n * (double)m);
   if (t_prof.on) t_prof.worked[kProfMap] += 1;
   return PROGOT_OK;
@@ -625,7 +669,7 @@ static int zero_counters(const Workspace& ws, int64_t rbmax, cudaStream_t s) {
 // arrival counters must be zero.
 static int metrics_core(const float* x, const float* a, int64_t n, const float* y, const float* b, int64_t m,
                         int32_t d, const float* f, const float* g, double eps, const Workspace& ws, cudaStream_t s,
-                        progot_coupling_metrics* out) {
+                        progot_coupling_metrics* out, const Cost& cost = Cost()) {
   int rc = t_host.init();
   if (rc) return rc;
   SweepParams pr = make_sweep(x, n, y, m, d, ws.xn, ws.yn, eps, ws);
@@ -633,6 +677,7 @@ static int metrics_core(const float* x, const float* a, int64_t n, const float* 
   pr.potB = g;
   pr.potA_old = f;
   pr.mode = kModeMetrics;
+  apply_cost(pr, cost, eps);
   CK(launch_lse_sweep_fp32(pr, s));
   CK(launch_sum_parts(ws.metpart, (int)cdiv(n, fp32_tile_rows()), kMetricSums, ws.metout, s));
   SweepParams pc = make_sweep(y, m, x, n, d, ws.yn, ws.xn, eps, ws);
@@ -640,6 +685,7 @@ static int metrics_core(const float* x, const float* a, int64_t n, const float* 
   pc.potB = f;
   pc.potA_old = g;
   pc.mode = kModeMetrics;
+  apply_cost(pc, cost, eps);
   CK(launch_lse_sweep_fp32(pc, s));
   CK(launch_sum_parts(ws.metpart, (int)cdiv(m, fp32_tile_rows()), kMetricSums, ws.metout + kMetricSums, s));
   CK(cudaMemcpyAsync(t_host.hd, ws.metout, sizeof(double) * 2 * kMetricSums, cudaMemcpyDeviceToHost, s));
@@ -660,9 +706,18 @@ static int metrics_core(const float* x, const float* a, int64_t n, const float* 
 // Mean cost of (x, y) in closed form from float64 first moments, computed on the device;
 // the y moments must already sit at ws.rout + (d + 1) when y_ready.
 static int mean_cost_dev(const float* x, int64_t n, const float* y, int64_t m, int32_t d, const Workspace& ws,
-                         bool y_ready, cudaStream_t s, double* out) {
+                         bool y_ready, cudaStream_t s, double* out, const Cost& cost = Cost()) {
   int rc = t_host.init();
   if (rc) return rc;
+  if (cost.pnorm()) {
+    // no closed form: sum h over all n m pairs on the CUDA cores
+    double* dst = ws.metout + 2 * kMetricSums;
+    CK(launch_pairwise_cost_sum(x, n, y, m, d, cost.kind, cost.p, ws.rpart, dst, s));
+    CK(cudaMemcpyAsync(t_host.hd, dst, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *out = t_host.hd[0] / ((double)cost.p * (double)n * (double)m);
+    return PROGOT_OK;
+  }
   CK(launch_moments(x, n, d, ws.rpart, reduce_parts(), ws.rout, s));
   if (!y_ready) CK(launch_moments(y, m, d, ws.rpart, reduce_parts(), ws.rout + (d + 1), s));
   double* dst = ws.metout + 2 * kMetricSums;
@@ -679,7 +734,7 @@ static int solve_impl(const float* x, const float* a, int64_t n, const float* y,
                       int32_t K, const double* alpha, const double* eps, double theta, const double* tau,
                       int32_t max_iter, int32_t precision, float* x_out, float* g_all, float* f_last, float* x_last,
                       int32_t* iters, double* errs, double* eps_out, void* workspace, size_t ws_bytes,
-                      cudaStream_t s) {
+                      cudaStream_t s, const Cost& cost = Cost()) {
   Workspace ws;
   int rc = carve(n, m, d, workspace, ws_bytes, &ws, precision);
   if (rc) return rc;
@@ -688,7 +743,7 @@ static int solve_impl(const float* x, const float* a, int64_t n, const float* y,
   if (x_out != x) CK(cudaMemcpyAsync(x_out, x, sizeof(float) * n * d, cudaMemcpyDeviceToDevice, s));
   CK(launch_row_sqnorm(y, m, d, ws.yn, s));
   CK(cudaMemsetAsync(ws.f0, 0, sizeof(float) * n, s));
-  if (eps == nullptr) CK(launch_moments(y, m, d, ws.rpart, reduce_parts(), ws.rout + (d + 1), s));
+  if (eps == nullptr && !cost.pnorm()) CK(launch_moments(y, m, d, ws.rpart, reduce_parts(), ws.rout + (d + 1), s));
   int worst = PROGOT_OK;
   std::string worst_msg;
   for (int k = 0; k < K; ++k) {
@@ -709,7 +764,7 @@ static int solve_impl(const float* x, const float* a, int64_t n, const float* y,
       eps_k = eps[k];
     } else {
       double cbar = 0.0;
-      rc = mean_cost_dev(x_out, n, y, m, d, ws, true, s, &cbar);
+      rc = mean_cost_dev(x_out, n, y, m, d, ws, true, s, &cbar, cost);
       if (rc) return rc;
       eps_k = theta * cbar / 20.0;
       if (!(eps_k > 0.0) || !std::isfinite(eps_k))
@@ -721,7 +776,7 @@ static int solve_impl(const float* x, const float* a, int64_t n, const float* y,
     double err = 0.0;
     TcOps ops;
     rc = sinkhorn_core(x_out, a, n, y, b, m, d, eps_k, tau[k], max_iter, precision, ws.f0, ws.f1, gk, ws.xn, ws.yn,
-                       ws, &it, &err, s, &ops);
+                       ws, &it, &err, s, &ops, false, cost);
     if (iters) iters[k] = it;
     if (errs) errs[k] = err;
     if (rc == PROGOT_ERR_NOT_CONVERGED) {
@@ -732,7 +787,7 @@ static int solve_impl(const float* x, const float* a, int64_t n, const float* y,
     } else if (rc) {
       return rc;
     }
-    rc = map_step(x_out, n, y, m, d, gk, ws.yn, eps_k, alpha[k], precision, ws, s, &ops);
+    rc = map_step(x_out, n, y, m, d, gk, ws.yn, eps_k, alpha[k], precision, ws, s, &ops, cost);
     if (rc) return rc;
   }
   if (f_last) CK(cudaMemcpyAsync(f_last, ws.f0, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
@@ -1053,6 +1108,126 @@ int coupling_diagonal(const float* x, const float* y, int64_t n, int32_t d, cons
   if (trace) *trace = t_host.hd[0];
   if (kl) *kl = -std::log((double)n) - t_host.hd[1] / (double)n;
   return PROGOT_OK;
+}
+
+int sinkhorn_potentials_pnorm(const float* x, const float* a, int64_t n, const float* y, const float* b, int64_t m,
+                              int32_t d, double p, double eps, double tau, int32_t max_iter, float* f, float* g,
+                              int32_t init_zero, int32_t* iters_out, double* err_out, void* workspace,
+                              size_t ws_bytes, progot_stream_t stream) {
+  t_last_error.clear();
+  int rc = check_common(x, n, y, m, d, PROGOT_FP32);
+  if (rc) return rc;
+  Cost cost;
+  rc = pnorm_cost(p, &cost);
+  if (rc) return rc;
+  if (f == nullptr || g == nullptr) return fail(PROGOT_ERR_INVALID_ARG, "f and g must not be NULL");
+  if (!(eps > 0.0) || !std::isfinite(eps)) return fail(PROGOT_ERR_INVALID_ARG, "eps must be positive and finite");
+  if (!(tau >= 0.0)) return fail(PROGOT_ERR_INVALID_ARG, "tau must be >= 0");
+  if (max_iter < 0) return fail(PROGOT_ERR_INVALID_ARG, "max_iter must be >= 0");
+  Workspace ws;
+  rc = carve(n, m, d, workspace, ws_bytes, &ws);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  rc = zero_counters(ws, ws_dims(n, m, d).rbmax, s);
+  if (rc) return rc;
+  if (init_zero) {
+    CK(cudaMemsetAsync(f, 0, sizeof(float) * n, s));
+    CK(cudaMemsetAsync(g, 0, sizeof(float) * m, s));
+  }
+  return sinkhorn_core(x, a, n, y, b, m, d, eps, tau, max_iter, PROGOT_FP32, f, ws.f1, g, ws.xn, ws.yn, ws, iters_out,
+                       err_out, s, nullptr, false, cost);
+}
+
+int progot_solve_pnorm(const float* x, const float* a, int64_t n, const float* y, const float* b, int64_t m, int32_t d,
+                       double p, int32_t K, const double* alpha, const double* eps, double theta, const double* tau,
+                       int32_t max_iter, float* x_out, float* g_all, float* f_last, float* x_last, int32_t* iters,
+                       double* errs, double* eps_out, void* workspace, size_t ws_bytes, progot_stream_t stream) {
+  t_last_error.clear();
+  int rc = check_common(x, n, y, m, d, PROGOT_FP32);
+  if (rc) return rc;
+  Cost cost;
+  rc = pnorm_cost(p, &cost);
+  if (rc) return rc;
+  if (K <= 0 || alpha == nullptr || tau == nullptr || x_out == nullptr || g_all == nullptr)
+    return fail(PROGOT_ERR_INVALID_ARG, "K > 0 and non-NULL alpha, tau, x_out, g_all are required");
+  if (eps == nullptr && (!(theta > 0.0) || !std::isfinite(theta)))
+    return fail(PROGOT_ERR_INVALID_ARG, "without an eps schedule theta must be positive and finite");
+  if (max_iter < 0) return fail(PROGOT_ERR_INVALID_ARG, "max_iter must be >= 0");
+  for (int k = 0; k < K; ++k) {
+    if (eps != nullptr && (!(eps[k] > 0.0) || !std::isfinite(eps[k])))
+      return fail(PROGOT_ERR_INVALID_ARG, "eps[%d] must be positive", k);
+    if (!(alpha[k] > 0.0 && alpha[k] <= 1.0)) return fail(PROGOT_ERR_INVALID_ARG, "alpha[%d] must lie in (0, 1]", k);
+    if (!(tau[k] >= 0.0)) return fail(PROGOT_ERR_INVALID_ARG, "tau[%d] must be >= 0", k);
+  }
+  return solve_impl(x, a, n, y, b, m, d, K, alpha, eps, theta, tau, max_iter, PROGOT_FP32, x_out, g_all, f_last,
+                    x_last, iters, errs, eps_out, workspace, ws_bytes, (cudaStream_t)stream, cost);
+}
+
+int entropic_map_apply_pnorm(const float* xq, int64_t nq, const float* y, int64_t m, int32_t d, double p, int32_t K,
+                             const float* g_all, const double* eps, const double* alpha, float* out, void* workspace,
+                             size_t ws_bytes, progot_stream_t stream) {
+  t_last_error.clear();
+  int rc = check_common(xq, nq, y, m, d, PROGOT_FP32);
+  if (rc) return rc;
+  Cost cost;
+  rc = pnorm_cost(p, &cost);
+  if (rc) return rc;
+  if (K <= 0 || g_all == nullptr || eps == nullptr || alpha == nullptr || out == nullptr)
+    return fail(PROGOT_ERR_INVALID_ARG, "K > 0 and non-NULL g_all, eps, alpha, out are required");
+  for (int k = 0; k < K; ++k) {
+    if (!(eps[k] > 0.0) || !std::isfinite(eps[k])) return fail(PROGOT_ERR_INVALID_ARG, "eps[%d] must be positive", k);
+    if (k < K - 1 && !(alpha[k] > 0.0 && alpha[k] <= 1.0))
+      return fail(PROGOT_ERR_INVALID_ARG, "alpha[%d] must lie in (0, 1]", k);
+  }
+  Workspace ws;
+  rc = carve(nq, m, d, workspace, ws_bytes, &ws);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  rc = zero_counters(ws, ws_dims(nq, m, d).rbmax, s);
+  if (rc) return rc;
+  if (out != xq) CK(cudaMemcpyAsync(out, xq, sizeof(float) * nq * d, cudaMemcpyDeviceToDevice, s));
+  for (int k = 0; k < K; ++k) {
+    const double al = (k == K - 1) ? 1.0 : alpha[k];
+    rc = map_step(out, nq, y, m, d, g_all + (int64_t)k * m, ws.yn, eps[k], al, PROGOT_FP32, ws, s, nullptr, cost);
+    if (rc) return rc;
+  }
+  return PROGOT_OK;
+}
+
+int coupling_metrics_pnorm(const float* x, const float* a, int64_t n, const float* y, const float* b, int64_t m,
+                           int32_t d, double p, const float* f, const float* g, double eps,
+                           progot_coupling_metrics* out, void* workspace, size_t ws_bytes, progot_stream_t stream) {
+  t_last_error.clear();
+  int rc = check_common(x, n, y, m, d, PROGOT_FP32);
+  if (rc) return rc;
+  Cost cost;
+  rc = pnorm_cost(p, &cost);
+  if (rc) return rc;
+  if (f == nullptr || g == nullptr || out == nullptr)
+    return fail(PROGOT_ERR_INVALID_ARG, "f, g and out must not be NULL");
+  if (!(eps > 0.0) || !std::isfinite(eps)) return fail(PROGOT_ERR_INVALID_ARG, "eps must be positive and finite");
+  Workspace ws;
+  rc = carve(n, m, d, workspace, ws_bytes, &ws);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  rc = zero_counters(ws, ws_dims(n, m, d).rbmax, s);
+  if (rc) return rc;
+  return metrics_core(x, a, n, y, b, m, d, f, g, eps, ws, s, out, cost);
+}
+
+int progot_mean_cost_pnorm(const float* x, int64_t n, const float* y, int64_t m, int32_t d, double p, double* out,
+                           void* workspace, size_t ws_bytes, progot_stream_t stream) {
+  t_last_error.clear();
+  int rc = check_common(x, n, y, m, d, PROGOT_FP32);
+  if (rc) return rc;
+  Cost cost;
+  rc = pnorm_cost(p, &cost);
+  if (rc) return rc;
+  if (out == nullptr) return fail(PROGOT_ERR_INVALID_ARG, "out must not be NULL");
+  Workspace ws;
+  rc = carve(n, m, d, workspace, ws_bytes, &ws);
+  if (rc) return rc;
+  return mean_cost_dev(x, n, y, m, d, ws, false, (cudaStream_t)stream, out, cost);
 }
 
 int progot_schedule_alpha(int32_t K, int32_t kind, double* out) {

@@ -78,7 +78,15 @@ struct SweepParams {
   double tau;
   double inv_nA;       // uniform weight 1/nA
   double log_w_uniform;  // log(1/nA)
+  int32_t cost;        // CostKind: kCostSqEuclid uses scale * (a . b) + bscale (potB - |b|^2);
+                       // the p-norm costs use scale * sum_k |a_k - b_k|^p + bscale potB
+  float cost_p;        // p of the p-norm cost
 };
+
+// Cost of the sweeps. kCostSqEuclid: |x - y|^2 through the dot product (tensor cores or
+// float32 FMAs); the p-norm cost h(z) = (1/p) sum_k |z_k|^p (Sec. 5.2) on CUDA cores,
+// with p = 1.5 (|z| sqrt|z|) specialised.
+enum CostKind : int32_t { kCostSqEuclid = 0, kCostP15 = 1, kCostPGeneral = 2 };
 
 // Combine two partial log-sum-exps (max, sum) in log2 units.
 __device__ __forceinline__ float2 lse_combine(float2 p, float2 q) {

@@ -24,6 +24,8 @@ struct MapParams {
   int32_t splits, tiles_per_split, dchunks;
   float scale, bscale;
   float alpha;
+  int32_t cost;        // CostKind (the p-norm map moves x by grad h*(sum_j Q_ij grad h(x - y_j)))
+  float cost_p;
 };
 
 void count_launch();
@@ -33,6 +35,12 @@ void set_last_error_message(const char* msg);
 // float32 CUDA-core sweeps (sweep_fp32.cu)
 cudaError_t launch_lse_sweep_fp32(const SweepParams& p, cudaStream_t stream);
 cudaError_t launch_map_sweep_fp32(const MapParams& p, cudaStream_t stream);
+// p-norm cost: barycentric displacement x <- x - alpha grad h*(sum_j Q_ij grad h(x_i - y_j))
+cudaError_t launch_map_sweep_pnorm(const MapParams& p, cudaStream_t stream);
+// out[0] = sum_ij h(x_i - y_j) for the p-norm cost (float64, fixed order; partial holds
+// reduce_parts() doubles)
+cudaError_t launch_pairwise_cost_sum(const float* X, int64_t n, const float* Y, int64_t m, int32_t d, int32_t cost,
+                                     float cost_p, double* partial, double* out, cudaStream_t s);
 int fp32_tile_rows();
 int fp32_tile_cols();
 int map_dchunk();

@@ -72,11 +72,35 @@ struct GemmSmem {
   float Bs[2][BK][BN];
 };
 
-// acc[r][c] = a_row(r) . b_col(c) for the thread's 8 x 8 block of a 128 x 128 tile.
-// Rows of the thread: ty*4 + {0..3} and 64 + ty*4 + {0..3}; columns likewise with tx.
-__device__ __forceinline__ void tile_dots(GemmSmem& sm, const float* __restrict__ A, int64_t nA,
-                                          const float* __restrict__ B, int64_t nB, int d, int64_t row0,
-                                          int64_t col0, bool vec_ok, float (&acc)[8][8]) {
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// One coordinate's contribution to the pair term of the sweep: a . b for the squared
+// Euclidean cost (the norms enter through the bias), |a - b|^p for the p-norm costs.
+template <int kCost>
+__device__ __forceinline__ float pair_term(float a, float b, float acc, float cp) {
+  if constexpr (kCost == kCostSqEuclid) {
+    return fmaf(a, b, acc);
+  } else if constexpr (kCost == kCostP15) {
+    const float z = fabsf(a - b);
+    return fmaf(z, sqrt_approx(z), acc);
+  } else {
+    const float z = fabsf(a - b);  // |z|^p = 2^(p log2 |z|); z = 0 gives 2^-inf = 0
+    return acc + fast_exp2(cp * __log2f(z));
+  }
+}
+
+// acc[r][c] = sum_k pair_term(a_row(r)_k, b_col(c)_k) for the thread's 8 x 8 block of a
+// 128 x 128 tile (a_row . b_col for the squared Euclidean cost). Rows of the thread:
+// ty*4 + {0..3} and 64 + ty*4 + {0..3}; columns likewise with tx. Coordinates beyond d
+// are zero on both sides and add nothing.
+template <int kCost>
+__device__ __forceinline__ void tile_accumulate(GemmSmem& sm, const float* __restrict__ A, int64_t nA,
+                                                const float* __restrict__ B, int64_t nB, int d, int64_t row0,
+                                                int64_t col0, bool vec_ok, float cp, float (&acc)[8][8]) {
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
   for (int r = 0; r < 8; ++r)
@@ -107,7 +131,7 @@ __device__ __forceinline__ void tile_dots(GemmSmem& sm, const float* __restrict_
 #pragma unroll
       for (int r = 0; r < 8; ++r)
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
+        for (int c = 0; c < 8; ++c) acc[r][c] = pair_term<kCost>(av[r], bv[c], acc[r][c], cp);
     }
     if (kc + 1 < nk) {
       la.store(sm.As[buf ^ 1]);
@@ -115,6 +139,12 @@ __device__ __forceinline__ void tile_dots(GemmSmem& sm, const float* __restrict_
     }
     __syncthreads();
   }
+}
+
+__device__ __forceinline__ void tile_dots(GemmSmem& sm, const float* __restrict__ A, int64_t nA,
+                                          const float* __restrict__ B, int64_t nB, int d, int64_t row0,
+                                          int64_t col0, bool vec_ok, float (&acc)[8][8]) {
+  tile_accumulate<kCostSqEuclid>(sm, A, nA, B, nB, d, row0, col0, vec_ok, 0.f, acc);
 }
 
 __device__ __forceinline__ int thread_row(int r) {  // 0..127
@@ -147,7 +177,8 @@ __device__ __forceinline__ float3 tilt_combine(float3 p, float3 q) {
 }
 
 // kTilt adds the tilted sum W per row (coupling metrics); otherwise the plain sweep.
-template <bool kTilt>
+// kCost selects the pair term (the squared Euclidean dot product or a p-norm cost).
+template <bool kTilt, int kCost>
 __global__ void __launch_bounds__(NT, 2) lse_sweep_fp32(SweepParams p) {
   if (p.state != nullptr && p.state->done) return;
   __shared__ GemmSmem sm;
@@ -178,9 +209,13 @@ __global__ void __launch_bounds__(NT, 2) lse_sweep_fp32(SweepParams p) {
     __syncthreads();  // beta_s of the previous tile is no longer read
     if (threadIdx.x < BN) {
       const int64_t j = col0 + threadIdx.x;
-      beta_s[threadIdx.x] = (j < p.nB) ? (potB[j] - p.Bn[j]) * p.bscale : -INFINITY;
+      float bn = 0.f;  // |b_j|^2 enters only the squared Euclidean bias (Bn is NULL otherwise)
+      if constexpr (kCost == kCostSqEuclid) {
+        if (j < p.nB) bn = p.Bn[j];
+      }
+      beta_s[threadIdx.x] = (j < p.nB) ? (potB[j] - bn) * p.bscale : -INFINITY;
     }
-    tile_dots(sm, p.A, p.nA, p.B, p.nB, p.d, row0, col0, vec_ok, acc);  // ends with __syncthreads
+    tile_accumulate<kCost>(sm, p.A, p.nA, p.B, p.nB, p.d, row0, col0, vec_ok, p.cost_p, acc);  // ends with a sync
     float bcol[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) bcol[c] = beta_s[thread_col(c)];
@@ -468,13 +503,221 @@ __global__ void __launch_bounds__(NT, 1) map_sweep_fp32(MapParams p) {
 }
 
 // ---------------------------------------------------------------- launchers
+// ------------------------------------------------------- p-norm map and cost sum
+// grad h of the p-norm cost, one coordinate: sign(z) |z|^(p-1).
+template <int kCost>
+__device__ __forceinline__ float grad_h_coord(float z, float cp) {
+  const float az = fabsf(z);
+  if constexpr (kCost == kCostP15) {
+    return copysignf(sqrt_approx(az), z);
+  } else {
+    return copysignf(fast_exp2((cp - 1.f) * __log2f(az)), z);
+  }
+}
+
+// grad h* of the p-norm cost, one coordinate: sign(w) |w|^(1/(p-1)).
+template <int kCost>
+__device__ __forceinline__ float grad_h_star_coord(float w, float cp) {
+  const float aw = fabsf(w);
+  if constexpr (kCost == kCostP15) {
+    return w * aw;
+  } else {
+    return copysignf(exp2f(__log2f(aw) / (cp - 1.f)), w);
+  }
+}
+
+// The barycentric displacement of Alg. 2 / Alg. 3 for the p-norm cost: with L_i known,
+// Q_ij = 2^{t_ij - L_i} / sum_j 2^{t_ij - L_i}, t_ij = (g_j - h(x_i - y_j)) log2(e) / eps,
+//   Z_i = grad h*(sum_j Q_ij grad h(x_i - y_j)),  x_i <- x_i - alpha Z_i.
+// Unlike the squared Euclidean map the inner sum is not a product with Y: each thread
+// evaluates grad h(x_ik - y_jk) for its 8 rows x 4 coordinates against every column of
+// the tile (CUDA cores, one square root per term for p = 1.5). The cost tile, the P
+// tile, the column splits and the last-CTA combine follow map_sweep_fp32.
+template <int kCost>
+__global__ void __launch_bounds__(NT, 1) map_sweep_pnorm(MapParams p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  MapSmem& sm = *reinterpret_cast<MapSmem*>(smem_raw);
+  __shared__ float beta_s[BN];
+  __shared__ float Lrow[BM];
+  __shared__ float den[BM];
+  __shared__ int s_last;
+
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t row0 = (int64_t)blockIdx.x * BM;
+  const int dch0 = blockIdx.z * DCH;
+  const int ntiles = (int)((p.nB + BN - 1) / BN);
+  const int t_begin = blockIdx.y * p.tiles_per_split;
+  const int t_end = min(ntiles, t_begin + p.tiles_per_split);
+  const bool vec_ok = ((p.d & 3) == 0) && ((reinterpret_cast<uintptr_t>(p.A) & 15) == 0) &&
+                      ((reinterpret_cast<uintptr_t>(p.B) & 15) == 0);
+  if (threadIdx.x < BM) {
+    const int64_t i = row0 + threadIdx.x;
+    Lrow[threadIdx.x] = (i < p.nA) ? p.L[i] : 0.f;
+  }
+  // this thread's coordinates of its rows (zero outside the cloud and beyond d)
+  float xv[8][4];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int64_t i = row0 + thread_row(r);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int kk = dch0 + tx * 4 + k;
+      xv[r][k] = (i < p.nA && kk < p.d) ? p.A[i * (int64_t)p.d + kk] : 0.f;
+    }
+  }
+  float o[8][4];
+  float rs[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    rs[r] = 0.f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) o[r][c] = 0.f;
+  }
+  float acc[8][8];
+  for (int tile = t_begin; tile < t_end; ++tile) {
+    const int64_t col0 = (int64_t)tile * BN;
+    __syncthreads();  // the previous tile's Ps / Ys / beta_s are no longer read
+    if (threadIdx.x < BN) {
+      const int64_t j = col0 + threadIdx.x;
+      beta_s[threadIdx.x] = (j < p.nB) ? p.potB[j] * p.bscale : -INFINITY;
+    }
+    for (int e = threadIdx.x; e < BN * DCH; e += NT) {
+      const int c = e / DCH, k = e % DCH;
+      const int64_t j = col0 + c;
+      const int kk = dch0 + k;
+      sm.Ys[c][k] = (j < p.nB && kk < p.d) ? __ldg(p.B + j * (int64_t)p.d + kk) : 0.f;
+    }
+    tile_accumulate<kCost>(sm.g, p.A, p.nA, p.B, p.nB, p.d, row0, col0, vec_ok, p.cost_p, acc);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int rr = thread_row(r);
+      const float Lr = Lrow[rr];
+      float part = 0.f;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int cc = thread_col(c);
+        const float pv = fast_exp2(fmaf(acc[r][c], p.scale, beta_s[cc]) - Lr);
+        sm.Ps[cc][rr] = pv;
+        part += pv;
+      }
+      rs[r] += part;
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int c = 0; c < BN; ++c) {
+      const float4 p0 = *reinterpret_cast<const float4*>(&sm.Ps[c][ty * 4]);
+      const float4 p1 = *reinterpret_cast<const float4*>(&sm.Ps[c][64 + ty * 4]);
+      const float4 yv = *reinterpret_cast<const float4*>(&sm.Ys[c][tx * 4]);
+      const float pr[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+      const float yk[4] = {yv.x, yv.y, yv.z, yv.w};
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) o[r][k] = fmaf(pr[r], grad_h_coord<kCost>(xv[r][k] - yk[k], p.cost_p), o[r][k]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    float v = rs[r];
+#pragma unroll
+    for (int off = 8; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    rs[r] = v;
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int64_t i = row0 + thread_row(r);
+    if (i >= p.nA) continue;
+    float* dst = p.Opart + ((int64_t)blockIdx.y * p.nA + i) * p.d;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int kk = dch0 + tx * 4 + k;
+      if (kk < p.d) dst[kk] = o[r][k];
+    }
+    if (blockIdx.z == 0 && tx == 0) p.Rpart[(int64_t)blockIdx.y * p.nA + i] = rs[r];
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(&p.cnt[blockIdx.x], 1u);
+    s_last = (prev == (unsigned)(p.splits * p.dchunks - 1));
+  }
+  __syncthreads();
+  if (!s_last) return;
+  // ---- last CTA of this row block: Z_i = grad h*(sum_s O_s / sum_s R_s), x <- x - alpha Z
+  if (threadIdx.x < BM) {
+    const int64_t i = row0 + threadIdx.x;
+    float dsum = 0.f;
+    if (i < p.nA)
+      for (int s = 0; s < p.splits; ++s) dsum += __ldcg(p.Rpart + (int64_t)s * p.nA + i);
+    den[threadIdx.x] = dsum;
+  }
+  __syncthreads();
+  const int64_t rem = p.nA - row0;
+  const int rows = rem < BM ? (int)rem : BM;
+  for (int e = threadIdx.x; e < rows * p.d; e += NT) {
+    const int r = e / p.d, k = e % p.d;
+    const int64_t i = row0 + r;
+    float num = 0.f;
+    for (int s = 0; s < p.splits; ++s) num += __ldcg(p.Opart + ((int64_t)s * p.nA + i) * p.d + k);
+    const float Z = grad_h_star_coord<kCost>(num / den[r], p.cost_p);
+    const float x = p.A[i * (int64_t)p.d + k];
+    p.out[i * (int64_t)p.d + k] = fmaf(-p.alpha, Z, x);
+  }
+  if (threadIdx.x == 0) p.cnt[blockIdx.x] = 0;
+}
+
+// Sum over all pairs of sum_k |x_ik - y_jk|^p (float64 per thread and per CTA, fixed
+// order): gridDim.x CTAs stride over the 128 x 128 tiles.
+template <int kCost>
+__global__ void __launch_bounds__(NT, 2) pairwise_cost_sum(const float* __restrict__ X, int64_t n,
+                                                           const float* __restrict__ Y, int64_t m, int32_t d,
+                                                           float cp, double* __restrict__ partial) {
+  __shared__ GemmSmem sm;
+  __shared__ double red[NT / 32];
+  const int64_t rb = (n + BM - 1) / BM, ct = (m + BN - 1) / BN;
+  const bool vec_ok = ((d & 3) == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0) &&
+                      ((reinterpret_cast<uintptr_t>(Y) & 15) == 0);
+  double tot = 0.0;
+  float acc[8][8];
+  for (int64_t w = blockIdx.x; w < rb * ct; w += gridDim.x) {
+    const int64_t row0 = (w / ct) * BM, col0 = (w % ct) * BN;
+    tile_accumulate<kCost>(sm, X, n, Y, m, d, row0, col0, vec_ok, cp, acc);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int64_t i = row0 + thread_row(r);
+      float part = 0.f;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int64_t j = col0 + thread_col(c);
+        if (i < n && j < m) part += acc[r][c];
+      }
+      tot += (double)part;
+    }
+  }
+  const double b = block_sum_f64<NT>(tot, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = b;
+}
+
 cudaError_t launch_lse_sweep_fp32(const SweepParams& p, cudaStream_t stream) {
   const int rb = (int)((p.nA + BM - 1) / BM);
   dim3 grid(rb, p.splits);
-  if (p.mode == kModeMetrics)
-    lse_sweep_fp32<true><<<grid, NT, 0, stream>>>(p);
-  else
-    lse_sweep_fp32<false><<<grid, NT, 0, stream>>>(p);
+  const bool tilt = p.mode == kModeMetrics;
+  if (p.cost == kCostP15) {
+    if (tilt)
+      lse_sweep_fp32<true, kCostP15><<<grid, NT, 0, stream>>>(p);
+    else
+      lse_sweep_fp32<false, kCostP15><<<grid, NT, 0, stream>>>(p);
+  } else if (p.cost == kCostPGeneral) {
+    if (tilt)
+      lse_sweep_fp32<true, kCostPGeneral><<<grid, NT, 0, stream>>>(p);
+    else
+      lse_sweep_fp32<false, kCostPGeneral><<<grid, NT, 0, stream>>>(p);
+  } else {
+    if (tilt)
+      lse_sweep_fp32<true, kCostSqEuclid><<<grid, NT, 0, stream>>>(p);
+    else
+      lse_sweep_fp32<false, kCostSqEuclid><<<grid, NT, 0, stream>>>(p);
+  }
   count_launch();
   return cudaGetLastError();
 }
@@ -494,6 +737,39 @@ cudaError_t launch_map_sweep_fp32(const MapParams& p, cudaStream_t stream) {
   map_sweep_fp32<<<grid, NT, smem, stream>>>(p);
   count_launch();
   return cudaGetLastError();
+}
+
+template <int kCost>
+static cudaError_t launch_map_pnorm_k(const MapParams& p, cudaStream_t stream) {
+  static thread_local bool attr_set = false;
+  const size_t smem = sizeof(MapSmem);
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(map_sweep_pnorm<kCost>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int rb = (int)((p.nA + BM - 1) / BM);
+  dim3 grid(rb, p.splits, p.dchunks);
+  map_sweep_pnorm<kCost><<<grid, NT, smem, stream>>>(p);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_map_sweep_pnorm(const MapParams& p, cudaStream_t stream) {
+  return p.cost == kCostP15 ? launch_map_pnorm_k<kCostP15>(p, stream) : launch_map_pnorm_k<kCostPGeneral>(p, stream);
+}
+
+cudaError_t launch_pairwise_cost_sum(const float* X, int64_t n, const float* Y, int64_t m, int32_t d, int32_t cost,
+                                     float cost_p, double* partial, double* out, cudaStream_t s) {
+  const int parts = reduce_parts();
+  if (cost == kCostP15)
+    pairwise_cost_sum<kCostP15><<<parts, NT, 0, s>>>(X, n, Y, m, d, cost_p, partial);
+  else
+    pairwise_cost_sum<kCostPGeneral><<<parts, NT, 0, s>>>(X, n, Y, m, d, cost_p, partial);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_sum_parts(partial, parts, 1, out, s);
 }
 
 int fp32_tile_rows() { return BM; }

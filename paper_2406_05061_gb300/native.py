@@ -69,6 +69,13 @@ SIGNATURES = [
     ("sinkhorn_divergence", ctypes.c_int,
      [_P, _P, _I64, _P, _P, _I64, _I32, _D, _D, _I32, _I32, _P, _P, _P, _P, _SZ, _P]),
     ("coupling_diagonal", ctypes.c_int, [_P, _P, _I64, _I32, _P, _P, _D, _P, _P, _P, _P, _SZ, _P]),
+    ("sinkhorn_potentials_pnorm", ctypes.c_int,
+     [_P, _P, _I64, _P, _P, _I64, _I32, _D, _D, _D, _I32, _P, _P, _I32, _P, _P, _P, _SZ, _P]),
+    ("progot_solve_pnorm", ctypes.c_int,
+     [_P, _P, _I64, _P, _P, _I64, _I32, _D, _I32, _P, _P, _D, _P, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
+    ("entropic_map_apply_pnorm", ctypes.c_int, [_P, _I64, _P, _I64, _I32, _D, _I32, _P, _P, _P, _P, _P, _SZ, _P]),
+    ("coupling_metrics_pnorm", ctypes.c_int, [_P, _P, _I64, _P, _P, _I64, _I32, _D, _P, _P, _D, _P, _P, _SZ, _P]),
+    ("progot_mean_cost_pnorm", ctypes.c_int, [_P, _I64, _P, _I64, _I32, _D, _P, _P, _SZ, _P]),
     ("progot_profile", ctypes.c_int, [_I32]),
     ("progot_profile_read", ctypes.c_int, [_I32, _P, _P, _P, _P]),
 ]
@@ -368,6 +375,103 @@ def coupling_diagonal(x, y, f, g, eps, log_diag=None, workspace=None, stream=Non
                                  ctypes.c_void_p(ws.ptr), ws.bytes, _stream(stream))
     _check(rc, allow_not_converged=False)
     return tr.value, kl.value
+
+
+# ------------------------------------------------------- p-norm cost (Sec. 5.2)
+def sinkhorn_potentials_pnorm(x, y, p, eps, tau, max_iter=10000, a=None, b=None, f=None, g=None, workspace=None,
+                              stream=None) -> SinkhornOut:
+    """Alg. 1 for the cost h(x - y) = (1/p) sum_k |x_k - y_k|^p (float32 CUDA cores)."""
+    torch = _torch()
+    _dev(x, "x"), _dev(y, "y")
+    n, d = x.shape
+    m = y.shape[0]
+    init_zero = 1 if (f is None and g is None) else 0
+    if f is None:
+        f = torch.zeros(n, dtype=torch.float32, device=x.device)
+    if g is None:
+        g = torch.zeros(m, dtype=torch.float32, device=x.device)
+    ws = _ws(workspace, n, m, d, "fp32")
+    it = ctypes.c_int32(0)
+    err = ctypes.c_double(0.0)
+    rc = lib().sinkhorn_potentials_pnorm(_dev(x, "x"), _opt(a, "a", (n,)), n, _dev(y, "y"), _opt(b, "b", (m,)), m, d,
+                                         float(p), float(eps), float(tau), int(max_iter), _dev(f, "f", (n,)),
+                                         _dev(g, "g", (m,)), init_zero, ctypes.byref(it), ctypes.byref(err),
+                                         ctypes.c_void_p(ws.ptr), ws.bytes, _stream(stream))
+    _check(rc)
+    return SinkhornOut(f, g, it.value, err.value, rc)
+
+
+def progot_solve_pnorm(x, y, p, alpha, tau, eps=None, theta=None, max_iter=10000, a=None, b=None, workspace=None,
+                       stream=None, out=None):
+    """Alg. 2 for the p-norm cost with an eps schedule, or the theta rule when eps is None.
+    Returns (ProgOTOut, eps_k array)."""
+    torch = _torch()
+    _dev(x, "x"), _dev(y, "y")
+    n, d = x.shape
+    m = y.shape[0]
+    K = len(alpha)
+    al_h, tau_h = _host_f64(alpha, K), _host_f64(tau, K)
+    eps_h = None if eps is None else _host_f64(eps, K)
+    if eps_h is None and theta is None:
+        raise ValueError("give eps or theta")
+    if out is None:
+        out = dict(x_out=torch.empty_like(x), g_all=torch.empty((K, m), dtype=torch.float32, device=x.device),
+                   f_last=torch.empty(n, dtype=torch.float32, device=x.device), x_last=torch.empty_like(x))
+    iters = np.zeros(K, dtype=np.int32)
+    errs = np.zeros(K, dtype=np.float64)
+    eps_out = np.zeros(K, dtype=np.float64)
+    ws = _ws(workspace, n, m, d, "fp32")
+    rc = lib().progot_solve_pnorm(_dev(x, "x"), _opt(a, "a", (n,)), n, _dev(y, "y"), _opt(b, "b", (m,)), m, d,
+                                  float(p), K, _hp(al_h), None if eps_h is None else _hp(eps_h),
+                                  float(theta or 0.0), _hp(tau_h), int(max_iter), _dev(out["x_out"], "x_out", (n, d)),
+                                  _dev(out["g_all"], "g_all", (K, m)), _opt(out.get("f_last"), "f_last", (n,)),
+                                  _opt(out.get("x_last"), "x_last", (n, d)), _hp(iters), _hp(errs), _hp(eps_out),
+                                  ctypes.c_void_p(ws.ptr), ws.bytes, _stream(stream))
+    _check(rc)
+    return (ProgOTOut(out["x_out"], out["g_all"], out.get("f_last"), out.get("x_last"), iters.tolist(),
+                      errs.tolist(), rc), eps_out)
+
+
+def entropic_map_apply_pnorm(xq, y, p, g_all, eps, alpha, out=None, workspace=None, stream=None):
+    """Alg. 3 for the p-norm cost; returns out (nq x d)."""
+    torch = _torch()
+    _dev(xq, "xq"), _dev(y, "y")
+    nq, d = xq.shape
+    m = y.shape[0]
+    K = g_all.shape[0] if g_all.dim() == 2 else 1
+    eps_h, al_h = _host_f64(eps, K), _host_f64(alpha, K)
+    if out is None:
+        out = torch.empty_like(xq)
+    ws = _ws(workspace, nq, m, d, "fp32")
+    rc = lib().entropic_map_apply_pnorm(_dev(xq, "xq"), nq, _dev(y, "y"), m, d, float(p), K,
+                                        _dev(g_all.contiguous(), "g_all"), _hp(eps_h), _hp(al_h),
+                                        _dev(out, "out", (nq, d)), ctypes.c_void_p(ws.ptr), ws.bytes, _stream(stream))
+    _check(rc, allow_not_converged=False)
+    return out
+
+
+def coupling_metrics_pnorm(x, y, p, f, g, eps, a=None, b=None, workspace=None, stream=None) -> dict:
+    """coupling_metrics for the p-norm cost."""
+    _dev(x, "x"), _dev(y, "y")
+    n, d = x.shape
+    m = y.shape[0]
+    ws = _ws(workspace, n, m, d, "fp32")
+    res = CouplingMetricsStruct()
+    rc = lib().coupling_metrics_pnorm(_dev(x, "x"), _opt(a, "a", (n,)), n, _dev(y, "y"), _opt(b, "b", (m,)), m, d,
+                                      float(p), _dev(f, "f", (n,)), _dev(g, "g", (m,)), float(eps), ctypes.byref(res),
+                                      ctypes.c_void_p(ws.ptr), ws.bytes, _stream(stream))
+    _check(rc, allow_not_converged=False)
+    return {k: getattr(res, k) for k, _ in CouplingMetricsStruct._fields_}
+
+
+def progot_mean_cost_pnorm(x, y, p, workspace=None, stream=None) -> float:
+    n, d = x.shape
+    m = y.shape[0]
+    ws = _ws(workspace, n, m, d, "fp32")
+    out = ctypes.c_double(0.0)
+    _check(lib().progot_mean_cost_pnorm(_dev(x, "x"), n, _dev(y, "y"), m, d, float(p), ctypes.byref(out),
+                                        ctypes.c_void_p(ws.ptr), ws.bytes, _stream(stream)), allow_not_converged=False)
+    return out.value
 
 
 def progot_schedule_alpha(K: int, kind="constant") -> np.ndarray:

@@ -148,3 +148,21 @@ def test_widened_entry_points_check_arguments_on_the_host(lib):
     assert rc == native.PROGOT_ERR_WORKSPACE
     rc = lib.coupling_diagonal(fake, fake, 8, 2, fake, fake, 0.0, None, None, None, ws, 1 << 20, None)
     assert rc == native.PROGOT_ERR_INVALID_ARG
+
+
+def test_pnorm_entry_points_check_p_on_the_host(lib):
+    fake = ctypes.c_void_p(0x100000)
+    ws = ctypes.c_void_p(0x200000)
+    for p in (1.0, 0.5, -2.0, 9.0, float("nan")):
+        rc = lib.sinkhorn_potentials_pnorm(fake, None, 8, fake, None, 8, 2, p, 1.0, 1e-3, 10, fake, fake, 1, None,
+                                           None, ws, 1 << 20, None)
+        assert rc == native.PROGOT_ERR_INVALID_ARG and "p" in native.last_error()
+    out = ctypes.c_double(0.0)
+    assert lib.progot_mean_cost_pnorm(fake, 8, fake, 8, 2, 1.0, ctypes.byref(out), ws, 1 << 20,
+                                      None) == native.PROGOT_ERR_INVALID_ARG
+    h = np.ones(2, dtype=np.float64)
+    hp = h.ctypes.data_as(ctypes.c_void_p)
+    # no eps schedule and no theta
+    rc = lib.progot_solve_pnorm(fake, None, 8, fake, None, 8, 2, 1.5, 2, hp, None, 0.0, hp, 10, fake, fake, None,
+                                None, None, None, None, ws, 1 << 20, None)
+    assert rc == native.PROGOT_ERR_INVALID_ARG and "theta" in native.last_error()
