@@ -527,13 +527,19 @@ def eps_schedule(X, b, Y, Y_test, alphas, s_grid=None, beta0: float = 5.0, tau: 
 # --------------------------------------------------------------------------
 # Sec. 5.2 coupling metrics and the eq. (5) dual objective.
 # --------------------------------------------------------------------------
-def coupling_cost(X, Y, f, g, eps: float, cost=None) -> float:
-    """<P, C> for P = exp((f (+) g - C)/eps)."""
+def coupling_cost(X, Y, f, g, eps: float, cost=None, X_cost=None) -> float:
+    """<P, C> for P = exp((f (+) g - C)/eps).
+
+    X_cost (optional, same number of rows as X): integrate the cost from X_cost instead,
+    sum_ij P_ij h(xc_i - y_j) with P still defined on X. ProgOT's coupling is computed on
+    the displaced cloud X^(K) but couples the original points (row i is point i), so
+    Sec. 5.2 measures its transport cost against the original X."""
     C = CostOperator(X, Y, cache_limit=0, cost=cost)
+    Cc = C if X_cost is None else CostOperator(X_cost, Y, cache_limit=0, cost=cost)
     tot = 0.0
-    for i0, Cb in C.row_blocks():
+    for (i0, Cb), (_, Ccb) in zip(C.row_blocks(), Cc.row_blocks()):
         P = np.exp((tensor_sum(f[i0:i0 + Cb.shape[0]], g) - Cb) / eps)
-        tot += float(np.sum(P * Cb))
+        tot += float(np.sum(P * Ccb))
     return tot
 
 

@@ -192,3 +192,19 @@ def test_symmetric_self_transport_matches_alternating_sinkhorn():
     kappa = np.mean(alt.f - sym.f)
     np.testing.assert_allclose(alt.f - kappa, sym.f, atol=1e-9)
     np.testing.assert_allclose(alt.g + kappa, sym.f, atol=1e-9)
+
+
+def test_coupling_cost_against_another_cloud_by_loops():
+    # P from (X, f, g), cost from X_cost: a plain double loop over the definition
+    rng = _rng(33)
+    X, Xc, Y = rng.normal(size=(5, 2)), rng.normal(size=(5, 2)), rng.normal(size=(4, 2))
+    f, g, eps = rng.normal(size=5), rng.normal(size=4), 0.8
+    for cost in (None, O.PNorm(1.5)):
+        h = (lambda z: float(np.sum(z * z))) if cost is None else (lambda z: float(np.sum(np.abs(z) ** 1.5) / 1.5))
+        want = 0.0
+        for i in range(5):
+            for j in range(4):
+                want += math.exp((f[i] + g[j] - h(X[i] - Y[j])) / eps) * h(Xc[i] - Y[j])
+        assert O.coupling_cost(X, Y, f, g, eps, cost, X_cost=Xc) == pytest.approx(want, rel=1e-12)
+        same = O.coupling_cost(X, Y, f, g, eps, cost)
+        assert O.coupling_cost(X, Y, f, g, eps, cost, X_cost=X) == pytest.approx(same, rel=1e-14)
