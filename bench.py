@@ -369,6 +369,83 @@ def run_blur(args, rank, world, local):
     return 0
 
 
+def run_coupling(args, rank, world, local):
+    """ProgOT as a coupling solver against Sinkhorn (Sec. 5.2) on a synthetic stand-in
+    for the 4i morphology data (n = 11000 control and m = 2800 treated cells, d = 47):
+    Sinkhorn at eps = beta eps0 for a log grid of beta, and constant-speed ProgOT with
+    K in {2, 4, 8} and eps_k = theta cbar_k (theta = 2^-4), tau_k linear from 1e-2 to
+    tau_K = 1e-3; both ground costs (squared Euclidean and (1/1.5)||.||_1.5^1.5).
+    Reports total Sinkhorn iterations, <P, C>, E(P), the marginal error and the time."""
+    import torch
+    from paper_2406_05061_gb300 import native
+    torch.cuda.set_device(local)
+    pr = W.gmm_pair(11000, 2800, 47, seed=6, k=8)
+    x, y = torch.from_numpy(pr.x).cuda(), torch.from_numpy(pr.y).cuda()
+    n, m, d = pr.n, pr.m, pr.d
+    theta, tau = 2.0 ** -4, 1e-3
+    ws = native.Workspace(n, m, d, "bf16x3")
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    rows = []
+
+    def timed(fn):
+        e0, e1 = ev(), ev()
+        e0.record()
+        r = fn()
+        e1.record()
+        e1.synchronize()
+        return r, e0.elapsed_time(e1) / 1e3
+
+    for cost in ("sqeuclidean", "pnorm1.5"):
+        pn = cost != "sqeuclidean"
+        prec = "fp32" if pn else args.precision
+        mc = native.progot_mean_cost_pnorm(x, y, 1.5, workspace=ws) if pn else native.progot_mean_cost(x, y, workspace=ws)
+        eps0 = mc / 20.0
+
+        def metrics(xs, f, g, eps):
+            # ProgOT's coupling lives on X^(K) and couples the original points: its cost is
+            # measured against the original X (x_cost); Sinkhorn's lives on X itself
+            xc = None if xs is x else x
+            if pn:
+                return native.coupling_metrics_pnorm(xs, y, 1.5, f, g, eps, x_cost=xc, workspace=ws)
+            return native.coupling_metrics(xs, y, f, g, eps, x_cost=xc, workspace=ws)
+
+        for beta in (2.0 ** -6, 2.0 ** -4, 2.0 ** -2):
+            eps = beta * eps0
+            if pn:
+                fn = lambda: native.sinkhorn_potentials_pnorm(x, y, 1.5, eps, tau, max_iter=20000, workspace=ws)
+            else:
+                fn = lambda: native.sinkhorn_potentials(x, y, eps, tau, max_iter=20000, precision=prec, workspace=ws)
+            fn()
+            r, sec = timed(fn)
+            met = metrics(x, r.f, r.g, eps)
+            rows.append({"cost": cost, "solver": "sinkhorn", "beta": beta, "eps": eps, "iters": r.iters,
+                         "status": r.status, "seconds": sec, **met})
+        for K in (2, 4, 8):
+            alpha = native.progot_schedule_alpha(K, "constant")
+            tau_k = native.progot_schedule_tau(K, 1e-2, tau)
+            if pn:
+                fn = lambda: native.progot_solve_pnorm(x, y, 1.5, alpha, tau_k, theta=theta, max_iter=20000,
+                                                       workspace=ws)
+            else:
+                fn = lambda: native.progot_solve_theta(x, y, alpha, theta, tau_k, max_iter=20000, precision=prec,
+                                                       workspace=ws)
+            fn()
+            (res, eps_k), sec = timed(fn)
+            met = metrics(res.x_last, res.f_last, res.g_all[K - 1], float(eps_k[-1]))
+            rows.append({"cost": cost, "solver": f"progot_K{K}", "theta": theta, "eps": [float(e) for e in eps_k],
+                         "iters": int(sum(res.iters)), "iters_per_step": res.iters, "status": res.status,
+                         "seconds": sec, **met})
+    k4 = next(r for r in rows if r["cost"] == "sqeuclidean" and r["solver"] == "progot_K4")
+    line = {"metric": "coupling_progot_k4_seconds", "value": k4["seconds"], "unit": "s", "n_gpus": 1,
+            "higher_is_better": False, "dtype": args.precision + " (sqeuclidean), fp32 (pnorm1.5)",
+            "data": "synthetic",
+            "config": {"workload": "coupling_11000x2800_d47", "n": n, "m": m, "d": d, "theta": theta, "tau": tau,
+                       "tau_schedule": "linear 1e-2 -> 1e-3", "betas": [2.0 ** -6, 2.0 ** -4, 2.0 ** -2]},
+            "runs": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -378,7 +455,7 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["fp32", "bf16x3", "bf16"])
     ap.add_argument("--no-compare", action="store_true", help="skip the float32 comparison solve")
     ap.add_argument("--workload", default="gmm8_8192_d64",
-                    choices=sorted(WORKLOADS) + ["batched256", "serving", "blur"])
+                    choices=sorted(WORKLOADS) + ["batched256", "serving", "blur", "coupling"])
     ap.add_argument("--blur-n", type=int, default=60000, help="blur: number of images (32 x 32)")
     ap.add_argument("--sigma", type=float, default=2.0, help="blur: kernel width")
     ap.add_argument("--requests", type=int, default=240, help="serving: requests replayed from the stream")
@@ -392,6 +469,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "batched256":
         return run_batched(args, rank, world, local)
+    if args.workload == "coupling":
+        return run_coupling(args, rank, world, local) if rank == 0 else 0
     if args.workload == "blur":
         return run_blur(args, rank, world, local) if rank == 0 else 0
     if args.workload == "serving":

@@ -327,12 +327,17 @@ typedef struct progot_coupling_metrics {
  * gives sum_j P_ij log P_ij per row; then <P, C> = <f, P 1> + <g, P^T 1> - eps
  * sum P log P. All reductions are float64 in a fixed order (deterministic).
  * x (device, n x d), y (device, m x d), f (device, n), g (device, m), a, b (device or
- * NULL = uniform). out (host). workspace: progot_workspace_size(n, m, d, PROGOT_FP32).
- * Synchronises the stream.
+ * NULL = uniform). x_cost (device, n x d, may be NULL): when given, transport_cost is
+ * sum_ij P_ij ||xc_i - y_j||^2 with P still defined on x. ProgOT's final coupling lives on
+ * the displaced cloud X^(K) (x_last of progot_solve) but couples the original points row
+ * for row, so Sec. 5.2 measures its cost against the original X: pass x = x_last and
+ * x_cost = the original X. The row sweep then also computes the cost tile of x_cost and
+ * keeps sum_j 2^(t_ij - max) c(xc_i, y_j) per row. out (host). workspace:
+ * progot_workspace_size(n, m, d, PROGOT_FP32). Synchronises the stream.
  */
 int coupling_metrics(const float* x, const float* a, int64_t n, const float* y, const float* b, int64_t m, int32_t d,
-                     const float* f, const float* g, double eps, progot_coupling_metrics* out, void* workspace,
-                     size_t ws_bytes, progot_stream_t stream);
+                     const float* f, const float* g, const float* x_cost, double eps, progot_coupling_metrics* out,
+                     void* workspace, size_t ws_bytes, progot_stream_t stream);
 
 /*
  * sinkhorn_divergence - the Sinkhorn divergence of eq. (8):
@@ -390,9 +395,10 @@ int progot_solve_pnorm(const float* x, const float* a, int64_t n, const float* y
 int entropic_map_apply_pnorm(const float* xq, int64_t nq, const float* y, int64_t m, int32_t d, double p, int32_t K,
                              const float* g_all, const double* eps, const double* alpha, float* out, void* workspace,
                              size_t ws_bytes, progot_stream_t stream);
-/* As coupling_metrics: <P, C> with C_ij = h(x_i - y_j), E(P), the eq. (5) objective. */
+/* As coupling_metrics: <P, C> with C_ij = h(x_i - y_j) (or h(xc_i - y_j) with x_cost),
+ * E(P), the eq. (5) objective. */
 int coupling_metrics_pnorm(const float* x, const float* a, int64_t n, const float* y, const float* b, int64_t m,
-                           int32_t d, double p, const float* f, const float* g, double eps,
+                           int32_t d, double p, const float* f, const float* g, const float* x_cost, double eps,
                            progot_coupling_metrics* out, void* workspace, size_t ws_bytes, progot_stream_t stream);
 /* (1/(n m)) sum_ij h(x_i - y_j), summed over all pairs (float64 per CTA, fixed order). out (host). */
 int progot_mean_cost_pnorm(const float* x, int64_t n, const float* y, int64_t m, int32_t d, double p, double* out,

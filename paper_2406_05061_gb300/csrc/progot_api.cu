@@ -154,6 +154,7 @@ struct Workspace {
   float* T;         // nmax * d
   float2* partial;  // partial_elems
   float* wpart;     // partial_elems (tilted sums of the coupling-metrics sweep)
+  float* cpart;     // partial_elems (cross-cloud cost sums of the coupling-metrics sweep)
   double* metpart;  // kMetricSums * (rbmax + 2)
   double* metout;   // 2 * kMetricSums + 2: reduced metric sums (row sweep, column sweep), mean cost
   double* errpart;  // rbmax + 2
@@ -221,6 +222,7 @@ static size_t ws_layout(const WsDims& w, Workspace* out, char* base) {
   ws.T = (float*)take(sizeof(float) * w.nmax * (size_t)w.d);
   ws.partial = (float2*)take(sizeof(float2) * w.partial_elems);
   ws.wpart = (float*)take(sizeof(float) * w.partial_elems);
+  ws.cpart = (float*)take(sizeof(float) * w.partial_elems);
   ws.metpart = (double*)take(sizeof(double) * kMetricSums * (w.rbmax + 2));
   ws.metout = (double*)take(sizeof(double) * (2 * kMetricSums + 2));
   ws.errpart = (double*)take(sizeof(double) * (w.rbmax + 2));
@@ -669,7 +671,7 @@ static int zero_counters(const Workspace& ws, int64_t rbmax, cudaStream_t s) {
 // arrival counters must be zero.
 static int metrics_core(const float* x, const float* a, int64_t n, const float* y, const float* b, int64_t m,
                         int32_t d, const float* f, const float* g, double eps, const Workspace& ws, cudaStream_t s,
-                        progot_coupling_metrics* out, const Cost& cost = Cost()) {
+                        progot_coupling_metrics* out, const Cost& cost = Cost(), const float* x_cost = nullptr) {
   int rc = t_host.init();
   if (rc) return rc;
   SweepParams pr = make_sweep(x, n, y, m, d, ws.xn, ws.yn, eps, ws);
@@ -678,6 +680,13 @@ static int metrics_core(const float* x, const float* a, int64_t n, const float* 
   pr.potA_old = f;
   pr.mode = kModeMetrics;
   apply_cost(pr, cost, eps);
+  if (x_cost != nullptr) {
+    // integrate the cost from x_cost (its squared norms in ws.L) against P on x
+    if (!cost.pnorm()) CK(launch_row_sqnorm(x_cost, n, d, ws.L, s));
+    pr.Ac = x_cost;
+    pr.Acn = cost.pnorm() ? nullptr : ws.L;
+    pr.cpart = ws.cpart;
+  }
   CK(launch_lse_sweep_fp32(pr, s));
   CK(launch_sum_parts(ws.metpart, (int)cdiv(n, fp32_tile_rows()), kMetricSums, ws.metout, s));
   SweepParams pc = make_sweep(y, m, x, n, d, ws.yn, ws.xn, eps, ws);
@@ -696,7 +705,7 @@ static int metrics_core(const float* x, const float* a, int64_t n, const float* 
   out->err_row = R[kSumErr];
   out->err_col = Cs[kSumErr];
   out->entropy = R[kSumMass] - R[kSumPlogP];
-  out->transport_cost = R[kSumPotR] + Cs[kSumPotR] - eps * R[kSumPlogP];
+  out->transport_cost = x_cost != nullptr ? R[kSumPC] : R[kSumPotR] + Cs[kSumPotR] - eps * R[kSumPlogP];
   out->dual = R[kSumPotW] + Cs[kSumPotW] - eps * R[kSumMass];
   if (!std::isfinite(out->transport_cost) || !std::isfinite(out->entropy) || !std::isfinite(out->dual))
     return fail(PROGOT_ERR_NUMERIC, "non-finite coupling metric");
@@ -1006,8 +1015,8 @@ int progot_schedule_tau(int32_t K, double tau_first, double tau_last, double* ou
 }
 
 int coupling_metrics(const float* x, const float* a, int64_t n, const float* y, const float* b, int64_t m, int32_t d,
-                     const float* f, const float* g, double eps, progot_coupling_metrics* out, void* workspace,
-                     size_t ws_bytes, progot_stream_t stream) {
+                     const float* f, const float* g, const float* x_cost, double eps, progot_coupling_metrics* out,
+                     void* workspace, size_t ws_bytes, progot_stream_t stream) {
   t_last_error.clear();
   int rc = check_common(x, n, y, m, d, PROGOT_FP32);
   if (rc) return rc;
@@ -1022,7 +1031,7 @@ int coupling_metrics(const float* x, const float* a, int64_t n, const float* y, 
   if (rc) return rc;
   CK(launch_row_sqnorm(x, n, d, ws.xn, s));
   CK(launch_row_sqnorm(y, m, d, ws.yn, s));
-  return metrics_core(x, a, n, y, b, m, d, f, g, eps, ws, s, out);
+  return metrics_core(x, a, n, y, b, m, d, f, g, eps, ws, s, out, Cost(), x_cost);
 }
 
 int sinkhorn_divergence(const float* x, const float* a, int64_t n, const float* y, const float* b, int64_t m,
@@ -1195,7 +1204,7 @@ int entropic_map_apply_pnorm(const float* xq, int64_t nq, const float* y, int64_
 }
 
 int coupling_metrics_pnorm(const float* x, const float* a, int64_t n, const float* y, const float* b, int64_t m,
-                           int32_t d, double p, const float* f, const float* g, double eps,
+                           int32_t d, double p, const float* f, const float* g, const float* x_cost, double eps,
                            progot_coupling_metrics* out, void* workspace, size_t ws_bytes, progot_stream_t stream) {
   t_last_error.clear();
   int rc = check_common(x, n, y, m, d, PROGOT_FP32);
@@ -1212,7 +1221,7 @@ int coupling_metrics_pnorm(const float* x, const float* a, int64_t n, const floa
   cudaStream_t s = (cudaStream_t)stream;
   rc = zero_counters(ws, ws_dims(n, m, d).rbmax, s);
   if (rc) return rc;
-  return metrics_core(x, a, n, y, b, m, d, f, g, eps, ws, s, out, cost);
+  return metrics_core(x, a, n, y, b, m, d, f, g, eps, ws, s, out, cost, x_cost);
 }
 
 int progot_mean_cost_pnorm(const float* x, int64_t n, const float* y, int64_t m, int32_t d, double p, double* out,

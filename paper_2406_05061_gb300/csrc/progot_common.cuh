@@ -25,7 +25,8 @@ enum MetricSum : int32_t {
   kSumPotR = 2,   // sum_i pot_i r_i
   kSumPlogP = 3,  // sum_i sum_j P_ij log P_ij
   kSumPotW = 4,   // sum_i pot_i w_i
-  kMetricSums = 5,
+  kSumPC = 5,     // sum_i sum_j P_ij c(ac_i, b_j) against the cost cloud Ac (when given)
+  kMetricSums = 6,
 };
 
 // Solver state kept on the device so that the Sinkhorn loop runs without a host
@@ -59,6 +60,9 @@ struct SweepParams {
   float2* partial;     // [splits][nA] (max, sum) in log2 units
   float* wpart;        // [splits][nA] tilted sums sum_j 2^{t_ij - max} (t_ij - max) (kModeMetrics)
   double* metpart;     // [row blocks][kMetricSums] (kModeMetrics)
+  const float* Ac;     // kModeMetrics: nA x d cloud whose cost to B is integrated against P, or nullptr
+  const float* Acn;    // |ac_i|^2 (squared Euclidean cost)
+  float* cpart;        // [splits][nA] sums_j 2^{t_ij - max} c(ac_i, b_j) (when Ac is given)
   double* errpart;     // [row blocks] float64 error partials
   unsigned int* cnt;   // [row blocks + 1] arrival counters (zero between launches)
   SolverState* state;  // nullptr when the sweep is not part of a Sinkhorn loop

@@ -176,15 +176,26 @@ __device__ __forceinline__ float3 tilt_combine(float3 p, float3 q) {
   return make_float3(M, s, w);
 }
 
-// kTilt adds the tilted sum W per row (coupling metrics); otherwise the plain sweep.
+// Rescale a plain weighted sum from the max mp to the max M of a combine (0 when empty).
+__device__ __forceinline__ float rescaled(float w, float mp, float M) {
+  return (mp == -INFINITY) ? 0.f : w * exp2f(mp - M);
+}
+
+// kTilt adds the tilted sum W per row (coupling metrics) and, when p.Ac is given, the
+// plain sum V = sum_j 2^{t_ij - M} c(ac_i, b_j) of the cost from another cloud (the
+// cost tile is computed first and parked in dynamic shared memory, one entry per
+// thread-owned pair); otherwise the plain sweep.
 // kCost selects the pair term (the squared Euclidean dot product or a p-norm cost).
 template <bool kTilt, int kCost>
-__global__ void __launch_bounds__(NT, 2) lse_sweep_fp32(SweepParams p) {
+__global__ void __launch_bounds__(NT, kTilt ? 1 : 2) lse_sweep_fp32(SweepParams p) {
   if (p.state != nullptr && p.state->done) return;
   __shared__ GemmSmem sm;
   __shared__ float beta_s[BN];
+  __shared__ float bn_s[BN];
   __shared__ double red[NT / 32];
   __shared__ int s_last;
+  extern __shared__ float cost_tile[];  // [BN][BM] in the cross-cloud metrics mode
+  const bool cross = kTilt && p.Ac != nullptr;
 
   const int fcur = p.state ? p.state->fcur : 0;
   const float* potB = (p.potB_alt && fcur == 1) ? p.potB_alt : p.potB;
@@ -196,12 +207,18 @@ __global__ void __launch_bounds__(NT, 2) lse_sweep_fp32(SweepParams p) {
   const bool vec_ok = ((p.d & 3) == 0) && ((reinterpret_cast<uintptr_t>(p.A) & 15) == 0) &&
                       ((reinterpret_cast<uintptr_t>(p.B) & 15) == 0);
 
-  float m_run[8], s_run[8], w_run[8];
+  float m_run[8], s_run[8], w_run[8], v_run[8], acn[8];
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
     m_run[r] = -INFINITY;
     s_run[r] = 0.f;
     w_run[r] = 0.f;
+    v_run[r] = 0.f;
+    acn[r] = 0.f;
+    if constexpr (kTilt && kCost == kCostSqEuclid) {
+      const int64_t i = row0 + thread_row(r);
+      if (cross && i < p.nA) acn[r] = p.Acn[i];
+    }
   }
   float acc[8][8];
   for (int tile = t_begin; tile < t_end; ++tile) {
@@ -214,6 +231,21 @@ __global__ void __launch_bounds__(NT, 2) lse_sweep_fp32(SweepParams p) {
         if (j < p.nB) bn = p.Bn[j];
       }
       beta_s[threadIdx.x] = (j < p.nB) ? (potB[j] - bn) * p.bscale : -INFINITY;
+      bn_s[threadIdx.x] = bn;
+    }
+    if constexpr (kTilt) {
+      if (cross) {
+        // cost of the cost cloud against this tile, each thread keeping its own 8 x 8
+        tile_accumulate<kCost>(sm, p.Ac, p.nA, p.B, p.nB, p.d, row0, col0, vec_ok, p.cost_p, acc);
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const float cv = (kCost == kCostSqEuclid) ? fmaf(-2.f, acc[r][c], acn[r] + bn_s[thread_col(c)])
+                                                      : acc[r][c] / p.cost_p;
+            cost_tile[thread_col(c) * BM + thread_row(r)] = cv;
+          }
+      }
     }
     tile_accumulate<kCost>(sm, p.A, p.nA, p.B, p.nB, p.d, row0, col0, vec_ok, p.cost_p, acc);  // ends with a sync
     float bcol[8];
@@ -234,14 +266,18 @@ __global__ void __launch_bounds__(NT, 2) lse_sweep_fp32(SweepParams p) {
         float s = s_run[r] * resc;
         if constexpr (kTilt) {
           float w = (m_run[r] == -INFINITY) ? 0.f : resc * fmaf(s_run[r], m_run[r] - mnew, w_run[r]);
+          float v = v_run[r] * resc;
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
             const float e = fast_exp2(t[c] - mnew);
             s += e;
             // padded columns have t = -inf and e = 0; the clamp keeps 0 * (-inf) out
             w = fmaf(e, fmaxf(t[c] - mnew, -256.f), w);
+            // padded columns: e = 0 and a finite cost entry
+            if (cross) v = fmaf(e, cost_tile[thread_col(c) * BM + thread_row(r)], v);
           }
           w_run[r] = w;
+          v_run[r] = v;
         } else {
 #pragma unroll
           for (int c = 0; c < 8; ++c) s += fast_exp2(t[c] - mnew);
@@ -256,19 +292,24 @@ __global__ void __launch_bounds__(NT, 2) lse_sweep_fp32(SweepParams p) {
   for (int r = 0; r < 8; ++r) {
     if constexpr (kTilt) {
       float3 v = make_float3(m_run[r], s_run[r], w_run[r]);
+      float vc = v_run[r];
 #pragma unroll
       for (int off = 8; off > 0; off >>= 1) {
         float3 o;
         o.x = __shfl_xor_sync(0xffffffffu, v.x, off);
         o.y = __shfl_xor_sync(0xffffffffu, v.y, off);
         o.z = __shfl_xor_sync(0xffffffffu, v.z, off);
-        v = tilt_combine(v, o);
+        const float oc = __shfl_xor_sync(0xffffffffu, vc, off);
+        const float3 mrg = tilt_combine(v, o);
+        vc = rescaled(vc, v.x, mrg.x) + rescaled(oc, o.x, mrg.x);
+        v = mrg;
       }
       if (tx == 0) {
         const int64_t i = row0 + thread_row(r);
         if (i < p.nA) {
           p.partial[(int64_t)blockIdx.y * p.nA + i] = make_float2(v.x, v.y);
           p.wpart[(int64_t)blockIdx.y * p.nA + i] = v.z;
+          if (cross) p.cpart[(int64_t)blockIdx.y * p.nA + i] = vc;
         }
       }
     } else {
@@ -307,23 +348,28 @@ __global__ void __launch_bounds__(NT, 2) lse_sweep_fp32(SweepParams p) {
     // coupling metrics of the rows of this block: with base_i = (pot_i - |a_i|^2) / eps,
     // log P_ij = base_i + ln2 t_ij, so r_i = exp(base_i + ln2 L_i) and
     // sum_j P_ij log P_ij = r_i (base_i + ln2 tbar_i), tbar_i = M + W / S
-    double q[kMetricSums] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    double q[kMetricSums] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     if (threadIdx.x < BM) {
       const int64_t i = row0 + threadIdx.x;
       if (i < p.nA) {
         const RowIn in = row_inputs(p, i, potA_cur);
         float3 v = make_float3(-INFINITY, 0.f, 0.f);
+        float vc = 0.f;
         for (int s = 0; s < p.splits; ++s) {
           const float2 ms = __ldcg(&p.partial[(int64_t)s * p.nA + i]);
-          v = tilt_combine(v, make_float3(ms.x, ms.y, __ldcg(&p.wpart[(int64_t)s * p.nA + i])));
+          const float3 in3 = make_float3(ms.x, ms.y, __ldcg(&p.wpart[(int64_t)s * p.nA + i]));
+          const float3 mrg = tilt_combine(v, in3);
+          if (cross) vc = rescaled(vc, v.x, mrg.x) + rescaled(__ldcg(&p.cpart[(int64_t)s * p.nA + i]), in3.x, mrg.x);
+          v = mrg;
         }
-        double r = 0.0, plogp = 0.0;
+        double r = 0.0, plogp = 0.0, pc = 0.0;
         if (v.y > 0.f) {
           const double base = ((double)in.pot - (double)in.an) / p.eps;
           const double L = (double)v.x + (double)__log2f(v.y);
           r = (double)expf((float)(base + kLn2 * L));
           const double tbar = (double)v.x + (double)v.z / (double)v.y;
           plogp = r * (base + kLn2 * tbar);
+          pc = r * (double)vc / (double)v.y;
         }
         if (out_target) out_target[i] = (float)r;
         q[kSumErr] = fabs(r - (double)in.w);
@@ -331,6 +377,7 @@ __global__ void __launch_bounds__(NT, 2) lse_sweep_fp32(SweepParams p) {
         q[kSumPotR] = (double)in.pot * r;
         q[kSumPlogP] = plogp;
         q[kSumPotW] = (double)in.pot * (double)in.w;
+        q[kSumPC] = pc;
       }
     }
     e = q[kSumErr];
@@ -702,21 +749,23 @@ cudaError_t launch_lse_sweep_fp32(const SweepParams& p, cudaStream_t stream) {
   const int rb = (int)((p.nA + BM - 1) / BM);
   dim3 grid(rb, p.splits);
   const bool tilt = p.mode == kModeMetrics;
-  if (p.cost == kCostP15) {
-    if (tilt)
-      lse_sweep_fp32<true, kCostP15><<<grid, NT, 0, stream>>>(p);
-    else
-      lse_sweep_fp32<false, kCostP15><<<grid, NT, 0, stream>>>(p);
+  // the cross-cloud metrics mode parks one cost tile in dynamic shared memory
+  const size_t dyn = (tilt && p.Ac != nullptr) ? sizeof(float) * BN * BM : 0;
+  if (tilt) {
+    auto k = p.cost == kCostP15        ? lse_sweep_fp32<true, kCostP15>
+             : p.cost == kCostPGeneral ? lse_sweep_fp32<true, kCostPGeneral>
+                                       : lse_sweep_fp32<true, kCostSqEuclid>;
+    if (dyn > 0) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+      if (e != cudaSuccess) return e;
+    }
+    k<<<grid, NT, dyn, stream>>>(p);
+  } else if (p.cost == kCostP15) {
+    lse_sweep_fp32<false, kCostP15><<<grid, NT, 0, stream>>>(p);
   } else if (p.cost == kCostPGeneral) {
-    if (tilt)
-      lse_sweep_fp32<true, kCostPGeneral><<<grid, NT, 0, stream>>>(p);
-    else
-      lse_sweep_fp32<false, kCostPGeneral><<<grid, NT, 0, stream>>>(p);
+    lse_sweep_fp32<false, kCostPGeneral><<<grid, NT, 0, stream>>>(p);
   } else {
-    if (tilt)
-      lse_sweep_fp32<true, kCostSqEuclid><<<grid, NT, 0, stream>>>(p);
-    else
-      lse_sweep_fp32<false, kCostSqEuclid><<<grid, NT, 0, stream>>>(p);
+    lse_sweep_fp32<false, kCostSqEuclid><<<grid, NT, 0, stream>>>(p);
   }
   count_launch();
   return cudaGetLastError();

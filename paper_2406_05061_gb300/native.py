@@ -65,7 +65,7 @@ SIGNATURES = [
     ("progot_schedule_tau", ctypes.c_int, [_I32, _D, _D, _P]),
     ("progot_solve_theta", ctypes.c_int,
      [_P, _P, _I64, _P, _P, _I64, _I32, _I32, _P, _D, _P, _I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
-    ("coupling_metrics", ctypes.c_int, [_P, _P, _I64, _P, _P, _I64, _I32, _P, _P, _D, _P, _P, _SZ, _P]),
+    ("coupling_metrics", ctypes.c_int, [_P, _P, _I64, _P, _P, _I64, _I32, _P, _P, _P, _D, _P, _P, _SZ, _P]),
     ("sinkhorn_divergence", ctypes.c_int,
      [_P, _P, _I64, _P, _P, _I64, _I32, _D, _D, _I32, _I32, _P, _P, _P, _P, _SZ, _P]),
     ("coupling_diagonal", ctypes.c_int, [_P, _P, _I64, _I32, _P, _P, _D, _P, _P, _P, _P, _SZ, _P]),
@@ -74,7 +74,7 @@ SIGNATURES = [
     ("progot_solve_pnorm", ctypes.c_int,
      [_P, _P, _I64, _P, _P, _I64, _I32, _D, _I32, _P, _P, _D, _P, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     ("entropic_map_apply_pnorm", ctypes.c_int, [_P, _I64, _P, _I64, _I32, _D, _I32, _P, _P, _P, _P, _P, _SZ, _P]),
-    ("coupling_metrics_pnorm", ctypes.c_int, [_P, _P, _I64, _P, _P, _I64, _I32, _D, _P, _P, _D, _P, _P, _SZ, _P]),
+    ("coupling_metrics_pnorm", ctypes.c_int, [_P, _P, _I64, _P, _P, _I64, _I32, _D, _P, _P, _P, _D, _P, _P, _SZ, _P]),
     ("progot_mean_cost_pnorm", ctypes.c_int, [_P, _I64, _P, _I64, _I32, _D, _P, _P, _SZ, _P]),
     ("progot_profile", ctypes.c_int, [_I32]),
     ("progot_profile_read", ctypes.c_int, [_I32, _P, _P, _P, _P]),
@@ -329,15 +329,17 @@ class CouplingMetricsStruct(ctypes.Structure):
                 ("transport_cost", "entropy", "dual", "mass", "err_row", "err_col")]
 
 
-def coupling_metrics(x, y, f, g, eps, a=None, b=None, workspace=None, stream=None) -> dict:
-    """<P, C>, E(P), the eq. (5) objective, sum P and both marginal errors (Sec. 5.2)."""
+def coupling_metrics(x, y, f, g, eps, a=None, b=None, x_cost=None, workspace=None, stream=None) -> dict:
+    """<P, C>, E(P), the eq. (5) objective, sum P and both marginal errors (Sec. 5.2);
+    with x_cost the transport cost integrates ||xc_i - y_j||^2 against P (on x)."""
     _dev(x, "x"), _dev(y, "y")
     n, d = x.shape
     m = y.shape[0]
     ws = _ws(workspace, n, m, d, "fp32")
     res = CouplingMetricsStruct()
     rc = lib().coupling_metrics(_dev(x, "x"), _opt(a, "a", (n,)), n, _dev(y, "y"), _opt(b, "b", (m,)), m, d,
-                                _dev(f, "f", (n,)), _dev(g, "g", (m,)), float(eps), ctypes.byref(res),
+                                _dev(f, "f", (n,)), _dev(g, "g", (m,)), _opt(x_cost, "x_cost", (n, d)), float(eps),
+                                ctypes.byref(res),
                                 ctypes.c_void_p(ws.ptr), ws.bytes, _stream(stream))
     _check(rc, allow_not_converged=False)
     return {k: getattr(res, k) for k, _ in CouplingMetricsStruct._fields_}
@@ -450,7 +452,7 @@ def entropic_map_apply_pnorm(xq, y, p, g_all, eps, alpha, out=None, workspace=No
     return out
 
 
-def coupling_metrics_pnorm(x, y, p, f, g, eps, a=None, b=None, workspace=None, stream=None) -> dict:
+def coupling_metrics_pnorm(x, y, p, f, g, eps, a=None, b=None, x_cost=None, workspace=None, stream=None) -> dict:
     """coupling_metrics for the p-norm cost."""
     _dev(x, "x"), _dev(y, "y")
     n, d = x.shape
@@ -458,7 +460,8 @@ def coupling_metrics_pnorm(x, y, p, f, g, eps, a=None, b=None, workspace=None, s
     ws = _ws(workspace, n, m, d, "fp32")
     res = CouplingMetricsStruct()
     rc = lib().coupling_metrics_pnorm(_dev(x, "x"), _opt(a, "a", (n,)), n, _dev(y, "y"), _opt(b, "b", (m,)), m, d,
-                                      float(p), _dev(f, "f", (n,)), _dev(g, "g", (m,)), float(eps), ctypes.byref(res),
+                                      float(p), _dev(f, "f", (n,)), _dev(g, "g", (m,)), _opt(x_cost, "x_cost", (n, d)),
+                                      float(eps), ctypes.byref(res),
                                       ctypes.c_void_p(ws.ptr), ws.bytes, _stream(stream))
     _check(rc, allow_not_converged=False)
     return {k: getattr(res, k) for k, _ in CouplingMetricsStruct._fields_}

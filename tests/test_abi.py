@@ -135,9 +135,11 @@ def test_widened_entry_points_check_arguments_on_the_host(lib):
                                 None, None, None, ws, 1 << 20, None)
     assert rc == native.PROGOT_ERR_INVALID_ARG
     met = native.CouplingMetricsStruct()
-    rc = lib.coupling_metrics(fake, None, 8, fake, None, 8, 2, fake, fake, -1.0, ctypes.byref(met), ws, 1 << 20, None)
+    rc = lib.coupling_metrics(fake, None, 8, fake, None, 8, 2, fake, fake, None, -1.0, ctypes.byref(met), ws, 1 << 20,
+                              None)
     assert rc == native.PROGOT_ERR_INVALID_ARG and "eps" in native.last_error()
-    rc = lib.coupling_metrics(fake, None, 8, fake, None, 8, 2, None, fake, 1.0, ctypes.byref(met), ws, 1 << 20, None)
+    rc = lib.coupling_metrics(fake, None, 8, fake, None, 8, 2, None, fake, None, 1.0, ctypes.byref(met), ws, 1 << 20,
+                              None)
     assert rc == native.PROGOT_ERR_INVALID_ARG
     val = ctypes.c_double(0.0)
     rc = lib.sinkhorn_divergence(fake, None, 8, fake, None, 8, 2, 1.0, -1.0, 10, 0, ctypes.byref(val), None, None,

@@ -211,3 +211,22 @@ def test_overflowing_warm_start_keeps_iterating(nat):
     ref = O.sinkhorn(None, p.x, None, p.y, eps, 1e-7)
     T = O.entropic_map(p.x, p.y, host(res.g), eps)
     assert map_rms_rel(T, O.entropic_map(p.x, p.y, ref.g, eps), p.y) <= TOL_FP32
+
+
+@pytest.mark.parametrize("d", [5, 64])
+def test_coupling_cost_against_the_original_cloud(nat, d):
+    # ProgOT's final coupling lives on X^(K) and is measured against the original X
+    p = W.gmm_pair(600, 450, d, seed=50 + d, k=3)
+    K = 3
+    alpha = O.alpha_schedule(K)
+    e0 = O.mean_cost(p.x, p.y) / 20
+    res = nat.progot_solve(dev(p.x), dev(p.y), alpha, [3 * e0, 2 * e0, e0], [1e-5] * K, max_iter=5000)
+    assert res.status == nat.PROGOT_OK, nat.last_error()
+    xl, f, g = host(res.x_last), host(res.f_last), host(res.g_all[K - 1])
+    met = nat.coupling_metrics(res.x_last, dev(p.y), res.f_last, res.g_all[K - 1], e0, x_cost=dev(p.x))
+    want = O.coupling_cost(xl, p.y, f, g, e0, X_cost=p.x)
+    assert met["transport_cost"] == pytest.approx(want, rel=TOL_FP32)
+    assert met["entropy"] == pytest.approx(O.coupling_entropy(xl, p.y, f, g, e0), rel=TOL_FP32)
+    # without x_cost the same call measures the cost on X^(K) itself
+    met2 = nat.coupling_metrics(res.x_last, dev(p.y), res.f_last, res.g_all[K - 1], e0)
+    assert met2["transport_cost"] == pytest.approx(O.coupling_cost(xl, p.y, f, g, e0), rel=TOL_FP32)

@@ -122,3 +122,15 @@ def test_coupling_metrics_and_mean_cost_pnorm(nat):
     assert met["dual"] == pytest.approx(dual, rel=TOL_FP32, abs=TOL_FP32 * met["transport_cost"])
     mc = nat.progot_mean_cost_pnorm(dev(pr.x), dev(pr.y), 1.5)
     assert mc == pytest.approx(O.mean_cost(pr.x, pr.y, P15), rel=1e-5)
+
+
+def test_coupling_metrics_pnorm_against_the_original_cloud(nat):
+    pr = W.gmm_pair(500, 400, 10, seed=65, k=3)
+    K = 2
+    alpha = O.alpha_schedule(K)
+    e0 = O.mean_cost(pr.x, pr.y, P15) / 20
+    res, _ = nat.progot_solve_pnorm(dev(pr.x), dev(pr.y), 1.5, alpha, [1e-5] * K, eps=[2 * e0, e0], max_iter=10000)
+    assert res.status == nat.PROGOT_OK, nat.last_error()
+    xl, f, g = host(res.x_last), host(res.f_last), host(res.g_all[K - 1])
+    met = nat.coupling_metrics_pnorm(res.x_last, dev(pr.y), 1.5, res.f_last, res.g_all[K - 1], e0, x_cost=dev(pr.x))
+    assert met["transport_cost"] == pytest.approx(O.coupling_cost(xl, pr.y, f, g, e0, P15, X_cost=pr.x), rel=TOL_FP32)
