@@ -521,7 +521,7 @@ def main():
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    native.profile(True, period=8)  # events around every 8th sweep launch
+    native.profile(True, period=1)  # Sinkhorn chunks timed whole; other sweeps launch by launch
     native.launch_count(reset=True)
     if pg:
         pg.barrier()

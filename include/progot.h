@@ -418,15 +418,16 @@ int64_t progot_launch_count(int32_t reset);
 
 /*
  * progot_profile - enable (enable >= 1) or disable (0) per-kernel timing on the calling
- * thread and reset its totals. While enabled, every enable-th log-sum-exp sweep and map
- * sweep launch (all of them for enable = 1) is bracketed by CUDA events recorded on the
- * launching stream; launches of a Sinkhorn loop after its stop (which return at entry)
- * are not counted. Sampling keeps the events' own cost (a few microseconds per pair)
- * out of most launches.
+ * thread and reset its totals. While enabled, the log-sum-exp sweeps of a Sinkhorn loop
+ * are timed by CUDA events around each chunk of sweeps the loop enqueues (an event
+ * between two sweeps would break their programmatic overlap and inflate the figure);
+ * a chunk counts when all its launches did work (launches after the loop's stop return
+ * at entry). Other sweep and map launches are sampled one by one, every enable-th
+ * launch (all of them for enable = 1).
  * progot_profile_read - totals since the last progot_profile call for kernel 0 (the
- * row/column log-sum-exp sweep) or 1 (the map sweep): sampled launches, their summed
+ * row/column log-sum-exp sweep) or 1 (the map sweep): timed launches, their summed
  * device time in ms and summed point pairs (rows x columns), and the number of
- * launches that did work (sampled or not). Reading synchronises on the recorded events.
+ * launches that did work (timed or not). Reading synchronises on the recorded events.
  * Any output pointer may be NULL.
  */
 int progot_profile(int32_t enable);

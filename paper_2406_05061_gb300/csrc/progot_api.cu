@@ -30,15 +30,18 @@ static thread_local std::string t_last_error;
 void set_last_error_message(const char* msg) { t_last_error = msg ? msg : ""; }
 
 // Opt-in per-kernel timing (progot_profile): CUDA events recorded on the launching
-// stream around every sweep. Launches of a Sinkhorn loop after its stop (no-op
-// launches) are discarded once the loop's final iteration count is known.
+// stream. Inside a Sinkhorn loop the events bracket each enqueued chunk of sweeps (an
+// event between two sweeps would break their programmatic overlap), and a chunk counts
+// only when all of its launches did work (launches after the loop's stop return at
+// entry); other sweeps (map passes, metrics) are sampled launch by launch.
 enum ProfKind { kProfLse = 0, kProfMap = 1, kProfKinds = 2 };
 struct ProfRec {
   cudaEvent_t a, b;
   int kind;
   double pairs;
   bool counted;
-  int64_t seq;  // sequence number of the launch among all profiled-kernel launches
+  int64_t seq;     // sequence number of the launch among all profiled-kernel launches
+  int64_t nl = 1;  // launches bracketed by the two events
 };
 struct Profiler {
   bool on = false;
@@ -89,7 +92,7 @@ static void prof_collect() {
       cudaEventElapsedTime(&ms, r.a, r.b);
       t_prof.ms[r.kind] += ms;
       t_prof.pairs[r.kind] += r.pairs;
-      t_prof.launches[r.kind] += 1;
+      t_prof.launches[r.kind] += r.nl;
     } else {
       cudaEventSynchronize(r.b);
     }
@@ -430,9 +433,9 @@ static void apply_cost(SweepParams& sp, const Cost& c, double eps) {
 // Launch one log-sum-exp sweep: float32 CUDA cores, or tcgen05 on the prepared split
 // operands (a_is_x: rows of the sweep are the x cloud).
 static int lse_sweep(const SweepParams& p, int32_t precision, cudaStream_t s, const TcOps* ops = nullptr,
-                     bool a_is_x = true, const Workspace* ws = nullptr) {
+                     bool a_is_x = true, const Workspace* ws = nullptr, bool in_loop = false) {
   ProfRec r;
-  const bool rec = prof_begin(r, s, kProfLse);
+  const bool rec = !in_loop && prof_begin(r, s, kProfLse);
   if (precision != PROGOT_FP32 && ops != nullptr && ops->on) {
     const CUtensorMap* ah = a_is_x ? &ops->xh_a : &ops->yh_a;
     const CUtensorMap* al = a_is_x ? &ops->xl_a : &ops->yl_a;
@@ -512,26 +515,41 @@ static int sinkhorn_core(const float* x, const float* a, int64_t n, const float*
         // alternate the operand roles so that the tensor-core sweep reads the bias rows
         // of the current f from one side's buffer while it writes the next f's rows
         // into the other side's buffer (x and y are the same cloud)
-        int r = lse_sweep(pf, precision, s, &ops, (sym_sweeps & 1) == 0, &ws);
+        int r = lse_sweep(pf, precision, s, &ops, (sym_sweeps & 1) == 0, &ws, true);
         if (r) return r;
         ++sym_sweeps;
         continue;
       }
-      int r = lse_sweep(pf, precision, s, &ops, true, &ws);
+      int r = lse_sweep(pf, precision, s, &ops, true, &ws, true);
       if (r) return r;
-      r = lse_sweep(pg, precision, s, &ops, false, &ws);
+      r = lse_sweep(pg, precision, s, &ops, false, &ws, true);
       if (r) return r;
     }
     return PROGOT_OK;
   };
-  const int64_t prof_seq0 = t_prof.seq[kProfLse];
   const int64_t need = (int64_t)max_iter + 1;  // f-sweeps that guarantee a stop
+  const int per_iter = symmetric ? 1 : 2;      // sweep launches per iteration
   int64_t launched = 0;
   int chunk = 2;
   int cur = 0;
+  std::vector<ProfRec> chunk_recs;  // events around each enqueued chunk (profiling on)
   auto issue = [&](int slot, int iters) -> int {
+    ProfRec pr;
+    if (t_prof.on) {
+      pr.a = t_prof.get();
+      pr.b = t_prof.get();
+      pr.seq = launched * per_iter;
+      pr.nl = (int64_t)iters * per_iter;
+      pr.kind = kProfLse;
+      pr.pairs = (double)pr.nl * (double)n * (double)m;
+      CK(cudaEventRecord(pr.a, s));
+    }
     int r = enqueue(iters);
     if (r) return r;
+    if (t_prof.on) {
+      CK(cudaEventRecord(pr.b, s));
+      chunk_recs.push_back(pr);
+    }
     launched += iters;
     CK(cudaMemcpyAsync(&t_host.hs[slot], ws.state, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
     CK(cudaEventRecord(t_host.ev[slot], s));
@@ -576,10 +594,12 @@ static int sinkhorn_core(const float* x, const float* a, int64_t n, const float*
   }
   if (t_prof.on) {
     // sweeps f_0, g_0, ..., g_{it-1}, f_it did work (f_0 .. f_it when symmetric); later
-    // launches returned at entry
-    const int64_t working = (symmetric ? 1 : 2) * (int64_t)fin.it + 1;
-    for (ProfRec& rr : t_prof.recs)
-      if (rr.kind == kProfLse && rr.seq >= prof_seq0) rr.counted = (rr.seq - prof_seq0) < working;
+    // launches returned at entry. A chunk is timed only when all its launches worked.
+    const int64_t working = (int64_t)per_iter * (int64_t)fin.it + 1;
+    for (ProfRec& rr : chunk_recs) {
+      rr.counted = rr.seq + rr.nl <= working;
+      t_prof.recs.push_back(rr);
+    }
     t_prof.worked[kProfLse] += working;
   }
   if (fin.fcur == 1) CK(cudaMemcpyAsync(f_a, f_b, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
