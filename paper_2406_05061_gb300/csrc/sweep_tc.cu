@@ -46,7 +46,8 @@ constexpr int A_BIAS_BYTES = BM * 32;        // 4 KB: 128 rows x 16 bf16 (32-byt
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded-wait limit per CTA
 
 struct TcShared {
-  uint64_t full[8];
+  uint64_t full[8];       // operand tiles of a stage landed
+  uint64_t bias_full[8];  // the stage's bias rows landed (plain arrival for stages without bias)
   uint64_t empty[8];
   uint64_t tmem_full[2];
   uint64_t tmem_empty[2];
@@ -57,6 +58,7 @@ struct TcShared {
   int32_t abort_flag;
   int32_t s_last;
   int32_t s_fin;
+  int32_t stop;           // the previous sweep already stopped the Sinkhorn loop
   double red[4];
   float2 ms[2][128];  // (max, sum) of LSE warpgroup 1 by segment parity, merged by warpgroup 0
 };
@@ -339,6 +341,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&sh.full[s], 1);
+      mbar_init(&sh.bias_full[s], 1);
       mbar_init(&sh.empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -349,6 +352,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     mbar_init(&sh.drain, 1);
     sh.abort_flag = 0;
+    sh.stop = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   // A-side bias operand: all ones (bf16 0x3F80), so that the K = 16 bias step adds
@@ -364,22 +368,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  // everything below may read results of the previous kernel in the stream
-  asm volatile("griddepcontrol.wait;" ::: "memory");
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = sh.tmem_base;
-  const bool stopped = p.state != nullptr && p.state->done;
-  const int fcur = p.state ? p.state->fcur : 0;
-  if (stopped) {
-    // the Sinkhorn loop already met its stop rule: release TMEM and leave
-    if (warp == 1) {
-      tc_fence_after();
-      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
-    }
-    return;
-  }
+  // The operand tiles do not depend on the previous sweep in the stream, so the producer
+  // loads the first stages and the MMA warp runs their operand products before the
+  // previous sweep has finished; only the bias rows (its new potential) and the LSE
+  // warps' reads of potentials and solver state wait for it (griddepcontrol.wait in the
+  // producer and in the LSE warps). When the previous sweep stopped the loop, the
+  // producer raises sh.stop through the pending bias barriers and every role winds down.
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer (whole warp, one lane issues)
@@ -390,10 +388,38 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // streamed A: each stage also carries the A K block (hi and lo) of its tile
     const uint32_t sabytes = NA == 0 ? A_TILE_BYTES * (tp.split3 ? 2u : 1u) : 0u;
     int a_issued = 0;
-    for (int k = 0; k < nseg && ok; ++k) {
+    bool waited = false, stopped = false;
+    int pend_s[8], pend_t[8], npend = 0;  // stages whose bias rows wait for the previous sweep
+    // wait for the previous sweep, then load the pending bias rows (or, when it stopped
+    // the loop, release the MMA warp through the pending bias barriers)
+    auto resolve = [&]() {
+      asm volatile("griddepcontrol.wait;" ::: "memory");
+      waited = true;
+      stopped = p.state != nullptr && *reinterpret_cast<volatile int32_t*>(&p.state->done) != 0;
+      if (elect_one()) {
+        if (stopped) sh.stop = 1;
+        for (int q = 0; q < npend; ++q) {
+          if (stopped) {
+            mbar_arrive(&sh.bias_full[pend_s[q]]);
+          } else {
+            unsigned char* st = smem + L.stage0 + pend_s[q] * L.stage_bytes;
+            mbar_arrive_expect_tx(&sh.bias_full[pend_s[q]], BIAS_TILE_BYTES);
+            tma_load_2d(st + L.bias_off, &mapBbias, &sh.bias_full[pend_s[q]], 0, pend_t[q] * BN);
+          }
+        }
+      }
+      __syncwarp();
+    };
+    for (int k = 0; k < nseg && ok && !stopped; ++k) {
       const Seg sg = segment(c, k, W, G, T);
       if (NA > 0) {
         const int ai = k % NA;
+        // reusing an A buffer waits for the MMA warp, which waits for the pending bias
+        // rows: they must be on their way first (as before reusing a stage below)
+        if (!waited && k >= NA) {
+          resolve();
+          if (stopped) break;
+        }
         ok = warp_wait(&sh.a_empty[ai], (uint32_t)(((k / NA) & 1) ^ 1), abort_flag);
         if (!ok) break;
         unsigned char* abuf = smem + L.a0 + ai * L.a_stride;
@@ -408,27 +434,42 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         __syncwarp();
         a_issued = k + 1;
       }
-      for (int t = sg.t0; t < sg.t1 && ok; ++t) {
+      for (int t = sg.t0; t < sg.t1 && ok && !stopped; ++t) {
         for (int kb = 0; kb < nkb; ++kb, ++u) {
           const int s = u % S;
+          if (!waited && u == S) {  // a stage is about to be reused: its bias must be on its way
+            resolve();
+            if (stopped) break;
+          }
           ok = warp_wait(&sh.empty[s], (uint32_t)(((u / S) & 1) ^ 1), abort_flag);
           if (!ok) break;
           unsigned char* st = smem + L.stage0 + s * L.stage_bytes;
           if (elect_one()) {
-            mbar_arrive_expect_tx(&sh.full[s], bbytes + sabytes + (kb == 0 ? BIAS_TILE_BYTES : 0u));
+            // after the wait the bias rows travel with the operands on full[s]; before it
+            // they follow later on bias_full[s]. bias_full[s] completes once per use of
+            // the stage either way (a plain arrival when it carries nothing).
+            const bool bias_now = waited && kb == 0;
+            mbar_arrive_expect_tx(&sh.full[s], bbytes + sabytes + (bias_now ? BIAS_TILE_BYTES : 0u));
             tma_load_2d(st, &mapBh, &sh.full[s], kb * KB, t * BN);
             if (tp.split3) tma_load_2d(st + L.b_lo_off, &mapBl, &sh.full[s], kb * KB, t * BN);
-            if (kb == 0) tma_load_2d(st + L.bias_off, &mapBbias, &sh.full[s], 0, t * BN);
+            if (bias_now) tma_load_2d(st + L.bias_off, &mapBbias, &sh.full[s], 0, t * BN);
             if (NA == 0) {
               tma_load_2d(st + L.a_stage_off, &mapAh, &sh.full[s], kb * KB, sg.r * BM);
               if (tp.split3) tma_load_2d(st + L.a_stage_off + A_TILE_BYTES, &mapAl, &sh.full[s], kb * KB, sg.r * BM);
             }
+            if (waited || kb != 0) mbar_arrive(&sh.bias_full[s]);
+          }
+          if (kb == 0 && !waited) {
+            pend_s[npend] = s;
+            pend_t[npend] = t;
+            ++npend;
           }
           __syncwarp();
         }
       }
     }
-    if (!ok) {
+    if (ok && !waited) resolve();  // fewer units than stages
+    if (!ok || stopped) {
       // drain this CTA's own copies still in flight before shared memory is released
       if (NA > 0)
         for (int k = max(0, a_issued - NA); k < a_issued; ++k)
@@ -478,6 +519,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 umma<BN>(d_tmem, al + adv, bh + adv, 1u);
               }
             }
+          }
+          __syncwarp();
+          if (u < S) {
+            // the first stages were loaded before the previous sweep finished: their bias
+            // rows (its new potential) may follow on bias_full[s]; later stages carry them
+            // on full[s]
+            ok = warp_wait(&sh.bias_full[s], (uint32_t)((u / S) & 1), abort_flag);
+            if (!ok) break;
+            if (*reinterpret_cast<volatile int32_t*>(&sh.stop) != 0) {
+              ok = false;  // the loop had already stopped: wind down (not a fault)
+              break;
+            }
+            tc_fence_after();
+          }
+          if (elect_one()) {
             if (kb == 0) umma<BN>(d_tmem, abias, bb, 1u);
             umma_commit(&sh.empty[s]);
           }
@@ -504,10 +560,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int row_local = quarter * 32 + lane;
     const int ltid = threadIdx.x - 64;  // 0..127 in warpgroup 0
     int tl = 0, jt = 0;
+    // potentials, weights and the solver state below are the previous sweep's results
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const bool stopped = p.state != nullptr && *reinterpret_cast<volatile int32_t*>(&p.state->done) != 0;
+    const int fcur = p.state ? p.state->fcur : 0;
     // A warp whose bounded wait failed turns "dead": it skips tile work but keeps
     // executing every named barrier below, so the other LSE warps never block on it.
     bool dead = false;
-    for (int k = 0; k < nseg; ++k) {
+    for (int k = 0; k < (stopped ? 0 : nseg); ++k) {
       const Seg sg = segment(c, k, W, G, T);
       float m_run = -INFINITY, s_run = 0.f;
       for (int t = sg.t0; t < sg.t1; ++t, ++tl) {
