@@ -38,6 +38,34 @@ WORKLOADS = {
                           nominal_sweeps=1062),
 }
 
+# DRAM traffic per launch of the dominant kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum) from one ncu capture of the default workload's sweep
+# (profiles/lse_sweep_tc_gmm8192_d64.md), valid only while the kernel's sources are the
+# ones captured: their SHA-256 prefix is checked at run time, else traffic is null.
+CAPTURED_TRAFFIC = {
+    ("lse_sweep_tc", "gmm8_8192_d64", "bf16x3"): dict(
+        bytes=4609024.0,
+        sources=("paper_2406_05061_gb300/csrc/sweep_tc.cu", "paper_2406_05061_gb300/csrc/sweep_epilogue.cuh",
+                 "paper_2406_05061_gb300/csrc/progot_common.cuh"),
+        sha256=("c5b25d8eebe3d45d", "33eed614b4d23717", "5f5f8ae4e51caf17")),
+}
+
+
+def captured_traffic(kernel: str, workload: str, precision: str):
+    import hashlib
+    rec = CAPTURED_TRAFFIC.get((kernel, workload, precision))
+    if rec is None:
+        return None
+    for path, want in zip(rec["sources"], rec["sha256"]):
+        try:
+            with open(os.path.join(ROOT, path), "rb") as fh:
+                if hashlib.sha256(fh.read()).hexdigest()[:16] != want:
+                    return None
+        except OSError:
+            return None
+    return rec["bytes"]
+
+
 # Measured peaks (MEASURED_PEAKS.json when present) and the unit counts used for the
 # CUDA-core roofline: 152 SMs x 128 FP32 FMA lanes x 2 flop at the max SM clock.
 FALLBACK_PEAKS = dict(hbm_gbs=6800.0, bf16_tflops=1900.0, bf16_tflops_sustained=1700.0, sm_max_mhz=2070.0)
@@ -453,7 +481,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16x3", choices=["fp32", "bf16x3", "bf16"])
-    ap.add_argument("--no-compare", action="store_true", help="skip the float32 comparison solve")
+    ap.add_argument("--compare", action="store_true",
+                    help="also time two float32 solves of the same workload (reported under other_precisions)")
+    ap.add_argument("--no-compare", action="store_true", help=argparse.SUPPRESS)  # the default
     ap.add_argument("--workload", default="gmm8_8192_d64",
                     choices=sorted(WORKLOADS) + ["batched256", "serving", "blur", "coupling"])
     ap.add_argument("--blur-n", type=int, default=60000, help="blur: number of images (32 x 32)")
@@ -569,7 +599,7 @@ def main():
     e2e_value = whole_job_rate(args.steps, world, e2e_total)
     # ------------------------------------------------ float32 path on the same workload
     compare = None
-    if args.precision != "fp32" and not args.no_compare:
+    if args.precision != "fp32" and args.compare and not args.no_compare:
         ws32 = native.Workspace(max(p.n, p.m, yt.shape[0]), max(p.n, p.m, yt.shape[0]), p.d, "fp32")
         tau32 = [wl["tau"]["fp32"]] * K
         r32 = native.progot_solve(x, y, alpha, eps, tau32, max_iter=10000, precision="fp32", workspace=ws32)
@@ -605,7 +635,9 @@ def main():
     achieved = flops_pair * pairs_per_launch / (avg_ms / 1e3) / 1e12
     sweeps_per_solve = (lse["worked"] + mp["worked"]) / args.steps
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "lse_sweep_fp32" if args.precision == "fp32" else "lse_sweep_tc",
+                "traffic": captured_traffic("lse_sweep_fp32" if args.precision == "fp32" else "lse_sweep_tc",
+                                            args.workload, args.precision),
+                "kernel": "lse_sweep_fp32" if args.precision == "fp32" else "lse_sweep_tc",
                 "launches_timed": lse["launches"], "launches_worked": lse["worked"], "avg_launch_ms": avg_ms,
                 "pairs_per_launch": pairs_per_launch,
                 "pairs_per_sec": pairs_per_launch / (avg_ms / 1e3), "peak_source": peak_src,
