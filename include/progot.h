@@ -412,6 +412,15 @@ int progot_mean_cost_pnorm(const float* x, int64_t n, const float* y, int64_t m,
  */
 int progot_set_stall_window(int32_t iters);
 
+/*
+ * progot_set_map_tc - choose the kernel of the map step (Alg. 2 / Alg. 3) on the
+ * tensor-core paths (PROGOT_BF16X3, PROGOT_BF16) for d <= 64: 1 (default) runs S = X Y^T
+ * and P Y on tcgen05 (P in bf16 hi/lo, Y^T in bf16 hi/lo, three products, float32
+ * accumulation in TMEM); 0 runs P Y on float32 CUDA cores after the tensor-core LSE
+ * pass (the path for d > 64 and PROGOT_FP32). Process-wide setting.
+ */
+int progot_set_map_tc(int32_t on);
+
 /* Number of kernels this library launched since the last call (process-wide counter);
  * used to report launches inside a timed region. */
 int64_t progot_launch_count(int32_t reset);

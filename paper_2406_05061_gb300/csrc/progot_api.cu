@@ -174,6 +174,8 @@ struct Workspace {
   void* yl;
   void* xb;         // bf16 bias rows (x side, rows padded to 128) x 16
   void* yb;
+  void* yth;        // Y^T as bf16 hi / lo: 64 x (nmax padded to 128), tensor-core map step (d <= 64)
+  void* ytl;
   int32_t* fault;   // set by a tensor-core CTA whose bounded wait expired
   size_t bytes;
 };
@@ -205,6 +207,12 @@ static WsDims ws_dims(int64_t n, int64_t m, int32_t d, int32_t precision = PROGO
   const int64_t rows_cap = (2 * mslots * kWaves / dch + w.rbmax + 1) * BMr + w.nmax;
   w.opart_elems = rows_cap * d;
   w.rpart_elems = rows_cap;
+  if (w.tc && w.dp == 64) {
+    // tensor-core map step: G * maxseg <= R + 3 G partial slots of 128 rows x 64
+    const int64_t slots = w.rbmax + 3 * (int64_t)num_sms();
+    w.opart_elems = std::max<int64_t>(w.opart_elems, slots * BMr * 64);
+    w.rpart_elems = std::max<int64_t>(w.rpart_elems, slots * BMr);
+  }
   return w;
 }
 
@@ -244,6 +252,9 @@ static size_t ws_layout(const WsDims& w, Workspace* out, char* base) {
   const size_t bb = w.tc ? 32 * (size_t)(cdiv(w.nmax, 256) * 256) : 0;
   ws.xb = take(bb);
   ws.yb = take(bb);
+  const size_t ytb = (w.tc && w.dp == 64) ? 2 * 64 * (size_t)(cdiv(w.nmax, 128) * 128) : 0;
+  ws.yth = take(ytb);
+  ws.ytl = take(ytb);
   ws.fault = (int32_t*)take(sizeof(int32_t));
   ws.bytes = off;
   if (out) *out = ws;
@@ -279,6 +290,9 @@ struct HostMirror {
   }
 };
 static thread_local HostMirror t_host;
+
+// Tensor-core map step for d <= 64 on the tensor-core path (progot_set_map_tc).
+static std::atomic<int> g_map_tc{1};
 
 static int check_common(const float* x, int64_t n, const float* y, int64_t m, int32_t d, int32_t precision) {
   if (x == nullptr || y == nullptr) return fail(PROGOT_ERR_INVALID_ARG, "x and y must not be NULL");
@@ -331,6 +345,8 @@ struct TcOps {
   // operand maps in the A role (128-row boxes) and the B role (bn-row boxes), bias maps
   // (bn-row boxes); CUtensorMap is 64-byte aligned by its own declaration
   CUtensorMap xh_a, xl_a, yh_a, yl_a, xh_b, xl_b, yh_b, yl_b, xb, yb;
+  // tensor-core map step (dp = 64): y-side bias rows in 128-row boxes, Y^T hi / lo
+  CUtensorMap yb128, yth, ytl;
   int nkb = 0;
   int split3 = 0;
   int bn = 128;
@@ -366,6 +382,11 @@ static int prep_tc(const float* x, int64_t n, const float* y, int64_t m, int32_t
   if (!rc) rc = make_map(&ops->yl_b, yl, m, dp, ops->bn);
   if (!rc) rc = make_map(&ops->xb, ws.xb, cdiv(n, 256) * 256, 16, ops->bn);
   if (!rc) rc = make_map(&ops->yb, ws.yb, cdiv(m, 256) * 256, 16, ops->bn);
+  if (!rc && dp == 64) {
+    rc = make_map(&ops->yb128, ws.yb, cdiv(m, 256) * 256, 16, 128);
+    if (!rc) rc = make_map(&ops->yth, ws.yth, 64, (int32_t)(cdiv(m, 128) * 128), 64);
+    if (!rc) rc = make_map(&ops->ytl, ws.ytl, 64, (int32_t)(cdiv(m, 128) * 128), 64);
+  }
   if (rc) return rc;
   const float bscale = (float)(kLog2e / eps);
   if (g_cur != nullptr) CK(launch_bias_prep(g_cur, yn, m, cdiv(m, 256) * 256, bscale, ws.yb, s));
@@ -482,7 +503,6 @@ static int sinkhorn_core(const float* x, const float* a, int64_t n, const float*
     if (rc) return rc;
   }
   const int cps = ops.on ? 1 : 2;
-  if (ops.on) CK(cudaMemsetAsync(ws.fault, 0, sizeof(int32_t), s));
   CK(launch_init_state(ws.state, s));
   SweepParams pf = make_sweep(x, n, y, m, d, xn, yn, eps, ws, cps);
   pf.wA = a;
@@ -641,6 +661,20 @@ static int map_step(float* X, int64_t n, const float* y, int64_t m, int32_t d, c
   apply_cost(pl, cost, eps);
   int rc = tc ? lse_sweep(pl, precision, s, ops, true, &ws) : lse_sweep(pl, PROGOT_FP32, s);
   if (rc) return rc;
+  if (tc && ops->nkb == 1 && g_map_tc.load()) {
+    // d <= 64: S and P Y both on the tensor cores
+    const int64_t m_pad = cdiv(m, 128) * 128;
+    CK(launch_split_yT(y, m, d, m_pad, ws.yth, ws.ytl, s));
+    int G = 0, maxseg = 0;
+    tc_plan(n, m, 128, num_sms(), &G, &maxseg);
+    ProfRec r;
+    const bool rec = prof_begin(r, s, kProfMap);
+    CK(launch_map_sweep_tc(X, X, ws.L, n, m, d, (float)alpha, &ops->xh_a, &ops->xl_a, &ops->yh_a, &ops->yl_a,
+                           &ops->yb128, &ops->yth, &ops->ytl, ws.Opart, ws.Rpart, ws.mcnt, G, maxseg, ws.fault, s));
+    if (rec) prof_end(r, s, kProfMap, (double)n * (double)m);
+    if (t_prof.on) t_prof.worked[kProfMap] += 1;
+    return PROGOT_OK;
+  }
   MapParams mp;
   memset(&mp, 0, sizeof(mp));
   mp.A = X;
@@ -682,6 +716,17 @@ static int map_step(float* X, int64_t n, const float* y, int64_t m, int32_t d, c
 static int zero_counters(const Workspace& ws, int64_t rbmax, cudaStream_t s) {
   CK(cudaMemsetAsync(ws.cnt, 0, sizeof(unsigned) * (rbmax + 2), s));
   CK(cudaMemsetAsync(ws.mcnt, 0, sizeof(unsigned) * (rbmax + 2), s));
+  CK(cudaMemsetAsync(ws.fault, 0, sizeof(int32_t), s));  // raised by a tensor-core kernel's expired wait
+  return PROGOT_OK;
+}
+
+// PROGOT_ERR_TIMEOUT when a tensor-core kernel of this call raised the fault flag
+// (synchronises the stream).
+static int check_fault(const Workspace& ws, cudaStream_t s) {
+  int32_t fault = 0;
+  CK(cudaMemcpyAsync(&fault, ws.fault, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (fault) return fail(PROGOT_ERR_TIMEOUT, "a tensor-core kernel hit its bounded wait (2 s) and aborted");
   return PROGOT_OK;
 }
 
@@ -820,7 +865,8 @@ static int solve_impl(const float* x, const float* a, int64_t n, const float* y,
     if (rc) return rc;
   }
   if (f_last) CK(cudaMemcpyAsync(f_last, ws.f0, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
-  CK(cudaStreamSynchronize(s));
+  rc = check_fault(ws, s);  // synchronises the stream
+  if (rc) return rc;
   if (worst) {
     t_last_error = worst_msg;
     return worst;
@@ -842,6 +888,11 @@ const char* progot_version(void) { return "0.1.0"; }
 size_t progot_workspace_size(int64_t n, int64_t m, int32_t d, int32_t precision) {
   if (n <= 0 || m <= 0 || d <= 0) return 0;
   return ws_layout(ws_dims(n, m, d, precision), nullptr, nullptr);
+}
+
+int progot_set_map_tc(int32_t on) {
+  g_map_tc.store(on ? 1 : 0);
+  return PROGOT_OK;
 }
 
 int progot_set_stall_window(int32_t iters) {
@@ -935,7 +986,7 @@ int entropic_map_apply(const float* xq, int64_t nq, const float* y, int64_t m, i
     rc = map_step(out, nq, y, m, d, gk, ws.yn, eps[k], al, precision, ws, s, &ops);
     if (rc) return rc;
   }
-  return PROGOT_OK;
+  return precision == PROGOT_FP32 ? PROGOT_OK : check_fault(ws, s);
 }
 
 int coupling_marginals(const float* x, int64_t n, const float* y, int64_t m, int32_t d, const float* f,

@@ -54,6 +54,7 @@ SIGNATURES = [
     ("progot_schedule_eps", ctypes.c_int,
      [_P, _I64, _P, _P, _I64, _P, _I64, _I32, _I32, _P, _P, _I32, _D, _D, _I32, _I32, _P, _P, _P, _P, _SZ, _P]),
     ("progot_set_stall_window", ctypes.c_int, [_I32]),
+    ("progot_set_map_tc", ctypes.c_int, [_I32]),
     ("progot_launch_count", ctypes.c_int64, [_I32]),
     ("progot_batched_workspace_size", _SZ, [_P, _I32, _I32, _I32]),
     ("progot_solve_batched", ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _P, _SZ, _P]),
@@ -516,6 +517,12 @@ def progot_schedule_eps(x, y, y_test, alpha, s_grid=None, beta0=5.0, tau=1e-6, m
                                      _hp(errors), ctypes.byref(pstar), ctypes.c_void_p(ws.ptr), ws.bytes,
                                      _stream(stream)), allow_not_converged=False)
     return eps_out, errors, pstar.value
+
+
+def set_map_tc(on: bool) -> None:
+    """Map step of the tensor-core paths (d <= 64) on tcgen05 (True, default) or with a
+    float32 CUDA-core P Y (False)."""
+    _check(lib().progot_set_map_tc(1 if on else 0), allow_not_converged=False)
 
 
 def set_stall_window(iters: int) -> None:

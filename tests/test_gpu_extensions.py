@@ -230,3 +230,33 @@ def test_coupling_cost_against_the_original_cloud(nat, d):
     # without x_cost the same call measures the cost on X^(K) itself
     met2 = nat.coupling_metrics(res.x_last, dev(p.y), res.f_last, res.g_all[K - 1], e0)
     assert met2["transport_cost"] == pytest.approx(O.coupling_cost(xl, p.y, f, g, e0), rel=TOL_FP32)
+
+
+@pytest.mark.parametrize("nq,m,d", [(1000, 700, 64), (333, 517, 17), (129, 130, 2), (4096, 3000, 48)])
+def test_map_step_on_tensor_cores(nat, nq, m, d):
+    # Alg. 3 with the tcgen05 map kernel (S = X Y^T and P Y on the tensor cores, d <= 64)
+    # against the oracle's Alg. 3 from the same g^(k), and against the float32 P Y path
+    p = W.gmm_pair(nq, m, d, seed=nq + m + d, k=4)
+    K = 2
+    alpha = O.alpha_schedule(K)
+    e0 = O.mean_cost(p.x, p.y) / 20
+    eps = [2 * e0, e0]
+    res = nat.progot_solve(dev(p.x), dev(p.y), alpha, eps, [1e-4] * K, max_iter=5000, precision="bf16x3")
+    assert res.status == nat.PROGOT_OK, nat.last_error()
+    g_all = host(res.g_all)
+    xq = W.gmm_pair(nq, 10, d, seed=7 + d, k=4).x
+    ref = O.progot_map(xq, p.y, g_all, eps, alpha)
+    try:
+        nat.set_map_tc(True)
+        t_tc = host(nat.entropic_map_apply(dev(xq), dev(p.y), res.g_all, eps, alpha, precision="bf16x3"))
+        nat.set_map_tc(False)
+        t_f32 = host(nat.entropic_map_apply(dev(xq), dev(p.y), res.g_all, eps, alpha, precision="bf16x3"))
+    finally:
+        nat.set_map_tc(True)
+    assert map_rms_rel(t_tc, ref, p.y) <= TOL_MIXED
+    assert map_rms_rel(t_f32, ref, p.y) <= TOL_MIXED
+    assert map_rms_rel(t_tc, t_f32, p.y) <= TOL_MIXED
+    # in place (out aliasing the query points) gives the same result
+    xq_dev = dev(xq)
+    nat.entropic_map_apply(xq_dev, dev(p.y), res.g_all, eps, alpha, precision="bf16x3", out=xq_dev)
+    assert map_rms_rel(host(xq_dev), t_tc, p.y) <= 1e-6
