@@ -12,14 +12,17 @@
 // beta_lo, 0, ...] (a three-way bf16 split of the float32 beta), so TMEM holds t_ij
 // directly and the cost matrix is never formed.
 //
-// CTA = 6 warps, one 128-row block of A and a range of 128-column tiles of B:
-//   warp 0: TMA producer (A once, then B hi/lo stages; its 32 lanes also write the
-//           beta rows of each tile into shared memory);
-//   warp 1: TMEM owner and MMA issuer (one lane), 2 x 128 fp32 TMEM columns, double
-//           buffered so that the MMAs of tile t + 1 overlap the LSE of tile t;
-//   warps 2-5: one TMEM lane (= one row) per thread; tcgen05.ld the 128 values of
-//           the tile and fold them into an online (max, sum) in log2 units.
-// Column splits are combined in split order by the last CTA of each row block, whose
+// Persistent CTAs of 12 warps; each owns a contiguous range of (128-row block,
+// BN-column tile) work units, cut at row-block boundaries into segments:
+//   warp 0: TMA producer (the A operand of a segment, B hi/lo and bias-row stages);
+//   warp 1: TMEM owner and MMA issuer (one lane), two BN-column fp32 accumulators so
+//           that the MMAs of tile t + 1 overlap the LSE of tile t;
+//   warps 2-9: two LSE warpgroups taking alternate tiles, one TMEM lane (= one row)
+//           per thread; tcgen05.ld the tile's values and fold them into an online
+//           (max, sum) in log2 units;
+//   warps 10-11: epilogue of the segments that end before the CTA's last one, so that
+//           the LSE warps go straight on to the next row block.
+// Column splits are combined in CTA order by the last CTA to finish a row block, whose
 // epilogue is shared with the float32 kernel (Sinkhorn update + marginal error,
 // raw L, or coupling marginal). Every mbarrier wait is bounded (2 s of global time);
 // on expiry the CTA records a fault, drains its own TMA and MMA work, frees TMEM and
@@ -36,7 +39,8 @@
 namespace progot {
 namespace tc {
 
-constexpr int NTHREADS = 320;    // 10 warps: producer, MMA, two LSE warpgroups
+constexpr int NTHREADS = 384;    // 12 warps: producer, MMA, two LSE warpgroups, two epilogue warps
+constexpr int EPI_TID0 = 320;    // first thread of the epilogue warps
 constexpr int TMEM_COLS = 512;   // two accumulators of up to 256 columns
 constexpr int A_TILE_BYTES = BM * KB * 2;    // 16 KB: 128 rows x 64 bf16
 constexpr int A_BIAS_BYTES = BM * 32;        // 4 KB: 128 rows x 16 bf16 (32-byte swizzle)
@@ -52,13 +56,17 @@ struct TcShared {
   uint64_t a_full[2];
   uint64_t a_empty[2];
   uint64_t drain;
+  uint64_t seg_full[2];   // a segment's merged (max, sum) handed to the epilogue warps
+  uint64_t seg_empty[2];  // ... and read by them
   uint32_t tmem_base;
   int32_t abort_flag;
-  int32_t s_last;
-  int32_t s_fin;
+  int32_t s_last, s_fin;  // segment epilogue flags of LSE warpgroup 0
+  int32_t e_last, e_fin;  // ... and of the epilogue warps
   int32_t stop;           // the previous sweep already stopped the Sinkhorn loop
   double red[4];
-  float2 ms[2][128];  // (max, sum) of LSE warpgroup 1 by segment parity, merged by warpgroup 0
+  double ered[4];
+  float2 ms[2][128];   // (max, sum) of LSE warpgroup 1 by segment parity, merged by warpgroup 0
+  float2 seg[2][128];  // merged (max, sum) of a handed-off segment, by segment parity
 };
 
 
@@ -108,8 +116,17 @@ __host__ __device__ inline SmemLayout smem_layout(int bn, int nkb, int split3, i
 }
 
 
+// Named barriers: 1 = both LSE warpgroups (256 threads), 2 = LSE warpgroup 0 (128),
+// 3 = the epilogue warps (64).
 __device__ __forceinline__ void lse_bar_all() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
-__device__ __forceinline__ void lse_bar() { asm volatile("bar.sync 2, 128;" ::: "memory"); }
+template <int NT>
+__device__ __forceinline__ void seg_bar() {
+  static_assert(NT == 128 || NT == 64, "segment epilogue groups");
+  if (NT == 128)
+    asm volatile("bar.sync 2, 128;" ::: "memory");
+  else
+    asm volatile("bar.sync 3, 64;" ::: "memory");
+}
 
 __device__ __forceinline__ float max3(float a, float b, float c) {
   float r;
@@ -153,6 +170,106 @@ __device__ __forceinline__ void write_bias_row(__nv_bfloat16* row16, float beta)
   dst[1] = make_uint4(0u, 0u, 0u, 0u);
 }
 
+// Epilogue of segment k of CTA c, run by NT threads (LSE warpgroup 0 with NT = 128 for
+// the CTA's last segment, the epilogue warps with NT = 64 for the others); thread tid
+// owns rows row0 + NT h of the row block. Publishes the segment's (max, sum) partials,
+// arrives on the row block's counter and, on the last arrival, combines the row
+// block's partials in CTA order, writes the rows' epilogue (and bias rows) and the
+// block's float64 error term, summed in the same tree for either NT (a shuffle sum per
+// 32 rows, then (q0 + q1) + (q2 + q3)); the last row block of the sweep finishes it.
+template <int NT>
+__device__ __forceinline__ void segment_epilogue(const TcParams& tp, int c, int k, const Seg& sg, int64_t W, int G,
+                                                 int T, int tid, int row0, const float2 (&mv)[BM / NT], int fcur,
+                                                 int32_t& s_last, int32_t& s_fin, double* red) {
+  constexpr int RPT = BM / NT;
+  const SweepParams& p = tp.p;
+  const float* potA_cur = p.potA_old;
+  float* out_target = p.out;
+  if (p.role == 1 || p.role == 3) {
+    potA_cur = (fcur == 0) ? p.out : p.out_alt;
+    out_target = (fcur == 0) ? p.out_alt : p.out;
+  }
+  // the rows' epilogue inputs are loaded now, overlapping the arrival below
+  RowIn rin[RPT];
+#pragma unroll
+  for (int h = 0; h < RPT; ++h) {
+    const int rl = row0 + NT * h;
+    const int64_t i = (int64_t)sg.r * BM + rl;
+    rin[h].an = 0.f;
+    rin[h].pot = 0.f;
+    rin[h].w = 0.f;
+    if (i < p.nA) {
+      p.partial[((int64_t)c * tp.maxseg + k) * BM + rl] = mv[h];
+      rin[h] = row_inputs(p, i, potA_cur);
+    }
+  }
+  const int c_first = cta_of((int64_t)sg.r * T, W, G);
+  const int c_last = cta_of((int64_t)sg.r * T + T - 1, W, G);
+  seg_bar<NT>();  // the partial stores of all rows happen before the arrival below
+  if (tid == 0) {
+    const unsigned prev = atomic_add_acq_rel_gpu(&p.cnt[sg.r], 1u);
+    s_last = (prev == (unsigned)(c_last - c_first));
+  }
+  seg_bar<NT>();  // ... and the other CTAs' partials are visible after it
+  if (!s_last) return;
+  double e[RPT];
+#pragma unroll
+  for (int h = 0; h < RPT; ++h) {
+    e[h] = 0.0;
+    const int rl = row0 + NT * h;
+    const int64_t i = (int64_t)sg.r * BM + rl;
+    if (i < p.nA) {
+      // issue the partial loads back to back, then combine them in CTA order
+      constexpr int kMaxC = 8;
+      const int nc = c_last - c_first + 1;
+      float2 pv[kMaxC];
+#pragma unroll
+      for (int q = 0; q < kMaxC; ++q) {
+        if (q < nc) {
+          const int cc = c_first + q;
+          const int kk = sg.r - (int)(work_begin(cc, W, G) / T);
+          pv[q] = __ldcg(&p.partial[((int64_t)cc * tp.maxseg + kk) * BM + rl]);
+        }
+      }
+      float2 acc = make_float2(-INFINITY, 0.f);
+#pragma unroll
+      for (int q = 0; q < kMaxC; ++q)
+        if (q < nc) acc = lse_combine(acc, pv[q]);
+      for (int cc = c_first + kMaxC; cc <= c_last; ++cc) {
+        const int kk = sg.r - (int)(work_begin(cc, W, G) / T);
+        acc = lse_combine(acc, __ldcg(&p.partial[((int64_t)cc * tp.maxseg + kk) * BM + rl]));
+      }
+      const float Lr = acc.x + __log2f(acc.y);
+      float val;
+      e[h] = row_epilogue(p, i, Lr, rin[h], out_target, &val);
+      if (tp.bias_out != nullptr && p.mode == kModePotential)
+        write_bias_row(tp.bias_out + i * 16, (val - rin[h].an) * p.bscale);
+    }
+  }
+  // block sum of the error terms, in a fixed order
+#pragma unroll
+  for (int h = 0; h < RPT; ++h) {
+    double v = e[h];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if ((tid & 31) == 0) red[(row0 + NT * h) >> 5] = v;
+  }
+  seg_bar<NT>();
+  if (tid == 0) {
+    const double tot = (red[0] + red[1]) + (red[2] + red[3]);
+    p.errpart[sg.r] = tot;
+    p.cnt[sg.r] = 0;
+    const unsigned prev = atomic_add_acq_rel_gpu(&p.cnt[tp.R], 1u);
+    s_fin = (prev == (unsigned)(tp.R - 1));
+  }
+  seg_bar<NT>();
+  if (s_fin && tid < 32) {
+    finish_sweep_warp(p, tp.R);
+    if (tid == 0) p.cnt[tp.R] = 0;
+  }
+  seg_bar<NT>();
+}
+
 template <int BN>
 __global__ void __launch_bounds__(NTHREADS, 1)
     lse_sweep_tc(const __grid_constant__ CUtensorMap mapAh, const __grid_constant__ CUtensorMap mapAl,
@@ -189,6 +306,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mbar_init(&sh.a_empty[b], 1);
     }
     mbar_init(&sh.drain, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sh.seg_full[b], 128);
+      mbar_init(&sh.seg_empty[b], 64);
+    }
     sh.abort_flag = 0;
     sh.stop = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -389,7 +510,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (elect_one()) umma_commit(&sh.drain);
     __syncwarp();
     warp_wait(&sh.drain, 0, abort_flag, true);
-  } else {
+  } else if (threadIdx.x < EPI_TID0) {
     // ------------------------------------------------------------ LSE warps
     // Two warpgroups: warpgroup wg reads TMEM buffer wg, i.e. the tiles with
     // (tile counter & 1) == wg, so two tiles are folded at once.
@@ -489,79 +610,36 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         m_run = (isnan(o.y) || isnan(s_run)) ? NAN : mrg.x;
         s_run = (isnan(o.y) || isnan(s_run)) ? NAN : mrg.y;
       }
-      // ---- segment done: publish the partial, last arrival combines the row block
-      const int64_t i = (int64_t)sg.r * BM + row_local;
-      if (i < p.nA) p.partial[((int64_t)c * tp.maxseg + k) * BM + row_local] = make_float2(m_run, s_run);
-      const float* potA_cur = p.potA_old;
-      float* out_target = p.out;
-      if (p.role == 1 || p.role == 3) {
-        potA_cur = (fcur == 0) ? p.out : p.out_alt;
-        out_target = (fcur == 0) ? p.out_alt : p.out;
+      // ---- segment done
+      if (k + 1 < nseg) {
+        // hand it to the epilogue warps and go on with the next segment's tiles (slot
+        // k & 1 was last read for segment k - 2)
+        const int sl = k & 1;
+        mbar_wait(&sh.seg_empty[sl], (uint32_t)(((k >> 1) & 1) ^ 1), abort_flag);
+        sh.seg[sl][row_local] = make_float2(m_run, s_run);
+        mbar_arrive(&sh.seg_full[sl]);
+        continue;
       }
-      // the row's epilogue inputs are loaded now, overlapping the arrival below
-      RowIn rin;
-      rin.an = 0.f;
-      rin.pot = 0.f;
-      rin.w = 0.f;
-      if (i < p.nA) rin = row_inputs(p, i, potA_cur);
-      lse_bar();  // the partial stores of all 128 rows happen before the arrival below
-      if (ltid == 0) {
-        const int c_first = cta_of((int64_t)sg.r * T, W, G);
-        const int c_last = cta_of((int64_t)sg.r * T + T - 1, W, G);
-        const unsigned prev = atomic_add_acq_rel_gpu(&p.cnt[sg.r], 1u);
-        sh.s_last = (prev == (unsigned)(c_last - c_first));
-      }
-      lse_bar();  // ... and the other CTAs' partials are visible after it
-      if (sh.s_last) {
-        const int c_first = cta_of((int64_t)sg.r * T, W, G);
-        const int c_last = cta_of((int64_t)sg.r * T + T - 1, W, G);
-        double e = 0.0;
-        if (i < p.nA) {
-          // issue the partial loads back to back, then combine them in CTA order
-          constexpr int kMaxC = 8;
-          const int nc = c_last - c_first + 1;
-          float2 pv[kMaxC];
-#pragma unroll
-          for (int q = 0; q < kMaxC; ++q) {
-            if (q < nc) {
-              const int cc = c_first + q;
-              const int kk = sg.r - (int)(work_begin(cc, W, G) / T);
-              pv[q] = __ldcg(&p.partial[((int64_t)cc * tp.maxseg + kk) * BM + row_local]);
-            }
-          }
-          float2 acc = make_float2(-INFINITY, 0.f);
-#pragma unroll
-          for (int q = 0; q < kMaxC; ++q)
-            if (q < nc) acc = lse_combine(acc, pv[q]);
-          for (int cc = c_first + kMaxC; cc <= c_last; ++cc) {
-            const int kk = sg.r - (int)(work_begin(cc, W, G) / T);
-            acc = lse_combine(acc, __ldcg(&p.partial[((int64_t)cc * tp.maxseg + kk) * BM + row_local]));
-          }
-          const float Lr = acc.x + __log2f(acc.y);
-          float val;
-          e = row_epilogue(p, i, Lr, rin, out_target, &val);
-          if (tp.bias_out != nullptr && p.mode == kModePotential)
-            write_bias_row(tp.bias_out + i * 16, (val - rin.an) * p.bscale);
-        }
-        // block sum of the error terms over the 128 LSE threads, in a fixed order
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
-        if (lane == 0) sh.red[quarter] = e;
-        lse_bar();
-        if (ltid == 0) {
-          const double tot = (sh.red[0] + sh.red[1]) + (sh.red[2] + sh.red[3]);
-          p.errpart[sg.r] = tot;
-          p.cnt[sg.r] = 0;
-          const unsigned prev = atomic_add_acq_rel_gpu(&p.cnt[tp.R], 1u);
-          sh.s_fin = (prev == (unsigned)(tp.R - 1));
-        }
-        lse_bar();
-        if (sh.s_fin && ltid < 32) {
-          finish_sweep_warp(p, tp.R);
-          if (ltid == 0) p.cnt[tp.R] = 0;
-        }
-        lse_bar();
-      }
+      const float2 mv[1] = {make_float2(m_run, s_run)};
+      segment_epilogue<128>(tp, c, k, sg, W, G, T, ltid, row_local, mv, fcur, sh.s_last, sh.s_fin, sh.red);
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue warps
+    // Segments before the CTA's last one: publish, arrive, and combine the row block on
+    // the last arrival, while the LSE warps work on the next segment.
+    const int etid = threadIdx.x - EPI_TID0;  // 0..63
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const bool stopped = p.state != nullptr && *reinterpret_cast<volatile int32_t*>(&p.state->done) != 0;
+    const int fcur = p.state ? p.state->fcur : 0;
+    for (int k = 0; k + 1 < (stopped ? 0 : nseg); ++k) {
+      const Seg sg = segment(c, k, W, G, T);
+      const int sl = k & 1;
+      const bool okw = mbar_wait(&sh.seg_full[sl], (uint32_t)((k >> 1) & 1), abort_flag);
+      float2 mv[2];
+      mv[0] = okw ? sh.seg[sl][etid] : make_float2(NAN, NAN);
+      mv[1] = okw ? sh.seg[sl][etid + 64] : make_float2(NAN, NAN);
+      mbar_arrive(&sh.seg_empty[sl]);
+      segment_epilogue<64>(tp, c, k, sg, W, G, T, etid, etid, mv, fcur, sh.e_last, sh.e_fin, sh.ered);
     }
   }
 
