@@ -2,6 +2,8 @@
 // for the warm start of Alg. 2, state initialisation, and deterministic float64
 // reductions (first moments for the closed-form mean cost of Alg. 4 and of the theta
 // rule, squared error for the Alg. 4 score, the coupling diagonal of Prop. 3).
+#include <algorithm>
+
 #include "progot_internal.h"
 
 namespace progot {
@@ -10,15 +12,16 @@ constexpr int kParts = 304;  // partial sums of the two-pass reductions
 
 int reduce_parts() { return kParts; }
 
-// One warp per row: |x_i|^2 summed in float64, stored as float32.
-__global__ void row_sqnorm_kernel(const float* __restrict__ X, int64_t n, int32_t d, float* __restrict__ out) {
+// One warp per row: |x_i - mu|^2 (mu = 0 when NULL) summed in float64, stored as float32.
+__global__ void row_sqnorm_kernel(const float* __restrict__ X, int64_t n, int32_t d, const float* __restrict__ mu,
+                                  float* __restrict__ out) {
   const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
   const float* x = X + row * (int64_t)d;
   double s = 0.0;
   for (int k = lane; k < d; k += 32) {
-    const double v = (double)x[k];
+    const double v = (double)x[k] - (mu ? (double)mu[k] : 0.0);
     s += v * v;
   }
 #pragma unroll
@@ -152,11 +155,53 @@ __global__ void mean_cost_closed(const double* __restrict__ mx, const double* __
   }
 }
 
-cudaError_t launch_row_sqnorm(const float* X, int64_t n, int32_t d, float* out, cudaStream_t s) {
+cudaError_t launch_row_sqnorm(const float* X, int64_t n, int32_t d, float* out, cudaStream_t s, const float* mu) {
   if (n <= 0) return cudaSuccess;
   const int rows_per_block = 8;
   const int64_t blocks = (n + rows_per_block - 1) / rows_per_block;
-  row_sqnorm_kernel<<<(unsigned)blocks, 256, 0, s>>>(X, n, d, out);
+  row_sqnorm_kernel<<<(unsigned)blocks, 256, 0, s>>>(X, n, d, mu, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// mu = (mean_i x_i + mean_j y_j) / 2 from the first moments mx, my (layout of
+// moments_pass1: [sum of squared norms, per-coordinate sums]).
+__global__ void center_kernel(const double* __restrict__ mx, const double* __restrict__ my, int64_t n, int64_t m,
+                              int32_t d, float* __restrict__ mu) {
+  for (int k = threadIdx.x; k < d; k += blockDim.x)
+    mu[k] = (float)(0.5 * (mx[1 + k] / (double)n + my[1 + k] / (double)m));
+}
+
+cudaError_t launch_center(const double* mx, const double* my, int64_t n, int64_t m, int32_t d, float* mu,
+                          cudaStream_t s) {
+  center_kernel<<<1, 256, 0, s>>>(mx, my, n, m, d, mu);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// L_i += bscale (|x_i|^2 - |x_i - mu|^2) = bscale (2 x_i . mu - |mu|^2): moves a row
+// log-sum-exp taken on centred operands to the uncentred form t_ij = scale x_i . y_j +
+// (g_j - |y_j|^2) bscale (one warp per row, float64 sums).
+__global__ void lse_uncenter_kernel(float* __restrict__ L, const float* __restrict__ X, int64_t n, int32_t d,
+                                    const float* __restrict__ mu, float bscale) {
+  const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  const float* x = X + row * (int64_t)d;
+  double s = 0.0;
+  for (int k = lane; k < d; k += 32) {
+    const double u = (double)mu[k];
+    s += (2.0 * (double)x[k] - u) * u;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (lane == 0) L[row] = (float)((double)L[row] + (double)bscale * s);
+}
+
+cudaError_t launch_lse_uncenter(float* L, const float* X, int64_t n, int32_t d, const float* mu, float bscale,
+                                cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  lse_uncenter_kernel<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(L, X, n, d, mu, bscale);
   count_launch();
   return cudaGetLastError();
 }
@@ -176,8 +221,12 @@ cudaError_t launch_init_state(SolverState* st, cudaStream_t s) {
 
 cudaError_t launch_moments(const float* X, int64_t n, int32_t d, double* partial, int parts, double* out,
                            cudaStream_t s) {
-  const int threads = 256;
-  const size_t smem = sizeof(double) * (threads / 32) * (size_t)(d + 1);
+  // up to 8 warps, each with its own d + 1 float64 accumulators in shared memory
+  const size_t per_warp = sizeof(double) * (size_t)(d + 1);
+  const int warps = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / per_warp));
+  const int threads = 32 * warps;
+  const size_t smem = per_warp * (size_t)warps;
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;  // d above 25,598
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(moments_pass1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -176,6 +176,10 @@ struct Workspace {
   void* yb;
   void* yth;        // Y^T as bf16 hi / lo: 64 x (nmax padded to 128), tensor-core map step (d <= 64)
   void* ytl;
+  float* mu;        // d: centre of the tensor-core operands
+  float* xnc;       // nmax: |x_i - mu|^2
+  float* ync;       // nmax: |y_j - mu|^2
+  double* cmom;     // 2 (d + 1): first moments of x and y for mu
   int32_t* fault;   // set by a tensor-core CTA whose bounded wait expired
   size_t bytes;
 };
@@ -255,6 +259,10 @@ static size_t ws_layout(const WsDims& w, Workspace* out, char* base) {
   const size_t ytb = (w.tc && w.dp == 64) ? 2 * 64 * (size_t)(cdiv(w.nmax, 128) * 128) : 0;
   ws.yth = take(ytb);
   ws.ytl = take(ytb);
+  ws.mu = (float*)take(w.tc ? sizeof(float) * (size_t)w.dp : 0);
+  ws.xnc = (float*)take(w.tc ? sizeof(float) * w.nmax : 0);
+  ws.ync = (float*)take(w.tc ? sizeof(float) * w.nmax : 0);
+  ws.cmom = (double*)take(w.tc ? sizeof(double) * 2 * (size_t)(w.d + 1) : 0);
   ws.fault = (int32_t*)take(sizeof(int32_t));
   ws.bytes = off;
   if (out) *out = ws;
@@ -347,18 +355,27 @@ struct TcOps {
   CUtensorMap xh_a, xl_a, yh_a, yl_a, xh_b, xl_b, yh_b, yl_b, xb, yb;
   // tensor-core map step (dp = 64): y-side bias rows in 128-row boxes, Y^T hi / lo
   CUtensorMap yb128, yth, ytl;
+  // centre mu of the operands and the squared norms |x_i - mu|^2, |y_j - mu|^2 that
+  // the tensor-core sweeps use in place of |x_i|^2, |y_j|^2
+  const float* mu = nullptr;
+  const float* xnc = nullptr;
+  const float* ync = nullptr;
   int nkb = 0;
   int split3 = 0;
   int bn = 128;
   bool on = false;
 };
 
-// Split sqrt(2 log2(e) / eps) X and Y into bf16 hi/lo and describe them for TMA; write
-// the bias rows of both sides from the current potentials (f on x, g on y) and the
-// squared norms.
+// Split sqrt(2 log2(e) / eps) (X - mu) and (Y - mu) into bf16 hi/lo and describe them
+// for TMA; write the bias rows of both sides from the current potentials (f on x, g on
+// y) and the centred squared norms. mu is the midpoint of the two clouds' means: the
+// cost |x - y|^2 = |x~|^2 + |y~|^2 - 2 x~ . y~ holds for any common centre, and the
+// bf16x3 products and their float32 accumulation lose accuracy in proportion to
+// |x~| |y~|, which centring keeps near the clouds' spread rather than their distance
+// from the origin. The potentials are the same for every centre.
 static int prep_tc(const float* x, int64_t n, const float* y, int64_t m, int32_t d, double eps, int32_t precision,
                    const Workspace& ws, TcOps* ops, cudaStream_t s, const float* f_cur = nullptr,
-                   const float* g_cur = nullptr, const float* xn = nullptr, const float* yn = nullptr) {
+                   const float* g_cur = nullptr) {
   ops->on = precision != PROGOT_FP32;
   if (!ops->on) return PROGOT_OK;
   const int32_t dp = pad64(d);
@@ -367,8 +384,16 @@ static int prep_tc(const float* x, int64_t n, const float* y, int64_t m, int32_t
   if (tc_stages(ops->nkb, ops->split3) < 2)
     return fail(PROGOT_ERR_INVALID_ARG, "d = %d is too large for the tensor-core sweep", d);
   const float sc = (float)std::sqrt(2.0 * kLog2e / eps);
-  CK(launch_split_bf16(x, n, d, dp, sc, ws.xh, ops->split3 ? ws.xl : nullptr, s));
-  CK(launch_split_bf16(y, m, d, dp, sc, ws.yh, ops->split3 ? ws.yl : nullptr, s));
+  CK(launch_moments(x, n, d, ws.rpart, reduce_parts(), ws.cmom, s));
+  CK(launch_moments(y, m, d, ws.rpart, reduce_parts(), ws.cmom + (d + 1), s));
+  CK(launch_center(ws.cmom, ws.cmom + (d + 1), n, m, d, ws.mu, s));
+  CK(launch_row_sqnorm(x, n, d, ws.xnc, s, ws.mu));
+  CK(launch_row_sqnorm(y, m, d, ws.ync, s, ws.mu));
+  ops->mu = ws.mu;
+  ops->xnc = ws.xnc;
+  ops->ync = ws.ync;
+  CK(launch_split_bf16(x, n, d, dp, sc, ws.xh, ops->split3 ? ws.xl : nullptr, s, ws.mu));
+  CK(launch_split_bf16(y, m, d, dp, sc, ws.yh, ops->split3 ? ws.yl : nullptr, s, ws.mu));
   ops->bn = tc_tile_cols(ops->nkb, ops->split3);
   void* xl = ops->split3 ? ws.xl : ws.xh;
   void* yl = ops->split3 ? ws.yl : ws.yh;
@@ -389,8 +414,8 @@ static int prep_tc(const float* x, int64_t n, const float* y, int64_t m, int32_t
   }
   if (rc) return rc;
   const float bscale = (float)(kLog2e / eps);
-  if (g_cur != nullptr) CK(launch_bias_prep(g_cur, yn, m, cdiv(m, 256) * 256, bscale, ws.yb, s));
-  if (f_cur != nullptr) CK(launch_bias_prep(f_cur, xn, n, cdiv(n, 256) * 256, bscale, ws.xb, s));
+  if (g_cur != nullptr) CK(launch_bias_prep(g_cur, ws.ync, m, cdiv(m, 256) * 256, bscale, ws.yb, s));
+  if (f_cur != nullptr) CK(launch_bias_prep(f_cur, ws.xnc, n, cdiv(n, 256) * 256, bscale, ws.xb, s));
   return PROGOT_OK;
 }
 
@@ -468,6 +493,9 @@ static int lse_sweep(const SweepParams& p, int32_t precision, cudaStream_t s, co
     tc_plan(p.nA, p.nB, ops->bn, num_sms(), &G, &maxseg);
     SweepParams q = p;
     q.splits = G;  // not used by the persistent kernel beyond bookkeeping
+    // the operands are centred: the row constants of the epilogue are the centred norms
+    if (q.An != nullptr) q.An = a_is_x ? ops->xnc : ops->ync;
+    if (q.Bn != nullptr) q.Bn = a_is_x ? ops->ync : ops->xnc;
     CK(launch_lse_sweep_tc(q, ah, al, bh, bl, bb, ops->nkb, ops->split3, ops->bn, G, maxseg,
                            ws ? ws->fault : nullptr, bias_out, s));
   } else {
@@ -499,7 +527,7 @@ static int sinkhorn_core(const float* x, const float* a, int64_t n, const float*
     ops.on = false;  // the p-norm cost runs on CUDA cores (float32)
     precision = PROGOT_FP32;
   } else {
-    rc = prep_tc(x, n, y, m, d, eps, precision, ws, &ops, s, f_a, symmetric ? f_a : g, xn, yn);
+    rc = prep_tc(x, n, y, m, d, eps, precision, ws, &ops, s, f_a, symmetric ? f_a : g);
     if (rc) return rc;
   }
   const int cps = ops.on ? 1 : 2;
@@ -674,6 +702,10 @@ static int map_step(float* X, int64_t n, const float* y, int64_t m, int32_t d, c
     if (rec) prof_end(r, s, kProfMap, (double)n * (double)m);
     if (t_prof.on) t_prof.worked[kProfMap] += 1;
     return PROGOT_OK;
+  }
+  if (tc) {
+    // the float32 map sweep below forms t_ij from the uncentred X and Y: move L there
+    CK(launch_lse_uncenter(ws.L, X, n, d, ops->mu, (float)(kLog2e / eps), s));
   }
   MapParams mp;
   memset(&mp, 0, sizeof(mp));
@@ -981,7 +1013,7 @@ int entropic_map_apply(const float* xq, int64_t nq, const float* y, int64_t m, i
     const double al = (k == K - 1) ? 1.0 : alpha[k];
     const float* gk = g_all + (int64_t)k * m;
     TcOps ops;
-    rc = prep_tc(out, nq, y, m, d, eps[k], precision, ws, &ops, s, nullptr, gk, nullptr, ws.yn);
+    rc = prep_tc(out, nq, y, m, d, eps[k], precision, ws, &ops, s, nullptr, gk);
     if (rc) return rc;
     rc = map_step(out, nq, y, m, d, gk, ws.yn, eps[k], al, precision, ws, s, &ops);
     if (rc) return rc;
@@ -1376,7 +1408,7 @@ int progot_schedule_eps(const float* x, int64_t n, const float* y, const float* 
     CK(cudaMemcpyAsync(ws.T, y_test, sizeof(float) * mt * d, cudaMemcpyDeviceToDevice, s));
     // tensor-core operands of the held-out points against Y, with the y-side bias of g
     TcOps ops;
-    rc = prep_tc(ws.T, mt, y, m, d, eps, precision, ws, &ops, s, nullptr, ws.gaux, nullptr, ws.yn);
+    rc = prep_tc(ws.T, mt, y, m, d, eps, precision, ws, &ops, s, nullptr, ws.gaux);
     if (rc) return rc;
     rc = map_step(ws.T, mt, y, m, d, ws.gaux, ws.yn, eps, 1.0, precision, ws, s, &ops);
     if (rc) return rc;

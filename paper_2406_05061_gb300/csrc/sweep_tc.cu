@@ -663,14 +663,16 @@ __global__ void bias_prep_kernel(const float* __restrict__ potB, const float* __
 }
 
 // ---------------------------------------------------------------- operand prep
-// hi/lo bf16 split of sqrt(c) * X, K padded with zeros to dp (a multiple of 64).
+// hi/lo bf16 split of sqrt(c) * (X - mu) (mu = 0 when NULL), K padded with zeros to dp
+// (a multiple of 64).
 __global__ void split_bf16_kernel(const float* __restrict__ X, int64_t n, int32_t d, int32_t dp, float scale,
-                                  __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+                                  const float* __restrict__ mu, __nv_bfloat16* __restrict__ hi,
+                                  __nv_bfloat16* __restrict__ lo) {
   const int64_t total = n * (int64_t)dp;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = e / dp;
     const int k = (int)(e - r * dp);
-    const float v = (k < d) ? X[r * d + k] * scale : 0.f;
+    const float v = (k < d) ? (X[r * d + k] - (mu ? mu[k] : 0.f)) * scale : 0.f;
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
     hi[e] = h;
     if (lo) lo[e] = __float2bfloat16_rn(v - __bfloat162float(h));
@@ -719,11 +721,12 @@ int tc_stages(int nkb, int split3) {
 }
 
 cudaError_t launch_split_bf16(const float* X, int64_t n, int32_t d, int32_t dp, float scale, void* hi, void* lo,
-                              cudaStream_t s) {
+                              cudaStream_t s, const float* mu) {
   const int64_t total = n * (int64_t)dp;
   int64_t blocks = (total + 255) / 256;
   if (blocks > 4096) blocks = 4096;
-  tc::split_bf16_kernel<<<(unsigned)blocks, 256, 0, s>>>(X, n, d, dp, scale, (__nv_bfloat16*)hi, (__nv_bfloat16*)lo);
+  tc::split_bf16_kernel<<<(unsigned)blocks, 256, 0, s>>>(X, n, d, dp, scale, mu, (__nv_bfloat16*)hi,
+                                                         (__nv_bfloat16*)lo);
   count_launch();
   return cudaGetLastError();
 }

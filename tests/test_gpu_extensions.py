@@ -260,3 +260,41 @@ def test_map_step_on_tensor_cores(nat, nq, m, d):
     xq_dev = dev(xq)
     nat.entropic_map_apply(xq_dev, dev(p.y), res.g_all, eps, alpha, precision="bf16x3", out=xq_dev)
     assert map_rms_rel(host(xq_dev), t_tc, p.y) <= 1e-6
+
+
+# ------------------------------------------- clouds far from the origin (centring)
+@pytest.mark.parametrize("d,offset", [(32, 200.0), (300, 30.0)])
+def test_tensor_core_path_far_from_the_origin(nat, d, offset):
+    # the squared Euclidean cost and hence f, g are invariant under a common
+    # translation; the tensor-core path centres its bf16 hi/lo operands, so a problem
+    # moved far from the origin keeps the parity of the original (uncentred, the bf16x3
+    # products of |x| |y| ~ d offset^2 would swamp the cost)
+    p = W.gmm_pair(700, 600, d, seed=49 + d, k=4)
+    v = np.full(d, offset, dtype=np.float64)
+    x, y = p.x + v, p.y + v
+    eps = 0.05 * O.mean_cost(p.x, p.y)
+    res = nat.sinkhorn_potentials(dev(x), dev(y), eps, 1e-4, max_iter=5000, precision="bf16x3")
+    assert res.status == nat.PROGOT_OK, nat.last_error()
+    f, g = host(res.f), host(res.g)
+    C = O.CostOperator(p.x, p.y)  # the same cost matrix
+    err = float(np.abs(O.row_marginal(C, f, g, eps) - 1.0 / p.n).sum() +
+                np.abs(O.col_marginal(C, f, g, eps) - 1.0 / p.m).sum())
+    assert err <= TOL_MIXED
+    ref = O.sinkhorn(None, p.x, None, p.y, eps, 1e-6, max_iter=5000)
+    T_gpu = O.entropic_map(p.x, p.y, g, eps)
+    assert map_rms_rel(T_gpu, O.entropic_map(p.x, p.y, ref.g, eps), p.y) <= TOL_MIXED
+
+
+def test_progot_far_from_the_origin_matches_the_translate(nat):
+    # Alg. 2 commutes with a common translation: X^(K)(X + v, Y + v) = X^(K)(X, Y) + v,
+    # through the tensor-core map step (d <= 64)
+    p = W.gmm_pair(900, 700, 16, seed=50, k=4)
+    v = np.linspace(40.0, 80.0, 16)
+    K = 3
+    alpha = O.alpha_schedule(K)
+    eps = [0.1 * O.mean_cost(p.x, p.y)] * K
+    tau = [1e-4] * K
+    res = nat.progot_solve(dev(p.x + v), dev(p.y + v), alpha, eps, tau, max_iter=5000, precision="bf16x3")
+    assert res.status == nat.PROGOT_OK, nat.last_error()
+    ref = O.progot(None, p.x, None, p.y, eps, alpha, [1e-6] * K)
+    assert map_rms_rel(host(res.x_out) - v, ref.x_out, p.y) <= TOL_MIXED
