@@ -109,6 +109,7 @@ static SweepParams noalloc_sweep(const float* A, int64_t nA, const float* B, int
   p.scale = (float)(2.0 * kLog2e / eps);
   p.bscale = (float)(kLog2e / eps);
   p.eps = eps;
+  p.inv_eps_f = (float)(1.0 / eps);
   p.inv_nA = 1.0 / (double)nA;
   p.log_w_uniform = std::log(1.0 / (double)nA);
   p.partial = partial;

@@ -164,17 +164,55 @@ cudaError_t launch_row_sqnorm(const float* X, int64_t n, int32_t d, float* out, 
   return cudaGetLastError();
 }
 
-// mu = (mean_i x_i + mean_j y_j) / 2 from the first moments mx, my (layout of
-// moments_pass1: [sum of squared norms, per-coordinate sums]).
-__global__ void center_kernel(const double* __restrict__ mx, const double* __restrict__ my, int64_t n, int64_t m,
-                              int32_t d, float* __restrict__ mu) {
-  for (int k = threadIdx.x; k < d; k += blockDim.x)
-    mu[k] = (float)(0.5 * (mx[1 + k] / (double)n + my[1 + k] / (double)m));
+// Per-coordinate column sums of X (blockIdx.y = 0) and Y (blockIdx.y = 1) in float64, in a
+// fixed order: warp w of block b sums rows b W + w + k gridDim.x W (W warps per block),
+// then the block adds its warps' sums in warp order.
+__global__ void center_pass1(const float* __restrict__ X, int64_t n, const float* __restrict__ Y, int64_t m,
+                             int32_t d, double* __restrict__ partial) {
+  extern __shared__ double acc[];  // d per warp
+  const float* Z = blockIdx.y ? Y : X;
+  const int64_t rows = blockIdx.y ? m : n;
+  const int warps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k = threadIdx.x; k < warps * d; k += blockDim.x) acc[k] = 0.0;
+  __syncthreads();
+  for (int64_t row = (int64_t)blockIdx.x * warps + warp; row < rows; row += (int64_t)gridDim.x * warps)
+    for (int k = lane; k < d; k += 32) acc[warp * d + k] += (double)Z[row * (int64_t)d + k];
+  __syncthreads();
+  double* out = partial + ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * d;
+  for (int k = threadIdx.x; k < d; k += blockDim.x) {
+    double t = 0.0;
+    for (int w = 0; w < warps; ++w) t += acc[w * d + k];
+    out[k] = t;
+  }
 }
 
-cudaError_t launch_center(const double* mx, const double* my, int64_t n, int64_t m, int32_t d, float* mu,
+// mu_k = (sum_x_k / n + sum_y_k / m) / 2 from the block partials, in block order.
+__global__ void center_finish(const double* __restrict__ partial, int parts, int64_t n, int64_t m, int32_t d,
+                              float* __restrict__ mu) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= d) return;
+  double sx = 0.0, sy = 0.0;
+  for (int b = 0; b < parts; ++b) {
+    sx += partial[(int64_t)b * d + k];
+    sy += partial[((int64_t)parts + b) * d + k];
+  }
+  mu[k] = (float)(0.5 * (sx / (double)n + sy / (double)m));
+}
+
+cudaError_t launch_center(const float* X, int64_t n, const float* Y, int64_t m, int32_t d, double* partial, float* mu,
                           cudaStream_t s) {
-  center_kernel<<<1, 256, 0, s>>>(mx, my, n, m, d, mu);
+  const size_t per_warp = sizeof(double) * (size_t)d;
+  const int warps = (int)std::max<size_t>(1, std::min<size_t>(8, (200 * 1024) / per_warp));
+  const size_t smem = per_warp * (size_t)warps;
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;  // d above 25,600
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(center_pass1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const int parts = kParts / 2;
+  center_pass1<<<dim3(parts, 2), 32 * warps, smem, s>>>(X, n, Y, m, d, partial);
+  count_launch();
+  center_finish<<<(d + 127) / 128, 128, 0, s>>>(partial, parts, n, m, d, mu);
   count_launch();
   return cudaGetLastError();
 }

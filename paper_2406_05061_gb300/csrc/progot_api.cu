@@ -179,7 +179,6 @@ struct Workspace {
   float* mu;        // d: centre of the tensor-core operands
   float* xnc;       // nmax: |x_i - mu|^2
   float* ync;       // nmax: |y_j - mu|^2
-  double* cmom;     // 2 (d + 1): first moments of x and y for mu
   int32_t* fault;   // set by a tensor-core CTA whose bounded wait expired
   size_t bytes;
 };
@@ -262,7 +261,6 @@ static size_t ws_layout(const WsDims& w, Workspace* out, char* base) {
   ws.mu = (float*)take(w.tc ? sizeof(float) * (size_t)w.dp : 0);
   ws.xnc = (float*)take(w.tc ? sizeof(float) * w.nmax : 0);
   ws.ync = (float*)take(w.tc ? sizeof(float) * w.nmax : 0);
-  ws.cmom = (double*)take(w.tc ? sizeof(double) * 2 * (size_t)(w.d + 1) : 0);
   ws.fault = (int32_t*)take(sizeof(int32_t));
   ws.bytes = off;
   if (out) *out = ws;
@@ -384,16 +382,12 @@ static int prep_tc(const float* x, int64_t n, const float* y, int64_t m, int32_t
   if (tc_stages(ops->nkb, ops->split3) < 2)
     return fail(PROGOT_ERR_INVALID_ARG, "d = %d is too large for the tensor-core sweep", d);
   const float sc = (float)std::sqrt(2.0 * kLog2e / eps);
-  CK(launch_moments(x, n, d, ws.rpart, reduce_parts(), ws.cmom, s));
-  CK(launch_moments(y, m, d, ws.rpart, reduce_parts(), ws.cmom + (d + 1), s));
-  CK(launch_center(ws.cmom, ws.cmom + (d + 1), n, m, d, ws.mu, s));
-  CK(launch_row_sqnorm(x, n, d, ws.xnc, s, ws.mu));
-  CK(launch_row_sqnorm(y, m, d, ws.ync, s, ws.mu));
+  CK(launch_center(x, n, y, m, d, ws.rpart, ws.mu, s));
   ops->mu = ws.mu;
   ops->xnc = ws.xnc;
   ops->ync = ws.ync;
-  CK(launch_split_bf16(x, n, d, dp, sc, ws.xh, ops->split3 ? ws.xl : nullptr, s, ws.mu));
-  CK(launch_split_bf16(y, m, d, dp, sc, ws.yh, ops->split3 ? ws.yl : nullptr, s, ws.mu));
+  CK(launch_split_bf16(x, n, d, dp, sc, ws.xh, ops->split3 ? ws.xl : nullptr, s, ws.mu, ws.xnc));
+  CK(launch_split_bf16(y, m, d, dp, sc, ws.yh, ops->split3 ? ws.yl : nullptr, s, ws.mu, ws.ync));
   ops->bn = tc_tile_cols(ops->nkb, ops->split3);
   void* xl = ops->split3 ? ws.xl : ws.xh;
   void* yl = ops->split3 ? ws.yl : ws.yh;
@@ -438,6 +432,7 @@ static SweepParams make_sweep(const float* A, int64_t nA, const float* B, int64_
   p.scale = (float)(2.0 * kLog2e / eps);
   p.bscale = (float)(kLog2e / eps);
   p.eps = eps;
+  p.inv_eps_f = (float)(1.0 / eps);
   p.inv_nA = 1.0 / (double)nA;
   p.log_w_uniform = std::log(1.0 / (double)nA);
   p.partial = ws.partial;

@@ -71,7 +71,8 @@ struct SweepParams {
   int32_t splits;      // column splits (gridDim.y)
   int32_t tiles_per_split;
   int32_t mode;        // SweepMode
-  int32_t role;        // 0 none, 1 f-update of a Sinkhorn loop (error + stop), 2 g-update (it++),
+  int32_t role;        // 0 none, 1 f-update of a Sinkhorn loop (error + stop; it++ when the
+                       //   loop goes on), 2 g-update (no state change),
                        // 3 symmetric self-transport update (A = B, potB = f): error + stop,
                        //   f <- (f + f_new) / 2 and it++
   int32_t max_iter;
@@ -79,6 +80,7 @@ struct SweepParams {
   float scale;         // 2 log2(e) / eps: multiplies x . y
   float bscale;        // log2(e) / eps: multiplies (potB_j - |b_j|^2)
   double eps;
+  float inv_eps_f;     // 1 / eps in float32 (the per-row error terms)
   double tau;
   double inv_nA;       // uniform weight 1/nA
   double log_w_uniform;  // log(1/nA)

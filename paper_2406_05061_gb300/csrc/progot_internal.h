@@ -48,7 +48,9 @@ int map_dchunk();
 // small kernels (prep.cu)
 cudaError_t launch_row_sqnorm(const float* X, int64_t n, int32_t d, float* out, cudaStream_t s,
                               const float* mu = nullptr);
-cudaError_t launch_center(const double* mx, const double* my, int64_t n, int64_t m, int32_t d, float* mu,
+// mu = (mean of the rows of X + mean of the rows of Y) / 2 (fixed-order float64 sums);
+// partial: reduce_parts() * 2 * d doubles of scratch.
+cudaError_t launch_center(const float* X, int64_t n, const float* Y, int64_t m, int32_t d, double* partial, float* mu,
                           cudaStream_t s);
 cudaError_t launch_lse_uncenter(float* L, const float* X, int64_t n, int32_t d, const float* mu, float bscale,
                                 cudaStream_t s);
@@ -75,7 +77,7 @@ cudaError_t launch_sum_parts(const double* partial, int parts, int width, double
 // tcgen05 sweeps (sweep_tc.cu): operands pre-scaled by sqrt(2 log2(e) / eps), split into
 // bf16 hi/lo with K padded to a multiple of 64; map* point at CUtensorMap objects.
 cudaError_t launch_split_bf16(const float* X, int64_t n, int32_t d, int32_t dp, float scale, void* hi, void* lo,
-                              cudaStream_t s, const float* mu = nullptr);
+                              cudaStream_t s, const float* mu = nullptr, float* norm = nullptr);
 // mapBbias: (nB padded to 128) x 16 bf16 rows [beta_hi, beta_mid, beta_lo, 0...] of the
 // B side; bias_out (optional): the same rows for the A side, written from the updated
 // potential in potential mode (the next sweep's B bias).

@@ -56,12 +56,12 @@ __device__ __forceinline__ void finish_sweep_warp(const SweepParams& p, int nblo
         st->done = 1;
       }
       if (!st->done) {
-        st->fcur ^= 1;  // the new f becomes current
-        if (p.role == 3) st->it += 1;
+        // the new f becomes current; the iteration (this f-update and the g-update that
+        // follows it, which changes no state) is counted here
+        st->fcur ^= 1;
+        st->it += 1;
       }
     }
-  } else if (p.role == 2) {
-    st->it += 1;
   }
 }
 
@@ -84,15 +84,17 @@ __device__ __forceinline__ RowIn row_inputs(const SweepParams& p, int64_t i, con
 }
 
 // Epilogue for one row given L = log2 sum_j 2^{t_ij}. Writes the row's output, returns
-// its error term (float64) and the written value in *val.
+// its error term and the written value in *val. The error terms are float32 (they only
+// feed the stop test against tau): on GB300 every float64 instruction of this epilogue
+// sits on the sweep's critical path at a small fraction of the float32 rate.
 //   potential: f_i = eps log w_i + |a_i|^2 - eps ln2 L, assembled in float64 adds and
 //              multiplies; error a_i |exp((f_old - f_new)/eps) - 1| with expm1 of the
 //              small float32 difference; the symmetric update (role 3) stores the
 //              average (f_old + f_new) / 2 and measures the error at f_old;
 //   marginal:  r_i = exp((pot_i - |a_i|^2)/eps + ln2 L), the exponent formed in float64
 //              (it is a difference of large terms) and exponentiated in float32.
-__device__ __forceinline__ double row_epilogue(const SweepParams& p, int64_t i, float L, const RowIn& in,
-                                               float* out_target, float* val) {
+__device__ __forceinline__ float row_epilogue(const SweepParams& p, int64_t i, float L, const RowIn& in,
+                                              float* out_target, float* val) {
   if (p.mode == kModePotential) {
     const double logw = p.wA ? (double)__logf(in.w) : p.log_w_uniform;
     const float fnew = (float)(p.eps * logw + (double)in.an - p.eps * kLn2 * (double)L);
@@ -103,23 +105,23 @@ __device__ __forceinline__ double row_epilogue(const SweepParams& p, int64_t i, 
       // a_i exp(d) is the row sum of P at the current f; far from feasibility (a warm
       // start at small eps) it overflows float32. Such a term only has to exceed tau,
       // so d is capped at 80 (the term stays below 1e35); a NaN stays NaN.
-      float d = (in.pot - fnew) * (float)(1.0 / p.eps);
+      float d = (in.pot - fnew) * p.inv_eps_f;
       if (d > 80.f) d = 80.f;
-      return (double)in.w * (double)fabsf(expm1f(d));
+      return in.w * fabsf(expm1f(d));
     }
-    return 0.0;
+    return 0.f;
   }
   if (p.mode == kModeLse) {
     out_target[i] = L;
     *val = L;
-    return 0.0;
+    return 0.f;
   }
   // marginal
   const double arg = ((double)in.pot - (double)in.an) / p.eps + kLn2 * (double)L;
   const float r = expf((float)arg);
   if (out_target) out_target[i] = r;
   *val = r;
-  return fabs((double)r - (double)in.w);
+  return fabsf(r - in.w);
 }
 
 }  // namespace progot

@@ -63,8 +63,8 @@ struct TcShared {
   int32_t s_last, s_fin;  // segment epilogue flags of LSE warpgroup 0
   int32_t e_last, e_fin;  // ... and of the epilogue warps
   int32_t stop;           // the previous sweep already stopped the Sinkhorn loop
-  double red[4];
-  double ered[4];
+  float red[4];
+  float ered[4];
   float2 ms[2][128];   // (max, sum) of LSE warpgroup 1 by segment parity, merged by warpgroup 0
   float2 seg[2][128];  // merged (max, sum) of a handed-off segment, by segment parity
 };
@@ -175,12 +175,14 @@ __device__ __forceinline__ void write_bias_row(__nv_bfloat16* row16, float beta)
 // owns rows row0 + NT h of the row block. Publishes the segment's (max, sum) partials,
 // arrives on the row block's counter and, on the last arrival, combines the row
 // block's partials in CTA order, writes the rows' epilogue (and bias rows) and the
-// block's float64 error term, summed in the same tree for either NT (a shuffle sum per
+// block's error term, summed in the same float32 tree for either NT (a shuffle sum per
 // 32 rows, then (q0 + q1) + (q2 + q3)); the last row block of the sweep finishes it.
+// The g-update of a Sinkhorn loop (role 2) measures no error and changes no solver
+// state, so its row blocks skip the sweep-level arrival altogether.
 template <int NT>
 __device__ __forceinline__ void segment_epilogue(const TcParams& tp, int c, int k, const Seg& sg, int64_t W, int G,
                                                  int T, int tid, int row0, const float2 (&mv)[BM / NT], int fcur,
-                                                 int32_t& s_last, int32_t& s_fin, double* red) {
+                                                 int32_t& s_last, int32_t& s_fin, float* red) {
   constexpr int RPT = BM / NT;
   const SweepParams& p = tp.p;
   const float* potA_cur = p.potA_old;
@@ -212,10 +214,10 @@ __device__ __forceinline__ void segment_epilogue(const TcParams& tp, int c, int 
   }
   seg_bar<NT>();  // ... and the other CTAs' partials are visible after it
   if (!s_last) return;
-  double e[RPT];
+  float e[RPT];
 #pragma unroll
   for (int h = 0; h < RPT; ++h) {
-    e[h] = 0.0;
+    e[h] = 0.f;
     const int rl = row0 + NT * h;
     const int64_t i = (int64_t)sg.r * BM + rl;
     if (i < p.nA) {
@@ -246,18 +248,22 @@ __device__ __forceinline__ void segment_epilogue(const TcParams& tp, int c, int 
         write_bias_row(tp.bias_out + i * 16, (val - rin[h].an) * p.bscale);
     }
   }
+  if (p.role == 2) {
+    if (tid == 0) p.cnt[sg.r] = 0;
+    return;  // the counter is read again only by the next sweep, after this grid ends
+  }
   // block sum of the error terms, in a fixed order
 #pragma unroll
   for (int h = 0; h < RPT; ++h) {
-    double v = e[h];
+    float v = e[h];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
     if ((tid & 31) == 0) red[(row0 + NT * h) >> 5] = v;
   }
   seg_bar<NT>();
   if (tid == 0) {
-    const double tot = (red[0] + red[1]) + (red[2] + red[3]);
-    p.errpart[sg.r] = tot;
+    const float tot = (red[0] + red[1]) + (red[2] + red[3]);
+    p.errpart[sg.r] = (double)tot;
     p.cnt[sg.r] = 0;
     const unsigned prev = atomic_add_acq_rel_gpu(&p.cnt[tp.R], 1u);
     s_fin = (prev == (unsigned)(tp.R - 1));
@@ -663,20 +669,28 @@ __global__ void bias_prep_kernel(const float* __restrict__ potB, const float* __
 }
 
 // ---------------------------------------------------------------- operand prep
-// hi/lo bf16 split of sqrt(c) * (X - mu) (mu = 0 when NULL), K padded with zeros to dp
-// (a multiple of 64).
+// One warp per row: hi/lo bf16 split of sqrt(c) (x_i - mu) (mu = 0 when NULL), K padded
+// with zeros to dp (a multiple of 64), and (when norm is not NULL) |x_i - mu|^2 summed in
+// float64 from the float32 differences.
 __global__ void split_bf16_kernel(const float* __restrict__ X, int64_t n, int32_t d, int32_t dp, float scale,
                                   const float* __restrict__ mu, __nv_bfloat16* __restrict__ hi,
-                                  __nv_bfloat16* __restrict__ lo) {
-  const int64_t total = n * (int64_t)dp;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = e / dp;
-    const int k = (int)(e - r * dp);
-    const float v = (k < d) ? (X[r * d + k] - (mu ? mu[k] : 0.f)) * scale : 0.f;
+                                  __nv_bfloat16* __restrict__ lo, float* __restrict__ norm) {
+  const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= n) return;
+  double s = 0.0;
+  for (int k = lane; k < dp; k += 32) {
+    const float u = (k < d) ? X[r * d + k] - (mu ? mu[k] : 0.f) : 0.f;
+    s += (double)u * (double)u;
+    const float v = u * scale;
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    hi[e] = h;
-    if (lo) lo[e] = __float2bfloat16_rn(v - __bfloat162float(h));
+    hi[r * dp + k] = h;
+    if (lo) lo[r * dp + k] = __float2bfloat16_rn(v - __bfloat162float(h));
   }
+  if (norm == nullptr) return;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (lane == 0) norm[r] = (float)s;
 }
 
 }  // namespace tc
@@ -721,12 +735,10 @@ int tc_stages(int nkb, int split3) {
 }
 
 cudaError_t launch_split_bf16(const float* X, int64_t n, int32_t d, int32_t dp, float scale, void* hi, void* lo,
-                              cudaStream_t s, const float* mu) {
-  const int64_t total = n * (int64_t)dp;
-  int64_t blocks = (total + 255) / 256;
-  if (blocks > 4096) blocks = 4096;
-  tc::split_bf16_kernel<<<(unsigned)blocks, 256, 0, s>>>(X, n, d, dp, scale, mu, (__nv_bfloat16*)hi,
-                                                         (__nv_bfloat16*)lo);
+                              cudaStream_t s, const float* mu, float* norm) {
+  if (n <= 0) return cudaSuccess;
+  tc::split_bf16_kernel<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(X, n, d, dp, scale, mu, (__nv_bfloat16*)hi,
+                                                                (__nv_bfloat16*)lo, norm);
   count_launch();
   return cudaGetLastError();
 }
