@@ -34,14 +34,17 @@ __global__ void scale_kernel(float* v, int64_t n, float factor) {
   if (i < n) v[i] *= factor;
 }
 
+// Both solver states (the second is used by loops that run the stop test one sweep later).
 __global__ void init_state_kernel(SolverState* st) {
-  st->it = 0;
-  st->done = 0;
-  st->status = kRunning;
-  st->fcur = 0;
-  st->best_it = 0;
-  st->err = 0.0;
-  st->best_err = INFINITY;
+  for (int q = 0; q < 2; ++q) {
+    st[q].it = 0;
+    st[q].done = 0;
+    st[q].status = kRunning;
+    st[q].fcur = 0;
+    st[q].best_it = 0;
+    st[q].err = 0.0;
+    st[q].best_err = INFINITY;
+  }
 }
 
 // Pass 1: block b sums rows b, b + parts, ... of (|x|^2, x_1 .. x_d) into partial[b].

@@ -163,7 +163,7 @@ struct Workspace {
   double* errpart;  // rbmax + 2
   unsigned* cnt;    // rbmax + 2
   unsigned* mcnt;   // rbmax + 2
-  SolverState* state;
+  SolverState* state;  // [2]
   double* rpart;    // parts * (d + 1)
   double* rout;     // 2 * (d + 1)
   float* Opart;     // opart_elems
@@ -242,7 +242,7 @@ static size_t ws_layout(const WsDims& w, Workspace* out, char* base) {
   ws.errpart = (double*)take(sizeof(double) * (w.rbmax + 2));
   ws.cnt = (unsigned*)take(sizeof(unsigned) * (w.rbmax + 2));
   ws.mcnt = (unsigned*)take(sizeof(unsigned) * (w.rbmax + 2));
-  ws.state = (SolverState*)take(sizeof(SolverState));
+  ws.state = (SolverState*)take(2 * sizeof(SolverState));  // [2]: see SweepParams::lag
   ws.rpart = (double*)take(sizeof(double) * reduce_parts() * (size_t)(w.d + 1));
   ws.rout = (double*)take(sizeof(double) * 2 * (size_t)(w.d + 1));
   ws.Opart = (float*)take(sizeof(float) * w.opart_elems);
@@ -550,8 +550,14 @@ static int sinkhorn_core(const float* x, const float* a, int64_t n, const float*
   pg.tau = tau;
   pg.max_iter = max_iter;
   apply_cost(pg, cost, eps);
+  // tensor-core loops run the stop test of an f-update in the g-update that follows it
+  // (SweepParams::lag): the f-update's last row block then ends the sweep without a
+  // sweep-level arrival and finish
+  const bool lag = ops.on && !symmetric;
+  pf.lag = pg.lag = lag ? 1 : 0;
 
   int64_t sym_sweeps = 0;
+  int64_t launched = 0;  // iterations enqueued so far
   auto enqueue = [&](int iters) -> int {
     for (int i = 0; i < iters; ++i) {
       if (symmetric) {
@@ -563,6 +569,7 @@ static int sinkhorn_core(const float* x, const float* a, int64_t n, const float*
         ++sym_sweeps;
         continue;
       }
+      pf.seq = pg.seq = (int32_t)(launched + i);
       int r = lse_sweep(pf, precision, s, &ops, true, &ws, true);
       if (r) return r;
       r = lse_sweep(pg, precision, s, &ops, false, &ws, true);
@@ -572,7 +579,6 @@ static int sinkhorn_core(const float* x, const float* a, int64_t n, const float*
   };
   const int64_t need = (int64_t)max_iter + 1;  // f-sweeps that guarantee a stop
   const int per_iter = symmetric ? 1 : 2;      // sweep launches per iteration
-  int64_t launched = 0;
   int chunk = 2;
   int cur = 0;
   std::vector<ProfRec> chunk_recs;  // events around each enqueued chunk (profiling on)
@@ -594,7 +600,9 @@ static int sinkhorn_core(const float* x, const float* a, int64_t n, const float*
       chunk_recs.push_back(pr);
     }
     launched += iters;
-    CK(cudaMemcpyAsync(&t_host.hs[slot], ws.state, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+    // after iteration launched - 1 the state is in state[launched & 1] (lagged) or state[0]
+    const SolverState* st_dev = ws.state + (lag ? (launched & 1) : 0);
+    CK(cudaMemcpyAsync(&t_host.hs[slot], st_dev, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
     CK(cudaEventRecord(t_host.ev[slot], s));
     return PROGOT_OK;
   };

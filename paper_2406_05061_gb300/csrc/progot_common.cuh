@@ -77,6 +77,13 @@ struct SweepParams {
                        //   f <- (f + f_new) / 2 and it++
   int32_t max_iter;
   int32_t stall_window;
+  // Stop test one sweep later (tensor-core Sinkhorn loops): the f-update of iteration
+  // seq writes its error partials but no state; the g-update of iteration seq reads
+  // state[seq & 1] and those partials, applies the f-update's stop test and writes
+  // state[(seq + 1) & 1] (a no-op g-update when the loop has stopped). 0: the last CTA
+  // of the f-update applies the test and state[0] is the only state.
+  int32_t lag;
+  int32_t seq;         // iteration of this sweep in its Sinkhorn loop (lag = 1)
   float scale;         // 2 log2(e) / eps: multiplies x . y
   float bscale;        // log2(e) / eps: multiplies (potB_j - |b_j|^2)
   double eps;

@@ -22,47 +22,59 @@ __device__ __forceinline__ double block_sum_f64(double v, double* red) {
   return tot;
 }
 
-// Called by one full warp of the last CTA of the whole sweep: sum the per-row-block
-// error partials in a fixed order (lane l takes blocks l, l + 32, ... in order, then a
-// fixed shuffle tree) and advance the device-side Sinkhorn state (lane 0).
-__device__ __forceinline__ void finish_sweep_warp(const SweepParams& p, int nblocks) {
+// Sum of the per-row-block error partials in a fixed order by one full warp (lane l
+// takes blocks l, l + 32, ... in order, then a fixed shuffle tree); every lane returns
+// the same total.
+__device__ __forceinline__ double sum_errpart_warp(const double* errpart, int nblocks) {
   const int lane = threadIdx.x & 31;
   double err = 0.0;
-  for (int b = lane; b < nblocks; b += 32) err += __ldcg(p.errpart + b);
+  for (int b = lane; b < nblocks; b += 32) err += __ldcg(errpart + b);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) err += __shfl_xor_sync(0xffffffffu, err, off);
-  if (lane != 0) return;
-  p.errpart[nblocks] = err;
-  SolverState* st = p.state;
-  if (st == nullptr) return;
-  if (p.role == 1 || p.role == 3) {
-    st->err = err;
-    const int it = st->it;
-    if (!isfinite(err)) {
-      st->status = kNumeric;
-      st->done = 1;
-    } else if (err <= p.tau) {
-      st->status = kConverged;
-      st->done = 1;
-    } else if (it >= p.max_iter) {
-      st->status = kMaxIter;
-      st->done = 1;
-    } else {
-      if (err < 0.99 * st->best_err) {
-        st->best_err = err;
-        st->best_it = it;
-      } else if (p.stall_window > 0 && it - st->best_it >= p.stall_window) {
-        st->status = kStalled;
-        st->done = 1;
-      }
-      if (!st->done) {
-        // the new f becomes current; the iteration (this f-update and the g-update that
-        // follows it, which changes no state) is counted here
-        st->fcur ^= 1;
-        st->it += 1;
-      }
+  return err;
+}
+
+// The stop test of Alg. 1 after an f-update whose row-marginal error is err: a
+// non-finite error, err <= tau, max_iter or a stall stop the loop; otherwise the new f
+// becomes current and the iteration (the f-update and the g-update that follows it,
+// which changes no state) is counted.
+__device__ __forceinline__ void f_update_transition(SolverState& st, double err, const SweepParams& p) {
+  st.err = err;
+  const int it = st.it;
+  if (!isfinite(err)) {
+    st.status = kNumeric;
+    st.done = 1;
+  } else if (err <= p.tau) {
+    st.status = kConverged;
+    st.done = 1;
+  } else if (it >= p.max_iter) {
+    st.status = kMaxIter;
+    st.done = 1;
+  } else {
+    if (err < 0.99 * st.best_err) {
+      st.best_err = err;
+      st.best_it = it;
+    } else if (p.stall_window > 0 && it - st.best_it >= p.stall_window) {
+      st.status = kStalled;
+      st.done = 1;
+    }
+    if (!st.done) {
+      st.fcur ^= 1;
+      st.it += 1;
     }
   }
+}
+
+// Called by one full warp of the last CTA of the whole sweep: sum the error partials
+// and, for an f-update (roles 1 and 3), advance the device-side Sinkhorn state (lane 0).
+__device__ __forceinline__ void finish_sweep_warp(const SweepParams& p, int nblocks) {
+  const double err = sum_errpart_warp(p.errpart, nblocks);
+  if ((threadIdx.x & 31) != 0) return;
+  p.errpart[nblocks] = err;
+  if (p.state == nullptr || !(p.role == 1 || p.role == 3)) return;
+  SolverState st = *p.state;
+  f_update_transition(st, err, p);
+  *p.state = st;
 }
 
 // Per-row inputs of the epilogue, loaded before the split combine so that their

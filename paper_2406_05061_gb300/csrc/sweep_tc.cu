@@ -170,6 +170,25 @@ __device__ __forceinline__ void write_bias_row(__nv_bfloat16* row16, float beta)
   dst[1] = make_uint4(0u, 0u, 0u, 0u);
 }
 
+static_assert(sizeof(SolverState) % 16 == 0, "the solver state is loaded in 16-byte pieces");
+
+// The Sinkhorn state this sweep runs under, read from L2 after griddepcontrol.wait; called
+// by a whole warp. For the g-update of a lagged loop it is the f-update's stop test
+// applied to state[seq & 1] with the f-update's error partials (every warp that needs
+// it computes the same value from the same loads in the same order).
+__device__ __forceinline__ SolverState sweep_state(const SweepParams& p) {
+  SolverState st;
+  const int4* src = reinterpret_cast<const int4*>(p.state + (p.lag ? (p.seq & 1) : 0));
+  int4* dst = reinterpret_cast<int4*>(&st);
+#pragma unroll
+  for (int q = 0; q < (int)(sizeof(SolverState) / 16); ++q) dst[q] = __ldcg(src + q);
+  if (p.lag && p.role == 2) {
+    const double err = sum_errpart_warp(p.errpart, (int)((p.nB + BM - 1) / BM));
+    if (!st.done) f_update_transition(st, err, p);
+  }
+  return st;
+}
+
 // Epilogue of segment k of CTA c, run by NT threads (LSE warpgroup 0 with NT = 128 for
 // the CTA's last segment, the epilogue warps with NT = 64 for the others); thread tid
 // owns rows row0 + NT h of the row block. Publishes the segment's (max, sum) partials,
@@ -265,8 +284,13 @@ __device__ __forceinline__ void segment_epilogue(const TcParams& tp, int c, int 
     const float tot = (red[0] + red[1]) + (red[2] + red[3]);
     p.errpart[sg.r] = (double)tot;
     p.cnt[sg.r] = 0;
-    const unsigned prev = atomic_add_acq_rel_gpu(&p.cnt[tp.R], 1u);
-    s_fin = (prev == (unsigned)(tp.R - 1));
+    s_fin = 0;
+    // a lagged loop's stop test runs in the next sweep, which reads the error partials
+    // once this grid has ended
+    if (!(p.lag && p.role == 1)) {
+      const unsigned prev = atomic_add_acq_rel_gpu(&p.cnt[tp.R], 1u);
+      s_fin = (prev == (unsigned)(tp.R - 1));
+    }
   }
   seg_bar<NT>();
   if (s_fin && tid < 32) {
@@ -360,7 +384,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     auto resolve = [&]() {
       asm volatile("griddepcontrol.wait;" ::: "memory");
       waited = true;
-      stopped = p.state != nullptr && *reinterpret_cast<volatile int32_t*>(&p.state->done) != 0;
+      stopped = p.state != nullptr && sweep_state(p).done != 0;
       if (elect_one()) {
         if (stopped) sh.stop = 1;
         for (int q = 0; q < npend; ++q) {
@@ -527,8 +551,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     int tl = 0, jt = 0;
     // potentials, weights and the solver state below are the previous sweep's results
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    const bool stopped = p.state != nullptr && *reinterpret_cast<volatile int32_t*>(&p.state->done) != 0;
-    const int fcur = p.state ? p.state->fcur : 0;
+    SolverState st0{};
+    if (p.state != nullptr) st0 = sweep_state(p);
+    const bool stopped = st0.done != 0;
+    const int fcur = st0.fcur;
     // A warp whose bounded wait failed turns "dead": it skips tile work but keeps
     // executing every named barrier below, so the other LSE warps never block on it.
     bool dead = false;
@@ -635,8 +661,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // the last arrival, while the LSE warps work on the next segment.
     const int etid = threadIdx.x - EPI_TID0;  // 0..63
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    const bool stopped = p.state != nullptr && *reinterpret_cast<volatile int32_t*>(&p.state->done) != 0;
-    const int fcur = p.state ? p.state->fcur : 0;
+    SolverState st0{};
+    if (p.state != nullptr) st0 = sweep_state(p);
+    const bool stopped = st0.done != 0;
+    const int fcur = st0.fcur;
+    // the g-update of a lagged loop records the f-update's stop test for the next sweeps
+    // (also when it is itself a no-op); no other CTA of this grid reads state[(seq + 1) & 1]
+    if (p.state != nullptr && p.lag && p.role == 2 && c == 0 && etid == 0) p.state[(p.seq + 1) & 1] = st0;
     for (int k = 0; k + 1 < (stopped ? 0 : nseg); ++k) {
       const Seg sg = segment(c, k, W, G, T);
       const int sl = k & 1;
