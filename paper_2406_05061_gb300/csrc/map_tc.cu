@@ -111,8 +111,8 @@ __global__ void __launch_bounds__(MT_NTHREADS, 1)
   MtShared& sh = *reinterpret_cast<MtShared*>(smem + MT_OFF_CTRL);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = blockIdx.x, G = mp.G, T = mp.T;
-  const int64_t W = (int64_t)mp.R * T;
-  const int nseg = num_segments(c, W, G, T);
+  const Split sp = make_split(mp.R, T, G);
+  const int nseg = num_segments(sp, c);
   volatile int32_t* abort_flag = &sh.abort_flag;
 
   if (threadIdx.x == 0) {
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(MT_NTHREADS, 1)
       return true;
     };
     for (int k = 0; k < nseg && ok; ++k) {
-      const Seg sg = segment(c, k, W, G, T);
+      const Seg sg = segment(sp, c, k);
       ok = warp_wait(&sh.a_empty, (uint32_t)((k & 1) ^ 1), abort_flag);
       if (!ok) break;
       if (elect_one()) {
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(MT_NTHREADS, 1)
       return true;
     };
     for (int k = 0; k < nseg && ok; ++k) {
-      const Seg sg = segment(c, k, W, G, T);
+      const Seg sg = segment(sp, c, k);
       ok = warp_wait(&sh.a_full, (uint32_t)(k & 1), abort_flag);
       if (!ok) break;
       tc_fence_after();
@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(MT_NTHREADS, 1)
     int tl = 0, jt = 0;  // tiles seen, own tiles
     bool dead = false;  // a failed wait: skip work, keep executing the named barriers
     for (int k = 0; k < nseg; ++k) {
-      const Seg sg = segment(c, k, W, G, T);
+      const Seg sg = segment(sp, c, k);
       const int64_t i = (int64_t)sg.r * BM + row_local;
       const bool row_ok = i < mp.nA;
       const float Lr = row_ok ? mp.L[i] : 0.f;
@@ -402,8 +402,8 @@ __global__ void __launch_bounds__(MT_NTHREADS, 1)
       }
       mt_bar_wg0();  // the slot stores of all 128 rows happen before the arrival
       if (ltid == 0) {
-        const int c_first = cta_of((int64_t)sg.r * T, W, G);
-        const int c_last = cta_of((int64_t)sg.r * T + T - 1, W, G);
+        int c_first, c_last;
+        contributors(sp, sg.r, &c_first, &c_last);
         const unsigned prev = atomic_add_acq_rel_gpu(&mp.cnt[sg.r], 1u);
         sh.s_last = (prev == (unsigned)(c_last - c_first));
       }
@@ -412,19 +412,17 @@ __global__ void __launch_bounds__(MT_NTHREADS, 1)
         // the row block's CTAs c_first..c_last hold one partial slot each; sum them in CTA
         // order, first the row sums (one thread per row), then the 128 x d block of P Y
         // with consecutive threads on consecutive coordinates (coalesced, independent loads)
-        const int c_first = cta_of((int64_t)sg.r * T, W, G);
-        const int c_last = cta_of((int64_t)sg.r * T + T - 1, W, G);
+        int c_first, c_last;
+        contributors(sp, sg.r, &c_first, &c_last);
         const int nc = c_last - c_first + 1;
         if (ltid < 8 && ltid < nc) {
           const int cc = c_first + ltid;
-          sh.slot[ltid] = cc * mp.maxseg + (sg.r - (int)(work_begin(cc, W, G) / T));
+          sh.slot[ltid] = cc * mp.maxseg + seg_of(sp, sg.r, cc);
         }
         {
           float den = 0.f;
-          for (int cc = c_first; cc <= c_last; ++cc) {
-            const int kk = sg.r - (int)(work_begin(cc, W, G) / T);
-            den += __ldcg(mp.Rpart + ((int64_t)cc * mp.maxseg + kk) * BM + row_local);
-          }
+          for (int cc = c_first; cc <= c_last; ++cc)
+            den += __ldcg(mp.Rpart + ((int64_t)cc * mp.maxseg + seg_of(sp, sg.r, cc)) * BM + row_local);
           sh.den[row_local] = den;
         }
         mt_bar_wg0();
@@ -441,7 +439,7 @@ __global__ void __launch_bounds__(MT_NTHREADS, 1)
               sl = sh.slot[q2];
             } else {
               const int cc = c_first + q2;
-              sl = (int64_t)cc * mp.maxseg + (sg.r - (int)(work_begin(cc, W, G) / T));
+              sl = (int64_t)cc * mp.maxseg + seg_of(sp, sg.r, cc);
             }
             num += __ldcg(mp.Opart + (sl * BM + rr) * 64 + kx);
           }

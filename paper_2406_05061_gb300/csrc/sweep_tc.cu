@@ -70,10 +70,11 @@ struct TcShared {
 };
 
 
-// Parameters beyond SweepParams. The CTAs are persistent: CTA c of G owns the work
-// units [c W / G, (c + 1) W / G) of the row-major (row block, column tile) space,
-// W = R T, cut at row-block boundaries into segments; a segment's (max, sum) partial
-// goes to slot (c * maxseg + k), k = its index within the CTA.
+// Parameters beyond SweepParams. The CTAs are persistent and split the (row block,
+// column tile) grid as tc::Split describes (whole row blocks in bands of G, then a
+// contiguous split of the rest), each CTA's share cut into segments of one row block;
+// a segment's (max, sum) partial goes to slot (c * maxseg + k), k = its index within
+// the CTA.
 struct TcParams {
   SweepParams p;
   int32_t nkb;        // K blocks of 64
@@ -199,8 +200,8 @@ __device__ __forceinline__ SolverState sweep_state(const SweepParams& p) {
 // The g-update of a Sinkhorn loop (role 2) measures no error and changes no solver
 // state, so its row blocks skip the sweep-level arrival altogether.
 template <int NT>
-__device__ __forceinline__ void segment_epilogue(const TcParams& tp, int c, int k, const Seg& sg, int64_t W, int G,
-                                                 int T, int tid, int row0, const float2 (&mv)[BM / NT], int fcur,
+__device__ __forceinline__ void segment_epilogue(const TcParams& tp, int c, int k, const Seg& sg, const Split& sp,
+                                                 int tid, int row0, const float2 (&mv)[BM / NT], int fcur,
                                                  int32_t& s_last, int32_t& s_fin, float* red) {
   constexpr int RPT = BM / NT;
   const SweepParams& p = tp.p;
@@ -224,8 +225,8 @@ __device__ __forceinline__ void segment_epilogue(const TcParams& tp, int c, int 
       rin[h] = row_inputs(p, i, potA_cur);
     }
   }
-  const int c_first = cta_of((int64_t)sg.r * T, W, G);
-  const int c_last = cta_of((int64_t)sg.r * T + T - 1, W, G);
+  int c_first, c_last;
+  contributors(sp, sg.r, &c_first, &c_last);
   seg_bar<NT>();  // the partial stores of all rows happen before the arrival below
   if (tid == 0) {
     const unsigned prev = atomic_add_acq_rel_gpu(&p.cnt[sg.r], 1u);
@@ -248,18 +249,15 @@ __device__ __forceinline__ void segment_epilogue(const TcParams& tp, int c, int 
       for (int q = 0; q < kMaxC; ++q) {
         if (q < nc) {
           const int cc = c_first + q;
-          const int kk = sg.r - (int)(work_begin(cc, W, G) / T);
-          pv[q] = __ldcg(&p.partial[((int64_t)cc * tp.maxseg + kk) * BM + rl]);
+          pv[q] = __ldcg(&p.partial[((int64_t)cc * tp.maxseg + seg_of(sp, sg.r, cc)) * BM + rl]);
         }
       }
       float2 acc = make_float2(-INFINITY, 0.f);
 #pragma unroll
       for (int q = 0; q < kMaxC; ++q)
         if (q < nc) acc = lse_combine(acc, pv[q]);
-      for (int cc = c_first + kMaxC; cc <= c_last; ++cc) {
-        const int kk = sg.r - (int)(work_begin(cc, W, G) / T);
-        acc = lse_combine(acc, __ldcg(&p.partial[((int64_t)cc * tp.maxseg + kk) * BM + rl]));
-      }
+      for (int cc = c_first + kMaxC; cc <= c_last; ++cc)
+        acc = lse_combine(acc, __ldcg(&p.partial[((int64_t)cc * tp.maxseg + seg_of(sp, sg.r, cc)) * BM + rl]));
       const float Lr = acc.x + __log2f(acc.y);
       float val;
       e[h] = row_epilogue(p, i, Lr, rin[h], out_target, &val);
@@ -317,8 +315,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   TcShared& sh = *reinterpret_cast<TcShared*>(smem + L.ctrl);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = blockIdx.x, G = tp.G, T = tp.T;
-  const int64_t W = (int64_t)tp.R * T;
-  const int nseg = num_segments(c, W, G, T);
+  const Split sp = make_split(tp.R, T, G);
+  const int nseg = num_segments(sp, c);
   const int nkb = tp.nkb, S = tp.stages, NA = tp.a_bufs;
   volatile int32_t* abort_flag = &sh.abort_flag;
 
@@ -400,7 +398,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       __syncwarp();
     };
     for (int k = 0; k < nseg && ok && !stopped; ++k) {
-      const Seg sg = segment(c, k, W, G, T);
+      const Seg sg = segment(sp, c, k);
       if (NA > 0) {
         const int ai = k % NA;
         // reusing an A buffer waits for the MMA warp, which waits for the pending bias
@@ -471,7 +469,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     bool ok = true;
     int u = 0, tl = 0;
     for (int k = 0; k < nseg && ok; ++k) {
-      const Seg sg = segment(c, k, W, G, T);
+      const Seg sg = segment(sp, c, k);
       const int ai = NA > 0 ? k % NA : 0;
       if (NA > 0) {
         ok = warp_wait(&sh.a_full[ai], (uint32_t)((k / NA) & 1), abort_flag);
@@ -559,7 +557,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // executing every named barrier below, so the other LSE warps never block on it.
     bool dead = false;
     for (int k = 0; k < (stopped ? 0 : nseg); ++k) {
-      const Seg sg = segment(c, k, W, G, T);
+      const Seg sg = segment(sp, c, k);
       float m_run = -INFINITY, s_run = 0.f;
       for (int t = sg.t0; t < sg.t1; ++t, ++tl) {
         if ((tl & 1) != wg) continue;
@@ -653,7 +651,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         continue;
       }
       const float2 mv[1] = {make_float2(m_run, s_run)};
-      segment_epilogue<128>(tp, c, k, sg, W, G, T, ltid, row_local, mv, fcur, sh.s_last, sh.s_fin, sh.red);
+      segment_epilogue<128>(tp, c, k, sg, sp, ltid, row_local, mv, fcur, sh.s_last, sh.s_fin, sh.red);
     }
   } else {
     // ------------------------------------------------------------ epilogue warps
@@ -669,14 +667,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // (also when it is itself a no-op); no other CTA of this grid reads state[(seq + 1) & 1]
     if (p.state != nullptr && p.lag && p.role == 2 && c == 0 && etid == 0) p.state[(p.seq + 1) & 1] = st0;
     for (int k = 0; k + 1 < (stopped ? 0 : nseg); ++k) {
-      const Seg sg = segment(c, k, W, G, T);
+      const Seg sg = segment(sp, c, k);
       const int sl = k & 1;
       const bool okw = mbar_wait(&sh.seg_full[sl], (uint32_t)((k >> 1) & 1), abort_flag);
       float2 mv[2];
       mv[0] = okw ? sh.seg[sl][etid] : make_float2(NAN, NAN);
       mv[1] = okw ? sh.seg[sl][etid + 64] : make_float2(NAN, NAN);
       mbar_arrive(&sh.seg_empty[sl]);
-      segment_epilogue<64>(tp, c, k, sg, W, G, T, etid, etid, mv, fcur, sh.e_last, sh.e_fin, sh.ered);
+      segment_epilogue<64>(tp, c, k, sg, sp, etid, etid, mv, fcur, sh.e_last, sh.e_fin, sh.ered);
     }
   }
 
@@ -786,13 +784,10 @@ cudaError_t launch_bias_prep(const float* potB, const float* Bn, int64_t nB, int
 // column tiles of width bn.
 void tc_plan(int64_t nA, int64_t nB, int bn, int sms, int* G, int* maxseg) {
   const int64_t R = (nA + tc::BM - 1) / tc::BM, T = (nB + bn - 1) / bn;
-  const int64_t W = R * T;
-  const int g = (int)std::min<int64_t>(W, sms);
+  const int g = (int)std::min<int64_t>(R * T, sms);
+  const tc::Split sp = tc::make_split((int)R, (int)T, g);
   int ms = 1;
-  for (int c = 0; c < g; ++c) {
-    const int64_t w0 = (int64_t)c * W / g, w1 = (int64_t)(c + 1) * W / g;
-    if (w1 > w0) ms = std::max<int>(ms, (int)((w1 - 1) / T - w0 / T + 1));
-  }
+  for (int c = 0; c < g; ++c) ms = std::max(ms, tc::num_segments(sp, c));
   *G = g;
   *maxseg = ms;
 }

@@ -145,28 +145,70 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Persistent work split: CTA c of G owns the units [c W / G, (c + 1) W / G) of the
-// row-major (row block, column tile) space, W = R T, cut at row-block boundaries into
-// segments (k = 0 .. num_segments - 1).
+// Persistent work split of the (row block, column tile) grid, R x T, over G CTAs.
+// Bands: the first nb G row blocks (nb = floor(R / G)) go whole to one CTA each, row
+// block b G + c to CTA c as its segment b, so that within a band all CTAs walk the
+// column tiles in the same order and a B tile that one CTA reads from HBM the others
+// read from L2 (for clouds whose operands exceed L2). Remainder: the W = (R - nb G) T
+// units of the last row blocks in row-major order, spread over the first Gr = min(W, G)
+// CTAs, CTA c owning [c W / Gr, (c + 1) W / Gr), cut at row-block boundaries into the
+// segments nb, nb + 1, ... With R < G (nb = 0) this is a plain contiguous split.
 struct Seg {
   int r, t0, t1;
 };
-__device__ __forceinline__ int64_t work_begin(int c, int64_t W, int G) { return (int64_t)c * W / G; }
-// CTA owning work unit w: the largest c with floor(c W / G) <= w.
-__device__ __forceinline__ int cta_of(int64_t w, int64_t W, int G) { return (int)(((w + 1) * G - 1) / W); }
-__device__ __forceinline__ Seg segment(int c, int k, int64_t W, int G, int T) {
-  const int64_t w0 = work_begin(c, W, G), w1 = work_begin(c + 1, W, G);
+struct Split {
+  int R, T, G, nb, Gr;
+  int64_t W;  // remainder units
+};
+__host__ __device__ inline Split make_split(int R, int T, int G) {
+  Split s;
+  s.R = R;
+  s.T = T;
+  s.G = G;
+  s.nb = R / G;
+  s.W = (int64_t)(R - s.nb * G) * T;
+  s.Gr = (int)(s.W < (int64_t)G ? s.W : (int64_t)G);
+  return s;
+}
+__host__ __device__ inline int64_t work_begin(const Split& s, int c) {
+  return c >= s.Gr ? s.W : (int64_t)c * s.W / s.Gr;
+}
+// CTA owning remainder unit w (0 <= w < W): the largest c with floor(c W / Gr) <= w.
+__host__ __device__ inline int cta_of(const Split& s, int64_t w) { return (int)(((w + 1) * s.Gr - 1) / s.W); }
+__host__ __device__ inline int num_segments(const Split& s, int c) {
+  const int64_t w0 = work_begin(s, c), w1 = work_begin(s, c + 1);
+  return s.nb + (w1 <= w0 ? 0 : (int)((w1 - 1) / s.T - w0 / s.T + 1));
+}
+__host__ __device__ inline Seg segment(const Split& s, int c, int k) {
   Seg sg;
-  sg.r = (int)(w0 / T) + k;
-  const int64_t rb0 = (int64_t)sg.r * T;
-  sg.t0 = (int)(max(w0, rb0) - rb0);
-  sg.t1 = (int)(min(w1, rb0 + T) - rb0);
+  if (k < s.nb) {
+    sg.r = k * s.G + c;
+    sg.t0 = 0;
+    sg.t1 = s.T;
+    return sg;
+  }
+  const int64_t w0 = work_begin(s, c), w1 = work_begin(s, c + 1);
+  const int64_t rr = w0 / s.T + (k - s.nb);
+  const int64_t rb0 = rr * s.T;
+  sg.r = s.nb * s.G + (int)rr;
+  sg.t0 = (int)((w0 > rb0 ? w0 : rb0) - rb0);
+  sg.t1 = (int)((w1 < rb0 + s.T ? w1 : rb0 + s.T) - rb0);
   return sg;
 }
-__device__ __forceinline__ int num_segments(int c, int64_t W, int G, int T) {
-  const int64_t w0 = work_begin(c, W, G), w1 = work_begin(c + 1, W, G);
-  if (w1 <= w0) return 0;
-  return (int)((w1 - 1) / T - w0 / T + 1);
+// The CTAs whose segments cover row block r are c_first .. c_last (in CTA order); the
+// segment index of CTA cc in row block r is seg_of(s, r, cc).
+__host__ __device__ inline void contributors(const Split& s, int r, int* c_first, int* c_last) {
+  if (r < s.nb * s.G) {
+    *c_first = *c_last = r % s.G;
+    return;
+  }
+  const int64_t rr = r - s.nb * s.G;
+  *c_first = cta_of(s, rr * s.T);
+  *c_last = cta_of(s, rr * s.T + s.T - 1);
+}
+__host__ __device__ inline int seg_of(const Split& s, int r, int cc) {
+  if (r < s.nb * s.G) return r / s.G;
+  return s.nb + (r - s.nb * s.G) - (int)(work_begin(s, cc) / s.T);
 }
 
 // Named barriers: 1 = both LSE warpgroups (256 threads), 2 = LSE warpgroup 0 (128).

@@ -298,3 +298,35 @@ def test_progot_far_from_the_origin_matches_the_translate(nat):
     assert res.status == nat.PROGOT_OK, nat.last_error()
     ref = O.progot(None, p.x, None, p.y, eps, alpha, [1e-6] * K)
     assert map_rms_rel(host(res.x_out) - v, ref.x_out, p.y) <= TOL_MIXED
+
+
+# ------------------------------- more row blocks than SMs: whole row blocks in bands
+@pytest.mark.parametrize("n,m,d", [(20000, 40000, 16), (39000, 20500, 320)])
+def test_banded_work_split_sampled_parity(nat, n, m, d):
+    # with at least G = 152 row blocks the tensor-core kernels hand whole row blocks to
+    # the CTAs in bands (every CTA walks the column tiles together) and split only the
+    # remaining row blocks; checked on rows and columns sampled and computed one by one
+    # by the oracle from the GPU's potentials, and against the float32 path
+    p = W.gmm_pair(n, m, d, seed=51 + d, k=4)
+    x, y = dev(p.x), dev(p.y)
+    eps = 0.1 * O.mean_cost(p.x[:2000], p.y[:2000])
+    res = nat.sinkhorn_potentials(x, y, eps, 1e-4, max_iter=3000, precision="bf16x3")
+    assert res.status == nat.PROGOT_OK, nat.last_error()
+    f, g = host(res.f), host(res.g)
+    rng = np.random.default_rng(52)
+    X64, Y64 = p.x.astype(np.float64), p.y.astype(np.float64)
+    rows, cols = rng.choice(n, 48, replace=False), rng.choice(m, 48, replace=False)
+    r = np.exp((f[rows, None] + g[None, :] - O.cost_matrix_rows(X64[rows], Y64)) / eps).sum(1)
+    c = np.exp((g[cols, None] + f[None, :] - O.cost_matrix_rows(Y64[cols], X64)) / eps).sum(1)
+    # the last update was a g-update: column sums are exact up to rounding, row sums
+    # carry the (converged) row error
+    np.testing.assert_allclose(c * m, 1.0, rtol=2e-3)
+    assert float(np.abs(r * n - 1.0).max()) <= 2e-2
+    ref = nat.sinkhorn_potentials(x, y, eps, 1e-5, max_iter=3000, precision="fp32")
+    T_tc = O.entropic_map(X64[rows], Y64, g, eps)
+    T_32 = O.entropic_map(X64[rows], Y64, host(ref.g), eps)
+    assert map_rms_rel(T_tc, T_32, p.y) <= TOL_MIXED
+    # one map step (Alg. 3) on the tensor cores with the same split (d <= 64) or the
+    # float32 P Y sweep after a banded log-sum-exp pass (d > 64)
+    out = nat.entropic_map_apply(x, y, res.g.reshape(1, -1), [eps], [1.0], precision="bf16x3")
+    assert map_rms_rel(host(out)[rows], T_tc, p.y) <= TOL_MIXED
