@@ -5,18 +5,21 @@
 // sweep. Both products run on the tensor cores:
 //   S = X Y^T as in the LSE sweep (bf16 hi/lo operands pre-scaled by sqrt(c), three
 //     products, beta added by one more K = 16 step) into one of two TMEM buffers;
-//   O += P Y with P_ij = 2^{t_ij - L_i} written by the LSE warps into shared memory as
-//     bf16 hi/lo (K-major, 128-byte swizzle) and Y^T as bf16 hi/lo (unscaled), three
-//     products Ph Yh + Ph Yl + Pl Yh, M = 128 rows, N = 64 coordinates, K = 128
-//     columns of the tile, into a third TMEM region.
+//   O += P Y~ with P_ij = 2^{t_ij - L_i} written by the LSE warps into shared memory as
+//     bf16 hi/lo (K-major, 128-byte swizzle), three products Ph Yh + Ph Yl + Pl Yh,
+//     M = 128 rows, N = 64 coordinates, K = 128 columns of the tile, into a third TMEM
+//     region. The B operand is the tile's own S operand Y~ = sqrt(c) (y - mu) (bf16
+//     hi/lo) read a second time as an MN-major matrix (its 128-byte rows are the K index
+//     j, each holding the 64 coordinates), so a stage is released only after the tile's
+//     P Y~ products; T_i = (O_i / R_i) / sqrt(c) + mu.
 // CTA = 10 warps: warp 0 TMA producer (A row block once per segment; per tile the
-// B hi/lo tiles with their bias rows, and the Y^T hi/lo tile), warp 1 MMA issuer (S of
-// tile q + 1 is issued before P Y of tile q, so the exponentials of tile q overlap the
+// B hi/lo tiles with their bias rows into one of three stages), warp 1 MMA issuer (S of
+// tile q + 1 is issued before P Y~ of tile q, so the exponentials of tile q overlap the
 // tensor cores), warps 2-9 two LSE warpgroups alternating tiles (one TMEM lane = one
 // row per thread: tcgen05.ld, exp2, row sums, the P tile in two 64-column halves). At
 // the end of a segment warpgroup 0 reads O out of TMEM into a per-CTA partial slot;
 // the last CTA of a row block sums the slots in CTA order (deterministic) and writes
-// x + alpha (O / R - x). Persistent CTAs and segments as in the LSE sweep. Every
+// x + alpha (T - x). Persistent CTAs and segments as in the LSE sweep. Every
 // mbarrier wait is bounded (2 s): on expiry the CTA raises a fault flag, drains its
 // copies and products, frees TMEM and leaves.
 #include <cuda.h>
@@ -34,22 +37,19 @@ constexpr int MT_TMEM_COLS = 512;          // S buffers at [0, 256), O at [256, 
 constexpr uint32_t MT_O_COL = 256;
 constexpr uint32_t MT_TILE = 128 * 64 * 2;  // 16 KB: 128 rows x 64 bf16 (A, B or P half)
 constexpr uint32_t MT_BIAS = 128 * 32;      // 4 KB: 128 rows x 16 bf16
-constexpr uint32_t MT_YT_BLK = 64 * 64 * 2; // 8 KB: 64 coordinates x 64 columns
+constexpr int MT_NST = 3;                   // operand stages (a stage lives from S(q) to P Y~(q))
 
 // Shared-memory layout (offsets from the 1024-aligned base).
 constexpr uint32_t MT_OFF_A = 0;                          // A hi, A lo
 constexpr uint32_t MT_OFF_ONES = 2 * MT_TILE;             // 32 KB
-constexpr uint32_t MT_OFF_ST = MT_OFF_ONES + 4096;        // 36 KB: 2 stages of B hi, B lo, bias
+constexpr uint32_t MT_OFF_ST = MT_OFF_ONES + 4096;        // 36 KB: stages of B hi, B lo, bias
 constexpr uint32_t MT_ST_BYTES = 2 * MT_TILE + MT_BIAS;   // 36 KB
-constexpr uint32_t MT_OFF_YT = MT_OFF_ST + 2 * MT_ST_BYTES;  // 108 KB: Y^T hi (2 blocks), lo (2)
-constexpr uint32_t MT_YT_BYTES = 4 * MT_YT_BLK;              // 32 KB
-constexpr uint32_t MT_OFF_P = MT_OFF_YT + MT_YT_BYTES;       // 140 KB: P halves 0 and 1, each hi + lo
-constexpr uint32_t MT_P_BYTES = 2 * MT_TILE;                 // 32 KB per half
-constexpr uint32_t MT_OFF_CTRL = MT_OFF_P + 2 * MT_P_BYTES;  // 204 KB
+constexpr uint32_t MT_OFF_P = MT_OFF_ST + MT_NST * MT_ST_BYTES;  // 144 KB: P halves 0 and 1, each hi + lo
+constexpr uint32_t MT_P_BYTES = 2 * MT_TILE;                     // 32 KB per half
+constexpr uint32_t MT_OFF_CTRL = MT_OFF_P + 2 * MT_P_BYTES;      // 208 KB
 
 struct MtShared {
-  uint64_t full[2], empty[2];    // S operand stages
-  uint64_t yfull, yempty;        // Y^T tile
+  uint64_t full[MT_NST], empty[MT_NST];  // operand stages
   uint64_t tmem_full[2], tmem_empty[2];
   uint64_t a_full, a_empty;
   uint64_t p_full[2];            // P half h of the current tile written (4 warps arrive)
@@ -79,10 +79,35 @@ struct MapTcParams {
   int32_t d;
   int32_t G, T, R, maxseg;
   float alpha;
+  float inv_sc;      // 1 / sqrt(c): the B operand is sqrt(c) (y - mu)
+  const float* mu;   // d: centre of the operands
 };
 
 __device__ __forceinline__ void mt_bar_all() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 __device__ __forceinline__ void mt_bar_wg0() { asm volatile("bar.sync 2, 128;" ::: "memory"); }
+
+// The B operand of P Y~: the stage's K-major S operand read as MN-major (rows of 128 B
+// along K = j, 64 coordinates each, 8-row groups 1024 B apart; with N = 64 there is one
+// group along N, so the leading offset is unused and set to the same 1024 B).
+__device__ __forceinline__ uint64_t desc_sw128_mn(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(1024 >> 4) << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;  // 128-byte swizzle
+  return d;
+}
+// M = 128, N = 64, bf16 x bf16 -> fp32, A K-major, B MN-major.
+__device__ __forceinline__ void umma_py(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  constexpr uint32_t kIdesc = make_idesc(BM, 64) | (1u << 16);
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
 
 // bf16 hi/lo pair of 8 consecutive values as two 16-byte chunks (paired conversions).
 __device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 v) { return *reinterpret_cast<uint32_t*>(&v); }
@@ -103,8 +128,7 @@ __device__ __forceinline__ void split8(const float* v, uint4& hi, uint4& lo) {
 __global__ void __launch_bounds__(MT_NTHREADS, 1)
     map_sweep_tc(const __grid_constant__ CUtensorMap mapAh, const __grid_constant__ CUtensorMap mapAl,
                  const __grid_constant__ CUtensorMap mapBh, const __grid_constant__ CUtensorMap mapBl,
-                 const __grid_constant__ CUtensorMap mapBbias, const __grid_constant__ CUtensorMap mapYTh,
-                 const __grid_constant__ CUtensorMap mapYTl, MapTcParams mp) {
+                 const __grid_constant__ CUtensorMap mapBbias, MapTcParams mp) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -116,17 +140,17 @@ __global__ void __launch_bounds__(MT_NTHREADS, 1)
   volatile int32_t* abort_flag = &sh.abort_flag;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < MT_NST; ++s) {
       mbar_init(&sh.full[s], 1);
       mbar_init(&sh.empty[s], 1);
+    }
+    for (int s = 0; s < 2; ++s) {
       mbar_init(&sh.tmem_full[s], 1);
       mbar_init(&sh.tmem_empty[s], 4);
       mbar_init(&sh.p_full[s], 4);
       mbar_init(&sh.p_empty[0][s], 1);
       mbar_init(&sh.p_empty[1][s], 1);
     }
-    mbar_init(&sh.yfull, 1);
-    mbar_init(&sh.yempty, 1);
     mbar_init(&sh.a_full, 1);
     mbar_init(&sh.a_empty, 1);
     mbar_init(&sh.o_full, 1);
@@ -154,26 +178,8 @@ __global__ void __launch_bounds__(MT_NTHREADS, 1)
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
-    // Y^T of a tile is only needed by its P Y products, which the MMA warp issues after
-    // the next tile's S: loading Y^T(q) after the S operands of tile q + 1 keeps the S
-    // pipeline a stage ahead while the single Y^T buffer waits for P Y(q - 1).
     bool ok = true;
-    int q = 0, a_issued = 0, n_st = 0, n_yt = 0;  // tiles started; A, S and Y^T loads issued
-    int t_prev = -1;                              // column tile whose Y^T is still to load
-    auto load_yt = [&](int qq, int tt) -> bool {
-      if (!warp_wait(&sh.yempty, (uint32_t)((qq & 1) ^ 1), abort_flag)) return false;
-      unsigned char* yt = smem + MT_OFF_YT;
-      if (elect_one()) {
-        mbar_arrive_expect_tx(&sh.yfull, MT_YT_BYTES);
-        tma_load_2d(yt, &mapYTh, &sh.yfull, tt * MT_BN, 0);
-        tma_load_2d(yt + MT_YT_BLK, &mapYTh, &sh.yfull, tt * MT_BN + 64, 0);
-        tma_load_2d(yt + 2 * MT_YT_BLK, &mapYTl, &sh.yfull, tt * MT_BN, 0);
-        tma_load_2d(yt + 3 * MT_YT_BLK, &mapYTl, &sh.yfull, tt * MT_BN + 64, 0);
-      }
-      __syncwarp();
-      n_yt = qq + 1;
-      return true;
-    };
+    int q = 0, a_issued = 0, n_st = 0;  // tiles started; A and stage loads issued
     for (int k = 0; k < nseg && ok; ++k) {
       const Seg sg = segment(sp, c, k);
       ok = warp_wait(&sh.a_empty, (uint32_t)((k & 1) ^ 1), abort_flag);
@@ -186,8 +192,8 @@ __global__ void __launch_bounds__(MT_NTHREADS, 1)
       __syncwarp();
       a_issued = k + 1;
       for (int t = sg.t0; t < sg.t1 && ok; ++t, ++q) {
-        const int s = q & 1;
-        ok = warp_wait(&sh.empty[s], (uint32_t)(((q >> 1) & 1) ^ 1), abort_flag);
+        const int s = q % MT_NST;
+        ok = warp_wait(&sh.empty[s], (uint32_t)(((q / MT_NST) & 1) ^ 1), abort_flag);
         if (!ok) break;
         unsigned char* st = smem + MT_OFF_ST + s * MT_ST_BYTES;
         if (elect_one()) {
@@ -198,20 +204,13 @@ __global__ void __launch_bounds__(MT_NTHREADS, 1)
         }
         __syncwarp();
         n_st = q + 1;
-        if (t_prev >= 0) {
-          ok = load_yt(q - 1, t_prev);
-          if (!ok) break;
-        }
-        t_prev = t;
       }
     }
-    if (ok && t_prev >= 0) ok = load_yt(q - 1, t_prev);
     if (!ok) {
       // drain the copies this CTA still has in flight before shared memory is released
       if (a_issued > 0) warp_wait(&sh.a_full, (uint32_t)((a_issued - 1) & 1), abort_flag, true);
-      for (int v = (n_st > 2 ? n_st - 2 : 0); v < n_st; ++v)
-        warp_wait(&sh.full[v & 1], (uint32_t)((v >> 1) & 1), abort_flag, true);
-      if (n_yt > 0) warp_wait(&sh.yfull, (uint32_t)((n_yt - 1) & 1), abort_flag, true);
+      for (int v = (n_st > MT_NST ? n_st - MT_NST : 0); v < n_st; ++v)
+        warp_wait(&sh.full[v % MT_NST], (uint32_t)((v / MT_NST) & 1), abort_flag, true);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
@@ -222,30 +221,31 @@ __global__ void __launch_bounds__(MT_NTHREADS, 1)
     int q = 0, oseg = 0;
     int pend = -1;
     bool pend_first = false, pend_last = false;
-    // P Y of tile qq: two halves of 64 columns (two P buffers), each 4 K steps x 3
-    // products into O
+    // P Y~ of tile qq: two halves of 64 columns (two P buffers), each 4 K steps x 3
+    // products into O; B is the tile's stage read as MN-major (K step = 16 rows =
+    // 2048 B), and the stage goes back to the producer after the second half
     auto issue_py = [&](int qq, bool first, bool last) -> bool {
-      if (!warp_wait(&sh.yfull, (uint32_t)(qq & 1), abort_flag)) return false;
       if (first && oseg > 0 && !warp_wait(&sh.o_empty, (uint32_t)((oseg - 1) & 1), abort_flag)) return false;
-      const uint32_t yt = smem_u32(smem + MT_OFF_YT);
+      const int s = qq % MT_NST;
+      const uint32_t st = smem_u32(smem + MT_OFF_ST + s * MT_ST_BYTES);
       for (int h = 0; h < 2; ++h) {
         if (!warp_wait(&sh.p_full[h], (uint32_t)(qq & 1), abort_flag)) return false;
         tc_fence_after();
         const uint64_t ah = desc_sw128(p0 + h * MT_P_BYTES), al = desc_sw128(p0 + h * MT_P_BYTES + MT_TILE);
-        const uint64_t bh = desc_sw128(yt + h * MT_YT_BLK), bl = desc_sw128(yt + (2 + h) * MT_YT_BLK);
+        const uint64_t bh = desc_sw128_mn(st + h * 8192), bl = desc_sw128_mn(st + MT_TILE + h * 8192);
         if (elect_one()) {
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
-            const uint64_t adv = (uint64_t)(kk * 2);
-            umma<64>(tmem_base + MT_O_COL, ah + adv, bh + adv, (first && h == 0 && kk == 0) ? 0u : 1u);
-            umma<64>(tmem_base + MT_O_COL, ah + adv, bl + adv, 1u);
-            umma<64>(tmem_base + MT_O_COL, al + adv, bh + adv, 1u);
+            const uint64_t adv = (uint64_t)(kk * 2), bdv = (uint64_t)(kk * 128);
+            umma_py(tmem_base + MT_O_COL, ah + adv, bh + bdv, (first && h == 0 && kk == 0) ? 0u : 1u);
+            umma_py(tmem_base + MT_O_COL, ah + adv, bl + bdv, 1u);
+            umma_py(tmem_base + MT_O_COL, al + adv, bh + bdv, 1u);
           }
           // buffer h is next used by tile qq + 1, i.e. by the other warpgroup: each
           // warpgroup waits on its own barriers, so neither mistakes the other's release
           umma_commit(&sh.p_empty[(qq + 1) & 1][h]);
           if (h == 1) {
-            umma_commit(&sh.yempty);
+            umma_commit(&sh.empty[s]);
             if (last) umma_commit(&sh.o_full);
           }
         }
@@ -260,13 +260,13 @@ __global__ void __launch_bounds__(MT_NTHREADS, 1)
       if (!ok) break;
       tc_fence_after();
       for (int t = sg.t0; t < sg.t1 && ok; ++t, ++q) {
-        const int b = q & 1;
+        const int b = q & 1, s = q % MT_NST;
         ok = warp_wait(&sh.tmem_empty[b], (uint32_t)(((q >> 1) & 1) ^ 1), abort_flag);
         if (!ok) break;
-        ok = warp_wait(&sh.full[b], (uint32_t)((q >> 1) & 1), abort_flag);
+        ok = warp_wait(&sh.full[s], (uint32_t)((q / MT_NST) & 1), abort_flag);
         if (!ok) break;
         tc_fence_after();
-        const uint32_t st = smem_u32(smem + MT_OFF_ST + b * MT_ST_BYTES);
+        const uint32_t st = smem_u32(smem + MT_OFF_ST + s * MT_ST_BYTES);
         const uint64_t ah = desc_sw128(a_hi), al = desc_sw128(a_lo);
         const uint64_t bh = desc_sw128(st), bl = desc_sw128(st + MT_TILE), bb = desc_sw32(st + 2 * MT_TILE);
         const uint32_t d_tmem = tmem_base + (uint32_t)(b * MT_BN);
@@ -279,7 +279,6 @@ __global__ void __launch_bounds__(MT_NTHREADS, 1)
             umma<MT_BN>(d_tmem, al + adv, bh + adv, 1u);
           }
           umma<MT_BN>(d_tmem, ones, bb, 1u);
-          umma_commit(&sh.empty[b]);
           umma_commit(&sh.tmem_full[b]);
           if (t == sg.t1 - 1) umma_commit(&sh.a_empty);
         }
@@ -445,7 +444,8 @@ __global__ void __launch_bounds__(MT_NTHREADS, 1)
           }
           const int64_t gi = (int64_t)sg.r * BM + rr;
           const float x = mp.X[gi * dd + kx];
-          mp.out[gi * dd + kx] = fmaf(mp.alpha, num / sh.den[rr] - x, x);
+          const float tx = fmaf(num / sh.den[rr], mp.inv_sc, mp.mu[kx]);
+          mp.out[gi * dd + kx] = fmaf(mp.alpha, tx - x, x);
         }
         mt_bar_wg0();
         if (ltid == 0) mp.cnt[sg.r] = 0;
@@ -464,35 +464,13 @@ __global__ void __launch_bounds__(MT_NTHREADS, 1)
   }
 }
 
-// Y^T as bf16 hi/lo: yt[k][j] = y[j][k] for k < d, j < m; zero for d <= k < 64 and
-// m <= j < m_pad. One thread per element, consecutive threads along j.
-__global__ void split_yT_kernel(const float* __restrict__ Y, int64_t m, int32_t d, int64_t m_pad,
-                                __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
-  const int64_t total = 64 * m_pad;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t k = e / m_pad, j = e - k * m_pad;
-    const float v = (k < d && j < m) ? Y[j * d + k] : 0.f;
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    hi[e] = h;
-    lo[e] = __float2bfloat16_rn(v - __bfloat162float(h));
-  }
-}
-
 }  // namespace tc
 
 size_t map_sweep_tc_smem() { return tc::MT_SMEM_TOTAL; }
 
-cudaError_t launch_split_yT(const float* Y, int64_t m, int32_t d, int64_t m_pad, void* hi, void* lo, cudaStream_t s) {
-  int64_t blocks = (64 * m_pad + 255) / 256;
-  if (blocks > 4096) blocks = 4096;
-  tc::split_yT_kernel<<<(unsigned)blocks, 256, 0, s>>>(Y, m, d, m_pad, (__nv_bfloat16*)hi, (__nv_bfloat16*)lo);
-  count_launch();
-  return cudaGetLastError();
-}
-
 cudaError_t launch_map_sweep_tc(const float* X, float* out, const float* L, int64_t nA, int64_t nB, int32_t d,
                                 float alpha, const void* mapAh, const void* mapAl, const void* mapBh,
-                                const void* mapBl, const void* mapBbias, const void* mapYTh, const void* mapYTl,
+                                const void* mapBl, const void* mapBbias, float inv_sc, const float* mu,
                                 float* Opart, float* Rpart, unsigned* cnt, int G, int maxseg, int32_t* fault,
                                 cudaStream_t stream) {
   static thread_local bool attr_set = false;
@@ -518,11 +496,12 @@ cudaError_t launch_map_sweep_tc(const float* X, float* out, const float* L, int6
   mp.R = (int)((nA + tc::BM - 1) / tc::BM);
   mp.maxseg = maxseg;
   mp.alpha = alpha;
+  mp.inv_sc = inv_sc;
+  mp.mu = mu;
   tc::map_sweep_tc<<<G, tc::MT_NTHREADS, tc::MT_SMEM_TOTAL, stream>>>(
       *reinterpret_cast<const CUtensorMap*>(mapAh), *reinterpret_cast<const CUtensorMap*>(mapAl),
       *reinterpret_cast<const CUtensorMap*>(mapBh), *reinterpret_cast<const CUtensorMap*>(mapBl),
-      *reinterpret_cast<const CUtensorMap*>(mapBbias), *reinterpret_cast<const CUtensorMap*>(mapYTh),
-      *reinterpret_cast<const CUtensorMap*>(mapYTl), mp);
+      *reinterpret_cast<const CUtensorMap*>(mapBbias), mp);
   count_launch();
   return cudaGetLastError();
 }

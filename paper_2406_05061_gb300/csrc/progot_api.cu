@@ -174,8 +174,6 @@ struct Workspace {
   void* yl;
   void* xb;         // bf16 bias rows (x side, rows padded to 128) x 16
   void* yb;
-  void* yth;        // Y^T as bf16 hi / lo: 64 x (nmax padded to 128), tensor-core map step (d <= 64)
-  void* ytl;
   float* mu;        // d: centre of the tensor-core operands
   float* xnc;       // nmax: |x_i - mu|^2
   float* ync;       // nmax: |y_j - mu|^2
@@ -255,9 +253,6 @@ static size_t ws_layout(const WsDims& w, Workspace* out, char* base) {
   const size_t bb = w.tc ? 32 * (size_t)(cdiv(w.nmax, 256) * 256) : 0;
   ws.xb = take(bb);
   ws.yb = take(bb);
-  const size_t ytb = (w.tc && w.dp == 64) ? 2 * 64 * (size_t)(cdiv(w.nmax, 128) * 128) : 0;
-  ws.yth = take(ytb);
-  ws.ytl = take(ytb);
   ws.mu = (float*)take(w.tc ? sizeof(float) * (size_t)w.dp : 0);
   ws.xnc = (float*)take(w.tc ? sizeof(float) * w.nmax : 0);
   ws.ync = (float*)take(w.tc ? sizeof(float) * w.nmax : 0);
@@ -352,7 +347,7 @@ struct TcOps {
   // (bn-row boxes); CUtensorMap is 64-byte aligned by its own declaration
   CUtensorMap xh_a, xl_a, yh_a, yl_a, xh_b, xl_b, yh_b, yl_b, xb, yb;
   // tensor-core map step (dp = 64): y-side bias rows in 128-row boxes, Y^T hi / lo
-  CUtensorMap yb128, yth, ytl;
+  CUtensorMap yb128;
   // centre mu of the operands and the squared norms |x_i - mu|^2, |y_j - mu|^2 that
   // the tensor-core sweeps use in place of |x_i|^2, |y_j|^2
   const float* mu = nullptr;
@@ -403,8 +398,6 @@ static int prep_tc(const float* x, int64_t n, const float* y, int64_t m, int32_t
   if (!rc) rc = make_map(&ops->yb, ws.yb, cdiv(m, 256) * 256, 16, ops->bn);
   if (!rc && dp == 64) {
     rc = make_map(&ops->yb128, ws.yb, cdiv(m, 256) * 256, 16, 128);
-    if (!rc) rc = make_map(&ops->yth, ws.yth, 64, (int32_t)(cdiv(m, 128) * 128), 64);
-    if (!rc) rc = make_map(&ops->ytl, ws.ytl, 64, (int32_t)(cdiv(m, 128) * 128), 64);
   }
   if (rc) return rc;
   const float bscale = (float)(kLog2e / eps);
@@ -693,15 +686,14 @@ static int map_step(float* X, int64_t n, const float* y, int64_t m, int32_t d, c
   int rc = tc ? lse_sweep(pl, precision, s, ops, true, &ws) : lse_sweep(pl, PROGOT_FP32, s);
   if (rc) return rc;
   if (tc && ops->nkb == 1 && g_map_tc.load()) {
-    // d <= 64: S and P Y both on the tensor cores
-    const int64_t m_pad = cdiv(m, 128) * 128;
-    CK(launch_split_yT(y, m, d, m_pad, ws.yth, ws.ytl, s));
+    // d <= 64: S and P Y both on the tensor cores (P Y reuses the centred, scaled y operand)
     int G = 0, maxseg = 0;
     tc_plan(n, m, 128, num_sms(), &G, &maxseg);
     ProfRec r;
     const bool rec = prof_begin(r, s, kProfMap);
     CK(launch_map_sweep_tc(X, X, ws.L, n, m, d, (float)alpha, &ops->xh_a, &ops->xl_a, &ops->yh_a, &ops->yl_a,
-                           &ops->yb128, &ops->yth, &ops->ytl, ws.Opart, ws.Rpart, ws.mcnt, G, maxseg, ws.fault, s));
+                           &ops->yb128, (float)std::sqrt(eps / (2.0 * kLog2e)), ops->mu, ws.Opart, ws.Rpart,
+                           ws.mcnt, G, maxseg, ws.fault, s));
     if (rec) prof_end(r, s, kProfMap, (double)n * (double)m);
     if (t_prof.on) t_prof.worked[kProfMap] += 1;
     return PROGOT_OK;

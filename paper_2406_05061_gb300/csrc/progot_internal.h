@@ -89,11 +89,11 @@ cudaError_t launch_bias_prep(const float* potB, const float* Bn, int64_t nB, int
 void tc_plan(int64_t nA, int64_t nB, int bn, int sms, int* G, int* maxseg);
 // Barycentric displacement on the tensor cores for d <= 64 (map_tc.cu): x <- x + alpha
 // (T(x) - x) in place (out may alias X), L from a log-sum-exp pass of the same t; the
-// A / B / bias maps use 128-row boxes, Y^T maps 64 x 64 boxes over (m_pad x 64) bf16.
-cudaError_t launch_split_yT(const float* Y, int64_t m, int32_t d, int64_t m_pad, void* hi, void* lo, cudaStream_t s);
+// A / B / bias maps use 128-row boxes; the B operand sqrt(c) (y - mu) also serves the
+// P Y product, whose result is mapped back with inv_sc = 1 / sqrt(c) and mu (d floats).
 cudaError_t launch_map_sweep_tc(const float* X, float* out, const float* L, int64_t nA, int64_t nB, int32_t d,
                                 float alpha, const void* mapAh, const void* mapAl, const void* mapBh,
-                                const void* mapBl, const void* mapBbias, const void* mapYTh, const void* mapYTl,
+                                const void* mapBl, const void* mapBbias, float inv_sc, const float* mu,
                                 float* Opart, float* Rpart, unsigned* cnt, int G, int maxseg, int32_t* fault,
                                 cudaStream_t stream);
 size_t map_sweep_tc_smem();
