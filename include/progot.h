@@ -415,7 +415,7 @@ int progot_set_stall_window(int32_t iters);
 /*
  * progot_set_map_tc - choose the kernel of the map step (Alg. 2 / Alg. 3) on the
  * tensor-core paths (PROGOT_BF16X3, PROGOT_BF16) for d <= 64: 1 (default) runs S = X Y^T
- * and P Y on tcgen05 (P in bf16 hi/lo, Y^T in bf16 hi/lo, three products, float32
+ * and P Y on tcgen05 (P and the centred, scaled Y in bf16 hi/lo, three products, float32
  * accumulation in TMEM); 0 runs P Y on float32 CUDA cores after the tensor-core LSE
  * pass (the path for d > 64 and PROGOT_FP32). Process-wide setting.
  */

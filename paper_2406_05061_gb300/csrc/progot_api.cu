@@ -346,7 +346,7 @@ struct TcOps {
   // operand maps in the A role (128-row boxes) and the B role (bn-row boxes), bias maps
   // (bn-row boxes); CUtensorMap is 64-byte aligned by its own declaration
   CUtensorMap xh_a, xl_a, yh_a, yl_a, xh_b, xl_b, yh_b, yl_b, xb, yb;
-  // tensor-core map step (dp = 64): y-side bias rows in 128-row boxes, Y^T hi / lo
+  // tensor-core map step (dp = 64): y-side bias rows in 128-row boxes
   CUtensorMap yb128;
   // centre mu of the operands and the squared norms |x_i - mu|^2, |y_j - mu|^2 that
   // the tensor-core sweeps use in place of |x_i|^2, |y_j|^2
