@@ -44,10 +44,10 @@ WORKLOADS = {
 # ones captured: their SHA-256 prefix is checked at run time, else traffic is null.
 CAPTURED_TRAFFIC = {
     ("lse_sweep_tc", "gmm8_8192_d64", "bf16x3"): dict(
-        bytes=4613632.0,
+        bytes=4627456.0,
         sources=("paper_2406_05061_gb300/csrc/sweep_tc.cu", "paper_2406_05061_gb300/csrc/sweep_epilogue.cuh",
                  "paper_2406_05061_gb300/csrc/progot_common.cuh", "paper_2406_05061_gb300/csrc/tc_common.cuh"),
-        sha256=("d0528a16385bd7c9", "33eed614b4d23717", "5f5f8ae4e51caf17", "855ddd4d44186262")),
+        sha256=("b18c4541e6095dba", "bcfd55d39f4813fc", "b26a7aa138618011", "735cd6a3dff3d7d7")),
 }
 
 
