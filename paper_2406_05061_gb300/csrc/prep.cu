@@ -189,17 +189,24 @@ __global__ void center_pass1(const float* __restrict__ X, int64_t n, const float
   }
 }
 
-// mu_k = (sum_x_k / n + sum_y_k / m) / 2 from the block partials, in block order.
+// mu_k = (sum_x_k / n + sum_y_k / m) / 2 from the block partials: one warp per
+// coordinate, lane l summing blocks l, l + 32, ... in order, then a fixed shuffle tree.
 __global__ void center_finish(const double* __restrict__ partial, int parts, int64_t n, int64_t m, int32_t d,
                               float* __restrict__ mu) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   if (k >= d) return;
   double sx = 0.0, sy = 0.0;
-  for (int b = 0; b < parts; ++b) {
+  for (int b = lane; b < parts; b += 32) {
     sx += partial[(int64_t)b * d + k];
     sy += partial[((int64_t)parts + b) * d + k];
   }
-  mu[k] = (float)(0.5 * (sx / (double)n + sy / (double)m));
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    sx += __shfl_xor_sync(0xffffffffu, sx, off);
+    sy += __shfl_xor_sync(0xffffffffu, sy, off);
+  }
+  if (lane == 0) mu[k] = (float)(0.5 * (sx / (double)n + sy / (double)m));
 }
 
 cudaError_t launch_center(const float* X, int64_t n, const float* Y, int64_t m, int32_t d, double* partial, float* mu,
@@ -215,7 +222,7 @@ cudaError_t launch_center(const float* X, int64_t n, const float* Y, int64_t m, 
   const int parts = kParts / 2;
   center_pass1<<<dim3(parts, 2), 32 * warps, smem, s>>>(X, n, Y, m, d, partial);
   count_launch();
-  center_finish<<<(d + 127) / 128, 128, 0, s>>>(partial, parts, n, m, d, mu);
+  center_finish<<<(d + 7) / 8, 256, 0, s>>>(partial, parts, n, m, d, mu);
   count_launch();
   return cudaGetLastError();
 }
