@@ -330,3 +330,31 @@ def test_banded_work_split_sampled_parity(nat, n, m, d):
     # float32 P Y sweep after a banded log-sum-exp pass (d > 64)
     out = nat.entropic_map_apply(x, y, res.g.reshape(1, -1), [eps], [1.0], precision="bf16x3")
     assert map_rms_rel(host(out)[rows], T_tc, p.y) <= TOL_MIXED
+
+
+# ------------------------------------------------ map Jacobian (conditional covariance)
+@pytest.mark.parametrize("precision,h,tol", [("fp32", 3e-3, 2e-3), ("bf16x3", 3e-2, 2e-2)])
+def test_map_jacobian_is_conditional_covariance(nat, precision, h, tol):
+    # grad T_eps(x) = (2 / eps) Cov_p(x)(Y) for c = |x - y|^2 (the Lipschitz lemma of the
+    # appendix, with the factor 2 of this cost): central differences of the GPU map on
+    # query points against the covariance the oracle forms from the GPU's own g
+    p = W.gmm_pair(600, 500, 3, seed=53, k=3)
+    eps = 0.2 * O.mean_cost(p.x, p.y)
+    res = nat.sinkhorn_potentials(dev(p.x), dev(p.y), eps, 1e-5, max_iter=5000, precision=precision)
+    assert res.status == nat.PROGOT_OK, nat.last_error()
+    g = host(res.g)
+    d = 3
+    xq = np.random.default_rng(54).normal(size=(6, d)) * 1.5
+    pts = np.concatenate([xq[:, None, :] + s * h * np.eye(d)[None] for s in (1.0, -1.0)], axis=1).reshape(-1, d)
+    T = host(nat.entropic_map_apply(dev(pts), dev(p.y), res.g.reshape(1, -1), [eps], [1.0],
+                                    precision=precision)).reshape(6, 2, d, d)
+    J = (T[:, 0] - T[:, 1]) / (2 * h)  # J[q, k, :] = dT / dx_k at point q
+    Y64 = p.y.astype(np.float64)
+    for q in range(6):
+        logits = (g - np.sum((xq[q] - Y64) ** 2, 1)) / eps
+        w = np.exp(logits - logits.max())
+        w /= w.sum()
+        mu = w @ Y64
+        cov = (Y64 - mu).T @ ((Y64 - mu) * w[:, None])
+        want = 2.0 / eps * cov
+        assert np.abs(J[q].T - want).max() <= tol * np.abs(want).max() + 1e-6
