@@ -12,16 +12,15 @@ constexpr int kParts = 304;  // partial sums of the two-pass reductions
 
 int reduce_parts() { return kParts; }
 
-// One warp per row: |x_i - mu|^2 (mu = 0 when NULL) summed in float64, stored as float32.
-__global__ void row_sqnorm_kernel(const float* __restrict__ X, int64_t n, int32_t d, const float* __restrict__ mu,
-                                  float* __restrict__ out) {
+// One warp per row: |x_i|^2 summed in float64, stored as float32.
+__global__ void row_sqnorm_kernel(const float* __restrict__ X, int64_t n, int32_t d, float* __restrict__ out) {
   const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
   const float* x = X + row * (int64_t)d;
   double s = 0.0;
   for (int k = lane; k < d; k += 32) {
-    const double v = (double)x[k] - (mu ? (double)mu[k] : 0.0);
+    const double v = (double)x[k];
     s += v * v;
   }
 #pragma unroll
@@ -158,11 +157,11 @@ __global__ void mean_cost_closed(const double* __restrict__ mx, const double* __
   }
 }
 
-cudaError_t launch_row_sqnorm(const float* X, int64_t n, int32_t d, float* out, cudaStream_t s, const float* mu) {
+cudaError_t launch_row_sqnorm(const float* X, int64_t n, int32_t d, float* out, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int rows_per_block = 8;
   const int64_t blocks = (n + rows_per_block - 1) / rows_per_block;
-  row_sqnorm_kernel<<<(unsigned)blocks, 256, 0, s>>>(X, n, d, mu, out);
+  row_sqnorm_kernel<<<(unsigned)blocks, 256, 0, s>>>(X, n, d, out);
   count_launch();
   return cudaGetLastError();
 }

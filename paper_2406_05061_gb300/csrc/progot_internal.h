@@ -46,8 +46,7 @@ int fp32_tile_cols();
 int map_dchunk();
 
 // small kernels (prep.cu)
-cudaError_t launch_row_sqnorm(const float* X, int64_t n, int32_t d, float* out, cudaStream_t s,
-                              const float* mu = nullptr);
+cudaError_t launch_row_sqnorm(const float* X, int64_t n, int32_t d, float* out, cudaStream_t s);
 // mu = (mean of the rows of X + mean of the rows of Y) / 2 (fixed-order float64 sums);
 // partial: reduce_parts() * 2 * d doubles of scratch.
 cudaError_t launch_center(const float* X, int64_t n, const float* Y, int64_t m, int32_t d, double* partial, float* mu,
