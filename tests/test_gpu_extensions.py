@@ -358,3 +358,26 @@ def test_map_jacobian_is_conditional_covariance(nat, precision, h, tol):
         cov = (Y64 - mu).T @ ((Y64 - mu) * w[:, None])
         want = 2.0 / eps * cov
         assert np.abs(J[q].T - want).max() <= tol * np.abs(want).max() + 1e-6
+
+
+# ---------------------------------------------------------------- one dimension
+@pytest.mark.parametrize("precision,tol", [("fp32", TOL_FP32), ("bf16x3", TOL_MIXED)])
+def test_one_dimensional_clouds(nat, precision, tol):
+    # d = 1 (K padded to 64 on the tensor cores): Sinkhorn and a two-step ProgOT against
+    # the oracle; in 1-D the entropic map is monotone, checked on the sorted queries
+    p = W.gmm_pair(700, 530, 1, seed=55, k=3)
+    eps = 0.05 * O.mean_cost(p.x, p.y)
+    res = nat.sinkhorn_potentials(dev(p.x), dev(p.y), eps, 1e-5, max_iter=5000, precision=precision)
+    assert res.status == nat.PROGOT_OK, nat.last_error()
+    ref = O.sinkhorn(None, p.x, None, p.y, eps, 1e-7, max_iter=5000)
+    T_gpu = O.entropic_map(p.x, p.y, host(res.g), eps)
+    assert map_rms_rel(T_gpu, O.entropic_map(p.x, p.y, ref.g, eps), p.y) <= tol
+    xs = np.sort(p.x[:, 0])[:, None]
+    Ts = host(nat.entropic_map_apply(dev(xs), dev(p.y), res.g.reshape(1, -1), [eps], [1.0], precision=precision))
+    assert np.all(np.diff(Ts[:, 0]) >= -tol * np.ptp(p.y))
+    K = 2
+    alpha = O.alpha_schedule(K)
+    r2 = nat.progot_solve(dev(p.x), dev(p.y), alpha, [eps, eps / 2], [1e-5, 1e-5], max_iter=5000, precision=precision)
+    assert r2.status == nat.PROGOT_OK, nat.last_error()
+    o2 = O.progot(None, p.x, None, p.y, [eps, eps / 2], alpha, [1e-7, 1e-7])
+    assert map_rms_rel(host(r2.x_out), o2.x_out, p.y) <= tol
