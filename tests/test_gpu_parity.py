@@ -348,3 +348,26 @@ def test_full_size_sphere_65536_d256_sampled_parity(nat):
     out = nat.entropic_map_apply(x, y, res.g.reshape(1, -1), [eps], [1.0], precision="bf16x3")
     T_ref = O.entropic_map(X64[rows], Y64, g, eps)
     assert map_rms_rel(host(out)[rows], T_ref, p.y) <= TOL_MIXED
+
+
+def test_full_size_progot_last_step_teacher_forced_bf16x3(nat):
+    """The benchmark workload (n = m = 8192, d = 64, K = 8, bf16x3, tau = 1e-4): the
+    last step is checked teacher-forced on 48 sampled rows, i.e. the oracle applies the
+    eq. (7) map with the GPU's own g_K to the GPU's own X^(K-1) (alpha_K = 1, so x_out is
+    that map), and the final coupling's row sums are recomputed in float64."""
+    p = W.gmm_pair(8192, 8192, 64, seed=1)
+    K = 8
+    alpha = O.alpha_schedule(K)
+    e0 = O.mean_cost(p.x[:2048], p.y[:2048]) / 20
+    eps = list(np.geomspace(5 * e0, 0.5 * e0, K))
+    res = nat.progot_solve(dev(p.x), dev(p.y), alpha, eps, [1e-4] * K, max_iter=5000, precision="bf16x3")
+    assert res.status == nat.PROGOT_OK, nat.last_error()
+    rows = np.random.default_rng(56).choice(8192, 48, replace=False)
+    xl = host(res.x_last)
+    gK, fK = host(res.g_all[K - 1]), host(res.f_last)
+    Y64 = p.y.astype(np.float64)
+    T_ref = O.entropic_map(xl[rows], Y64, gK, eps[-1])
+    assert map_rms_rel(host(res.x_out)[rows], T_ref, p.y) <= TOL_MIXED
+    C = O.cost_matrix_rows(xl[rows], Y64)
+    r = np.exp((fK[rows, None] + gK[None, :] - C) / eps[-1]).sum(1)
+    assert np.abs(r * 8192 - 1.0).max() <= 1e-2
