@@ -428,10 +428,21 @@ __global__ void __launch_bounds__(MT_NTHREADS, 1)
         const int64_t rem = mp.nA - (int64_t)sg.r * BM;
         const int rows = rem < BM ? (int)rem : BM;
         const int dd = mp.d;
-#pragma unroll 4
-        for (int e = ltid; e < rows * dd; e += 128) {
-          const int rr = e / dd, kx = e - rr * dd;
-          float num = 0.f;
+        const int64_t r0 = (int64_t)sg.r * BM;
+        // Thread ltid owns the float4 groups f = ltid + 128 j of the 128 x 64 block (rows
+        // f / 16, coordinates 4 (f % 16) .. + 3, the same four for every j). Each pass
+        // issues the loads of eight groups together, contributor by contributor (the sums
+        // keep the CTA order), then all eight groups' x before any store: out aliases x,
+        // so a store between loads would serialise them.
+        const int c0 = (ltid & 15) * 4;
+        float muv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) muv[u] = (c0 + u < dd) ? mp.mu[c0 + u] : 0.f;
+#pragma unroll 1
+        for (int pass = 0; pass < 2; ++pass) {
+          float4 acc[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
           for (int q2 = 0; q2 < nc; ++q2) {
             int64_t sl;
             if (q2 < 8) {
@@ -440,12 +451,40 @@ __global__ void __launch_bounds__(MT_NTHREADS, 1)
               const int cc = c_first + q2;
               sl = (int64_t)cc * mp.maxseg + seg_of(sp, sg.r, cc);
             }
-            num += __ldcg(mp.Opart + (sl * BM + rr) * 64 + kx);
+            const float4* src = reinterpret_cast<const float4*>(mp.Opart + sl * BM * 64);
+            float4 v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = __ldcg(src + ltid + 128 * (pass * 8 + j));
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              acc[j].x += v[j].x;
+              acc[j].y += v[j].y;
+              acc[j].z += v[j].z;
+              acc[j].w += v[j].w;
+            }
           }
-          const int64_t gi = (int64_t)sg.r * BM + rr;
-          const float x = mp.X[gi * dd + kx];
-          const float tx = fmaf(num / sh.den[rr], mp.inv_sc, mp.mu[kx]);
-          mp.out[gi * dd + kx] = fmaf(mp.alpha, tx - x, x);
+          float xs[8][4];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int row = (ltid + 128 * (pass * 8 + j)) >> 4;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              xs[j][u] = (row < rows && c0 + u < dd) ? mp.X[(r0 + row) * dd + c0 + u] : 0.f;
+          }
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int row = (ltid + 128 * (pass * 8 + j)) >> 4;
+            if (row >= rows) continue;
+            const float den = sh.den[row];
+            const float num[4] = {acc[j].x, acc[j].y, acc[j].z, acc[j].w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              if (c0 + u < dd) {
+                const float tx = fmaf(num[u] / den, mp.inv_sc, muv[u]);
+                mp.out[(r0 + row) * dd + c0 + u] = fmaf(mp.alpha, tx - xs[j][u], xs[j][u]);
+              }
+            }
+          }
         }
         mt_bar_wg0();
         if (ltid == 0) mp.cnt[sg.r] = 0;
