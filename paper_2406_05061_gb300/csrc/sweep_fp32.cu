@@ -537,14 +537,37 @@ __global__ void __launch_bounds__(NT, 1) map_sweep_fp32(MapParams p) {
   __syncthreads();
   const int64_t rem = p.nA - row0;
   const int rows = rem < BM ? (int)rem : BM;
-  for (int e = threadIdx.x; e < rows * p.d; e += NT) {
-    const int r = e / p.d, k = e % p.d;
-    const int64_t i = row0 + r;
-    float num = 0.f;
-    for (int s = 0; s < p.splits; ++s) num += __ldcg(p.Opart + ((int64_t)s * p.nA + i) * p.d + k);
-    const float T = num / den[r];
-    const float x = p.A[i * (int64_t)p.d + k];
-    p.out[i * (int64_t)p.d + k] = fmaf(p.alpha, T - x, x);
+  // eight elements per thread per round: x first, then the split sums with the loads of
+  // a split issued together, then the stores (out aliases x: a store between loads
+  // would serialise them); the splits are added in split order as before
+  const int total = rows * p.d;
+  for (int e0 = threadIdx.x; e0 < total; e0 += NT * 8) {
+    float num[8], xs[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      num[u] = 0.f;
+      xs[u] = 0.f;
+      const int e = e0 + NT * u;
+      if (e < total) xs[u] = p.A[row0 * (int64_t)p.d + e];
+    }
+    for (int s = 0; s < p.splits; ++s) {
+      const float* src = p.Opart + ((int64_t)s * p.nA + row0) * p.d;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + NT * u;
+        if (e < total) num[u] += __ldcg(src + e);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + NT * u;
+      if (e >= total) continue;
+      const int r = e / p.d, k = e % p.d;
+      const float x = xs[u];
+      const float T = num[u] / den[r];
+      p.out[row0 * (int64_t)p.d + e] = fmaf(p.alpha, T - x, x);
+      (void)k;
+    }
   }
   if (threadIdx.x == 0) p.cnt[blockIdx.x] = 0;
 }
@@ -701,14 +724,37 @@ __global__ void __launch_bounds__(NT, 1) map_sweep_pnorm(MapParams p) {
   __syncthreads();
   const int64_t rem = p.nA - row0;
   const int rows = rem < BM ? (int)rem : BM;
-  for (int e = threadIdx.x; e < rows * p.d; e += NT) {
-    const int r = e / p.d, k = e % p.d;
-    const int64_t i = row0 + r;
-    float num = 0.f;
-    for (int s = 0; s < p.splits; ++s) num += __ldcg(p.Opart + ((int64_t)s * p.nA + i) * p.d + k);
-    const float Z = grad_h_star_coord<kCost>(num / den[r], p.cost_p);
-    const float x = p.A[i * (int64_t)p.d + k];
-    p.out[i * (int64_t)p.d + k] = fmaf(-p.alpha, Z, x);
+  // eight elements per thread per round: x first, then the split sums with the loads of
+  // a split issued together, then the stores (out aliases x: a store between loads
+  // would serialise them); the splits are added in split order as before
+  const int total = rows * p.d;
+  for (int e0 = threadIdx.x; e0 < total; e0 += NT * 8) {
+    float num[8], xs[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      num[u] = 0.f;
+      xs[u] = 0.f;
+      const int e = e0 + NT * u;
+      if (e < total) xs[u] = p.A[row0 * (int64_t)p.d + e];
+    }
+    for (int s = 0; s < p.splits; ++s) {
+      const float* src = p.Opart + ((int64_t)s * p.nA + row0) * p.d;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + NT * u;
+        if (e < total) num[u] += __ldcg(src + e);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + NT * u;
+      if (e >= total) continue;
+      const int r = e / p.d, k = e % p.d;
+      const float x = xs[u];
+      const float Z = grad_h_star_coord<kCost>(num[u] / den[r], p.cost_p);
+      p.out[row0 * (int64_t)p.d + e] = fmaf(-p.alpha, Z, x);
+      (void)k;
+    }
   }
   if (threadIdx.x == 0) p.cnt[blockIdx.x] = 0;
 }
