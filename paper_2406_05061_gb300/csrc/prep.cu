@@ -1,7 +1,8 @@
 // Small O((n + m) d) kernels: squared norms (float64 accumulation), potential scaling
-// for the warm start of Alg. 2, state initialisation, and deterministic float64
-// reductions (first moments for the closed-form mean cost of Alg. 4 and of the theta
-// rule, squared error for the Alg. 4 score, the coupling diagonal of Prop. 3).
+// for the warm start of Alg. 2, state initialisation, deterministic float64 reductions
+// (first moments for the closed-form mean cost of Alg. 4 and of the theta rule, the
+// centre of the tensor-core operands, squared error for the Alg. 4 score, the coupling
+// diagonal of Prop. 3) and the move of a centred log-sum-exp back to uncentred form.
 #include <algorithm>
 
 #include "progot_internal.h"

@@ -1,11 +1,13 @@
 // Host orchestration of the ProgOT hot path and its C ABI (include/progot.h).
 //
 // The Sinkhorn loop of Alg. 1 runs without a host round trip per iteration: every
-// f-sweep measures the row-marginal error of the current (f, g) in its epilogue and
-// the last CTA decides on the device whether to stop (SolverState). Later sweeps of a
+// f-sweep measures the row-marginal error of the current (f, g) in its epilogue and the
+// stop test runs on the device (SolverState): in the f-sweep's last CTA, or, in
+// tensor-core loops, in the g-sweep that follows (SweepParams::lag). Later sweeps of a
 // stopped loop return at entry, so the host enqueues iterations in growing chunks and
 // reads the state back (pinned memory, one event per chunk) while the next chunk is
-// already queued.
+// already queued. The tensor-core operands are centred (prep_tc) and the large-n
+// sweeps split whole row blocks in bands (tc::Split).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
