@@ -10,6 +10,7 @@ import pytest
 from scipy import optimize, special
 from scipy.linalg import sqrtm
 
+import closed_forms as CF
 from oracle import progot_oracle as O
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -350,6 +351,45 @@ def test_eps_schedule_alg4_structure():
     np.testing.assert_allclose(sched, (1 - t) * 5 * info["eps0"] + t * info["eps_K"], rtol=1e-14)
 
 
+# Two-point targets (closed form in tests/closed_forms.py). Case A: uniform b, the default
+# grid s_p = 2^-3..2^3; case B: b = (0.7, 0.3) on a grid that keeps the Gibbs kernel's
+# off-diagonal entry away from zero, so the score depends on the potential g.
+ALG4_Y = (np.array([0.0, 0.0]), np.array([2.0, 0.0]))
+ALG4_CASES = {
+    "A": dict(b=(0.5, 0.5), Z=np.array([[0.6, 0.0], [1.4, 0.3], [1.0, -0.2]]),
+              s_grid=[2.0 ** e for e in range(-3, 4)]),
+    "B": dict(b=(0.7, 0.3), Z=np.array([[0.7, 0.0], [1.3, 0.1]]), s_grid=[10.0, 14.0, 20.0, 28.0, 40.0]),
+}
+
+
+def _alg4_case(name):
+    c = ALG4_CASES[name]
+    X = _rng(5).normal(size=(5, 2))
+    Y = np.stack(ALG4_Y)
+    b = None if c["b"] == (0.5, 0.5) else np.array(c["b"])
+    return X, Y, b, c
+
+
+@pytest.mark.parametrize("name", ["A", "B"])
+def test_eps_schedule_two_point_closed_form(name):
+    """Alg. 4 against its closed form on a two-point target: eps0, sigma, every s_p's
+    score (the eq. (7) map of the held-out points from the two-point Sinkhorn plan), p*
+    and the interpolated schedule."""
+    X, Y, b, c = _alg4_case(name)
+    K = 4
+    al = O.alpha_schedule(K)
+    sched, info = O.eps_schedule(X, b, Y, c["Z"], al, s_grid=c["s_grid"], tau=1e-13)
+    want, scores, p, eps0, sigma = CF.two_point_alg4(X, *ALG4_Y, c["Z"], K, c["s_grid"], b=c["b"])
+    assert abs(info["eps0"] - eps0) <= 1e-13 * eps0 and abs(info["sigma"] - sigma) <= 1e-13 * sigma
+    np.testing.assert_allclose(info["errors"], scores, rtol=1e-9, atol=1e-12)
+    srt = np.sort(scores)
+    assert srt[1] - srt[0] > 0.05 * srt[0]  # the minimiser is clear
+    assert info["p_star"] == p
+    np.testing.assert_allclose(sched, want, rtol=1e-12)
+    if name == "B":
+        assert 0 < p < len(c["s_grid"]) - 1  # an interior choice: the scores are not monotone
+
+
 # ------------------------------------------------ planted mistakes are caught
 @pytest.mark.filterwarnings("ignore::RuntimeWarning")
 def test_planted_mistakes_are_caught(monkeypatch):
@@ -386,6 +426,19 @@ def test_planted_mistakes_are_caught(monkeypatch):
     np.testing.assert_allclose(good, pr.x_out, atol=1e-8)
     bad = O.progot_map(X, Y, [gk + e * np.log(b) for gk, e in zip(pr.g_all, [0.8, 0.5])], [0.8, 0.5], al)
     assert np.max(np.abs(bad - pr.x_out)) > 1e-4
+    # (5) Alg. 4 scoring the held-out points with a zero potential (the Sinkhorn solve
+    # ignored) picks another s_p on the two-point target with non-uniform b
+    orig_map = O.progot_map
+    monkeypatch.setattr(O, "progot_map", lambda Xq, Yy, g_all, eps, al: orig_map(Xq, Yy, [np.zeros_like(g) for g in g_all], eps, al))
+    with pytest.raises(AssertionError):
+        test_eps_schedule_two_point_closed_form("B")
+    monkeypatch.undo()
+    # (6) sigma taken from the source-target cost instead of C_YY moves the eps grid
+    orig_mc = O.mean_cost
+    monkeypatch.setattr(O, "mean_cost", lambda U, V, *a, **k: orig_mc(U, V, *a, **k) if U is not V else orig_mc(_rng(5).normal(size=(5, 2)), V, *a, **k))
+    with pytest.raises(AssertionError):
+        test_eps_schedule_two_point_closed_form("A")
+    monkeypatch.undo()
 
 
 def test_sinkhorn_continues_through_an_overflowing_error():
