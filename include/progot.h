@@ -142,7 +142,8 @@ int coupling_marginals(const float* x, int64_t n, const float* y, int64_t m, int
  * - n and m must each be at most 65536; larger sizes return PROGOT_ERR_INVALID_ARG with
  *   an explanatory progot_last_error_string(). Only PROGOT_FP32 is accepted.
  * - The first call on a device looks up the device address of the array (a one-time
- *   set-up per device); make that first call before any stream capture.
+ *   set-up per device, repeated only when the device's context was reset, e.g. by
+ *   cudaDeviceReset); make that first call before any stream capture.
  * - All calls share the one array, which keeps the last call's contents (the arrival
  *   counters are cleared at the start of every call). Calls whose GPU work overlaps
  *   (other streams, other host threads on the same device) race on it: serialise them.

@@ -22,8 +22,7 @@ What it computes, in float64, step by step in the paper's order and notation:
 * eq. (8): the Sinkhorn divergence D_eps(X, Y) built from the eq. (5) objective.
 * Sec. 5.3 / Prop. 3: trace and KL of the coupling diagonal against Id / n.
 
-Readings where the paper's printed formulas are garbled or silent (each one is
-also listed in the design notes):
+Readings where the paper's printed formulas are garbled or silent:
 
 * Alg. 1 loop condition: iterate WHILE ||P 1 - a||_1 > tau (the printed "<" would
   never start the loop).

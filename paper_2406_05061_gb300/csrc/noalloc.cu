@@ -44,10 +44,30 @@ constexpr size_t kNoAllocBytes = kOffCntCol + round256(sizeof(unsigned) * (kNoAl
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 // Device address of g_noalloc_scratch per device ordinal, looked up once per device
-// (host code must not use the symbol itself: on the host it is only a stand-in).
+// (host code must not use the symbol itself: on the host it is only a stand-in). The
+// lookup is keyed on the device's current CUDA context too: after cudaDeviceReset the
+// module is loaded again at another address, and the next call looks it up again.
 constexpr int kMaxDevices = 64;
 static unsigned char* g_scratch_addr[kMaxDevices] = {nullptr};
+static void* g_scratch_ctx[kMaxDevices] = {nullptr};
 static std::mutex g_scratch_mu;
+
+typedef int (*CtxGetCurrentFn)(void**);
+static void* current_context() {
+  static CtxGetCurrentFn fn = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<CtxGetCurrentFn>(p);
+    looked = true;
+  }
+  void* ctx = nullptr;
+  if (fn == nullptr || fn(&ctx) != 0) return nullptr;
+  return ctx;
+}
 
 static int scratch_for_current_device(unsigned char** out, const char** why) {
   int dev = 0;
@@ -60,7 +80,8 @@ static int scratch_for_current_device(unsigned char** out, const char** why) {
     return PROGOT_ERR_INVALID_ARG;
   }
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (g_scratch_addr[dev] == nullptr) {
+  void* ctx = current_context();
+  if (g_scratch_addr[dev] == nullptr || ctx == nullptr || ctx != g_scratch_ctx[dev]) {
     void* ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
     if (e != cudaSuccess || ptr == nullptr) {
@@ -68,6 +89,7 @@ static int scratch_for_current_device(unsigned char** out, const char** why) {
       return PROGOT_ERR_CUDA;
     }
     g_scratch_addr[dev] = static_cast<unsigned char*>(ptr);
+    g_scratch_ctx[dev] = current_context();  // the lookup made the device's context current
   }
   *out = g_scratch_addr[dev];
   return PROGOT_OK;
@@ -85,6 +107,11 @@ static int sm_count() {
   return sms;
 }
 
+// The scratch layout assumes the float32 sweep's 128 x 128 tiles (one error partial per
+// 128-row block, at most kNoAllocPartials split partials); a kernel built with other tile
+// sizes must not run on it.
+static bool tiles_match_layout() { return fp32_tile_rows() == 128 && fp32_tile_cols() == 128; }
+
 // One marginal sweep "rows of A against rows of B" on the static scratch.
 static SweepParams noalloc_sweep(const float* A, int64_t nA, const float* B, int64_t nB, int32_t d, const float* An,
                                  const float* Bn, double eps, float2* partial, double* errpart, unsigned* cnt) {
@@ -97,8 +124,9 @@ static SweepParams noalloc_sweep(const float* A, int64_t nA, const float* B, int
   p.nA = nA;
   p.nB = nB;
   p.d = d;
-  const int64_t rb = (nA + 127) / 128;
-  const int64_t ct = (nB + 127) / 128;
+  const int64_t BMr = fp32_tile_rows(), BNc = fp32_tile_cols();
+  const int64_t rb = (nA + BMr - 1) / BMr;
+  const int64_t ct = (nB + BNc - 1) / BNc;
   int64_t s = (int64_t)sm_count() * 2 / rb;
   if (s < 1) s = 1;
   if (s > ct) s = ct;
@@ -136,7 +164,9 @@ extern "C" int coupling_marginals_noalloc(const float* x, int64_t n, const float
                         "coupling_marginals_noalloc supports at most 65536 points per side (static scratch); "
                         "use coupling_marginals with a workspace for larger problems");
   if (precision != PROGOT_FP32) return noalloc_fail(PROGOT_ERR_INVALID_ARG, "only PROGOT_FP32 is supported");
-  if (!(eps > 0.0)) return noalloc_fail(PROGOT_ERR_INVALID_ARG, "eps must be positive");
+  if (!(eps > 0.0) || !std::isfinite(eps)) return noalloc_fail(PROGOT_ERR_INVALID_ARG, "eps must be positive and finite");
+  if (!tiles_match_layout())
+    return noalloc_fail(PROGOT_ERR_INVALID_ARG, "the float32 sweep's tile sizes do not match the static scratch layout");
   unsigned char* base = nullptr;
   const char* why = "";
   int rc = scratch_for_current_device(&base, &why);
@@ -169,7 +199,7 @@ extern "C" int coupling_marginals_noalloc(const float* x, int64_t n, const float
   if (launch_lse_sweep_fp32(pc, s) != cudaSuccess) return noalloc_fail(PROGOT_ERR_CUDA, "column sweep launch failed");
   if (err_l1_out != nullptr) {
     double er = 0.0, ec = 0.0;
-    const int64_t rbr = (n + 127) / 128, rbc = (m + 127) / 128;
+    const int64_t rbr = (n + fp32_tile_rows() - 1) / fp32_tile_rows(), rbc = (m + fp32_tile_rows() - 1) / fp32_tile_rows();
     if (cudaMemcpyAsync(&er, err_row + rbr, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaMemcpyAsync(&ec, err_col + rbc, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)

@@ -557,9 +557,11 @@ NOALLOC_MAX_POINTS = 65536
 
 
 def coupling_marginals_noalloc(x, y, f, g, eps, a=None, b=None, precision="fp32", row=None, col=None,
-                               stream=None):
+                               stream=None, want_err=True):
     """coupling_marginals through the allocation-free entry point: the library uses its
-    own static device scratch (n, m <= 65536); the caller supplies inputs and outputs."""
+    own static device scratch (n, m <= 65536); the caller supplies inputs and outputs.
+    With want_err=False no error is requested (NULL) and the call stays asynchronous;
+    the returned error is then None."""
     torch = _torch()
     _dev(x, "x"), _dev(y, "y")
     n, d = x.shape
@@ -572,9 +574,9 @@ def coupling_marginals_noalloc(x, y, f, g, eps, a=None, b=None, precision="fp32"
     rc = lib().coupling_marginals_noalloc(_dev(x, "x"), n, _dev(y, "y"), m, d, _dev(f, "f", (n,)),
                                           _dev(g, "g", (m,)), float(eps), _prec(precision), _dev(row, "row", (n,)),
                                           _dev(col, "col", (m,)), _opt(a, "a", (n,)), _opt(b, "b", (m,)),
-                                          ctypes.byref(err), _stream(stream))
+                                          ctypes.byref(err) if want_err else None, _stream(stream))
     _check(rc, allow_not_converged=False)
-    return row, col, err.value
+    return row, col, (err.value if want_err else None)
 
 
 class ProblemStruct(ctypes.Structure):

@@ -5,10 +5,12 @@ Tolerances (float32 path): map RMS error relative to the target spread <= 1e-4 a
 marginal L1 error (recomputed by the oracle in float64 from the GPU's potentials)
 <= 1e-4 plus the solve's own tau."""
 import os
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 import pytest
 
+import closed_forms as CF
 from oracle import progot_oracle as O
 from paper_2406_05061_gb300 import workloads as W
 
@@ -48,6 +50,27 @@ def marginal_l1(X, Y, f, g, eps, a=None, b=None):
     a = np.full(n, 1.0 / n) if a is None else a
     b = np.full(m, 1.0 / m) if b is None else b
     return float(np.abs(O.row_marginal(C, f, g, eps) - a).sum() + np.abs(O.col_marginal(C, f, g, eps) - b).sum())
+
+
+def fp64_marginals(X, Y, f, g, eps, rows_per_block=8):
+    """Row and column sums of P = exp((f (+) g - C)/eps) over ALL pairs in float64, C
+    from the oracle's cost (differences, no norm expansion) in blocks of rows; the blocks
+    run on host threads and are summed in block order."""
+    X, Y = np.asarray(X, np.float64), np.asarray(Y, np.float64)
+    f, g = np.asarray(f, np.float64), np.asarray(g, np.float64)
+    n = X.shape[0]
+
+    def block(i0):
+        i1 = min(n, i0 + rows_per_block)
+        P = np.exp((f[i0:i1, None] + g[None, :] - O.cost_matrix_rows(X[i0:i1], Y)) / eps)
+        return i0, P.sum(1), P.sum(0)
+
+    row, col = np.empty(n), np.zeros(Y.shape[0])
+    with ThreadPoolExecutor(max(1, min(32, os.cpu_count() or 1))) as ex:
+        for i0, r, c in ex.map(block, range(0, n, rows_per_block)):
+            row[i0:i0 + r.shape[0]] = r
+            col += c
+    return row, col
 
 
 def eps_for(p, frac=0.05):
@@ -185,6 +208,25 @@ def test_schedule_eps_alg4_parity(nat):
         np.testing.assert_allclose(eps_gpu, eps_ref, rtol=1e-9)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_schedule_eps_two_point_closed_form(nat, precision):
+    """Alg. 4 on the GPU against its closed form on a two-point target with weights
+    b = (0.7, 0.3) (tests/closed_forms.py): every s_p's score, p* and the schedule."""
+    y1, y2 = np.array([0.0, 0.0]), np.array([2.0, 0.0])
+    Z = np.array([[0.7, 0.0], [1.3, 0.1]])
+    X = np.random.default_rng(5).normal(size=(5, 2)).astype(np.float32).astype(np.float64)
+    s_grid = [10.0, 14.0, 20.0, 28.0, 40.0]
+    b = np.array([0.7, 0.3])
+    al = O.alpha_schedule(4)
+    eps_gpu, scores, pstar = nat.progot_schedule_eps(dev(X), dev(np.stack([y1, y2])), dev(Z), al, s_grid=s_grid,
+                                                     tau=1e-6, b=dev(b), precision=precision)
+    want, cf_scores, p, eps0, sigma = CF.two_point_alg4(X, y1, y2, Z, 4, s_grid, b=(0.7, 0.3))
+    tol = 1e-4 if precision == "fp32" else 1e-3
+    np.testing.assert_allclose(scores, cf_scores, rtol=tol)
+    assert pstar == p
+    np.testing.assert_allclose(eps_gpu, want, rtol=1e-6)
+
+
 # ------------------------------------------------------------ edge cases
 def test_max_iter_zero_reports_initial_error(nat):
     p = W.gmm_pair(200, 150, 4, seed=1, k=2)
@@ -307,26 +349,25 @@ def test_progot_solve_parity_bf16x3(nat):
     assert marginal_l1(host(res.x_last), p.y, host(res.f_last), host(res.g_all[K - 1]), eps[-1]) <= TOL_MIXED
 
 
-def test_full_size_gmm64_sampled_parity_bf16x3(nat):
-    """n = m = 8192, d = 64 in the benchmark's launch configuration, bf16x3 sweeps:
-    marginals and map on 48 sampled rows computed one by one by the oracle from the
-    GPU's potentials, and the map against the oracle's map from the same g."""
+def test_full_size_gmm64_parity_bf16x3(nat):
+    """n = m = 8192, d = 64 in the benchmark's launch configuration, bf16x3 sweeps at
+    eps = 5 eps0 (the first scheduled step): both marginals of the GPU's (f, g)
+    recomputed over all 8192^2 pairs in float64 (L1 <= 1e-3), and the GPU's map on 48
+    sampled rows against the oracle's eq. (7) map from the same g."""
     p = W.gmm_pair(8192, 8192, 64, seed=1)
     eps = 5 * O.mean_cost(p.x[:2048], p.y[:2048]) / 20
     x, y = dev(p.x), dev(p.y)
     res = nat.sinkhorn_potentials(x, y, eps, 1e-4, max_iter=2000, precision="bf16x3")
     assert res.status == nat.PROGOT_OK, nat.last_error()
     f, g = host(res.f), host(res.g)
+    row, col = fp64_marginals(p.x, p.y, f, g, eps)
+    l1 = np.abs(row - 1.0 / 8192).sum() + np.abs(col - 1.0 / 8192).sum()
+    assert l1 <= TOL_MIXED, l1
     rows = np.random.default_rng(1).choice(8192, 48, replace=False)
     X64, Y64 = p.x.astype(np.float64), p.y.astype(np.float64)
-    Cs = O.cost_matrix_rows(X64[rows], Y64)
-    r_ref = np.exp((f[rows, None] + g[None, :] - Cs) / eps).sum(1)
-    # the sampled rows' share of the FP64 row-marginal error, scaled to all rows
-    assert np.abs(r_ref - 1.0 / 8192).sum() * 8192 / 48 <= 2 * TOL_MIXED
-    fp = nat.sinkhorn_potentials(x, y, eps, 1e-5, max_iter=2000, precision="fp32")
-    T_gpu = O.entropic_map(X64[rows], Y64, g, eps)
-    T_ref = O.entropic_map(X64[rows], Y64, host(fp.g), eps)
-    assert map_rms_rel(T_gpu, T_ref, p.y) <= TOL_MIXED
+    out = nat.entropic_map_apply(x, y, res.g.reshape(1, -1), [eps], [1.0], precision="bf16x3")
+    T_ref = O.entropic_map(X64[rows], Y64, g, eps)
+    assert map_rms_rel(host(out)[rows], T_ref, p.y) <= TOL_MIXED
 
 
 def test_full_size_sphere_65536_d256_sampled_parity(nat):
@@ -350,24 +391,48 @@ def test_full_size_sphere_65536_d256_sampled_parity(nat):
     assert map_rms_rel(host(out)[rows], T_ref, p.y) <= TOL_MIXED
 
 
-def test_full_size_progot_last_step_teacher_forced_bf16x3(nat):
-    """The benchmark workload (n = m = 8192, d = 64, K = 8, bf16x3, tau = 1e-4): the
-    last step is checked teacher-forced on 48 sampled rows, i.e. the oracle applies the
-    eq. (7) map with the GPU's own g_K to the GPU's own X^(K-1) (alpha_K = 1, so x_out is
-    that map), and the final coupling's row sums are recomputed in float64."""
-    p = W.gmm_pair(8192, 8192, 64, seed=1)
+def test_benchmark_workload_every_step_teacher_forced_bf16x3(nat):
+    """The benchmark workload exactly as bench.py runs it: n = m = 8192, d = 64, K = 8
+    constant-speed steps, bf16x3, tau = 1e-4, eps_k from the GPU's Alg. 4 scheduler on
+    the held-out target draw. Every step k is teacher-forced on 48 sampled rows: the
+    oracle applies eq. (7) with the GPU's g^(k) to the GPU's X^(k-1), and the GPU's
+    displacement (X^(k) - (1 - alpha_k) X^(k-1)) / alpha_k must match it within map RMS
+    1e-3; the sampled rows' float64 row sums of (f^(k), g^(k)), scaled to all rows, stay
+    within 1e-3. X^(k) and f^(k) come from solves truncated after step k, which repeat
+    the full solve's launches: their g's must equal the full solve's bit for bit. At the
+    last step both marginals of (X^(K-1), Y, f_K, g_K) are recomputed over all 8192^2
+    pairs in float64: L1 <= 1e-3."""
+    p = W.gmm_pair(8192, 8192, 64, seed=1, k=8)
+    yt = W.heldout_target(p)
     K = 8
-    alpha = O.alpha_schedule(K)
-    e0 = O.mean_cost(p.x[:2048], p.y[:2048]) / 20
-    eps = list(np.geomspace(5 * e0, 0.5 * e0, K))
-    res = nat.progot_solve(dev(p.x), dev(p.y), alpha, eps, [1e-4] * K, max_iter=5000, precision="bf16x3")
-    assert res.status == nat.PROGOT_OK, nat.last_error()
+    alpha = nat.progot_schedule_alpha(K, "constant")
+    tau = [1e-4] * K
+    x, y = dev(p.x), dev(p.y)
+    eps, _, _ = nat.progot_schedule_eps(x, y, dev(yt), alpha, tau=tau[-1], precision="bf16x3")
+    eps = [float(e) for e in eps]
+    full = nat.progot_solve(x, y, alpha, eps, tau, max_iter=10000, precision="bf16x3")
+    assert full.status == nat.PROGOT_OK, nat.last_error()
     rows = np.random.default_rng(56).choice(8192, 48, replace=False)
-    xl = host(res.x_last)
-    gK, fK = host(res.g_all[K - 1]), host(res.f_last)
     Y64 = p.y.astype(np.float64)
-    T_ref = O.entropic_map(xl[rows], Y64, gK, eps[-1])
-    assert map_rms_rel(host(res.x_out)[rows], T_ref, p.y) <= TOL_MIXED
-    C = O.cost_matrix_rows(xl[rows], Y64)
-    r = np.exp((fK[rows, None] + gK[None, :] - C) / eps[-1]).sum(1)
-    assert np.abs(r * 8192 - 1.0).max() <= 1e-2
+    X_prev = p.x.astype(np.float64)
+    for k in range(K):
+        if k < K - 1:
+            part = nat.progot_solve(x, y, alpha[:k + 1], eps[:k + 1], tau[:k + 1], max_iter=10000,
+                                    precision="bf16x3")
+            assert part.status == nat.PROGOT_OK, nat.last_error()
+            assert torch.equal(part.g_all, full.g_all[:k + 1])
+            X_k, f_k = host(part.x_out), host(part.f_last)
+        else:
+            assert np.array_equal(host(full.x_last), X_prev)
+            X_k, f_k = host(full.x_out), host(full.f_last)
+        g_k = host(full.g_all[k])
+        T_ref = O.entropic_map(X_prev[rows], Y64, g_k, eps[k])
+        T_gpu = (X_k[rows] - (1.0 - alpha[k]) * X_prev[rows]) / alpha[k]
+        assert map_rms_rel(T_gpu, T_ref, p.y) <= TOL_MIXED, (k, map_rms_rel(T_gpu, T_ref, p.y))
+        C = O.cost_matrix_rows(X_prev[rows], Y64)
+        r = np.exp((f_k[rows, None] + g_k[None, :] - C) / eps[k]).sum(1)
+        assert np.abs(r - 1.0 / 8192).sum() * 8192 / 48 <= TOL_MIXED, k
+        X_prev = X_k
+    row, col = fp64_marginals(host(full.x_last), p.y, host(full.f_last), host(full.g_all[K - 1]), eps[-1])
+    l1 = np.abs(row - 1.0 / 8192).sum() + np.abs(col - 1.0 / 8192).sum()
+    assert l1 <= TOL_MIXED, l1
