@@ -422,6 +422,40 @@ int progot_set_stall_window(int32_t iters);
  */
 int progot_set_map_tc(int32_t on);
 
+/*
+ * progot_set_loop_tc - choose how the tensor-core paths run a Sinkhorn loop (Alg. 1):
+ * 1 (default) as one persistent cooperative launch that runs every f- and g-update and
+ * the stop test on the device (the betas of each update's potential pass between the
+ * GPU's CTAs as tagged words, so a tile of the next update waits only for the row
+ * blocks it reads); 0 as one launch per update (the host enqueues chunks of
+ * iterations). Both compute the same iteration of Alg. 1 and stop at the same test.
+ * Shapes the persistent kernel cannot hold in shared memory use the per-update kernel.
+ * Process-wide setting.
+ */
+int progot_set_loop_tc(int32_t on);
+
+/*
+ * progot_set_wait_limit_ns - the bounded-wait limit of the persistent Sinkhorn loop's
+ * waits (on its own pipeline, on another CTA's row blocks, on the stop test), in
+ * nanoseconds of GPU global time; 0 restores the default of 2 s. A wait that runs past
+ * it makes the launch abort: every CTA stops issuing work, retires the copies and
+ * products it has in flight (those drains keep the 2 s limit), frees its tensor memory
+ * and returns, and the entry point returns PROGOT_ERR_TIMEOUT; the CUDA context stays
+ * usable. A very small limit makes ordinary waits expire, which is how the timeout
+ * path is exercised. Process-wide setting.
+ */
+int progot_set_wait_limit_ns(uint64_t ns);
+
+/*
+ * progot_test_withhold_initial_betas - test hook for the timeout path: with on = 1 the
+ * persistent Sinkhorn loops that start afterwards skip writing the initial betas of g
+ * (the words their first f-update reads), so those tiles wait for words that no sweep
+ * writes until the bounded wait (progot_set_wait_limit_ns) expires and the entry point
+ * returns PROGOT_ERR_TIMEOUT. Nothing faults or hangs; the context stays usable. 0
+ * (default) restores normal operation. Process-wide setting.
+ */
+int progot_test_withhold_initial_betas(int32_t on);
+
 /* Number of kernels this library launched since the last call (process-wide counter);
  * used to report launches inside a timed region. */
 int64_t progot_launch_count(int32_t reset);

@@ -1,0 +1,881 @@
+// Persistent tensor-core Sinkhorn loop (Alg. 1): one cooperative launch runs a chunk
+// of (f-update, g-update) iterations, the stop test included, without returning to the
+// host between sweeps.
+//
+// Every sweep is the log-sum-exp of lse_sweep_tc: for the rows a_i of one cloud,
+//   L_i = log2 sum_j 2^{t_ij},  t_ij = c (a_i . b_j) + beta_j,  c = 2 log2(e) / eps,
+//   beta_j = (pot_j - |b_j|^2) log2(e) / eps,
+// with both clouds centred, scaled by sqrt(c) and split into bf16 hi/lo ("bf16x3") so
+// that the tensor cores accumulate c (a_i . b_j) in float32 TMEM. Unlike the per-sweep
+// kernel, beta_j is added by the LSE warps (float32) instead of by a bias MMA: the
+// operand products of a sweep then depend on nothing the previous sweep computes, and
+// the MMA warp runs up to two tiles into the next sweep while the previous one
+// finishes.
+//
+// Data flow between sweeps. The row-block finisher of a sweep (the last CTA to arrive
+// on the row block) writes, for each of its rows, the new potential and a tagged beta
+// word (low 32 bits: beta as float32, high 32 bits: the index of the sweep that wrote
+// it, plus one) into a buffer chosen by the iteration's parity. A CTA about to fold a
+// column tile of the next sweep checks the tags of the tile's betas (fetched by the
+// producer warp with a bulk copy) and, only where a tag is stale, reloads the words
+// from L2 until they carry the expected tag. So a tile waits exactly for the row blocks
+// it reads, and no grid-wide barrier sits between sweeps.
+//
+// Stop test (Alg. 1: error <= tau, max_iter, a stall, a non-finite error). The f-update
+// of iteration k measures the row-marginal error of the current (f, g) and writes
+// per-row-block partials; once all row blocks of that f-update are done (a monotonic
+// counter), one warp per CTA sums the partials in a fixed order and applies the test
+// (every CTA computes the same state). The g-update of iteration k runs meanwhile; when
+// the test stops the loop, that g-update writes nothing and the loop ends after it.
+//
+// Warps: 0 TMA producer (A row block, B hi/lo stages, tagged betas), 1 TMEM owner and
+// MMA issuer, 2-9 two LSE warpgroups (alternate tiles), 10-11 segment epilogues
+// (publish, arrive, combine on the last arrival, potentials, betas, error partials) and
+// the stop decision. All waits are bounded: an mbarrier wait, a tag poll or a counter
+// poll that runs past the wait limit raises the CTA's abort flag and the grid's fault
+// word; every role then winds down (copies and products in flight drained, TMEM
+// freed) and the host returns PROGOT_ERR_TIMEOUT.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstddef>
+
+#include "progot_internal.h"
+#include "sweep_epilogue.cuh"
+#include "tc_common.cuh"
+
+namespace progot {
+namespace tc {
+namespace loop {
+
+constexpr int NTHREADS = 384;
+constexpr int EPI_TID0 = 320;
+constexpr int TMEM_COLS = 512;
+constexpr int BETA_SLOTS = 6;  // tagged-beta ring (even: slot s always serves warpgroup s & 1)
+constexpr int A_TILE_BYTES = BM * KB * 2;
+
+struct Shared {
+  uint64_t full[8];
+  uint64_t empty[8];
+  uint64_t beta_full[BETA_SLOTS];
+  uint64_t beta_empty[BETA_SLOTS];
+  uint64_t tmem_full[2];
+  uint64_t tmem_empty[2];
+  uint64_t a_full[2];
+  uint64_t a_empty[2];
+  uint64_t drain;
+  uint64_t seg_full[2];
+  uint64_t seg_empty[2];
+  uint64_t dec_full;        // one phase per iteration: the stop decision is in dec_stop
+  uint32_t tmem_base;
+  int32_t abort_flag;
+  int32_t e_last;
+  int32_t dec_stop[2];      // by iteration parity
+  int32_t entry_done;
+  alignas(16) SolverState st;  // the stop test's state as this CTA computed it (copied in 16-byte pieces)
+  float ered[4];
+  float2 ms[2][128];
+  float2 seg[2][128];
+};
+
+static_assert(offsetof(Shared, st) % 16 == 0, "the state is copied into shared memory in 16-byte pieces");
+static_assert(offsetof(Shared, ms) % 8 == 0 && offsetof(Shared, seg) % 8 == 0, "float2 slots");
+static_assert(sizeof(Shared) % 16 == 0, "the control block follows 16-byte aligned buffers");
+
+struct Layout {
+  uint32_t a0, a_stride, a_lo_off, stage0, stage_bytes, b_lo_off, beta0, beta_slot, fbuf0, ctrl, total;
+};
+
+__host__ __device__ inline Layout layout(int bn, int nkb, int split3, int stages, int a_bufs) {
+  Layout L;
+  uint32_t off = 0;
+  L.a0 = off;
+  L.a_lo_off = nkb * A_TILE_BYTES;
+  L.a_stride = nkb * A_TILE_BYTES * (split3 ? 2 : 1);
+  off += a_bufs * L.a_stride;
+  L.stage0 = off;
+  L.b_lo_off = (uint32_t)bn * KB * 2;
+  L.stage_bytes = L.b_lo_off * (split3 ? 2 : 1);
+  off += stages * L.stage_bytes;
+  L.beta0 = off;
+  L.beta_slot = (uint32_t)bn * 8;
+  off += BETA_SLOTS * L.beta_slot;
+  L.fbuf0 = off;  // float betas: [warpgroup][2][bn]
+  off += 4 * (uint32_t)bn * 4;
+  L.ctrl = off;
+  off += (uint32_t)sizeof(Shared);
+  L.total = off + 1024;
+  return L;
+}
+
+// One sweep direction: rows of A (whose potential is updated) against the columns of B.
+struct Side {
+  SweepParams p;            // mode = potential, role 1 (f) or 2 (g), centred norms, weights, eps
+  float* out0;              // f-update: the two f buffers (state.fcur selects the current one);
+  float* out1;              //   g-update: out0 = g
+  uint64_t* beta_out[2];    // tagged betas of A's rows, by iteration parity
+  const uint64_t* beta_in[2];  // tagged betas of B's rows
+  unsigned long long* cnt;  // [R] arrivals per row block (monotonic over the loop)
+  unsigned long long* done; // finished row blocks (monotonic over the loop)
+  float2* partial;          // [G * maxseg * 128] (max, sum) slots
+  int32_t R, T;
+  int64_t nA, nB;
+};
+
+struct Params {
+  Side side[2];  // 0: f-update (A = X, B = Y), 1: g-update (A = Y, B = X)
+  double* errpart;          // [2][R_x] row-marginal error partials by iteration parity
+  SolverState* state;       // read at entry, written by CTA 0 after every stop test
+  int32_t* fault;           // grid-wide abort / fault word
+  unsigned long long wait_ns;
+  int32_t nkb, split3, stages, a_bufs, G, maxseg;
+  int32_t seq0, niter;      // iterations seq0 .. seq0 + niter - 1 of the loop
+};
+
+// ------------------------------------------------------------------ waits
+__device__ __forceinline__ bool grid_aborted(const Params& P) {
+  return *reinterpret_cast<volatile int32_t*>(P.fault) != 0;
+}
+
+// Bounded mbarrier wait; false on expiry (then the CTA's abort flag and the grid's
+// fault word are raised) or when the CTA already aborted (unless ignore_abort).
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int32_t* abort_flag,
+                                         const Params& P, bool ignore_abort = false) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  const unsigned long long lim = ignore_abort ? kWaitNs : P.wait_ns;
+  for (uint32_t i = 1;; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 15) == 0) {
+      if (!ignore_abort && *abort_flag) return false;
+      if (global_ns() - t0 > lim) {
+        *abort_flag = 1;
+        atomicExch(P.fault, 1);
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ bool warp_wait_bar(uint64_t* bar, uint32_t parity, volatile int32_t* abort_flag,
+                                              const Params& P, bool ignore_abort = false) {
+  const bool ok = wait_bar(bar, parity, abort_flag, P, ignore_abort);
+  return __all_sync(0xffffffffu, ok) != 0;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long atom_add_acq_rel_u64(unsigned long long* p, unsigned long long v) {
+  unsigned long long old;
+  asm volatile("atom.add.acq_rel.gpu.global.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ void red_add_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Poll a monotonic counter until it reaches `target` (acquire); bounded.
+__device__ __forceinline__ bool wait_counter(const unsigned long long* c, unsigned long long target,
+                                             volatile int32_t* abort_flag, const Params& P) {
+  if (ld_acquire_u64(c) >= target) return true;
+  const unsigned long long t0 = global_ns();
+  for (uint32_t i = 1;; ++i) {
+    if (ld_acquire_u64(c) >= target) return true;
+    if ((i & 15) == 0) {
+      if (*abort_flag || grid_aborted(P)) {
+        *abort_flag = 1;
+        return false;
+      }
+      if (global_ns() - t0 > P.wait_ns) {
+        *abort_flag = 1;
+        atomicExch(P.fault, 1);
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ float max3(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ uint64_t pack2(float a, float b) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void unpack2(uint64_t v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+
+__device__ __forceinline__ uint64_t beta_word(float beta, uint32_t tag) {
+  return ((uint64_t)tag << 32) | (uint64_t)__float_as_uint(beta);
+}
+
+// Named barriers: 1 = both LSE warpgroups (256), 3 = epilogue warps (64),
+// 4 + wg = LSE warpgroup wg (128).
+__device__ __forceinline__ void bar_lse_all() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ void bar_epi() { asm volatile("bar.sync 3, 64;" ::: "memory"); }
+__device__ __forceinline__ void bar_wg(int wg) { asm volatile("bar.sync %0, 128;" ::"r"(4 + wg) : "memory"); }
+
+// Tag of the betas written by sweep `sigma` (sigma = 2 k for the f-update of iteration
+// k, 2 k + 1 for its g-update): sigma + 1. The initial betas of g carry tag 0.
+__device__ __forceinline__ uint32_t tag_of(int it, int side) { return (uint32_t)(2 * it + side + 1); }
+
+// ------------------------------------------------------------------ kernel
+template <int BN>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    sinkhorn_loop_tc(const __grid_constant__ CUtensorMap mXh_a, const __grid_constant__ CUtensorMap mXl_a,
+                     const __grid_constant__ CUtensorMap mYh_a, const __grid_constant__ CUtensorMap mYl_a,
+                     const __grid_constant__ CUtensorMap mXh_b, const __grid_constant__ CUtensorMap mXl_b,
+                     const __grid_constant__ CUtensorMap mYh_b, const __grid_constant__ CUtensorMap mYl_b,
+                     const Params P) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const Layout L = layout(BN, P.nkb, P.split3, P.stages, P.a_bufs);
+  Shared& sh = *reinterpret_cast<Shared*>(smem + L.ctrl);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = blockIdx.x, G = P.G, nkb = P.nkb, S = P.stages, NA = P.a_bufs;
+  volatile int32_t* abort_flag = &sh.abort_flag;
+  constexpr uint32_t B_TILE_BYTES = (uint32_t)BN * KB * 2;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&sh.full[s], 1);
+      mbar_init(&sh.empty[s], 1);
+    }
+    for (int s = 0; s < BETA_SLOTS; ++s) {
+      mbar_init(&sh.beta_full[s], 1);
+      mbar_init(&sh.beta_empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sh.tmem_full[b], 1);
+      mbar_init(&sh.tmem_empty[b], 4);
+      mbar_init(&sh.a_full[b], 1);
+      mbar_init(&sh.a_empty[b], 1);
+      mbar_init(&sh.seg_full[b], 128);
+      mbar_init(&sh.seg_empty[b], 64);
+    }
+    mbar_init(&sh.drain, 1);
+    mbar_init(&sh.dec_full, 1);
+    sh.abort_flag = 0;
+    // the state this chunk starts from (written by the previous launch or the initialiser)
+    {
+      const int4* src = reinterpret_cast<const int4*>(P.state);
+      int4* dst = reinterpret_cast<int4*>(&sh.st);
+      for (int q = 0; q < (int)(sizeof(SolverState) / 16); ++q) dst[q] = __ldcg(src + q);
+    }
+    sh.entry_done = sh.st.done;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem_base)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = sh.tmem_base;
+  const int it_end = sh.entry_done ? P.seq0 : P.seq0 + P.niter;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    int u = 0, ka = 0, tb = 0;  // B stage units, A segments, tiles (beta slots) issued
+    bool ok = true;
+    for (int it = P.seq0; it < it_end && ok; ++it) {
+      if (it > P.seq0) {
+        // the next f-update runs only if the stop test of iteration it - 1 let it
+        warp_wait_bar(&sh.dec_full, (uint32_t)((it - 1 - P.seq0) & 1), abort_flag, P, true);
+        if (sh.dec_stop[(it - 1) & 1] || *abort_flag) break;
+      }
+      for (int sd = 0; sd < 2 && ok; ++sd) {
+        const Side& Sd = P.side[sd];
+        const CUtensorMap* mAh = sd == 0 ? &mXh_a : &mYh_a;
+        const CUtensorMap* mAl = sd == 0 ? &mXl_a : &mYl_a;
+        const CUtensorMap* mBh = sd == 0 ? &mYh_b : &mXh_b;
+        const CUtensorMap* mBl = sd == 0 ? &mYl_b : &mXl_b;
+        const uint64_t* bsrc = Sd.beta_in[it & 1];  // f-update: g of the previous g-update; g-update: this iteration's f
+        const Split sp = make_split(Sd.R, Sd.T, G);
+        const int nseg = num_segments(sp, c);
+        for (int k = 0; k < nseg && ok; ++k, ++ka) {
+          const Seg sg = segment(sp, c, k);
+          const int ai = ka % NA;
+          ok = warp_wait_bar(&sh.a_empty[ai], (uint32_t)(((ka / NA) & 1) ^ 1), abort_flag, P);
+          if (!ok) break;
+          unsigned char* abuf = smem + L.a0 + ai * L.a_stride;
+          if (elect_one()) {
+            mbar_arrive_expect_tx(&sh.a_full[ai], L.a_stride);
+            for (int kb = 0; kb < nkb; ++kb) {
+              tma_load_2d(abuf + kb * A_TILE_BYTES, mAh, &sh.a_full[ai], kb * KB, sg.r * BM);
+              if (P.split3) tma_load_2d(abuf + L.a_lo_off + kb * A_TILE_BYTES, mAl, &sh.a_full[ai], kb * KB, sg.r * BM);
+            }
+          }
+          __syncwarp();
+          for (int t = sg.t0; t < sg.t1 && ok; ++t, ++tb) {
+            // tagged betas of the tile's columns (possibly stale: the LSE warps check the tags)
+            const int bs = tb % BETA_SLOTS;
+            ok = warp_wait_bar(&sh.beta_empty[bs], (uint32_t)(((tb / BETA_SLOTS) & 1) ^ 1), abort_flag, P);
+            if (!ok) break;
+            if (elect_one()) {
+              mbar_arrive_expect_tx(&sh.beta_full[bs], L.beta_slot);
+              bulk_load(smem + L.beta0 + bs * L.beta_slot, bsrc + (int64_t)t * BN, L.beta_slot, &sh.beta_full[bs]);
+            }
+            __syncwarp();
+            for (int kb = 0; kb < nkb; ++kb, ++u) {
+              const int s = u % S;
+              ok = warp_wait_bar(&sh.empty[s], (uint32_t)(((u / S) & 1) ^ 1), abort_flag, P);
+              if (!ok) break;
+              unsigned char* st = smem + L.stage0 + s * L.stage_bytes;
+              if (elect_one()) {
+                mbar_arrive_expect_tx(&sh.full[s], B_TILE_BYTES * (P.split3 ? 2u : 1u));
+                tma_load_2d(st, mBh, &sh.full[s], kb * KB, t * BN);
+                if (P.split3) tma_load_2d(st + L.b_lo_off, mBl, &sh.full[s], kb * KB, t * BN);
+              }
+              __syncwarp();
+            }
+          }
+        }
+      }
+    }
+    // drain this CTA's own copies still in flight before shared memory is released
+    if (!ok || *abort_flag) {
+      for (int k = max(0, ka - NA); k < ka; ++k)
+        warp_wait_bar(&sh.a_full[k % NA], (uint32_t)((k / NA) & 1), abort_flag, P, true);
+      for (int v = max(0, u - S); v < u; ++v) warp_wait_bar(&sh.full[v % S], (uint32_t)((v / S) & 1), abort_flag, P, true);
+      for (int v = max(0, tb - BETA_SLOTS); v < tb; ++v)
+        warp_wait_bar(&sh.beta_full[v % BETA_SLOTS], (uint32_t)((v / BETA_SLOTS) & 1), abort_flag, P, true);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    bool ok = true;
+    int u = 0, tl = 0, ka = 0;
+    for (int it = P.seq0; it < it_end && ok; ++it) {
+      if (it > P.seq0) {
+        warp_wait_bar(&sh.dec_full, (uint32_t)((it - 1 - P.seq0) & 1), abort_flag, P, true);
+        if (sh.dec_stop[(it - 1) & 1] || *abort_flag) break;
+      }
+      for (int sd = 0; sd < 2 && ok; ++sd) {
+        const Side& Sd = P.side[sd];
+        const Split sp = make_split(Sd.R, Sd.T, G);
+        const int nseg = num_segments(sp, c);
+        for (int k = 0; k < nseg && ok; ++k, ++ka) {
+          const Seg sg = segment(sp, c, k);
+          const int ai = ka % NA;
+          ok = warp_wait_bar(&sh.a_full[ai], (uint32_t)((ka / NA) & 1), abort_flag, P);
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t a_hi = smem_u32(smem + L.a0 + ai * L.a_stride);
+          const uint32_t a_lo = a_hi + L.a_lo_off;
+          for (int t = sg.t0; t < sg.t1 && ok; ++t, ++tl) {
+            const int b = tl & 1;
+            ok = warp_wait_bar(&sh.tmem_empty[b], (uint32_t)(((tl >> 1) & 1) ^ 1), abort_flag, P);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t d_tmem = tmem_base + (uint32_t)(b * BN);
+            for (int kb = 0; kb < nkb; ++kb, ++u) {
+              const int s = u % S;
+              ok = warp_wait_bar(&sh.full[s], (uint32_t)((u / S) & 1), abort_flag, P);
+              if (!ok) break;
+              tc_fence_after();
+              const uint32_t st = smem_u32(smem + L.stage0 + s * L.stage_bytes);
+              const uint64_t bh = desc_sw128(st), bl = desc_sw128(st + L.b_lo_off);
+              const uint64_t ah = desc_sw128(a_hi + kb * A_TILE_BYTES), al = desc_sw128(a_lo + kb * A_TILE_BYTES);
+              if (elect_one()) {
+#pragma unroll
+                for (int kk = 0; kk < KB / 16; ++kk) {
+                  // +32 bytes per K = 16 step inside the 128-byte swizzle atom (encoded >> 4)
+                  const uint64_t adv = (uint64_t)(kk * 2);
+                  umma<BN>(d_tmem, ah + adv, bh + adv, (kb > 0 || kk > 0) ? 1u : 0u);
+                  if (P.split3) {
+                    umma<BN>(d_tmem, ah + adv, bl + adv, 1u);
+                    umma<BN>(d_tmem, al + adv, bh + adv, 1u);
+                  }
+                }
+                umma_commit(&sh.empty[s]);
+              }
+              __syncwarp();
+            }
+            if (!ok) break;
+            if (elect_one()) umma_commit(&sh.tmem_full[b]);
+            __syncwarp();
+          }
+          if (!ok) break;
+          if (elect_one()) umma_commit(&sh.a_empty[ai]);
+          __syncwarp();
+        }
+      }
+    }
+    if (elect_one()) umma_commit(&sh.drain);
+    __syncwarp();
+    warp_wait_bar(&sh.drain, 0, abort_flag, P, true);
+  } else if (threadIdx.x < EPI_TID0) {
+    // ------------------------------------------------------------ LSE warps
+    const int wg = (warp - 2) >> 2;
+    const int quarter = warp & 3;
+    const int row_local = quarter * 32 + lane;
+    float* fbuf = reinterpret_cast<float*>(smem + L.fbuf0) + wg * 2 * BN;
+    constexpr int EPL = BN / 128;  // beta words per lane and warp (a quarter of the tile each)
+    int tl = 0, jt = 0, kseg = 0;
+    bool dead = false;
+    for (int it = P.seq0; it < it_end; ++it) {
+      if (it > P.seq0) {
+        // every LSE warp reads the same decision after the same wait (the decider always
+        // arrives), so all of them leave at the same iteration
+        wait_bar(&sh.dec_full, (uint32_t)((it - 1 - P.seq0) & 1), abort_flag, P, true);
+        __syncwarp();
+        if (sh.dec_stop[(it - 1) & 1]) break;
+      }
+      for (int sd = 0; sd < 2; ++sd) {
+        const Side& Sd = P.side[sd];
+        const uint64_t* bsrc = Sd.beta_in[it & 1];
+        const uint32_t want = sd == 0 ? (uint32_t)(2 * it) : (uint32_t)(2 * it + 1);
+        const Split sp = make_split(Sd.R, Sd.T, G);
+        const int nseg = num_segments(sp, c);
+        for (int k = 0; k < nseg; ++k, ++kseg) {
+          const Seg sg = segment(sp, c, k);
+          float m_run = -INFINITY, s_run = 0.f;
+          for (int t = sg.t0; t < sg.t1; ++t, ++tl) {
+            if ((tl & 1) != wg) continue;
+            const uint32_t ph = (uint32_t)(jt & 1);
+            float* fb = fbuf + (jt & 1) * BN;
+            ++jt;
+            // ---- betas of the tile: check the tags of this warp's quarter, reload stale words
+            const int bs = tl % BETA_SLOTS;
+            if (!dead && !warp_wait_bar(&sh.beta_full[bs], (uint32_t)((tl / BETA_SLOTS) & 1), abort_flag, P))
+              dead = true;
+            if (!dead) {
+              const uint64_t* slot = reinterpret_cast<const uint64_t*>(smem + L.beta0 + bs * L.beta_slot);
+              const int e0 = quarter * (BN / 4) + lane * EPL;
+              const int64_t col0 = (int64_t)t * BN + e0;
+              uint64_t w[EPL];
+              bool stale = false;
+#pragma unroll
+              for (int e = 0; e < EPL; ++e) {
+                w[e] = slot[e0 + e];
+                stale |= (col0 + e < Sd.nB) && (uint32_t)(w[e] >> 32) != want;
+              }
+              if (__any_sync(0xffffffffu, stale)) {
+                const unsigned long long t0 = global_ns();
+                for (uint32_t i = 1;; ++i) {
+                  stale = false;
+#pragma unroll
+                  for (int e = 0; e < EPL; ++e) {
+                    if (col0 + e < Sd.nB && (uint32_t)(w[e] >> 32) != want) {
+                      w[e] = ld_relaxed_u64(bsrc + col0 + e);
+                      stale |= (uint32_t)(w[e] >> 32) != want;
+                    }
+                  }
+                  if (!__any_sync(0xffffffffu, stale)) break;
+                  if ((i & 15) == 0) {
+                    int bad = 0;
+                    if (*abort_flag || grid_aborted(P)) bad = 1;
+                    if (global_ns() - t0 > P.wait_ns) bad = 2;
+                    bad = __shfl_sync(0xffffffffu, bad, 0);
+                    if (bad) {
+                      if (lane == 0) {
+                        *abort_flag = 1;
+                        if (bad == 2) atomicExch(P.fault, 1);
+                      }
+                      dead = true;
+                      break;
+                    }
+                  }
+                }
+              }
+#pragma unroll
+              for (int e = 0; e < EPL; ++e)
+                fb[e0 + e] = (col0 + e < Sd.nB) ? __uint_as_float((uint32_t)w[e]) : -INFINITY;
+            }
+            bar_wg(wg);  // the whole tile's float betas are in fb
+            if (quarter == 0 && lane == 0 && !dead) mbar_arrive(&sh.beta_empty[bs]);
+            if (dead) continue;
+            int okv = 0;
+            if (lane == 0) okv = wait_bar(&sh.tmem_full[wg], ph, abort_flag, P) ? 1 : 0;
+            if (__shfl_sync(0xffffffffu, okv, 0) == 0) {
+              dead = true;
+              continue;
+            }
+            __syncwarp();
+            tc_fence_after();
+            const uint32_t taddr0 = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(wg * BN);
+#pragma unroll 1
+            for (int half = 0; half < BN / 128; ++half) {
+              const uint32_t taddr = taddr0 + (uint32_t)(half * 128);
+              float v[4][32];
+              PROGOT_TMEM_LD32(taddr + 0, v[0]);
+              PROGOT_TMEM_LD32(taddr + 32, v[1]);
+              PROGOT_TMEM_LD32(taddr + 64, v[2]);
+              PROGOT_TMEM_LD32(taddr + 96, v[3]);
+              tmem_wait_ld();
+              if (half == BN / 128 - 1) {
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sh.tmem_empty[wg]);
+              }
+              // t_ij = c (a_i . b_j) + beta_j
+              const float* fbh = fb + half * 128;
+#pragma unroll
+              for (int cc = 0; cc < 4; ++cc)
+#pragma unroll
+                for (int i = 0; i < 32; i += 4) {
+                  const float4 b4 = *reinterpret_cast<const float4*>(fbh + cc * 32 + i);
+                  float a0, a1, a2, a3;
+                  unpack2(add2(pack2(v[cc][i], v[cc][i + 1]), pack2(b4.x, b4.y)), a0, a1);
+                  unpack2(add2(pack2(v[cc][i + 2], v[cc][i + 3]), pack2(b4.z, b4.w)), a2, a3);
+                  v[cc][i] = a0;
+                  v[cc][i + 1] = a1;
+                  v[cc][i + 2] = a2;
+                  v[cc][i + 3] = a3;
+                }
+              float mx[8];
+#pragma unroll
+              for (int q = 0; q < 8; ++q) mx[q] = v[q >> 1][(q & 1) * 16];
+#pragma unroll
+              for (int cc = 0; cc < 4; ++cc)
+#pragma unroll
+                for (int i = 1; i < 16; i += 2) {
+                  mx[cc * 2] = max3(mx[cc * 2], v[cc][i], v[cc][i + 1 < 16 ? i + 1 : i]);
+                  mx[cc * 2 + 1] = max3(mx[cc * 2 + 1], v[cc][16 + i], v[cc][16 + (i + 1 < 16 ? i + 1 : i)]);
+                }
+              const float tmax = max3(max3(mx[0], mx[1], mx[2]), max3(mx[3], mx[4], mx[5]), fmaxf(mx[6], mx[7]));
+              const float mnew = fmaxf(m_run, tmax);
+              if (mnew != -INFINITY) {
+                const uint64_t negm = pack2(-mnew, -mnew);
+                uint64_t acc[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[q] = 0ull;
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc)
+#pragma unroll
+                  for (int i = 0; i < 32; i += 2) {
+                    float a0, a1;
+                    unpack2(add2(pack2(v[cc][i], v[cc][i + 1]), negm), a0, a1);
+                    acc[(i >> 1) & 3] = add2(acc[(i >> 1) & 3], pack2(fast_exp2(a0), fast_exp2(a1)));
+                  }
+                float s0, s1, s2, s3, s4, s5, s6, s7;
+                unpack2(acc[0], s0, s1);
+                unpack2(acc[1], s2, s3);
+                unpack2(acc[2], s4, s5);
+                unpack2(acc[3], s6, s7);
+                s_run = s_run * fast_exp2(m_run - mnew) + (((s0 + s1) + (s2 + s3)) + ((s4 + s5) + (s6 + s7)));
+                m_run = mnew;
+              }
+            }
+          }
+          if (dead) {
+            m_run = NAN;
+            s_run = NAN;
+          }
+          // merge warpgroup 1 into warpgroup 0, then hand the segment to the epilogue warps
+          if (wg == 1) sh.ms[kseg & 1][row_local] = make_float2(m_run, s_run);
+          bar_lse_all();
+          if (wg == 1) continue;
+          {
+            const float2 o = sh.ms[kseg & 1][row_local];
+            const float2 mrg = lse_combine(make_float2(m_run, s_run), o);
+            const bool bad = isnan(o.y) || isnan(s_run);
+            m_run = bad ? NAN : mrg.x;
+            s_run = bad ? NAN : mrg.y;
+          }
+          const int sl = kseg & 1;
+          wait_bar(&sh.seg_empty[sl], (uint32_t)(((kseg >> 1) & 1) ^ 1), abort_flag, P);
+          sh.seg[sl][row_local] = make_float2(m_run, s_run);
+          mbar_arrive(&sh.seg_full[sl]);
+        }
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue warps and stop decision
+    const int etid = threadIdx.x - EPI_TID0;  // 0..63
+    int kseg = 0;
+    for (int it = P.seq0; it < it_end; ++it) {
+      for (int sd = 0; sd < 2; ++sd) {
+        const Side& Sd = P.side[sd];
+        const SweepParams& p = Sd.p;
+        const Split sp = make_split(Sd.R, Sd.T, G);
+        const int nseg = num_segments(sp, c);
+        const bool skip = sd == 1 && sh.st.done != 0;  // the stop test ended the loop: g stays
+        const int fcur = sh.st.fcur;
+        const float* pot_cur = (sd == 0) ? (fcur == 0 ? Sd.out0 : Sd.out1) : nullptr;
+        float* out = (sd == 0) ? (fcur == 0 ? Sd.out1 : Sd.out0) : Sd.out0;
+        uint64_t* bout = Sd.beta_out[sd == 0 ? (it & 1) : ((it + 1) & 1)];
+        const uint32_t tag = tag_of(it, sd);
+        for (int k = 0; k < nseg; ++k, ++kseg) {
+          const Seg sg = segment(sp, c, k);
+          const int sl = kseg & 1;
+          const bool okw = wait_bar(&sh.seg_full[sl], (uint32_t)((kseg >> 1) & 1), abort_flag, P);
+          float2 mv[2];
+          mv[0] = okw ? sh.seg[sl][etid] : make_float2(NAN, NAN);
+          mv[1] = okw ? sh.seg[sl][etid + 64] : make_float2(NAN, NAN);
+          mbar_arrive(&sh.seg_empty[sl]);
+          RowIn rin[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int rl = etid + 64 * h;
+            const int64_t i = (int64_t)sg.r * BM + rl;
+            rin[h].an = 0.f;
+            rin[h].pot = 0.f;
+            rin[h].w = 0.f;
+            if (i < Sd.nA) {
+              Sd.partial[((int64_t)c * P.maxseg + k) * BM + rl] = mv[h];
+              rin[h] = row_inputs(p, i, pot_cur);
+            }
+          }
+          int c_first, c_last;
+          contributors(sp, sg.r, &c_first, &c_last);
+          const unsigned long long nc = (unsigned long long)(c_last - c_first + 1);
+          bar_epi();  // all rows' partial stores happen before the arrival
+          if (etid == 0) {
+            const unsigned long long prev = atom_add_acq_rel_u64(&Sd.cnt[sg.r], 1ull);
+            sh.e_last = (prev + 1 == (unsigned long long)(it + 1) * nc);
+          }
+          bar_epi();
+          if (sh.e_last) {
+            float e[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              e[h] = 0.f;
+              const int rl = etid + 64 * h;
+              const int64_t i = (int64_t)sg.r * BM + rl;
+              if (i < Sd.nA) {
+                constexpr int kMaxC = 8;
+                const int ncc = c_last - c_first + 1;
+                float2 pv[kMaxC];
+#pragma unroll
+                for (int q = 0; q < kMaxC; ++q)
+                  if (q < ncc) {
+                    const int cc = c_first + q;
+                    pv[q] = __ldcg(&Sd.partial[((int64_t)cc * P.maxseg + seg_of(sp, sg.r, cc)) * BM + rl]);
+                  }
+                float2 acc = make_float2(-INFINITY, 0.f);
+#pragma unroll
+                for (int q = 0; q < kMaxC; ++q)
+                  if (q < ncc) acc = lse_combine(acc, pv[q]);
+                for (int cc = c_first + kMaxC; cc <= c_last; ++cc)
+                  acc = lse_combine(acc, __ldcg(&Sd.partial[((int64_t)cc * P.maxseg + seg_of(sp, sg.r, cc)) * BM + rl]));
+                const float Lr = acc.x + __log2f(acc.y);
+                if (!skip) {
+                  float val;
+                  e[h] = row_epilogue(p, i, Lr, rin[h], out, &val);
+                  st_relaxed_u64(bout + i, beta_word((val - rin[h].an) * p.bscale, tag));
+                }
+              }
+            }
+            if (sd == 0) {
+              // row-block sum of the error terms in a fixed order
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                float v = e[h];
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+                if ((etid & 31) == 0) sh.ered[(etid + 64 * h) >> 5] = v;
+              }
+            }
+            bar_epi();
+            if (etid == 0) {
+              if (sd == 0) P.errpart[(int64_t)(it & 1) * Sd.R + sg.r] = (double)((sh.ered[0] + sh.ered[1]) + (sh.ered[2] + sh.ered[3]));
+              asm volatile("fence.proxy.async.global;" ::: "memory");  // the betas are read by bulk copies
+              red_add_release_u64(Sd.done, 1ull);
+            }
+          }
+          bar_epi();
+        }
+        if (sd == 0) {
+          // ---- stop test of iteration it (decider: warp 10), once every row block of the f-update is done
+          if (etid < 32) {
+            bool okc = true;
+            if (etid == 0) {
+              okc = wait_counter(P.side[1].done, (unsigned long long)it * (unsigned long long)P.side[1].R, abort_flag, P) &&
+                    wait_counter(P.side[0].done, (unsigned long long)(it + 1) * (unsigned long long)P.side[0].R,
+                                 abort_flag, P);
+              __threadfence();
+            }
+            okc = __shfl_sync(0xffffffffu, okc ? 1 : 0, 0) != 0;
+            __syncwarp();  // the other lanes' loads below follow lane 0's acquire
+            const double err = okc ? sum_errpart_warp(P.errpart + (int64_t)(it & 1) * P.side[0].R, P.side[0].R) : (double)NAN;
+            if (etid == 0) {
+              SolverState st = sh.st;
+              if (okc) {
+                f_update_transition(st, err, P.side[0].p);
+              } else {
+                st.done = 1;
+                st.status = kNumeric;  // replaced by PROGOT_ERR_TIMEOUT on the host (fault word)
+              }
+              sh.st = st;
+              sh.dec_stop[it & 1] = st.done;
+              if (c == 0) *P.state = st;
+              mbar_arrive(&sh.dec_full);
+            }
+          }
+          bar_epi();  // both epilogue warps see the decision
+        }
+      }
+      if (sh.st.done) break;
+    }
+  }
+
+  // ---------------------------------------------------------------- teardown
+  tc_fence_before();
+  __syncthreads();
+  if (sh.abort_flag != 0 && threadIdx.x == 0) atomicExch(P.fault, 1);
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// Initial tagged betas of one side from its potential: tag 0, beta = (pot - |b|^2) log2(e)/eps.
+__global__ void beta_init_kernel(const float* __restrict__ pot, const float* __restrict__ nrm, int64_t n, float bscale,
+                                 uint64_t* __restrict__ out) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  out[j] = beta_word((pot[j] - nrm[j]) * bscale, 0u);
+}
+
+}  // namespace loop
+}  // namespace tc
+
+// ---------------------------------------------------------------- host side
+// Pipeline shape of the persistent loop: two resident A buffers and as many B stages
+// (2..8) as fit in 227 KB; 0 stages when no shape fits (the per-sweep kernel serves it).
+static void loop_shape(int bn, int nkb, int split3, int* stages, int* a_bufs) {
+  *stages = 0;
+  *a_bufs = 2;
+  for (int na = 2; na >= 1; --na) {
+    int best = 0;
+    for (int s = 2; s <= 8; ++s)
+      if (tc::loop::layout(bn, nkb, split3, s, na).total <= 227 * 1024) best = s;
+    if (best >= 2) {
+      *stages = best;
+      *a_bufs = na;
+      return;
+    }
+  }
+}
+
+bool loop_tc_supported(int bn, int nkb, int split3) {
+  int s, na;
+  loop_shape(bn, nkb, split3, &s, &na);
+  return s >= 2 && (bn == 128 || bn == 256);
+}
+
+void loop_tc_plan(int64_t n, int64_t m, int bn, int sms, int* G, int* maxseg) {
+  const int64_t Rx = (n + tc::BM - 1) / tc::BM, Ry = (m + tc::BM - 1) / tc::BM;
+  const int64_t Tx = (n + bn - 1) / bn, Ty = (m + bn - 1) / bn;
+  const int g = (int)std::min<int64_t>(std::min<int64_t>(Rx * Ty, Ry * Tx), sms);
+  int ms = 1;
+  const tc::Split s0 = tc::make_split((int)Rx, (int)Ty, g), s1 = tc::make_split((int)Ry, (int)Tx, g);
+  for (int c = 0; c < g; ++c) ms = std::max(ms, std::max(tc::num_segments(s0, c), tc::num_segments(s1, c)));
+  *G = g;
+  *maxseg = ms;
+}
+
+size_t loop_tc_smem(int bn, int nkb, int split3) {
+  int s, na;
+  loop_shape(bn, nkb, split3, &s, &na);
+  return tc::loop::layout(bn, nkb, split3, s, na).total;
+}
+
+cudaError_t launch_beta_init(const float* pot, const float* nrm, int64_t n, float bscale, void* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  tc::loop::beta_init_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pot, nrm, n, bscale, (uint64_t*)out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <int BN>
+static cudaError_t launch_loop(const tc::loop::Params& P, size_t smem, const void* const* maps, cudaStream_t stream) {
+  static thread_local size_t attr_bytes = 0;
+  if (smem > attr_bytes) {
+    cudaError_t e =
+        cudaFuncSetAttribute(tc::loop::sinkhorn_loop_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_bytes = smem;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(P.G);
+  cfg.blockDim = dim3(tc::loop::NTHREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;  // CTAs wait on one another: all must be resident
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const CUtensorMap* m[8];
+  for (int q = 0; q < 8; ++q) m[q] = reinterpret_cast<const CUtensorMap*>(maps[q]);
+  return cudaLaunchKernelEx(&cfg, tc::loop::sinkhorn_loop_tc<BN>, *m[0], *m[1], *m[2], *m[3], *m[4], *m[5], *m[6],
+                            *m[7], P);
+}
+
+cudaError_t launch_sinkhorn_loop_tc(const LoopLaunch& Lq, cudaStream_t stream) {
+  int stages, a_bufs;
+  loop_shape(Lq.bn, Lq.nkb, Lq.split3, &stages, &a_bufs);
+  if (stages < 2 || (Lq.bn != 128 && Lq.bn != 256)) return cudaErrorInvalidValue;
+  tc::loop::Params P;
+  memset(&P, 0, sizeof(P));
+  for (int sd = 0; sd < 2; ++sd) {
+    const LoopSideLaunch& s = Lq.side[sd];
+    tc::loop::Side& d = P.side[sd];
+    d.p = s.p;
+    d.out0 = s.out0;
+    d.out1 = s.out1;
+    d.beta_out[0] = (uint64_t*)s.beta_out[0];
+    d.beta_out[1] = (uint64_t*)s.beta_out[1];
+    d.beta_in[0] = (const uint64_t*)s.beta_in[0];
+    d.beta_in[1] = (const uint64_t*)s.beta_in[1];
+    d.cnt = s.cnt;
+    d.done = s.done;
+    d.partial = s.partial;
+    d.nA = s.p.nA;
+    d.nB = s.p.nB;
+    d.R = (int)((s.p.nA + tc::BM - 1) / tc::BM);
+    d.T = (int)((s.p.nB + Lq.bn - 1) / Lq.bn);
+  }
+  P.errpart = Lq.errpart;
+  P.state = Lq.state;
+  P.fault = Lq.fault;
+  P.wait_ns = Lq.wait_ns;
+  P.nkb = Lq.nkb;
+  P.split3 = Lq.split3;
+  P.stages = stages;
+  P.a_bufs = a_bufs;
+  P.G = Lq.G;
+  P.maxseg = Lq.maxseg;
+  P.seq0 = Lq.seq0;
+  P.niter = Lq.niter;
+  const size_t smem = tc::loop::layout(Lq.bn, Lq.nkb, Lq.split3, stages, a_bufs).total;
+  cudaError_t e = Lq.bn == 256 ? launch_loop<256>(P, smem, Lq.maps, stream) : launch_loop<128>(P, smem, Lq.maps, stream);
+  count_launch();
+  return e;
+}
+
+}  // namespace progot

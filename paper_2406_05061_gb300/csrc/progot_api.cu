@@ -180,6 +180,14 @@ struct Workspace {
   float* xnc;       // nmax: |x_i - mu|^2
   float* ync;       // nmax: |y_j - mu|^2
   int32_t* fault;   // set by a tensor-core CTA whose bounded wait expired
+  // persistent tensor-core Sinkhorn loop
+  uint64_t* lbeta;  // tagged betas: x side [2][nbeta], then y side [2][nbeta]
+  int64_t nbeta;    // words per buffer (nmax rounded up to 256)
+  unsigned long long* lcnt;  // arrivals: x row blocks [rbmax], y row blocks [rbmax], done_x, done_y
+  float2* lpart;    // (max, sum) slots: f-update bank, then g-update bank (lslots each)
+  int64_t lslots;
+  int64_t lrb;      // rbmax of the carve (row-block capacity of lcnt and lerr)
+  double* lerr;     // [2][rbmax] error partials by iteration parity
   size_t bytes;
 };
 
@@ -259,6 +267,15 @@ static size_t ws_layout(const WsDims& w, Workspace* out, char* base) {
   ws.xnc = (float*)take(w.tc ? sizeof(float) * w.nmax : 0);
   ws.ync = (float*)take(w.tc ? sizeof(float) * w.nmax : 0);
   ws.fault = (int32_t*)take(sizeof(int32_t));
+  ws.nbeta = w.tc ? cdiv(w.nmax, 256) * 256 : 0;
+  ws.lbeta = (uint64_t*)take(sizeof(uint64_t) * 4 * (size_t)ws.nbeta);
+  ws.lcnt = (unsigned long long*)take(w.tc ? sizeof(unsigned long long) * (2 * (size_t)w.rbmax + 2) : 0);
+  // G * maxseg <= R + 2 G slots of 128 rows per bank (each CTA's segments: its whole row
+  // blocks, plus at most two partial ones of the contiguous remainder)
+  ws.lslots = w.tc ? w.rbmax + 3 * (int64_t)num_sms() : 0;
+  ws.lpart = (float2*)take(sizeof(float2) * 2 * (size_t)ws.lslots * 128);
+  ws.lrb = w.rbmax;
+  ws.lerr = (double*)take(w.tc ? sizeof(double) * 2 * (size_t)w.rbmax : 0);
   ws.bytes = off;
   if (out) *out = ws;
   return off;
@@ -296,6 +313,14 @@ static thread_local HostMirror t_host;
 
 // Tensor-core map step for d <= 64 on the tensor-core path (progot_set_map_tc).
 static std::atomic<int> g_map_tc{1};
+// Persistent tensor-core Sinkhorn loop (progot_set_loop_tc) and the bounded-wait limit of
+// the tensor-core kernels (progot_set_wait_limit_ns).
+static std::atomic<int> g_loop_tc{1};
+constexpr unsigned long long kDefaultWaitNs = 2000000000ull;
+static std::atomic<unsigned long long> g_wait_ns{kDefaultWaitNs};
+// Test hook (progot_test_withhold_initial_betas): the persistent loop starts without the
+// initial betas of g, so its first tiles wait on words that no sweep writes.
+static std::atomic<int> g_withhold_betas{0};
 
 static int check_common(const float* x, int64_t n, const float* y, int64_t m, int32_t d, int32_t precision) {
   if (x == nullptr || y == nullptr) return fail(PROGOT_ERR_INVALID_ARG, "x and y must not be NULL");
@@ -496,6 +521,113 @@ static int lse_sweep(const SweepParams& p, int32_t precision, cudaStream_t s, co
   return PROGOT_OK;
 }
 
+// Sinkhorn loop (Alg. 1) as one persistent tensor-core launch (loop_tc.cu): f and g
+// betas flow between sweeps as tagged words, the stop test runs inside the kernel. pf and
+// pg are the f- and g-update descriptions built by sinkhorn_core; ops describes the
+// prepared operands. On return the current f is in f_a, g in g, and the y-side bias
+// rows (ws.yb) hold g for a map step at the same eps.
+static int sinkhorn_loop_persistent(SweepParams pf, SweepParams pg, int64_t n, int64_t m, int32_t max_iter,
+                                    double tau, float* f_a, float* f_b, float* g, const Workspace& ws,
+                                    const TcOps& ops, int32_t* iters_out, double* err_out, cudaStream_t s) {
+  pf.An = ops.xnc;
+  pf.Bn = ops.ync;
+  pg.An = ops.ync;
+  pg.Bn = ops.xnc;
+  const int64_t nb = ws.nbeta, rb = ws.lrb;
+  uint64_t* bx[2] = {ws.lbeta, ws.lbeta + nb};
+  uint64_t* by[2] = {ws.lbeta + 2 * nb, ws.lbeta + 3 * nb};
+  CK(cudaMemsetAsync(ws.lbeta, 0xFF, sizeof(uint64_t) * 4 * (size_t)nb, s));  // tags no sweep expects
+  if (!g_withhold_betas.load()) CK(launch_beta_init(g, ops.ync, m, pf.bscale, by[0], s));
+  CK(cudaMemsetAsync(ws.lcnt, 0, sizeof(unsigned long long) * (2 * (size_t)rb + 2), s));
+  CK(launch_init_state(ws.state, s));
+  LoopLaunch L;
+  memset(&L, 0, sizeof(L));
+  LoopSideLaunch& F = L.side[0];
+  LoopSideLaunch& Gs = L.side[1];
+  F.p = pf;
+  F.out0 = f_a;
+  F.out1 = f_b;
+  F.beta_out[0] = bx[0];
+  F.beta_out[1] = bx[1];
+  F.beta_in[0] = by[0];
+  F.beta_in[1] = by[1];
+  F.cnt = ws.lcnt;
+  F.done = ws.lcnt + 2 * rb;
+  F.partial = ws.lpart;
+  Gs.p = pg;
+  Gs.out0 = g;
+  Gs.out1 = nullptr;
+  Gs.beta_out[0] = by[0];
+  Gs.beta_out[1] = by[1];
+  Gs.beta_in[0] = bx[0];
+  Gs.beta_in[1] = bx[1];
+  Gs.cnt = ws.lcnt + rb;
+  Gs.done = ws.lcnt + 2 * rb + 1;
+  Gs.partial = ws.lpart + ws.lslots * 128;
+  const CUtensorMap* maps[8] = {&ops.xh_a, &ops.xl_a, &ops.yh_a, &ops.yl_a, &ops.xh_b, &ops.xl_b, &ops.yh_b, &ops.yl_b};
+  for (int q = 0; q < 8; ++q) L.maps[q] = maps[q];
+  L.errpart = ws.lerr;
+  L.state = ws.state;
+  L.fault = ws.fault;
+  L.wait_ns = g_wait_ns.load();
+  L.nkb = ops.nkb;
+  L.split3 = ops.split3;
+  L.bn = ops.bn;
+  loop_tc_plan(n, m, ops.bn, num_sms(), &L.G, &L.maxseg);
+  if ((int64_t)L.G * L.maxseg > ws.lslots)
+    return fail(PROGOT_ERR_WORKSPACE, "persistent loop needs %lld partial slots, the workspace has %lld",
+                (long long)L.G * L.maxseg, (long long)ws.lslots);
+  L.seq0 = 0;
+  // max_iter + 1 f-updates always reach the stop test's max_iter branch; the tags of
+  // sweep k are 2 k + 1 and 2 k + 2, so iterations stay below 2^30
+  L.niter = (int)std::min<int64_t>((int64_t)max_iter + 1, (int64_t)1 << 30);
+  ProfRec pr;
+  if (t_prof.on) {
+    pr.a = t_prof.get();
+    pr.b = t_prof.get();
+    pr.kind = kProfLse;
+    pr.seq = t_prof.seq[kProfLse];
+    CK(cudaEventRecord(pr.a, s));
+  }
+  CK(launch_sinkhorn_loop_tc(L, s));
+  if (t_prof.on) CK(cudaEventRecord(pr.b, s));
+  int rc = t_host.init();
+  if (rc) return rc;
+  int32_t fault = 0;
+  CK(cudaMemcpyAsync(&t_host.hs[0], ws.state, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&fault, ws.fault, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const SolverState fin = t_host.hs[0];
+  if (fault) return fail(PROGOT_ERR_TIMEOUT, "the persistent Sinkhorn loop hit its bounded wait and aborted");
+  // every iteration up to the stop ran both sweeps (the last g-update without writes)
+  const int64_t sweeps = 2 * ((int64_t)fin.it + 1);
+  if (t_prof.on) {
+    pr.nl = sweeps;
+    pr.pairs = (double)sweeps * (double)n * (double)m;
+    pr.counted = true;
+    t_prof.recs.push_back(pr);
+    t_prof.seq[kProfLse] += sweeps;
+    t_prof.worked[kProfLse] += sweeps;
+  }
+  if (fin.fcur == 1) CK(cudaMemcpyAsync(f_a, f_b, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+  // the map step that may follow reads g through the y-side bias rows
+  CK(launch_bias_prep(g, ops.ync, m, cdiv(m, 256) * 256, pf.bscale, ws.yb, s));
+  if (iters_out) *iters_out = fin.it;
+  if (err_out) *err_out = fin.err;
+  switch (fin.status) {
+    case kConverged:
+      return PROGOT_OK;
+    case kNumeric:
+      return fail(PROGOT_ERR_NUMERIC, "non-finite marginal error after %d iterations", fin.it);
+    case kStalled:
+      return fail(PROGOT_ERR_NOT_CONVERGED, "marginal error %.3e stalled above tau %.3e after %d iterations", fin.err,
+                  tau, fin.it);
+    default:
+      return fail(PROGOT_ERR_NOT_CONVERGED, "marginal error %.3e above tau %.3e after %d iterations", fin.err, tau,
+                  fin.it);
+  }
+}
+
 // Sinkhorn loop (Alg. 1) on device-resident state. f lives in {f_a, f_b} (ping-pong);
 // on return the current f is copied into f_a. Norms xn, yn must be ready.
 // ops_out (optional) receives the tensor-core operand descriptions, valid for a map
@@ -550,6 +682,10 @@ static int sinkhorn_core(const float* x, const float* a, int64_t n, const float*
   // sweep-level arrival and finish
   const bool lag = ops.on && !symmetric;
   pf.lag = pg.lag = lag ? 1 : 0;
+  if (lag && g_loop_tc.load() && loop_tc_supported(ops.bn, ops.nkb, ops.split3)) {
+    pf.lag = pg.lag = 0;
+    return sinkhorn_loop_persistent(pf, pg, n, m, max_iter, tau, f_a, f_b, g, ws, ops, iters_out, err_out, s);
+  }
 
   int64_t sym_sweeps = 0;
   int64_t launched = 0;  // iterations enqueued so far
@@ -921,6 +1057,21 @@ size_t progot_workspace_size(int64_t n, int64_t m, int32_t d, int32_t precision)
 
 int progot_set_map_tc(int32_t on) {
   g_map_tc.store(on ? 1 : 0);
+  return PROGOT_OK;
+}
+
+int progot_set_loop_tc(int32_t on) {
+  g_loop_tc.store(on ? 1 : 0);
+  return PROGOT_OK;
+}
+
+int progot_set_wait_limit_ns(uint64_t ns) {
+  g_wait_ns.store(ns == 0 ? kDefaultWaitNs : (unsigned long long)ns);
+  return PROGOT_OK;
+}
+
+int progot_test_withhold_initial_betas(int32_t on) {
+  g_withhold_betas.store(on ? 1 : 0);
   return PROGOT_OK;
 }
 

@@ -55,6 +55,9 @@ SIGNATURES = [
      [_P, _I64, _P, _P, _I64, _P, _I64, _I32, _I32, _P, _P, _I32, _D, _D, _I32, _I32, _P, _P, _P, _P, _SZ, _P]),
     ("progot_set_stall_window", ctypes.c_int, [_I32]),
     ("progot_set_map_tc", ctypes.c_int, [_I32]),
+    ("progot_set_loop_tc", ctypes.c_int, [_I32]),
+    ("progot_set_wait_limit_ns", ctypes.c_int, [ctypes.c_uint64]),
+    ("progot_test_withhold_initial_betas", ctypes.c_int, [_I32]),
     ("progot_launch_count", ctypes.c_int64, [_I32]),
     ("progot_batched_workspace_size", _SZ, [_P, _I32, _I32, _I32]),
     ("progot_solve_batched", ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _P, _SZ, _P]),
@@ -523,6 +526,23 @@ def set_map_tc(on: bool) -> None:
     """Map step of the tensor-core paths (d <= 64) on tcgen05 (True, default) or with a
     float32 CUDA-core P Y (False)."""
     _check(lib().progot_set_map_tc(1 if on else 0), allow_not_converged=False)
+
+
+def set_loop_tc(on: bool) -> None:
+    """Sinkhorn loops of the tensor-core paths as one persistent launch (True, default)
+    or one launch per update (False)."""
+    _check(lib().progot_set_loop_tc(1 if on else 0), allow_not_converged=False)
+
+
+def set_wait_limit_ns(ns: int) -> None:
+    """Bounded-wait limit of the persistent Sinkhorn loop in ns (0: the 2 s default)."""
+    _check(lib().progot_set_wait_limit_ns(int(ns)), allow_not_converged=False)
+
+
+def test_withhold_initial_betas(on: bool) -> None:
+    """Test hook: persistent Sinkhorn loops start without g's initial betas, so their
+    bounded wait expires (PROGOT_ERR_TIMEOUT)."""
+    _check(lib().progot_test_withhold_initial_betas(1 if on else 0), allow_not_converged=False)
 
 
 def set_stall_window(iters: int) -> None:
