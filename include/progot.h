@@ -425,9 +425,9 @@ int progot_set_map_tc(int32_t on);
 /*
  * progot_set_loop_tc - choose how the tensor-core paths run a Sinkhorn loop (Alg. 1):
  * 1 (default) as one persistent cooperative launch that runs every f- and g-update and
- * the stop test on the device (the betas of each update's potential pass between the
- * GPU's CTAs as tagged words, so a tile of the next update waits only for the row
- * blocks it reads); 0 as one launch per update (the host enqueues chunks of
+ * the stop test on the device (each update's bias rows pass between the GPU's CTAs
+ * behind per-row-block ready flags, so a tile of the next update waits only for the
+ * row blocks it reads); 0 as one launch per update (the host enqueues chunks of
  * iterations). Both compute the same iteration of Alg. 1 and stop at the same test.
  * Shapes the persistent kernel cannot hold in shared memory use the per-update kernel.
  * Process-wide setting.
@@ -441,18 +441,18 @@ int progot_set_loop_tc(int32_t on);
  * it makes the launch abort: every CTA stops issuing work, retires the copies and
  * products it has in flight (those drains keep the 2 s limit), frees its tensor memory
  * and returns, and the entry point returns PROGOT_ERR_TIMEOUT; the CUDA context stays
- * usable. A very small limit makes ordinary waits expire, which is how the timeout
- * path is exercised. Process-wide setting.
+ * usable. Process-wide setting.
  */
 int progot_set_wait_limit_ns(uint64_t ns);
 
 /*
  * progot_test_withhold_initial_betas - test hook for the timeout path: with on = 1 the
- * persistent Sinkhorn loops that start afterwards skip writing the initial betas of g
- * (the words their first f-update reads), so those tiles wait for words that no sweep
- * writes until the bounded wait (progot_set_wait_limit_ns) expires and the entry point
- * returns PROGOT_ERR_TIMEOUT. Nothing faults or hangs; the context stays usable. 0
- * (default) restores normal operation. Process-wide setting.
+ * persistent Sinkhorn loops that start afterwards never publish the initial g's betas
+ * (their row blocks' ready flags stay at "nothing published"), so the first f-update
+ * waits for words that no sweep provides until the bounded wait
+ * (progot_set_wait_limit_ns) expires and the entry point returns PROGOT_ERR_TIMEOUT.
+ * Nothing faults or hangs; the context stays usable. 0 (default) restores normal
+ * operation. Process-wide setting.
  */
 int progot_test_withhold_initial_betas(int32_t on);
 

@@ -1,25 +1,23 @@
-// Persistent tensor-core Sinkhorn loop (Alg. 1): one cooperative launch runs a chunk
-// of (f-update, g-update) iterations, the stop test included, without returning to the
-// host between sweeps.
+// Persistent tensor-core Sinkhorn loop (Alg. 1): one cooperative launch runs the
+// (f-update, g-update) iterations of a solve, the stop test included, without returning
+// to the host between sweeps.
 //
 // Every sweep is the log-sum-exp of lse_sweep_tc: for the rows a_i of one cloud,
 //   L_i = log2 sum_j 2^{t_ij},  t_ij = c (a_i . b_j) + beta_j,  c = 2 log2(e) / eps,
 //   beta_j = (pot_j - |b_j|^2) log2(e) / eps,
-// with both clouds centred, scaled by sqrt(c) and split into bf16 hi/lo ("bf16x3") so
-// that the tensor cores accumulate c (a_i . b_j) in float32 TMEM. Unlike the per-sweep
-// kernel, beta_j is added by the LSE warps (float32) instead of by a bias MMA: the
-// operand products of a sweep then depend on nothing the previous sweep computes, and
-// the MMA warp runs up to two tiles into the next sweep while the previous one
-// finishes.
+// with both clouds centred, scaled by sqrt(c) and split into bf16 hi/lo ("bf16x3"), so
+// that the tensor cores accumulate c (a_i . b_j) in float32 TMEM; one more K = 16 MMA
+// (ones against the three-way bf16 split of beta_j) adds the bias, so the LSE warps read
+// t_ij directly.
 //
-// Data flow between sweeps. The row-block finisher of a sweep (the last CTA to arrive
-// on the row block) writes, for each of its rows, the new potential and a tagged beta
-// word (low 32 bits: beta as float32, high 32 bits: the index of the sweep that wrote
-// it, plus one) into a buffer chosen by the iteration's parity. A CTA about to fold a
-// column tile of the next sweep checks the tags of the tile's betas (fetched by the
-// producer warp with a bulk copy) and, only where a tag is stale, reloads the words
-// from L2 until they carry the expected tag. So a tile waits exactly for the row blocks
-// it reads, and no grid-wide barrier sits between sweeps.
+// Data flow between sweeps. The row-block finisher of a sweep (the last CTA to arrive on
+// the row block) writes the new potential and the bias rows of its 128 rows into a buffer
+// chosen by the iteration's parity, then publishes the row block's ready flag (the index
+// of the sweep that wrote it, plus one) with a release store. The producer warp of a CTA
+// loads a column tile's operands as soon as a stage is free, and its bias rows once the
+// flags of the row blocks under that tile carry the expected value. So a tile waits for
+// exactly the row blocks it reads, the operand products of the next sweep's first tile
+// run while the previous sweep finishes, and no grid-wide barrier sits between sweeps.
 //
 // Stop test (Alg. 1: error <= tau, max_iter, a stall, a non-finite error). The f-update
 // of iteration k measures the row-marginal error of the current (f, g) and writes
@@ -28,12 +26,12 @@
 // (every CTA computes the same state). The g-update of iteration k runs meanwhile; when
 // the test stops the loop, that g-update writes nothing and the loop ends after it.
 //
-// Warps: 0 TMA producer (A row block, B hi/lo stages, tagged betas), 1 TMEM owner and
-// MMA issuer, 2-9 two LSE warpgroups (alternate tiles), 10-11 segment epilogues
-// (publish, arrive, combine on the last arrival, potentials, betas, error partials) and
-// the stop decision. All waits are bounded: an mbarrier wait, a tag poll or a counter
-// poll that runs past the wait limit raises the CTA's abort flag and the grid's fault
-// word; every role then winds down (copies and products in flight drained, TMEM
+// Warps: 0 TMA producer (A row block, B hi/lo stages, bias rows), 1 TMEM owner and MMA
+// issuer, 2-9 two LSE warpgroups (alternate tiles), 10-11 segment epilogues (publish,
+// arrive, combine on the last arrival, potentials, bias rows, flags, error partials)
+// and the stop decision. All waits are bounded: an mbarrier wait, a flag poll or a
+// counter poll that runs past the wait limit raises the CTA's abort flag and the grid's
+// fault word; every role then winds down (copies and products in flight drained, TMEM
 // freed) and the host returns PROGOT_ERR_TIMEOUT.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -52,14 +50,15 @@ namespace loop {
 constexpr int NTHREADS = 384;
 constexpr int EPI_TID0 = 320;
 constexpr int TMEM_COLS = 512;
-constexpr int BETA_SLOTS = 6;  // tagged-beta ring (even: slot s always serves warpgroup s & 1)
 constexpr int A_TILE_BYTES = BM * KB * 2;
+constexpr int A_BIAS_BYTES = BM * 32;  // 128 rows x 16 bf16 of ones (32-byte swizzle)
+constexpr int BIAS_SLOTS = 2;          // bias-row ring, one slot per tile
 
 struct Shared {
   uint64_t full[8];
   uint64_t empty[8];
-  uint64_t beta_full[BETA_SLOTS];
-  uint64_t beta_empty[BETA_SLOTS];
+  uint64_t bias_full[2];    // a tile's bias rows landed (loaded once the producer saw their flags)
+  uint64_t bias_empty[2];
   uint64_t tmem_full[2];
   uint64_t tmem_empty[2];
   uint64_t a_full[2];
@@ -84,9 +83,10 @@ static_assert(offsetof(Shared, ms) % 8 == 0 && offsetof(Shared, seg) % 8 == 0, "
 static_assert(sizeof(Shared) % 16 == 0, "the control block follows 16-byte aligned buffers");
 
 struct Layout {
-  uint32_t a0, a_stride, a_lo_off, stage0, stage_bytes, b_lo_off, beta0, beta_slot, fbuf0, ctrl, total;
+  uint32_t a0, a_stride, a_lo_off, a_bias, bias0, bias_slot, stage0, stage_bytes, b_lo_off, ctrl, total;
 };
 
+// A buffers, the ones of the bias product, the bias-row ring, then the stages (B hi, B lo).
 __host__ __device__ inline Layout layout(int bn, int nkb, int split3, int stages, int a_bufs) {
   Layout L;
   uint32_t off = 0;
@@ -94,15 +94,16 @@ __host__ __device__ inline Layout layout(int bn, int nkb, int split3, int stages
   L.a_lo_off = nkb * A_TILE_BYTES;
   L.a_stride = nkb * A_TILE_BYTES * (split3 ? 2 : 1);
   off += a_bufs * L.a_stride;
+  L.a_bias = off;
+  off += A_BIAS_BYTES;
+  L.bias0 = off;
+  L.bias_slot = (uint32_t)bn * 32;
+  off += BIAS_SLOTS * L.bias_slot;
+  off = (off + 1023) & ~1023u;  // 128-byte swizzled stages start on 1024-byte boundaries
   L.stage0 = off;
   L.b_lo_off = (uint32_t)bn * KB * 2;
   L.stage_bytes = L.b_lo_off * (split3 ? 2 : 1);
   off += stages * L.stage_bytes;
-  L.beta0 = off;
-  L.beta_slot = (uint32_t)bn * 8;
-  off += BETA_SLOTS * L.beta_slot;
-  L.fbuf0 = off;  // float betas: [warpgroup][2][bn]
-  off += 4 * (uint32_t)bn * 4;
   L.ctrl = off;
   off += (uint32_t)sizeof(Shared);
   L.total = off + 1024;
@@ -114,8 +115,10 @@ struct Side {
   SweepParams p;            // mode = potential, role 1 (f) or 2 (g), centred norms, weights, eps
   float* out0;              // f-update: the two f buffers (state.fcur selects the current one);
   float* out1;              //   g-update: out0 = g
-  uint64_t* beta_out[2];    // tagged betas of A's rows, by iteration parity
-  const uint64_t* beta_in[2];  // tagged betas of B's rows
+  __nv_bfloat16* bias_out[2];  // bias rows of A (rows x 16 bf16), by iteration parity
+  uint32_t* flag_out;          // [R] ready flags of A's row blocks (sweep index + 1)
+  const uint32_t* flag_in;     // ready flags of B's row blocks
+  int32_t RB;                  // row blocks of B
   unsigned long long* cnt;  // [R] arrivals per row block (monotonic over the loop)
   unsigned long long* done; // finished row blocks (monotonic over the loop)
   float2* partial;          // [G * maxseg * 128] (max, sum) slots
@@ -169,14 +172,6 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
-  uint64_t v;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
-  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
 __device__ __forceinline__ unsigned long long atom_add_acq_rel_u64(unsigned long long* p, unsigned long long v) {
   unsigned long long old;
   asm volatile("atom.add.acq_rel.gpu.global.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
@@ -207,12 +202,6 @@ __device__ __forceinline__ bool wait_counter(const unsigned long long* c, unsign
   }
 }
 
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
 
 __device__ __forceinline__ float max3(float a, float b, float c) {
   float r;
@@ -233,8 +222,62 @@ __device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
   return r;
 }
 
-__device__ __forceinline__ uint64_t beta_word(float beta, uint32_t tag) {
-  return ((uint64_t)tag << 32) | (uint64_t)__float_as_uint(beta);
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// beta split into three bf16 terms (hi, mid, lo) in the first three of 16 slots
+// (-inf in the first slot for a non-finite beta).
+__device__ __forceinline__ void write_bias_row(__nv_bfloat16* row16, float beta) {
+  __nv_bfloat16 h1, h2, h3;
+  if (isfinite(beta)) {
+    h1 = __float2bfloat16_rn(beta);
+    const float r1 = beta - __bfloat162float(h1);
+    h2 = __float2bfloat16_rn(r1);
+    h3 = __float2bfloat16_rn(r1 - __bfloat162float(h2));
+  } else {
+    h1 = __float2bfloat16_rn(-INFINITY);
+    h2 = __float2bfloat16_rn(0.f);
+    h3 = __float2bfloat16_rn(0.f);
+  }
+  uint4 lo4;
+  lo4.x = (uint32_t)__bfloat16_as_ushort(h1) | ((uint32_t)__bfloat16_as_ushort(h2) << 16);
+  lo4.y = (uint32_t)__bfloat16_as_ushort(h3);
+  lo4.z = 0u;
+  lo4.w = 0u;
+  uint4* dst = reinterpret_cast<uint4*>(row16);
+  dst[0] = lo4;
+  dst[1] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// Poll the ready flags of row blocks [r0, r1) until each is at least `want` (acquire);
+// bounded. Called by one lane.
+__device__ __forceinline__ bool wait_flags(const uint32_t* flags, int r0, int r1, uint32_t want,
+                                           volatile int32_t* abort_flag, const Params& P) {
+  for (int r = r0; r < r1; ++r) {
+    if (ld_acquire_u32(flags + r) >= want) continue;
+    const unsigned long long t0 = global_ns();
+    for (uint32_t i = 1;; ++i) {
+      if (ld_acquire_u32(flags + r) >= want) break;
+      if ((i & 15) == 0) {
+        if (*abort_flag || grid_aborted(P)) {
+          *abort_flag = 1;
+          return false;
+        }
+        if (global_ns() - t0 > P.wait_ns) {
+          *abort_flag = 1;
+          atomicExch(P.fault, 1);
+          return false;
+        }
+      }
+    }
+  }
+  return true;
 }
 
 // Named barriers: 1 = both LSE warpgroups (256), 3 = epilogue warps (64),
@@ -243,9 +286,12 @@ __device__ __forceinline__ void bar_lse_all() { asm volatile("bar.sync 1, 256;" 
 __device__ __forceinline__ void bar_epi() { asm volatile("bar.sync 3, 64;" ::: "memory"); }
 __device__ __forceinline__ void bar_wg(int wg) { asm volatile("bar.sync %0, 128;" ::"r"(4 + wg) : "memory"); }
 
-// Tag of the betas written by sweep `sigma` (sigma = 2 k for the f-update of iteration
-// k, 2 k + 1 for its g-update): sigma + 1. The initial betas of g carry tag 0.
-__device__ __forceinline__ uint32_t tag_of(int it, int side) { return (uint32_t)(2 * it + side + 1); }
+// Flag value published by sweep sigma (sigma = 2 k for the f-update of iteration k,
+// 2 k + 1 for its g-update): sigma + 2, and sweep sigma waits for flags >= sigma + 1 on
+// the other side. Flags start at 0 ("nothing published"); the host publishes the initial
+// g's row blocks with 1.
+__device__ __forceinline__ uint32_t flag_of(int it, int side) { return (uint32_t)(2 * it + side + 2); }
+__device__ __forceinline__ uint32_t flag_wanted(int it, int side) { return (uint32_t)(2 * it + side + 1); }
 
 // ------------------------------------------------------------------ kernel
 template <int BN>
@@ -254,6 +300,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                      const __grid_constant__ CUtensorMap mYh_a, const __grid_constant__ CUtensorMap mYl_a,
                      const __grid_constant__ CUtensorMap mXh_b, const __grid_constant__ CUtensorMap mXl_b,
                      const __grid_constant__ CUtensorMap mYh_b, const __grid_constant__ CUtensorMap mYl_b,
+                     const __grid_constant__ CUtensorMap mXb0, const __grid_constant__ CUtensorMap mXb1,
+                     const __grid_constant__ CUtensorMap mYb0, const __grid_constant__ CUtensorMap mYb1,
                      const Params P) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem =
@@ -263,16 +311,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = blockIdx.x, G = P.G, nkb = P.nkb, S = P.stages, NA = P.a_bufs;
   volatile int32_t* abort_flag = &sh.abort_flag;
-  constexpr uint32_t B_TILE_BYTES = (uint32_t)BN * KB * 2;
+  constexpr uint32_t B_TILE_BYTES = (uint32_t)BN * KB * 2, BIAS_TILE_BYTES = (uint32_t)BN * 32;
+  constexpr int RB_PER_TILE = BN / BM;  // row blocks of B under one column tile
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&sh.full[s], 1);
       mbar_init(&sh.empty[s], 1);
     }
-    for (int s = 0; s < BETA_SLOTS; ++s) {
-      mbar_init(&sh.beta_full[s], 1);
-      mbar_init(&sh.beta_empty[s], 1);
+    for (int s = 0; s < BIAS_SLOTS; ++s) {
+      mbar_init(&sh.bias_full[s], 1);
+      mbar_init(&sh.bias_empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&sh.tmem_full[b], 1);
@@ -285,7 +334,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     mbar_init(&sh.drain, 1);
     mbar_init(&sh.dec_full, 1);
     sh.abort_flag = 0;
-    // the state this chunk starts from (written by the previous launch or the initialiser)
+    // the state this launch starts from (written by the initialiser or an earlier launch)
     {
       const int4* src = reinterpret_cast<const int4*>(P.state);
       int4* dst = reinterpret_cast<int4*>(&sh.st);
@@ -293,6 +342,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     sh.entry_done = sh.st.done;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // A side of the bias product: all ones (bf16 0x3F80), so that the K = 16 step adds
+  // beta_hi + beta_mid + beta_lo whatever the order of the 16-byte chunks in a row
+  {
+    uint32_t* ab = reinterpret_cast<uint32_t*>(smem + L.a_bias);
+    for (int i = threadIdx.x; i < A_BIAS_BYTES / 4; i += NTHREADS) ab[i] = 0x3F803F80u;
+    fence_async_smem();
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem_base)),
@@ -308,7 +364,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
-    int u = 0, ka = 0, tb = 0;  // B stage units, A segments, tiles (beta slots) issued
+    int u = 0, ka = 0, ub = 0;  // stage units, A segments, bias tiles issued
     bool ok = true;
     for (int it = P.seq0; it < it_end && ok; ++it) {
       if (it > P.seq0) {
@@ -322,7 +378,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const CUtensorMap* mAl = sd == 0 ? &mXl_a : &mYl_a;
         const CUtensorMap* mBh = sd == 0 ? &mYh_b : &mXh_b;
         const CUtensorMap* mBl = sd == 0 ? &mYl_b : &mXl_b;
-        const uint64_t* bsrc = Sd.beta_in[it & 1];  // f-update: g of the previous g-update; g-update: this iteration's f
+        // bias rows of B: f-update: g of the previous g-update; g-update: this iteration's f
+        const CUtensorMap* mBb = sd == 0 ? ((it & 1) ? &mYb1 : &mYb0) : ((it & 1) ? &mXb1 : &mXb0);
+        const uint32_t want = flag_wanted(it, sd);
         const Split sp = make_split(Sd.R, Sd.T, G);
         const int nseg = num_segments(sp, c);
         for (int k = 0; k < nseg && ok; ++k, ++ka) {
@@ -339,16 +397,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
           }
           __syncwarp();
-          for (int t = sg.t0; t < sg.t1 && ok; ++t, ++tb) {
-            // tagged betas of the tile's columns (possibly stale: the LSE warps check the tags)
-            const int bs = tb % BETA_SLOTS;
-            ok = warp_wait_bar(&sh.beta_empty[bs], (uint32_t)(((tb / BETA_SLOTS) & 1) ^ 1), abort_flag, P);
-            if (!ok) break;
-            if (elect_one()) {
-              mbar_arrive_expect_tx(&sh.beta_full[bs], L.beta_slot);
-              bulk_load(smem + L.beta0 + bs * L.beta_slot, bsrc + (int64_t)t * BN, L.beta_slot, &sh.beta_full[bs]);
-            }
-            __syncwarp();
+          for (int t = sg.t0; t < sg.t1 && ok; ++t) {
             for (int kb = 0; kb < nkb; ++kb, ++u) {
               const int s = u % S;
               ok = warp_wait_bar(&sh.empty[s], (uint32_t)(((u / S) & 1) ^ 1), abort_flag, P);
@@ -361,6 +410,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               }
               __syncwarp();
             }
+            if (!ok) break;
+            // the tile's bias rows, once the row blocks of B under it are ready
+            const int bs = ub % BIAS_SLOTS;
+            ok = warp_wait_bar(&sh.bias_empty[bs], (uint32_t)(((ub / BIAS_SLOTS) & 1) ^ 1), abort_flag, P);
+            if (!ok) break;
+            int okf = 1;
+            if (lane == 0) {
+              const int r0 = t * RB_PER_TILE, r1 = min(Sd.RB, r0 + RB_PER_TILE);
+              okf = wait_flags(Sd.flag_in, r0, r1, want, abort_flag, P) ? 1 : 0;
+              if (okf) {
+                mbar_arrive_expect_tx(&sh.bias_full[bs], BIAS_TILE_BYTES);
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+                tma_load_2d(smem + L.bias0 + bs * L.bias_slot, mBb, &sh.bias_full[bs], 0, t * BN);
+              }
+            }
+            ok = __shfl_sync(0xffffffffu, okf, 0) != 0;
+            if (!ok) break;
+            ++ub;
           }
         }
       }
@@ -370,11 +437,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (int k = max(0, ka - NA); k < ka; ++k)
         warp_wait_bar(&sh.a_full[k % NA], (uint32_t)((k / NA) & 1), abort_flag, P, true);
       for (int v = max(0, u - S); v < u; ++v) warp_wait_bar(&sh.full[v % S], (uint32_t)((v / S) & 1), abort_flag, P, true);
-      for (int v = max(0, tb - BETA_SLOTS); v < tb; ++v)
-        warp_wait_bar(&sh.beta_full[v % BETA_SLOTS], (uint32_t)((v / BETA_SLOTS) & 1), abort_flag, P, true);
+      for (int v = max(0, ub - BIAS_SLOTS); v < ub; ++v)
+        warp_wait_bar(&sh.bias_full[v % BIAS_SLOTS], (uint32_t)((v / BIAS_SLOTS) & 1), abort_flag, P, true);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
+    const uint64_t abias = desc_sw32(smem_u32(smem + L.a_bias));
     bool ok = true;
     int u = 0, tl = 0, ka = 0;
     for (int it = P.seq0; it < it_end && ok; ++it) {
@@ -424,7 +492,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               __syncwarp();
             }
             if (!ok) break;
-            if (elect_one()) umma_commit(&sh.tmem_full[b]);
+            // bias: t_ij = c (a_i . b_j) + beta_j, once the producer has the row blocks' bias rows
+            const int bs = tl % BIAS_SLOTS;  // one bias slot per tile, in tile order
+            ok = warp_wait_bar(&sh.bias_full[bs], (uint32_t)((tl / BIAS_SLOTS) & 1), abort_flag, P);
+            if (!ok) break;
+            tc_fence_after();
+            if (elect_one()) {
+              umma<BN>(d_tmem, abias, desc_sw32(smem_u32(smem + L.bias0 + bs * L.bias_slot)), 1u);
+              umma_commit(&sh.bias_empty[bs]);
+              umma_commit(&sh.tmem_full[b]);
+            }
             __syncwarp();
           }
           if (!ok) break;
@@ -441,8 +518,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int wg = (warp - 2) >> 2;
     const int quarter = warp & 3;
     const int row_local = quarter * 32 + lane;
-    float* fbuf = reinterpret_cast<float*>(smem + L.fbuf0) + wg * 2 * BN;
-    constexpr int EPL = BN / 128;  // beta words per lane and warp (a quarter of the tile each)
     int tl = 0, jt = 0, kseg = 0;
     bool dead = false;
     for (int it = P.seq0; it < it_end; ++it) {
@@ -455,8 +530,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
       for (int sd = 0; sd < 2; ++sd) {
         const Side& Sd = P.side[sd];
-        const uint64_t* bsrc = Sd.beta_in[it & 1];
-        const uint32_t want = sd == 0 ? (uint32_t)(2 * it) : (uint32_t)(2 * it + 1);
         const Split sp = make_split(Sd.R, Sd.T, G);
         const int nseg = num_segments(sp, c);
         for (int k = 0; k < nseg; ++k, ++kseg) {
@@ -465,57 +538,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           for (int t = sg.t0; t < sg.t1; ++t, ++tl) {
             if ((tl & 1) != wg) continue;
             const uint32_t ph = (uint32_t)(jt & 1);
-            float* fb = fbuf + (jt & 1) * BN;
             ++jt;
-            // ---- betas of the tile: check the tags of this warp's quarter, reload stale words
-            const int bs = tl % BETA_SLOTS;
-            if (!dead && !warp_wait_bar(&sh.beta_full[bs], (uint32_t)((tl / BETA_SLOTS) & 1), abort_flag, P))
-              dead = true;
-            if (!dead) {
-              const uint64_t* slot = reinterpret_cast<const uint64_t*>(smem + L.beta0 + bs * L.beta_slot);
-              const int e0 = quarter * (BN / 4) + lane * EPL;
-              const int64_t col0 = (int64_t)t * BN + e0;
-              uint64_t w[EPL];
-              bool stale = false;
-#pragma unroll
-              for (int e = 0; e < EPL; ++e) {
-                w[e] = slot[e0 + e];
-                stale |= (col0 + e < Sd.nB) && (uint32_t)(w[e] >> 32) != want;
-              }
-              if (__any_sync(0xffffffffu, stale)) {
-                const unsigned long long t0 = global_ns();
-                for (uint32_t i = 1;; ++i) {
-                  stale = false;
-#pragma unroll
-                  for (int e = 0; e < EPL; ++e) {
-                    if (col0 + e < Sd.nB && (uint32_t)(w[e] >> 32) != want) {
-                      w[e] = ld_relaxed_u64(bsrc + col0 + e);
-                      stale |= (uint32_t)(w[e] >> 32) != want;
-                    }
-                  }
-                  if (!__any_sync(0xffffffffu, stale)) break;
-                  if ((i & 15) == 0) {
-                    int bad = 0;
-                    if (*abort_flag || grid_aborted(P)) bad = 1;
-                    if (global_ns() - t0 > P.wait_ns) bad = 2;
-                    bad = __shfl_sync(0xffffffffu, bad, 0);
-                    if (bad) {
-                      if (lane == 0) {
-                        *abort_flag = 1;
-                        if (bad == 2) atomicExch(P.fault, 1);
-                      }
-                      dead = true;
-                      break;
-                    }
-                  }
-                }
-              }
-#pragma unroll
-              for (int e = 0; e < EPL; ++e)
-                fb[e0 + e] = (col0 + e < Sd.nB) ? __uint_as_float((uint32_t)w[e]) : -INFINITY;
-            }
-            bar_wg(wg);  // the whole tile's float betas are in fb
-            if (quarter == 0 && lane == 0 && !dead) mbar_arrive(&sh.beta_empty[bs]);
             if (dead) continue;
             int okv = 0;
             if (lane == 0) okv = wait_bar(&sh.tmem_full[wg], ph, abort_flag, P) ? 1 : 0;
@@ -536,25 +559,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               PROGOT_TMEM_LD32(taddr + 96, v[3]);
               tmem_wait_ld();
               if (half == BN / 128 - 1) {
+                // the whole accumulator is in registers: hand the TMEM buffer back
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sh.tmem_empty[wg]);
               }
-              // t_ij = c (a_i . b_j) + beta_j
-              const float* fbh = fb + half * 128;
-#pragma unroll
-              for (int cc = 0; cc < 4; ++cc)
-#pragma unroll
-                for (int i = 0; i < 32; i += 4) {
-                  const float4 b4 = *reinterpret_cast<const float4*>(fbh + cc * 32 + i);
-                  float a0, a1, a2, a3;
-                  unpack2(add2(pack2(v[cc][i], v[cc][i + 1]), pack2(b4.x, b4.y)), a0, a1);
-                  unpack2(add2(pack2(v[cc][i + 2], v[cc][i + 3]), pack2(b4.z, b4.w)), a2, a3);
-                  v[cc][i] = a0;
-                  v[cc][i + 1] = a1;
-                  v[cc][i + 2] = a2;
-                  v[cc][i + 3] = a3;
-                }
               float mx[8];
 #pragma unroll
               for (int q = 0; q < 8; ++q) mx[q] = v[q >> 1][(q & 1) * 16];
@@ -626,8 +635,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int fcur = sh.st.fcur;
         const float* pot_cur = (sd == 0) ? (fcur == 0 ? Sd.out0 : Sd.out1) : nullptr;
         float* out = (sd == 0) ? (fcur == 0 ? Sd.out1 : Sd.out0) : Sd.out0;
-        uint64_t* bout = Sd.beta_out[sd == 0 ? (it & 1) : ((it + 1) & 1)];
-        const uint32_t tag = tag_of(it, sd);
+        __nv_bfloat16* bout = Sd.bias_out[sd == 0 ? (it & 1) : ((it + 1) & 1)];
+        const uint32_t flag = flag_of(it, sd);
         for (int k = 0; k < nseg; ++k, ++kseg) {
           const Seg sg = segment(sp, c, k);
           const int sl = kseg & 1;
@@ -685,7 +694,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 if (!skip) {
                   float val;
                   e[h] = row_epilogue(p, i, Lr, rin[h], out, &val);
-                  st_relaxed_u64(bout + i, beta_word((val - rin[h].an) * p.bscale, tag));
+                  write_bias_row(bout + i * 16, (val - rin[h].an) * p.bscale);
                 }
               }
             }
@@ -701,33 +710,39 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             bar_epi();
             if (etid == 0) {
-              if (sd == 0) P.errpart[(int64_t)(it & 1) * Sd.R + sg.r] = (double)((sh.ered[0] + sh.ered[1]) + (sh.ered[2] + sh.ered[3]));
-              asm volatile("fence.proxy.async.global;" ::: "memory");  // the betas are read by bulk copies
+              if (sd == 0)
+                P.errpart[(int64_t)(it & 1) * Sd.R + sg.r] =
+                    (double)((sh.ered[0] + sh.ered[1]) + (sh.ered[2] + sh.ered[3]));
+              // the bias rows are read by TMA (async proxy) once the flag is seen
+              asm volatile("fence.proxy.async.global;" ::: "memory");
+              if (!skip) st_release_u32(Sd.flag_out + sg.r, flag);
               red_add_release_u64(Sd.done, 1ull);
             }
           }
           bar_epi();
         }
         if (sd == 0) {
-          // ---- stop test of iteration it (decider: warp 10), once every row block of the f-update is done
+          // ---- stop test of iteration it (warp 10), once every row block of the f-update is done
           if (etid < 32) {
             bool okc = true;
             if (etid == 0) {
-              okc = wait_counter(P.side[1].done, (unsigned long long)it * (unsigned long long)P.side[1].R, abort_flag, P) &&
+              okc = wait_counter(P.side[1].done, (unsigned long long)it * (unsigned long long)P.side[1].R, abort_flag,
+                                 P) &&
                     wait_counter(P.side[0].done, (unsigned long long)(it + 1) * (unsigned long long)P.side[0].R,
                                  abort_flag, P);
               __threadfence();
             }
             okc = __shfl_sync(0xffffffffu, okc ? 1 : 0, 0) != 0;
             __syncwarp();  // the other lanes' loads below follow lane 0's acquire
-            const double err = okc ? sum_errpart_warp(P.errpart + (int64_t)(it & 1) * P.side[0].R, P.side[0].R) : (double)NAN;
+            const double err =
+                okc ? sum_errpart_warp(P.errpart + (int64_t)(it & 1) * P.side[0].R, P.side[0].R) : (double)NAN;
             if (etid == 0) {
               SolverState st = sh.st;
               if (okc) {
                 f_update_transition(st, err, P.side[0].p);
               } else {
                 st.done = 1;
-                st.status = kNumeric;  // replaced by PROGOT_ERR_TIMEOUT on the host (fault word)
+                st.status = kNumeric;  // reported as PROGOT_ERR_TIMEOUT by the host (fault word)
               }
               sh.st = st;
               sh.dec_stop[it & 1] = st.done;
@@ -752,12 +767,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
 }
 
-// Initial tagged betas of one side from its potential: tag 0, beta = (pot - |b|^2) log2(e)/eps.
-__global__ void beta_init_kernel(const float* __restrict__ pot, const float* __restrict__ nrm, int64_t n, float bscale,
-                                 uint64_t* __restrict__ out) {
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  out[j] = beta_word((pot[j] - nrm[j]) * bscale, 0u);
+__global__ void fill_u32_kernel(uint32_t* __restrict__ p, int64_t n, uint32_t v) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
 }
 
 }  // namespace loop
@@ -779,6 +791,13 @@ static void loop_shape(int bn, int nkb, int split3, int* stages, int* a_bufs) {
       return;
     }
   }
+}
+
+cudaError_t launch_fill_u32(uint32_t* p, int64_t n, uint32_t v, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  tc::loop::fill_u32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, n, v);
+  count_launch();
+  return cudaGetLastError();
 }
 
 bool loop_tc_supported(int bn, int nkb, int split3) {
@@ -804,13 +823,6 @@ size_t loop_tc_smem(int bn, int nkb, int split3) {
   return tc::loop::layout(bn, nkb, split3, s, na).total;
 }
 
-cudaError_t launch_beta_init(const float* pot, const float* nrm, int64_t n, float bscale, void* out, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  tc::loop::beta_init_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pot, nrm, n, bscale, (uint64_t*)out);
-  count_launch();
-  return cudaGetLastError();
-}
-
 template <int BN>
 static cudaError_t launch_loop(const tc::loop::Params& P, size_t smem, const void* const* maps, cudaStream_t stream) {
   static thread_local size_t attr_bytes = 0;
@@ -830,10 +842,10 @@ static cudaError_t launch_loop(const tc::loop::Params& P, size_t smem, const voi
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  const CUtensorMap* m[8];
-  for (int q = 0; q < 8; ++q) m[q] = reinterpret_cast<const CUtensorMap*>(maps[q]);
+  const CUtensorMap* m[12];
+  for (int q = 0; q < 12; ++q) m[q] = reinterpret_cast<const CUtensorMap*>(maps[q]);
   return cudaLaunchKernelEx(&cfg, tc::loop::sinkhorn_loop_tc<BN>, *m[0], *m[1], *m[2], *m[3], *m[4], *m[5], *m[6],
-                            *m[7], P);
+                            *m[7], *m[8], *m[9], *m[10], *m[11], P);
 }
 
 cudaError_t launch_sinkhorn_loop_tc(const LoopLaunch& Lq, cudaStream_t stream) {
@@ -848,10 +860,10 @@ cudaError_t launch_sinkhorn_loop_tc(const LoopLaunch& Lq, cudaStream_t stream) {
     d.p = s.p;
     d.out0 = s.out0;
     d.out1 = s.out1;
-    d.beta_out[0] = (uint64_t*)s.beta_out[0];
-    d.beta_out[1] = (uint64_t*)s.beta_out[1];
-    d.beta_in[0] = (const uint64_t*)s.beta_in[0];
-    d.beta_in[1] = (const uint64_t*)s.beta_in[1];
+    d.bias_out[0] = (__nv_bfloat16*)s.bias_out[0];
+    d.bias_out[1] = (__nv_bfloat16*)s.bias_out[1];
+    d.flag_out = s.flag_out;
+    d.flag_in = s.flag_in;
     d.cnt = s.cnt;
     d.done = s.done;
     d.partial = s.partial;
@@ -859,6 +871,7 @@ cudaError_t launch_sinkhorn_loop_tc(const LoopLaunch& Lq, cudaStream_t stream) {
     d.nB = s.p.nB;
     d.R = (int)((s.p.nA + tc::BM - 1) / tc::BM);
     d.T = (int)((s.p.nB + Lq.bn - 1) / Lq.bn);
+    d.RB = (int)((s.p.nB + tc::BM - 1) / tc::BM);
   }
   P.errpart = Lq.errpart;
   P.state = Lq.state;

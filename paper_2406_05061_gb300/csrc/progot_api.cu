@@ -181,8 +181,9 @@ struct Workspace {
   float* ync;       // nmax: |y_j - mu|^2
   int32_t* fault;   // set by a tensor-core CTA whose bounded wait expired
   // persistent tensor-core Sinkhorn loop
-  uint64_t* lbeta;  // tagged betas: x side [2][nbeta], then y side [2][nbeta]
-  int64_t nbeta;    // words per buffer (nmax rounded up to 256)
+  void* xb2;        // second bias-row buffers (the loop alternates xb / xb2 and yb / yb2)
+  void* yb2;
+  uint32_t* lflag;  // ready flags: x row blocks [rbmax], y row blocks [rbmax]
   unsigned long long* lcnt;  // arrivals: x row blocks [rbmax], y row blocks [rbmax], done_x, done_y
   float2* lpart;    // (max, sum) slots: f-update bank, then g-update bank (lslots each)
   int64_t lslots;
@@ -267,8 +268,9 @@ static size_t ws_layout(const WsDims& w, Workspace* out, char* base) {
   ws.xnc = (float*)take(w.tc ? sizeof(float) * w.nmax : 0);
   ws.ync = (float*)take(w.tc ? sizeof(float) * w.nmax : 0);
   ws.fault = (int32_t*)take(sizeof(int32_t));
-  ws.nbeta = w.tc ? cdiv(w.nmax, 256) * 256 : 0;
-  ws.lbeta = (uint64_t*)take(sizeof(uint64_t) * 4 * (size_t)ws.nbeta);
+  ws.xb2 = take(bb);
+  ws.yb2 = take(bb);
+  ws.lflag = (uint32_t*)take(w.tc ? sizeof(uint32_t) * 2 * (size_t)w.rbmax : 0);
   ws.lcnt = (unsigned long long*)take(w.tc ? sizeof(unsigned long long) * (2 * (size_t)w.rbmax + 2) : 0);
   // G * maxseg <= R + 2 G slots of 128 rows per bank (each CTA's segments: its whole row
   // blocks, plus at most two partial ones of the contiguous remainder)
@@ -521,11 +523,12 @@ static int lse_sweep(const SweepParams& p, int32_t precision, cudaStream_t s, co
   return PROGOT_OK;
 }
 
-// Sinkhorn loop (Alg. 1) as one persistent tensor-core launch (loop_tc.cu): f and g
-// betas flow between sweeps as tagged words, the stop test runs inside the kernel. pf and
-// pg are the f- and g-update descriptions built by sinkhorn_core; ops describes the
-// prepared operands. On return the current f is in f_a, g in g, and the y-side bias
-// rows (ws.yb) hold g for a map step at the same eps.
+// Sinkhorn loop (Alg. 1) as one persistent tensor-core launch (loop_tc.cu): the bias rows
+// of each update's potential pass between the GPU's CTAs behind per-row-block ready
+// flags, the stop test runs inside the kernel. pf and pg are the f- and g-update
+// descriptions built by sinkhorn_core; ops describes the prepared operands, whose bias
+// rows (ws.xb from f, ws.yb from g) prep_tc has written. On return the current f is in
+// f_a, g in g, and the y-side bias rows (ws.yb) hold g for a map step at the same eps.
 static int sinkhorn_loop_persistent(SweepParams pf, SweepParams pg, int64_t n, int64_t m, int32_t max_iter,
                                     double tau, float* f_a, float* f_b, float* g, const Workspace& ws,
                                     const TcOps& ops, int32_t* iters_out, double* err_out, cudaStream_t s) {
@@ -533,13 +536,22 @@ static int sinkhorn_loop_persistent(SweepParams pf, SweepParams pg, int64_t n, i
   pf.Bn = ops.ync;
   pg.An = ops.ync;
   pg.Bn = ops.xnc;
-  const int64_t nb = ws.nbeta, rb = ws.lrb;
-  uint64_t* bx[2] = {ws.lbeta, ws.lbeta + nb};
-  uint64_t* by[2] = {ws.lbeta + 2 * nb, ws.lbeta + 3 * nb};
-  CK(cudaMemsetAsync(ws.lbeta, 0xFF, sizeof(uint64_t) * 4 * (size_t)nb, s));  // tags no sweep expects
-  if (!g_withhold_betas.load()) CK(launch_beta_init(g, ops.ync, m, pf.bscale, by[0], s));
+  const int64_t rb = ws.lrb;
+  // the second bias buffers: their padding rows (-inf) matter, the others are written
+  // by the sweeps before any tile reads them
+  CK(launch_bias_prep(f_a, ops.xnc, n, cdiv(n, 256) * 256, pf.bscale, ws.xb2, s));
+  CK(launch_bias_prep(g, ops.ync, m, cdiv(m, 256) * 256, pf.bscale, ws.yb2, s));
+  // ready flags: nothing published, then the initial g's row blocks (in ws.yb) as flag 1,
+  // which the first f-update waits for. The test hook leaves them unpublished, so the
+  // first f-update's bounded wait expires.
+  CK(cudaMemsetAsync(ws.lflag, 0, sizeof(uint32_t) * 2 * (size_t)rb, s));
+  if (!g_withhold_betas.load()) CK(launch_fill_u32(ws.lflag + rb, cdiv(m, 128), 1u, s));
   CK(cudaMemsetAsync(ws.lcnt, 0, sizeof(unsigned long long) * (2 * (size_t)rb + 2), s));
   CK(launch_init_state(ws.state, s));
+  CUtensorMap xb2_map, yb2_map;
+  int rc = make_map(&xb2_map, ws.xb2, cdiv(n, 256) * 256, 16, ops.bn);
+  if (!rc) rc = make_map(&yb2_map, ws.yb2, cdiv(m, 256) * 256, 16, ops.bn);
+  if (rc) return rc;
   LoopLaunch L;
   memset(&L, 0, sizeof(L));
   LoopSideLaunch& F = L.side[0];
@@ -547,25 +559,26 @@ static int sinkhorn_loop_persistent(SweepParams pf, SweepParams pg, int64_t n, i
   F.p = pf;
   F.out0 = f_a;
   F.out1 = f_b;
-  F.beta_out[0] = bx[0];
-  F.beta_out[1] = bx[1];
-  F.beta_in[0] = by[0];
-  F.beta_in[1] = by[1];
+  F.bias_out[0] = ws.xb;
+  F.bias_out[1] = ws.xb2;
+  F.flag_out = ws.lflag;
+  F.flag_in = ws.lflag + rb;
   F.cnt = ws.lcnt;
   F.done = ws.lcnt + 2 * rb;
   F.partial = ws.lpart;
   Gs.p = pg;
   Gs.out0 = g;
   Gs.out1 = nullptr;
-  Gs.beta_out[0] = by[0];
-  Gs.beta_out[1] = by[1];
-  Gs.beta_in[0] = bx[0];
-  Gs.beta_in[1] = bx[1];
+  Gs.bias_out[0] = ws.yb;
+  Gs.bias_out[1] = ws.yb2;
+  Gs.flag_out = ws.lflag + rb;
+  Gs.flag_in = ws.lflag;
   Gs.cnt = ws.lcnt + rb;
   Gs.done = ws.lcnt + 2 * rb + 1;
   Gs.partial = ws.lpart + ws.lslots * 128;
-  const CUtensorMap* maps[8] = {&ops.xh_a, &ops.xl_a, &ops.yh_a, &ops.yl_a, &ops.xh_b, &ops.xl_b, &ops.yh_b, &ops.yl_b};
-  for (int q = 0; q < 8; ++q) L.maps[q] = maps[q];
+  const CUtensorMap* maps[12] = {&ops.xh_a, &ops.xl_a, &ops.yh_a, &ops.yl_a, &ops.xh_b, &ops.xl_b,
+                                 &ops.yh_b, &ops.yl_b, &ops.xb,   &xb2_map,   &ops.yb,   &yb2_map};
+  for (int q = 0; q < 12; ++q) L.maps[q] = maps[q];
   L.errpart = ws.lerr;
   L.state = ws.state;
   L.fault = ws.fault;
@@ -591,7 +604,7 @@ static int sinkhorn_loop_persistent(SweepParams pf, SweepParams pg, int64_t n, i
   }
   CK(launch_sinkhorn_loop_tc(L, s));
   if (t_prof.on) CK(cudaEventRecord(pr.b, s));
-  int rc = t_host.init();
+  rc = t_host.init();
   if (rc) return rc;
   int32_t fault = 0;
   CK(cudaMemcpyAsync(&t_host.hs[0], ws.state, sizeof(SolverState), cudaMemcpyDeviceToHost, s));

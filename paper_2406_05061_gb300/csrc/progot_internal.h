@@ -100,21 +100,24 @@ int tc_stages(int nkb, int split3);
 int tc_tile_cols(int nkb, int split3);  // 128 or 256
 
 // Persistent tensor-core Sinkhorn loop (loop_tc.cu). Side 0 is the f-update (rows of X
-// against Y), side 1 the g-update. Tagged beta words: low 32 bits beta as float32, high
-// 32 bits the tag of the sweep that wrote it.
+// against Y), side 1 the g-update. A finisher publishes its row block's bias rows, then
+// the row block's ready flag (the index of the sweep that wrote it, plus one).
 struct LoopSideLaunch {
   SweepParams p;             // potential mode; An / Bn the centred norms; role 1 (f) or 2 (g)
   float* out0;               // f-update: f buffers 0 and 1 (the state's fcur selects); g-update: g
   float* out1;
-  void* beta_out[2];         // tagged betas of this side's rows, by iteration parity
-  const void* beta_in[2];    // tagged betas of the other side's rows
+  void* bias_out[2];         // bias rows (rows x 16 bf16) of this side's rows, by iteration parity
+  uint32_t* flag_out;        // [row blocks] ready flags of this side, zero at the loop's start
+  const uint32_t* flag_in;   // the other side's flags
   unsigned long long* cnt;   // [row blocks] arrival counters, zero at the loop's start
   unsigned long long* done;  // finished row blocks, zero at the loop's start
   float2* partial;           // (max, sum) slots of this side's sweeps
 };
 struct LoopLaunch {
   LoopSideLaunch side[2];
-  const void* maps[8];       // CUtensorMap: X hi, X lo, Y hi, Y lo (128-row boxes); X hi, X lo, Y hi, Y lo (bn-row boxes)
+  // CUtensorMap: X hi, X lo, Y hi, Y lo (128-row boxes); X hi, X lo, Y hi, Y lo (bn-row
+  // boxes); bias rows X[0], X[1], Y[0], Y[1] (bn-row boxes)
+  const void* maps[12];
   double* errpart;           // [2][row blocks of X]
   SolverState* state;
   int32_t* fault;
@@ -122,8 +125,7 @@ struct LoopLaunch {
   int nkb, split3, bn, G, maxseg, seq0, niter;
 };
 cudaError_t launch_sinkhorn_loop_tc(const LoopLaunch& L, cudaStream_t stream);
-// out[j] = tagged word of (pot_j - nrm_j) bscale with tag 0
-cudaError_t launch_beta_init(const float* pot, const float* nrm, int64_t n, float bscale, void* out, cudaStream_t s);
+cudaError_t launch_fill_u32(uint32_t* p, int64_t n, uint32_t v, cudaStream_t s);
 bool loop_tc_supported(int bn, int nkb, int split3);
 void loop_tc_plan(int64_t n, int64_t m, int bn, int sms, int* G, int* maxseg);
 size_t loop_tc_smem(int bn, int nkb, int split3);
