@@ -74,6 +74,8 @@ struct Shared {
   int32_t entry_done;
   alignas(16) SolverState st;  // the stop test's state as this CTA computed it (copied in 16-byte pieces)
   float ered[4];
+  int32_t cslot[8];         // partial slots of the row block's first eight contributors (CTA order)
+  int32_t cfirst, ccount;   // the row block's first contributor and their number
   float2 ms[2][128];
   float2 seg[2][128];
 };
@@ -119,6 +121,9 @@ struct Side {
   uint32_t* flag_out;          // [R] ready flags of A's row blocks (sweep index + 1)
   const uint32_t* flag_in;     // ready flags of B's row blocks
   int32_t RB;                  // row blocks of B
+  // float32 pieces of the potential's constants: eps ln2 = c_hi + c_lo, eps = e_hi + e_lo,
+  // eps log(1 / nA) = w_hi + w_lo (uniform weights)
+  float c_hi, c_lo, e_hi, e_lo, w_hi, w_lo;
   unsigned long long* cnt;  // [R] arrivals per row block (monotonic over the loop)
   unsigned long long* done; // finished row blocks (monotonic over the loop)
   float2* partial;          // [G * maxseg * 128] (max, sum) slots
@@ -280,6 +285,40 @@ __device__ __forceinline__ bool wait_flags(const uint32_t* flags, int r0, int r1
   return true;
 }
 
+// New potential of row i from its log2-sum-exp L (Alg. 1's update, the row constant
+// |a_i|^2 included): f_i = eps log w_i + |a_i|^2 - eps ln2 L, in float32 with the
+// product eps ln2 L folded into FMAs on a hi/lo split of eps ln2, so that |a_i|^2 - eps
+// ln2 L is rounded once (GB300's float64 pipe is narrow and this is the sweep's critical
+// path). L itself is float32 (relative error 2^-24 of a value ~ |a_i|^2 / (eps ln2)),
+// which bounds the result's absolute error to a few float32 ulps of |a_i|^2 either way.
+// Writes out[i]; returns the f-update's marginal-error term w_i |exp((f_old - f_new)/eps) - 1|
+// (the exponent capped at 80, as in the per-sweep kernels) or 0 for the g-update.
+__device__ __forceinline__ float loop_row_potential(const Side& Sd, int sd, int64_t i, float L, const RowIn& in,
+                                                    float* out, float* val) {
+  float t = fmaf(-Sd.c_hi, L, in.an);
+  t = fmaf(-Sd.c_lo, L, t);
+  float fnew;
+  if (Sd.p.wA) {
+    const float lw = __logf(in.w);
+    fnew = t + fmaf(Sd.e_hi, lw, Sd.e_lo * lw);
+  } else {
+    fnew = (t + Sd.w_lo) + Sd.w_hi;
+  }
+  out[i] = fnew;
+  *val = fnew;
+  if (sd != 0) return 0.f;
+  float dlt = (in.pot - fnew) * Sd.p.inv_eps_f;
+  if (dlt > 80.f) dlt = 80.f;
+  return in.w * fabsf(expm1f(dlt));
+}
+
+// Combine of two partial (max, sum) pairs in log2 units with the hardware exp2.
+__device__ __forceinline__ float2 combine_fast(float2 p, float2 q) {
+  const float M = fmaxf(p.x, q.x);
+  if (M == -INFINITY) return make_float2(-INFINITY, 0.f);
+  return make_float2(M, p.y * fast_exp2(p.x - M) + q.y * fast_exp2(q.x - M));
+}
+
 // Named barriers: 1 = both LSE warpgroups (256), 3 = epilogue warps (64),
 // 4 + wg = LSE warpgroup wg (128).
 __device__ __forceinline__ void bar_lse_all() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
@@ -292,6 +331,7 @@ __device__ __forceinline__ void bar_wg(int wg) { asm volatile("bar.sync %0, 128;
 // g's row blocks with 1.
 __device__ __forceinline__ uint32_t flag_of(int it, int side) { return (uint32_t)(2 * it + side + 2); }
 __device__ __forceinline__ uint32_t flag_wanted(int it, int side) { return (uint32_t)(2 * it + side + 1); }
+
 
 // ------------------------------------------------------------------ kernel
 template <int BN>
@@ -640,34 +680,59 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int k = 0; k < nseg; ++k, ++kseg) {
           const Seg sg = segment(sp, c, k);
           const int sl = kseg & 1;
+          // the rows' epilogue inputs do not depend on the sweep: load them while the LSE
+          // warps finish the segment
+          RowIn rin[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int64_t i = (int64_t)sg.r * BM + etid + 64 * h;
+            rin[h].an = 0.f;
+            rin[h].pot = 0.f;
+            rin[h].w = 0.f;
+            if (i < Sd.nA) rin[h] = row_inputs(p, i, pot_cur);
+          }
+          // the row block's contributors and their partial slots, once per segment (the
+          // work split's 64-bit divisions stay off the finisher's path); the previous
+          // segment's readers passed the barrier at its end
+          if (etid < 8) {
+            int c_first, c_last;
+            contributors(sp, sg.r, &c_first, &c_last);
+            const int cc = c_first + etid;
+            if (cc <= c_last) sh.cslot[etid] = cc * P.maxseg + seg_of(sp, sg.r, cc);
+            if (etid == 0) {
+              sh.cfirst = c_first;
+              sh.ccount = c_last - c_first + 1;
+            }
+          }
           const bool okw = wait_bar(&sh.seg_full[sl], (uint32_t)((kseg >> 1) & 1), abort_flag, P);
           float2 mv[2];
           mv[0] = okw ? sh.seg[sl][etid] : make_float2(NAN, NAN);
           mv[1] = okw ? sh.seg[sl][etid + 64] : make_float2(NAN, NAN);
           mbar_arrive(&sh.seg_empty[sl]);
-          RowIn rin[2];
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int rl = etid + 64 * h;
-            const int64_t i = (int64_t)sg.r * BM + rl;
-            rin[h].an = 0.f;
-            rin[h].pot = 0.f;
-            rin[h].w = 0.f;
-            if (i < Sd.nA) {
-              Sd.partial[((int64_t)c * P.maxseg + k) * BM + rl] = mv[h];
-              rin[h] = row_inputs(p, i, pot_cur);
-            }
+            if ((int64_t)sg.r * BM + rl < Sd.nA) Sd.partial[((int64_t)c * P.maxseg + k) * BM + rl] = mv[h];
           }
-          int c_first, c_last;
-          contributors(sp, sg.r, &c_first, &c_last);
-          const unsigned long long nc = (unsigned long long)(c_last - c_first + 1);
-          bar_epi();  // all rows' partial stores happen before the arrival
+          bar_epi();  // all rows' partial stores (and the contributor slots) happen before the arrival
+          const int c_first = sh.cfirst, ncc = sh.ccount;
           if (etid == 0) {
             const unsigned long long prev = atom_add_acq_rel_u64(&Sd.cnt[sg.r], 1ull);
-            sh.e_last = (prev + 1 == (unsigned long long)(it + 1) * nc);
+            sh.e_last = (prev + 1 == (unsigned long long)(it + 1) * (unsigned long long)ncc);
           }
           bar_epi();
           if (sh.e_last) {
+            // the other contributors' partials of both rows, loads issued together (this
+            // CTA's own from registers), then combined in CTA order
+            constexpr int kMaxC = 8;
+            float2 pv[2][kMaxC];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int rl = etid + 64 * h;
+#pragma unroll
+              for (int q = 0; q < kMaxC; ++q)
+                if (q < ncc) pv[h][q] = (c_first + q == c) ? mv[h] : __ldcg(&Sd.partial[(int64_t)sh.cslot[q] * BM + rl]);
+            }
             float e[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -675,25 +740,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               const int rl = etid + 64 * h;
               const int64_t i = (int64_t)sg.r * BM + rl;
               if (i < Sd.nA) {
-                constexpr int kMaxC = 8;
-                const int ncc = c_last - c_first + 1;
-                float2 pv[kMaxC];
-#pragma unroll
-                for (int q = 0; q < kMaxC; ++q)
-                  if (q < ncc) {
-                    const int cc = c_first + q;
-                    pv[q] = __ldcg(&Sd.partial[((int64_t)cc * P.maxseg + seg_of(sp, sg.r, cc)) * BM + rl]);
-                  }
                 float2 acc = make_float2(-INFINITY, 0.f);
 #pragma unroll
                 for (int q = 0; q < kMaxC; ++q)
-                  if (q < ncc) acc = lse_combine(acc, pv[q]);
-                for (int cc = c_first + kMaxC; cc <= c_last; ++cc)
-                  acc = lse_combine(acc, __ldcg(&Sd.partial[((int64_t)cc * P.maxseg + seg_of(sp, sg.r, cc)) * BM + rl]));
+                  if (q < ncc) acc = combine_fast(acc, pv[h][q]);
+                for (int q = kMaxC; q < ncc; ++q) {
+                  const int cc = c_first + q;
+                  acc = combine_fast(acc, cc == c ? mv[h]
+                                                  : __ldcg(&Sd.partial[((int64_t)cc * P.maxseg + seg_of(sp, sg.r, cc)) *
+                                                                           BM + rl]));
+                }
                 const float Lr = acc.x + __log2f(acc.y);
                 if (!skip) {
                   float val;
-                  e[h] = row_epilogue(p, i, Lr, rin[h], out, &val);
+                  e[h] = loop_row_potential(Sd, sd, i, Lr, rin[h], out, &val);
                   write_bias_row(bout + i * 16, (val - rin[h].an) * p.bscale);
                 }
               }
@@ -872,6 +932,13 @@ cudaError_t launch_sinkhorn_loop_tc(const LoopLaunch& Lq, cudaStream_t stream) {
     d.R = (int)((s.p.nA + tc::BM - 1) / tc::BM);
     d.T = (int)((s.p.nB + Lq.bn - 1) / Lq.bn);
     d.RB = (int)((s.p.nB + tc::BM - 1) / tc::BM);
+    const double cl = s.p.eps * kLn2, wl = s.p.eps * s.p.log_w_uniform;
+    d.c_hi = (float)cl;
+    d.c_lo = (float)(cl - (double)d.c_hi);
+    d.e_hi = (float)s.p.eps;
+    d.e_lo = (float)(s.p.eps - (double)d.e_hi);
+    d.w_hi = (float)wl;
+    d.w_lo = (float)(wl - (double)d.w_hi);
   }
   P.errpart = Lq.errpart;
   P.state = Lq.state;
