@@ -43,6 +43,13 @@ WORKLOADS = {
 # only while the kernel's sources are the ones captured: their SHA-256 prefix is
 # checked at run time, else traffic is null.
 CAPTURED_TRAFFIC = {
+    # per sweep: one launch of 62 sweeps read 4.66 MB and wrote 0.22 MB (the operands stay
+    # in L2 across the sweeps of a launch)
+    ("sinkhorn_loop_tc", "gmm8_8192_d64", "bf16x3"): dict(
+        bytes=78625.0,
+        sources=("paper_2406_05061_gb300/csrc/loop_tc.cu", "paper_2406_05061_gb300/csrc/sweep_epilogue.cuh",
+                 "paper_2406_05061_gb300/csrc/progot_common.cuh", "paper_2406_05061_gb300/csrc/tc_common.cuh"),
+        sha256=('5ce3235e7f7b4d6f', 'bcfd55d39f4813fc', 'b26a7aa138618011', '735cd6a3dff3d7d7')),
     ("lse_sweep_tc", "gmm8_8192_d64", "bf16x3"): dict(
         bytes=4627456.0,
         sources=("paper_2406_05061_gb300/csrc/sweep_tc.cu", "paper_2406_05061_gb300/csrc/sweep_epilogue.cuh",
@@ -381,6 +388,43 @@ def run_serving(args, rank, world, local):
     return 0
 
 
+def run_sweeps(args, rank, world, local):
+    """Sinkhorn sweeps alone (Alg. 1) at the default workload's size: n = m = 8192, d = 64,
+    bf16x3, a fixed number of iterations (tau = 0, max_iter = --iters) at eps = 0.3 eps0
+    (near the last scheduled step); reports the time per sweep of the loop kernel. A
+    short single-kernel case for profiling."""
+    import torch
+    from paper_2406_05061_gb300 import native
+    torch.cuda.set_device(local)
+    wl = WORKLOADS["gmm8_8192_d64"]
+    p = W.gmm_pair(**wl["gen"])
+    x, y = torch.from_numpy(p.x).cuda(), torch.from_numpy(p.y).cuda()
+    ws = native.Workspace(p.n, p.m, p.d, args.precision)
+    eps = 0.3 * native.progot_mean_cost(x, y, workspace=ws) / 20.0
+    run = lambda: native.sinkhorn_potentials(x, y, eps, 0.0, max_iter=args.iters, precision=args.precision,
+                                             workspace=ws)
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize()
+    native.profile(True, period=1)
+    native.launch_count(reset=True)
+    for _ in range(args.steps):
+        r = run()
+    torch.cuda.synchronize()
+    lse = native.profile_read("lse_sweep")
+    native.profile(False)
+    per_ms = lse["ms"] / max(1, lse["launches"])
+    split = 3.0 if args.precision == "bf16x3" else 1.0
+    tf = 2.0 * p.d * split * p.n * p.m / (per_ms * 1e-3) / 1e12
+    line = {"metric": "sinkhorn_sweep_us", "value": per_ms * 1e3, "unit": "us/sweep", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": False, "dtype": args.precision,
+            "data": "synthetic", "config": {"workload": "sweeps_gmm8192_d64", "n": p.n, "m": p.m, "d": p.d,
+                                            "eps": eps, "iters": r.iters, "sweeps_timed": lse["launches"]},
+            "tflops": tf, "gpu_launches": native.launch_count()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_blur(args, rank, world, local):
     """The de-blurring benchmark of Sec. 5.3 on synthetic images: n grey 32 x 32 images
     (d = 1024) against their Gaussian blurs; by Prop. 3 the optimal coupling is Id / n.
@@ -549,7 +593,8 @@ def main():
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the other precision's solves on the same workload (other_precisions)")
     ap.add_argument("--workload", default="gmm8_8192_d64",
-                    choices=sorted(WORKLOADS) + ["batched256", "serving", "blur", "coupling"])
+                    choices=sorted(WORKLOADS) + ["batched256", "serving", "blur", "coupling", "sweeps"])
+    ap.add_argument("--iters", type=int, default=30, help="sweeps: Sinkhorn iterations per solve")
     ap.add_argument("--blur-n", type=int, default=60000, help="blur: number of images (32 x 32)")
     ap.add_argument("--sigma", type=float, default=2.0, help="blur: kernel width")
     ap.add_argument("--requests", type=int, default=240, help="serving: requests replayed from the stream")
@@ -567,6 +612,8 @@ def main():
         return run_coupling(args, rank, world, local) if rank == 0 else 0
     if args.workload == "blur":
         return run_blur(args, rank, world, local) if rank == 0 else 0
+    if args.workload == "sweeps":
+        return run_sweeps(args, rank, world, local) if rank == 0 else 0
     if args.workload == "serving":
         return run_serving(args, rank, world, local)
 
