@@ -96,6 +96,15 @@ cudaError_t launch_map_sweep_tc(const float* X, float* out, const float* L, int6
                                 float* Opart, float* Rpart, unsigned* cnt, int G, int maxseg, int32_t* fault,
                                 cudaStream_t stream);
 size_t map_sweep_tc_smem();
+// The same for 64 < d <= 256 (map_tc_wide.cu): tiles of 64 columns (B maps and bias rows
+// in 64-row boxes), the X operand resident, one launch per chunk oc of 64 output
+// coordinates (out may alias X; each chunk writes only its coordinates).
+bool map_tc_wide_supported(int nkb);
+cudaError_t launch_map_sweep_tc_wide(const float* X, float* out, const float* L, int64_t nA, int64_t nB, int32_t d,
+                                     int32_t nkb, int32_t oc, float alpha, const void* mapAh, const void* mapAl,
+                                     const void* mapBh, const void* mapBl, const void* mapBbias, float inv_sc,
+                                     const float* mu, float* Opart, float* Rpart, unsigned* cnt, int G, int maxseg,
+                                     int32_t* fault, cudaStream_t stream);
 int tc_stages(int nkb, int split3);
 int tc_tile_cols(int nkb, int split3);  // 128 or 256
 
