@@ -207,12 +207,15 @@ typedef struct progot_problem {
 
 /*
  * progot_solve_batched - Alg. 2 on `count` independent problems of uneven sizes (the
- * batched workload of many small ProgOT problems). The problems run through
- * progot_solve on n_streams internal CUDA streams, each driven by a host worker
+ * batched workload of many small ProgOT problems); the call returns when every problem
+ * is done. With the persistent engine (progot_set_batch_engine, the default where every
+ * problem fits it) the batch runs as one persistent launch on `stream` (see
+ * progot_batch_plan below; n_streams is then unused). Otherwise the problems run
+ * through progot_solve on n_streams internal CUDA streams, each driven by a host worker
  * thread, largest problems first; the internal streams wait for `stream` at entry and
- * `stream` waits for them at exit; the call returns when every problem is done.
- * Results are bit-identical to solving each problem alone (launch shapes depend only on
- * a problem's sizes). workspace: at least progot_batched_workspace_size(...) bytes.
+ * `stream` waits for them at exit, and results are bit-identical to solving each
+ * problem alone (launch shapes depend only on a problem's sizes). workspace: at least
+ * progot_batched_workspace_size(...) bytes (which covers the engine in use).
  * Returns the first hard error of any problem, else PROGOT_ERR_NOT_CONVERGED if any
  * problem did not reach its tau, else PROGOT_OK; per-problem codes in problems[i].status.
  */
@@ -220,6 +223,64 @@ size_t progot_batched_workspace_size(const progot_problem* problems, int32_t cou
                                      int32_t n_streams);
 int progot_solve_batched(progot_problem* problems, int32_t count, int32_t max_iter, int32_t precision,
                          int32_t n_streams, void* workspace, size_t ws_bytes, progot_stream_t stream);
+
+/*
+ * progot_set_batch_engine - how progot_solve_batched runs a batch: 1 (default) = one
+ * persistent launch over all problems (the progot_batch_plan engine below) when every
+ * problem has d <= 64 and the precision is bf16x3 or bf16, else, and with 0, the
+ * per-problem solves on host-driven streams described above (bit-identical to solving
+ * each problem alone). The persistent engine's results match the single-problem path
+ * within the mixed-precision tolerances but not bit for bit (its centre of the operands
+ * is fixed per problem, its column tiles and segments differ); they depend only on the
+ * problem itself, not on the rest of the batch. This library setting has no counterpart
+ * in the paper.
+ */
+int progot_set_batch_engine(int32_t engine);
+
+/*
+ * Persistent batched engine: Alg. 2 (and each step's Alg. 1 loop) for many independent
+ * problems in one persistent launch, tasks of (problem, phase, row block, column
+ * segment) drawn from a device-side work queue by one CTA per SM; a problem's phases
+ * (centre, operand split with warm start, f-updates, g-updates, map step) follow one
+ * another through the queue, different problems interleave.
+ *
+ * progot_batch_plan_workspace_size - device bytes a plan over these problems needs
+ *   (operands, bias rows, potentials, partials, queue; 256-byte aligned internally).
+ * progot_batch_plan_create - validates the problems (device pointers x, y, a, b, x_out,
+ *   g_all, f_last as in progot_solve; host alpha, eps, tau of length K; 1 <= d <= 64;
+ *   n, m <= 2^24; precision PROGOT_BF16X3 or PROGOT_BF16), carves the caller's workspace
+ *   (caller-owned, must stay valid until destroy), encodes the tensor maps and copies
+ *   the descriptors and step constants to the device (synchronous host-to-device
+ *   copies). The problems' device buffers must stay valid for the plan's life; the host
+ *   arrays are read only here. *plan receives the handle.
+ * progot_batch_plan_run - enqueues one solve of the whole batch on `stream`: a counter
+ *   reset, a queue initialisation and the persistent kernel; with use_graph != 0 these
+ *   are captured once into a CUDA graph that every later call replays. Outputs (x_out,
+ *   g_all, f_last) are written by the time the stream reaches the end of the run.
+ * progot_batch_plan_collect - synchronises `stream` and copies the per-step iteration
+ *   counts and errors into problems[i].iters / errs (host, may be NULL) and each
+ *   problem's code into problems[i].status; returns PROGOT_ERR_TIMEOUT if a bounded
+ *   device wait expired, else the first PROGOT_ERR_NUMERIC, else
+ *   PROGOT_ERR_NOT_CONVERGED if any step missed its tau, else PROGOT_OK.
+ * progot_batch_plan_set_target - column segmentation of the sweep tasks: each problem's
+ *   f- and g-updates are cut into at least `target` tasks (segments of a row block's
+ *   column tiles, at most 8 and at most the number of tiles). Not while a run is in
+ *   flight.
+ * progot_batch_plan_autotune - times complete runs of the batch for the targets 1, 4,
+ *   16, 64 and 256 (one warm-up and two timed runs each, on `stream`) and keeps the
+ *   fastest; *target_out and *ms_out (may be NULL) receive it and its time.
+ * progot_batch_plan_destroy - frees the host-side plan and its graph (not the workspace).
+ * This engine is a serving-side device; the paper has no counterpart.
+ */
+typedef struct progot_batch_plan progot_batch_plan;
+size_t progot_batch_plan_workspace_size(const progot_problem* problems, int32_t count, int32_t precision);
+int progot_batch_plan_create(const progot_problem* problems, int32_t count, int32_t max_iter, int32_t precision,
+                             void* workspace, size_t ws_bytes, progot_batch_plan** plan);
+int progot_batch_plan_run(progot_batch_plan* plan, int32_t use_graph, progot_stream_t stream);
+int progot_batch_plan_collect(progot_batch_plan* plan, progot_problem* problems, progot_stream_t stream);
+int progot_batch_plan_set_target(progot_batch_plan* plan, int32_t target);
+int progot_batch_plan_autotune(progot_batch_plan* plan, int32_t* target_out, double* ms_out, progot_stream_t stream);
+void progot_batch_plan_destroy(progot_batch_plan* plan);
 
 /*
  * Continuous-batching server. progot_server_create allocates one device arena of

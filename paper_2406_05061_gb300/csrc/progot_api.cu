@@ -371,6 +371,14 @@ static int make_map(CUtensorMap* map, void* base, int64_t rows, int32_t dp, int 
   return PROGOT_OK;
 }
 
+int encode_operand_map(void* map, void* base, int64_t rows, int32_t dp, int box_rows) {
+  return make_map(reinterpret_cast<CUtensorMap*>(map), base, rows, dp, box_rows);
+}
+int32_t stall_window_setting() { return g_stall_window.load(); }
+unsigned long long wait_limit_setting() { return g_wait_ns.load(); }
+int device_sm_count() { return num_sms(); }
+int fail_message(int code, const char* msg) { return fail(code, "%s", msg); }
+
 struct TcOps {
   // operand maps in the A role (128-row boxes) and the B role (bn-row boxes), bias maps
   // (bn-row boxes); CUtensorMap is 64-byte aligned by its own declaration

@@ -134,6 +134,16 @@ struct LoopLaunch {
   int nkb, split3, bn, G, maxseg, seq0, niter;
 };
 cudaError_t launch_sinkhorn_loop_tc(const LoopLaunch& L, cudaStream_t stream);
+
+// Library settings and helpers shared with the batched engine (progot_api.cu).
+// encode_operand_map: 2-D bf16 tensor map (CUtensorMap*) over a rows x dp row-major
+// buffer, 64-wide 128-byte-swizzled boxes (dp a multiple of 64) or 16-wide 32-byte
+// swizzled bias boxes (dp = 16), box_rows rows per box.
+int encode_operand_map(void* map, void* base, int64_t rows, int32_t dp, int box_rows);
+int32_t stall_window_setting();
+unsigned long long wait_limit_setting();
+int device_sm_count();
+int fail_message(int code, const char* msg);  // sets the last-error text, returns code
 cudaError_t launch_fill_u32(uint32_t* p, int64_t n, uint32_t v, cudaStream_t s);
 bool loop_tc_supported(int bn, int nkb, int split3);
 void loop_tc_plan(int64_t n, int64_t m, int bn, int sms, int* G, int* maxseg);

@@ -46,16 +46,39 @@ static size_t slice_bytes(const progot_problem* probs, int32_t count, int32_t pr
   return round_up256(progot_workspace_size(n, m, d, precision));
 }
 
+// Engine of progot_solve_batched: 1 = one persistent launch over the whole batch
+// (batch_tc.cu) when every problem fits it, 0 = per-problem solves on host-driven streams.
+static std::atomic<int> g_batch_engine{1};
+
+static bool persistent_eligible(const progot_problem* probs, int32_t count, int32_t precision) {
+  if (precision != PROGOT_BF16X3 && precision != PROGOT_BF16) return false;
+  for (int i = 0; i < count; ++i)
+    if (probs[i].d > 64 || probs[i].n > ((int64_t)1 << 24) || probs[i].m > ((int64_t)1 << 24)) return false;
+  return true;
+}
+
 }  // namespace progot
 
 using namespace progot;
 
 extern "C" {
 
+int progot_set_batch_engine(int32_t engine) {
+  if (engine != 0 && engine != 1) {
+    set_last_error_message("engine must be 0 (streams) or 1 (persistent)");
+    return PROGOT_ERR_INVALID_ARG;
+  }
+  g_batch_engine.store(engine);
+  return PROGOT_OK;
+}
+
 size_t progot_batched_workspace_size(const progot_problem* problems, int32_t count, int32_t precision,
                                      int32_t n_streams) {
   if (problems == nullptr || count <= 0 || n_streams <= 0) return 0;
-  return slice_bytes(problems, count, precision) * (size_t)n_streams + 256;
+  size_t need = slice_bytes(problems, count, precision) * (size_t)n_streams + 256;
+  if (g_batch_engine.load() == 1 && persistent_eligible(problems, count, precision))
+    need = std::max(need, progot_batch_plan_workspace_size(problems, count, precision));
+  return need;
 }
 
 int progot_solve_batched(progot_problem* problems, int32_t count, int32_t max_iter, int32_t precision,
@@ -70,6 +93,17 @@ int progot_solve_batched(progot_problem* problems, int32_t count, int32_t max_it
       set_last_error_message("a problem has a NULL pointer or a non-positive size");
       return PROGOT_ERR_INVALID_ARG;
     }
+  }
+  if (g_batch_engine.load() == 1 && persistent_eligible(problems, count, precision) &&
+      ws_bytes >= progot_batch_plan_workspace_size(problems, count, precision)) {
+    // one persistent launch over the whole batch
+    progot_batch_plan* plan = nullptr;
+    int rc = progot_batch_plan_create(problems, count, max_iter, precision, workspace, ws_bytes, &plan);
+    if (rc) return rc;
+    rc = progot_batch_plan_run(plan, 0, stream);
+    if (!rc) rc = progot_batch_plan_collect(plan, problems, stream);
+    progot_batch_plan_destroy(plan);
+    return rc;
   }
   const size_t slice = slice_bytes(problems, count, precision);
   if (ws_bytes < slice * (size_t)n_streams) {

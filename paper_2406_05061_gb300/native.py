@@ -61,6 +61,14 @@ SIGNATURES = [
     ("progot_launch_count", ctypes.c_int64, [_I32]),
     ("progot_batched_workspace_size", _SZ, [_P, _I32, _I32, _I32]),
     ("progot_solve_batched", ctypes.c_int, [_P, _I32, _I32, _I32, _I32, _P, _SZ, _P]),
+    ("progot_set_batch_engine", ctypes.c_int, [_I32]),
+    ("progot_batch_plan_workspace_size", _SZ, [_P, _I32, _I32]),
+    ("progot_batch_plan_create", ctypes.c_int, [_P, _I32, _I32, _I32, _P, _SZ, _P]),
+    ("progot_batch_plan_run", ctypes.c_int, [_P, _I32, _P]),
+    ("progot_batch_plan_collect", ctypes.c_int, [_P, _P, _P]),
+    ("progot_batch_plan_set_target", ctypes.c_int, [_P, _I32]),
+    ("progot_batch_plan_autotune", ctypes.c_int, [_P, _P, _P, _P]),
+    ("progot_batch_plan_destroy", None, [_P]),
     ("progot_server_create", ctypes.c_void_p, [_SZ, _I32, _I32, _I32]),
     ("progot_server_submit", ctypes.c_int64, [_P, _P]),
     ("progot_server_wait", ctypes.c_int, [_P, _I64, _P]),
@@ -629,10 +637,8 @@ def _problem_struct(x, y, alpha, eps, tau, x_out, g_all, f_last=None, a=None, b=
     return s, holder
 
 
-def progot_solve_batched(problems, max_iter=10000, precision="bf16x3", n_streams=8, stream=None):
-    """Solve a list of problems (dicts with x, y CUDA tensors and alpha, eps, tau) together.
-
-    Returns a list of dicts with x_out, g_all, f_last, iters, errs, status per problem."""
+def _batch_structs(problems):
+    """ProblemStruct array and output holders for a list of problem dicts (CUDA tensors)."""
     torch = _torch()
     keep = []
     arr = (ProblemStruct * len(problems))()
@@ -647,6 +653,25 @@ def progot_solve_batched(problems, max_iter=10000, precision="bf16x3", n_streams
         arr[i], holder = _problem_struct(x, y, pr["alpha"], pr["eps"], pr["tau"], x_out, g_all, f_last,
                                          pr.get("a"), pr.get("b"), keep)
         outs.append(holder)
+    return arr, outs
+
+
+def _batch_results(arr, outs):
+    return [dict(x_out=h["x_out"], g_all=h["g_all"], f_last=h["f_last"], iters=h["iters"].tolist(),
+                 errs=h["errs"].tolist(), status=int(arr[i].status)) for i, h in enumerate(outs)]
+
+
+def set_batch_engine(engine: str):
+    """'persistent' (one launch over the batch, the default) or 'streams' (per-problem solves)."""
+    _check(lib().progot_set_batch_engine({"streams": 0, "persistent": 1}[engine]))
+
+
+def progot_solve_batched(problems, max_iter=10000, precision="bf16x3", n_streams=8, stream=None):
+    """Solve a list of problems (dicts with x, y CUDA tensors and alpha, eps, tau) together.
+
+    Returns a list of dicts with x_out, g_all, f_last, iters, errs, status per problem."""
+    torch = _torch()
+    arr, outs = _batch_structs(problems)
     L = lib()
     pc = _prec(precision)
     ws_bytes = int(L.progot_batched_workspace_size(arr, len(problems), pc, n_streams))
@@ -654,8 +679,56 @@ def progot_solve_batched(problems, max_iter=10000, precision="bf16x3", n_streams
     rc = L.progot_solve_batched(arr, len(problems), int(max_iter), pc, int(n_streams), ctypes.c_void_p(ws.data_ptr()),
                                 ws_bytes + 256, _stream(stream))
     _check(rc)
-    return [dict(x_out=h["x_out"], g_all=h["g_all"], f_last=h["f_last"], iters=h["iters"].tolist(),
-                 errs=h["errs"].tolist(), status=int(arr[i].status)) for i, h in enumerate(outs)]
+    return _batch_results(arr, outs)
+
+
+class BatchPlan:
+    """A batch of problems prepared once for repeated persistent solves (progot_batch_plan_*
+    in include/progot.h): run() enqueues one solve of the whole batch (a CUDA graph replay
+    by default), collect() waits and returns the per-problem results."""
+
+    def __init__(self, problems, max_iter=10000, precision="bf16x3"):
+        torch = _torch()
+        self._arr, self._outs = _batch_structs(problems)
+        L = lib()
+        pc = _prec(precision)
+        n = len(problems)
+        ws_bytes = int(L.progot_batch_plan_workspace_size(self._arr, n, pc))
+        self._ws = torch.empty(ws_bytes + 256, dtype=torch.uint8, device="cuda")
+        h = ctypes.c_void_p()
+        _check(L.progot_batch_plan_create(self._arr, n, int(max_iter), pc, ctypes.c_void_p(self._ws.data_ptr()),
+                                          ws_bytes + 256, ctypes.byref(h)))
+        self._h = h
+
+    def run(self, graph=True, stream=None):
+        _check(lib().progot_batch_plan_run(self._h, 1 if graph else 0, _stream(stream)))
+
+    def collect(self, stream=None, check=True):
+        rc = int(lib().progot_batch_plan_collect(self._h, self._arr, _stream(stream)))
+        if check:
+            _check(rc)
+        return _batch_results(self._arr, self._outs)
+
+    def set_target(self, target: int):
+        _check(lib().progot_batch_plan_set_target(self._h, int(target)))
+
+    def autotune(self, stream=None):
+        """Time complete runs for each segmentation target; keep and return the fastest (target, ms)."""
+        t = ctypes.c_int32(0)
+        ms = ctypes.c_double(0.0)
+        _check(lib().progot_batch_plan_autotune(self._h, ctypes.byref(t), ctypes.byref(ms), _stream(stream)))
+        return int(t.value), float(ms.value)
+
+    def close(self):
+        if self._h:
+            lib().progot_batch_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

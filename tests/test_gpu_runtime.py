@@ -57,7 +57,11 @@ def test_batched_equals_single(nat, precision, tau):
     for p in probs:
         al, eps = schedule(p, K)
         specs.append(dict(x=dev(p.x), y=dev(p.y), alpha=al, eps=eps, tau=[tau] * K))
-    res = nat.progot_solve_batched(specs, max_iter=5000, precision=precision, n_streams=4)
+    nat.set_batch_engine("streams")  # the per-problem engine is the bit-identical one
+    try:
+        res = nat.progot_solve_batched(specs, max_iter=5000, precision=precision, n_streams=4)
+    finally:
+        nat.set_batch_engine("persistent")
     for sp, r in zip(specs, res):
         assert r["status"] == nat.PROGOT_OK
         solo = nat.progot_solve(sp["x"], sp["y"], sp["alpha"], sp["eps"], sp["tau"], max_iter=5000, precision=precision)
