@@ -6,10 +6,10 @@
 //   MOM    (x and y row blocks)  column sums of both clouds; the phase's finisher sets the
 //                                problem's centre mu = (mean x + mean y) / 2 and copies x
 //                                into the working cloud X (= x_out);
-//   SPLIT  (x and y row blocks)  step k's operands: sqrt(c_k) (v - mu) as bf16 hi/lo (K
-//                                padded to 64), the centred squared norms, the warm start
-//                                (1 - alpha_k) f, g^(k) = (1 - alpha_k) g^(k-1), and the
-//                                bias rows of g;
+//   SPLIT  (x and y row blocks)  step k's operands: c_k (x - mu) as bf16 hi/lo (K padded
+//                                to 64) and |x - mu|^2, (y - mu) and |y - mu|^2 at the
+//                                first step only, the warm start (1 - alpha_k) f,
+//                                g^(k) = (1 - alpha_k) g^(k-1), and the bias rows of g;
 //   FUP    (x row block, column segment)   the f-update of Alg. 1, its row-marginal
 //                                error measured at the current f; the finisher applies the
 //                                stop test (err <= tau, max_iter, a stall, a non-finite
@@ -19,9 +19,10 @@
 //                                with T_i = sum_j 2^{t_ij - L_i} y_j / sum_j 2^{t_ij - L_i}
 //                                and L_i from the last f-update (whose g is the final g).
 // The last task of a phase (an arrival counter) runs the phase's finish and appends the
-// next phase's tasks to one device-wide queue (a ring of task slots with per-slot
-// sequence words, reserved with atomics). Persistent CTAs, one per SM, pop tasks in
-// order. A task never waits for another CTA: what it reads was written by an earlier
+// next phase's tasks to a device-wide queue of eight priority levels (rings of task slots
+// with per-slot sequence words, reserved with atomics), at the level of the problem's
+// estimated remaining chain, so that the problems that need the most iterations are not
+// held up behind the others. Persistent CTAs, one per SM, pop the most urgent task. A task never waits for another CTA: what it reads was written by an earlier
 // phase of its own problem, published through the queue (release on the slot's sequence
 // word, acquire by the popping CTA, proxy fences around the TMA reads). The problems'
 // phases interleave, so while one problem waits for its phase's last task the other
@@ -29,9 +30,10 @@
 // (segments per row block, set per problem from a tuned target of tasks per phase) lets
 // the last large problems spread over the GPU.
 //
-// Arithmetic per task is that of the single-problem tensor-core path: t_ij = c (x~_i .
-// y~_j) + beta_j in log2 units from three bf16 products of the pre-scaled, centred hi/lo
-// operands plus one K = 16 product of ones with the three-way bf16 split of beta_j,
+// Arithmetic per task follows the single-problem tensor-core path: t_ij = c (x~_i . y~_j)
+// + beta_j in log2 units from three bf16 products of centred hi/lo operands (here the
+// scale c = 2 log2(e) / eps_k sits in the x operand alone, so the y operand is split once
+// per problem) plus one K = 16 product of ones with the three-way bf16 split of beta_j,
 // float32 online log-sum-exp per row, a deterministic combine of the column segments in
 // segment order, the potential f_i = eps log w_i + |x~_i|^2 - eps ln2 L_i in float32 FMAs
 // on a hi/lo split of eps ln2, and P Y~ on the tensor cores for the map. A problem's
@@ -68,12 +70,13 @@ namespace bat {
 constexpr int NTHREADS = 384;
 constexpr int EPI_TID0 = 320;
 constexpr int NST = 3;          // operand stages
-constexpr int NTQ = 4;          // task ring
+constexpr int NTQ = 2;          // task ring: the producer holds at most one task beyond the ones in work
 constexpr int TMEM_COLS = 512;  // S buffers at [0, 128) and [128, 256), map accumulator O at [256, 320)
 constexpr uint32_t O_COL = 256;
 constexpr int SW_BN = 128;      // sweep tile columns
 constexpr int MP_BN = 64;       // map tile columns
 constexpr int kMaxSegs = 8;
+constexpr int kLevels = 8;      // priority levels of the task queue (0 = most urgent)
 // Limit of the idle waits (a CTA waiting for the next task to exist): a CTA can sit idle
 // for as long as the last phases of the slowest problem take, so this limit is longer
 // than the pipeline waits' (which a task's own work bounds).
@@ -96,7 +99,7 @@ enum MapIdx : int32_t { kXh = 0, kXl, kYh, kYl, kXb, kYb, kYh64, kYl64, kYb64, k
 // Constants of step k of one problem (host-computed from eps_k, alpha_k, tau_k).
 struct StepC {
   double tau;
-  float sc, inv_sc;     // sqrt(c) and 1 / sqrt(c), c = 2 log2(e) / eps
+  float c;             // c = 2 log2(e) / eps, the scale of the x operand
   float bscale;         // log2(e) / eps
   float inv_eps_f;      // 1 / eps
   float c_hi, c_lo;     // eps ln2 = c_hi + c_lo
@@ -144,11 +147,11 @@ struct Prob {
 
 struct Params {
   const Prob* probs;
-  int4* qslots;              // task = (problem, kind, row block, segment or side)
-  unsigned long long* qseq;  // per-slot sequence words
-  unsigned long long* qhead;
-  unsigned long long* qtail;
-  unsigned long long qmask;  // ring size - 1 (a power of two)
+  int4* qslots;              // [kLevels][Q] task = (problem, kind, row block, segment or side)
+  unsigned long long* qseq;  // [kLevels][Q] per-slot sequence words
+  unsigned long long* qctl;  // level l: head at [64 l], tail at [64 l + 16], count of published
+                             // unclaimed tasks (signed) at [64 l + 32], each on its own 128-byte line
+  unsigned long long qmask;  // ring size Q - 1 (a power of two)
   unsigned* remaining;       // problems not finished
   int32_t* fault;
   unsigned long long wait_ns;
@@ -171,6 +174,8 @@ struct Shared {
   float ered[4];
   float2 ms[2][128];
   float2 seg[2][128];
+  float mu_s[64];   // the centre for the map task's update (written after a barrier of the task)
+  float mu_sp[64];  // the centre for the split task (its own array: written before the task's first barrier)
 };
 static_assert(offsetof(Shared, tq) % 16 == 0, "task slots");
 constexpr size_t SMEM_TOTAL = OFF_CTRL + sizeof(Shared) + 1024;
@@ -301,9 +306,10 @@ __device__ __forceinline__ void split8(const float* v, uint4& hi, uint4& lo) {
   lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-// Named barriers: 1 = both LSE warpgroups (256), 3 = epilogue warps (64).
+// Named barriers: 1 = both LSE warpgroups (256), 2 = LSE warpgroup 0 (128), 3 = epilogue warps (64).
 __device__ __forceinline__ void bar_lse_all() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 __device__ __forceinline__ void bar_epi() { asm volatile("bar.sync 3, 64;" ::: "memory"); }
+__device__ __forceinline__ void bar_wg0() { asm volatile("bar.sync 2, 128;" ::: "memory"); }
 
 // Column tiles [t0, t1) of a sweep or map task.
 __device__ __forceinline__ void task_tiles(const Prob& pr, int4 t, int* t0, int* t1) {
@@ -318,47 +324,82 @@ __device__ __forceinline__ void task_tiles(const Prob& pr, int4 t, int* t0, int*
   *t1 = (int)((int64_t)(t.w + 1) * T / segs);
 }
 
-// Pop the next task (one lane): reserve a position, wait (bounded) until its slot is
-// published, read it and hand the slot back to the producer one ring length later.
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Pop the next task (one lane). Each level counts its published, unclaimed tasks; a
+// consumer claims one by decrementing the count of the most urgent level that shows
+// some (undoing the decrement if it lost the race), and only then reserves the level's
+// next position with one atomic add, so no consumer ever holds a position without a
+// task and no compare-and-swap retries pile up on one word. The slot goes back to the
+// producers one ring length later. Bounded (kIdleNs) and left early when the grid has
+// faulted.
 __device__ bool queue_pop(const Params& P, int4* t, volatile int32_t* abort_flag) {
-  const unsigned long long pos = atomicAdd(P.qhead, 1ull);
-  unsigned long long* seq = P.qseq + (pos & P.qmask);
-  if (ld_acq_u64(seq) != pos + 1) {
-    const unsigned long long t0 = global_ns();
-    for (uint32_t i = 1;; ++i) {
-      if (ld_acq_u64(seq) == pos + 1) break;
-      if ((i & 7) == 0) {
-        if (*abort_flag || grid_fault(P)) {
-          *abort_flag = 1;
-          return false;
+  const unsigned long long Q = P.qmask + 1ull;
+  const unsigned long long t0 = global_ns();
+  for (uint32_t i = 0;; ++i) {
+    long long av[kLevels];
+#pragma unroll
+    for (int l = 0; l < kLevels; ++l) av[l] = (long long)ld_relaxed_u64(P.qctl + 64 * l + 32);
+    int lv = -1;
+#pragma unroll
+    for (int l = kLevels - 1; l >= 0; --l)
+      if (av[l] > 0) lv = l;
+    if (lv >= 0) {
+      unsigned long long* avail = P.qctl + 64 * lv + 32;
+      if ((long long)atomicAdd(avail, ~0ull) > 0) {
+        const unsigned long long pos = atomicAdd(P.qctl + 64 * lv, 1ull);
+        const unsigned long long idx = (unsigned long long)lv * Q + (pos & P.qmask);
+        unsigned long long* seq = P.qseq + idx;
+        // a claimed position's task is published (by its enqueuer, which never waits) at
+        // the latest shortly after the count announced it
+        const unsigned long long tw = global_ns();
+        for (uint32_t j = 0; ld_acq_u64(seq) != pos + 1ull; ++j) {
+          if ((j & 15) == 15 && global_ns() - tw > P.wait_ns) {
+            *abort_flag = 1;
+            atomicExch(P.fault, 1);
+            return false;
+          }
         }
-        if (global_ns() - t0 > kIdleNs) {
-          *abort_flag = 1;
-          atomicExch(P.fault, 1);
-          return false;
-        }
+        *t = __ldcg(P.qslots + idx);
+        st_rel_u64(seq, pos + Q);
+        return true;
       }
-      __nanosleep(128);
+      atomicAdd(avail, 1ull);  // lost the race for the last one: undo and look again
+      continue;
     }
+    if ((i & 7) == 7) {
+      if (*abort_flag || grid_fault(P)) {
+        *abort_flag = 1;
+        return false;
+      }
+      if (global_ns() - t0 > kIdleNs) {
+        *abort_flag = 1;
+        atomicExch(P.fault, 1);
+        return false;
+      }
+    }
+    __nanosleep(64);
   }
-  *t = __ldcg(P.qslots + (pos & P.qmask));
-  st_rel_u64(seq, pos + P.qmask + 1);
-  return true;
 }
 
 // Append n tasks (a full warp): lane 0 reserves positions, each lane publishes its
 // tasks. The ring holds every task that can be outstanding, so a slot is always free;
 // the wait for it is bounded all the same.
 template <class F>
-__device__ bool enqueue_warp(const Params& P, int n, F make, volatile int32_t* abort_flag) {
+__device__ bool enqueue_warp(const Params& P, int level, int n, F make, volatile int32_t* abort_flag) {
   const int lane = threadIdx.x & 31;
+  const unsigned long long base = (unsigned long long)level * (P.qmask + 1ull);
   unsigned long long pos0 = 0;
-  if (lane == 0) pos0 = atomicAdd(P.qtail, (unsigned long long)n);
+  if (lane == 0) pos0 = atomicAdd(P.qctl + 64 * level + 16, (unsigned long long)n);
   pos0 = __shfl_sync(0xffffffffu, pos0, 0);
   bool ok = true;
   for (int i = lane; i < n && ok; i += 32) {
     const unsigned long long pos = pos0 + (unsigned long long)i;
-    unsigned long long* seq = P.qseq + (pos & P.qmask);
+    unsigned long long* seq = P.qseq + base + (pos & P.qmask);
     if (ld_acq_u64(seq) != pos) {
       const unsigned long long t0 = global_ns();
       for (uint32_t it = 1;; ++it) {
@@ -372,10 +413,13 @@ __device__ bool enqueue_warp(const Params& P, int n, F make, volatile int32_t* a
       }
       if (!ok) break;
     }
-    P.qslots[pos & P.qmask] = make(i);
+    P.qslots[base + (pos & P.qmask)] = make(i);
     st_rel_u64(seq, pos + 1);
   }
-  return __all_sync(0xffffffffu, ok) != 0;
+  ok = __all_sync(0xffffffffu, ok) != 0;
+  // announce the tasks once all are published
+  if (lane == 0 && ok) atomicAdd(P.qctl + 64 * level + 32, (unsigned long long)n);
+  return ok;
 }
 
 // Task of ring position idx, read by a whole warp (lane 0 hands the slot back).
@@ -423,17 +467,29 @@ __device__ void task_mom(const Prob& pr, int rb, int side, unsigned char* smem) 
   const int d = pr.d;
   const int64_t rows = side ? pr.m : pr.n;
   const float* src = side ? pr.y : pr.x;
-  double a0 = 0.0, a1 = 0.0;
+  // all loads of the warp's 16 rows first (they are independent), then sums and copies
+  float v0[16], v1[16];
+#pragma unroll
   for (int q = 0; q < 16; ++q) {
     const int64_t row = (int64_t)rb * BM + lw + 8 * q;
-    if (row >= rows) break;
-    const float v0 = lane < d ? src[row * d + lane] : 0.f;
-    const float v1 = lane + 32 < d ? src[row * d + lane + 32] : 0.f;
-    a0 += (double)v0;
-    a1 += (double)v1;
-    if (side == 0) {
-      if (lane < d) pr.X[row * d + lane] = v0;
-      if (lane + 32 < d) pr.X[row * d + lane + 32] = v1;
+    const bool ok = row < rows;
+    v0[q] = ok && lane < d ? src[row * d + lane] : 0.f;
+    v1[q] = ok && lane + 32 < d ? src[row * d + lane + 32] : 0.f;
+  }
+  double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    a0 += (double)v0[q];
+    a1 += (double)v1[q];
+  }
+  if (side == 0) {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int64_t row = (int64_t)rb * BM + lw + 8 * q;
+      if (row < rows) {
+        if (lane < d) pr.X[row * d + lane] = v0[q];
+        if (lane + 32 < d) pr.X[row * d + lane + 32] = v1[q];
+      }
     }
   }
   // the map P tile's memory holds the reduction: warpgroup 0 reaches this barrier only
@@ -450,52 +506,99 @@ __device__ void task_mom(const Prob& pr, int rb, int side, unsigned char* smem) 
   }
 }
 
-// SPLIT: step k's operand rows sqrt(c) (v - mu) in bf16 hi/lo, centred norms, warm start
-// and (y side) the bias rows of g; bias rows of padding rows are -inf.
-__device__ void task_split(const Prob& pr, int rb, int side, int split3) {
-  const int ltid = threadIdx.x - 64, lw = ltid >> 5, lane = threadIdx.x & 31;
+// Squared norm sum_c u_c^2 of up to 32 values in float32 without rounding loss: each
+// square's exact value is p + e (p = u u rounded, e = fma(u, u, -p)), and the terms are
+// accumulated as an unevaluated float pair with Knuth's TwoSum (about 48 bits, more than
+// the float32 norm keeps), which the float64 pipe, a small fraction of the float32 rate
+// on this GPU, would otherwise have to do.
+__device__ __forceinline__ void sq_sum_pair(const float* u, int nv, float& hi, float& lo) {
+  hi = 0.f;
+  lo = 0.f;
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    if (c < nv) {
+      const float pr = u[c] * u[c];
+      const float er = fmaf(u[c], u[c], -pr);
+      const float sm = hi + pr;
+      const float bb = sm - hi;
+      const float ts = (hi - (sm - bb)) + (pr - bb);
+      hi = sm;
+      lo += ts + er;
+    }
+  }
+}
+
+// SPLIT: step k's operands, thread = (row, half of the 64 coordinates). x side, every
+// step: c_k (x - mu) as bf16 hi/lo (K padded to 64), |x - mu|^2, the warm start
+// (1 - alpha_k) f. y side: (y - mu) as bf16 hi/lo and |y - mu|^2 once (k = 0; neither
+// depends on eps, the scale c_k sits in the x operand), every step the warm start
+// g^(k) = (1 - alpha_k) g^(k-1) and the bias rows of g. Bias rows of padding rows are -inf.
+__device__ void task_split(const Prob& pr, int rb, int side, int split3, float* mu_s, double* nrm_s) {
+  const int ltid = threadIdx.x - 64;
+  const int r = ltid & 127, h = ltid >> 7;
   const int d = pr.d;
   const int k = __ldcg(&pr.st->k);
   const StepC& C = pr.sc[k];
   const int64_t rows = side ? pr.m : pr.n;
   const int64_t rows_pad = (int64_t)(side ? pr.Ry : pr.Rx) * BM;
-  const float* src = side ? pr.y : pr.X;
-  __nv_bfloat16* hi = side ? pr.yh : pr.xh;
-  __nv_bfloat16* lo = side ? pr.yl : pr.xl;
-  __nv_bfloat16* bias = side ? pr.yb : pr.xb;
+  const int64_t row = (int64_t)rb * BM + r;
+  const bool operands = side == 0 || k == 0;
+  if (operands && ltid < 64) mu_s[ltid] = __ldcg(pr.mu + ltid);
+  // after this barrier the map task before (if any) has finished its products, so the
+  // P tile's memory may hold the half-row norms below
+  bar_lse_all();
   float* nrm = side ? pr.yn : pr.xn;
-  float* fc = pr.f[__ldcg(&pr.st->fcur)];
-  const float mu0 = __ldcg(pr.mu + lane), mu1 = __ldcg(pr.mu + lane + 32);
-  for (int q = 0; q < 16; ++q) {
-    const int64_t row = (int64_t)rb * BM + lw + 8 * q;
-    if (row < rows) {
-      const float u0 = lane < d ? __ldcg(src + row * d + lane) - mu0 : 0.f;
-      const float u1 = lane + 32 < d ? __ldcg(src + row * d + lane + 32) - mu1 : 0.f;
-      double s = (double)u0 * (double)u0;
-      s += (double)u1 * (double)u1;
-      const float v0 = u0 * C.sc, v1 = u1 * C.sc;
-      const __nv_bfloat16 h0 = __float2bfloat16_rn(v0), h1 = __float2bfloat16_rn(v1);
-      hi[row * 64 + lane] = h0;
-      hi[row * 64 + lane + 32] = h1;
-      if (split3) {
-        lo[row * 64 + lane] = __float2bfloat16_rn(v0 - __bfloat162float(h0));
-        lo[row * 64 + lane + 32] = __float2bfloat16_rn(v1 - __bfloat162float(h1));
-      }
+  if (operands) {
+    const float* src = side ? pr.y : pr.X;
+    __nv_bfloat16* hi = side ? pr.yh : pr.xh;
+    __nv_bfloat16* lo = side ? pr.yl : pr.xl;
+    const float scale = side ? 1.f : C.c;
+    const int c0 = 32 * h;
+    const int nv = min(32, max(0, d - c0));  // coordinates of this half inside the cloud
+    float u[32];
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-      if (lane == 0) {
-        const float nr = (float)s;
-        nrm[row] = nr;
-        if (side) {
-          const float gk = k ? C.keep * __ldcg(pr.g_all + (int64_t)(k - 1) * pr.m + row) : 0.f;
-          pr.g_all[(int64_t)k * pr.m + row] = gk;
-          write_bias16(bias + row * 16, (gk - nr) * C.bscale);
-        } else {
-          fc[row] = k ? C.keep * __ldcg(fc + row) : 0.f;
-        }
+    for (int c = 0; c < 32; ++c) u[c] = (row < rows && c < nv) ? __ldcg(src + row * d + c0 + c) : 0.f;
+#pragma unroll
+    for (int c = 0; c < 32; ++c) u[c] = c < nv ? u[c] - mu_s[c0 + c] : 0.f;
+    float shi, slo;
+    sq_sum_pair(u, nv, shi, slo);
+    if (row < rows) {
+      uint32_t hw[16], lw[16];
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        const __nv_bfloat162 hh = __floats2bfloat162_rn(u[2 * e] * scale, u[2 * e + 1] * scale);
+        const float2 hf = __bfloat1622float2(hh);
+        const __nv_bfloat162 ll = __floats2bfloat162_rn(u[2 * e] * scale - hf.x, u[2 * e + 1] * scale - hf.y);
+        hw[e] = bf2_bits(hh);
+        lw[e] = bf2_bits(ll);
       }
-    } else if (row < rows_pad && lane == 0) {
-      write_bias16(bias + row * 16, -INFINITY);
+      uint4* dh = reinterpret_cast<uint4*>(hi + row * 64 + c0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) dh[q] = make_uint4(hw[4 * q], hw[4 * q + 1], hw[4 * q + 2], hw[4 * q + 3]);
+      if (split3) {
+        uint4* dl = reinterpret_cast<uint4*>(lo + row * 64 + c0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dl[q] = make_uint4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
+      }
+    }
+    if (h == 1) nrm_s[r] = (double)shi + (double)slo;
+    bar_lse_all();
+    if (h == 0 && row < rows) nrm[row] = (float)(((double)shi + (double)slo) + nrm_s[r]);
+  }
+  if (h == 0) {
+    if (row < rows) {
+      if (side) {
+        const float gk = k ? C.keep * __ldcg(pr.g_all + (int64_t)(k - 1) * pr.m + row) : 0.f;
+        pr.g_all[(int64_t)k * pr.m + row] = gk;
+        // the norm: this thread's own store above, or an earlier step's
+        const float nr = __ldcg(nrm + row);
+        write_bias16(pr.yb + row * 16, (gk - nr) * C.bscale);
+      } else {
+        float* fc = pr.f[__ldcg(&pr.st->fcur)];
+        fc[row] = k ? C.keep * __ldcg(fc + row) : 0.f;
+      }
+    } else if (row < rows_pad) {
+      write_bias16((side ? pr.yb : pr.xb) + row * 16, -INFINITY);
     }
   }
 }
@@ -568,28 +671,49 @@ __device__ void phase_finish(const Params& P, const Prob& pr, int pi, int kind, 
     kn = __shfl_sync(0xffffffffu, kn, 0);
     next = kn < pr.K ? kSplit : kExit;
   }
+  // queue level of the next phase from the problem's estimated remaining chain (what
+  // decides when it finishes): the phases left (the steps left at the mean iteration
+  // count of its finished steps, a guess before the first, and the rest of the current
+  // step, which once past the mean is taken to need as many iterations again; two
+  // sweeps per iteration and three more phases per step) times a phase's latency (a
+  // fixed part plus the column tiles of one sweep task), one level per factor of two
+  int level = kLevels - 1;
+  if (next != kExit) {
+    if (lane == 0) {
+      const int kc = __ldcg(&st->k), itc = __ldcg(&st->it);
+      double sum = 0.0;
+      for (int q = 0; q < kc; ++q) sum += (double)__ldcg(pr.iters + q);
+      const double avg = kc > 0 ? sum / kc : 24.0;
+      const double cur = fmax(fmax(avg - itc, (double)itc), 1.0);
+      const double phases = (double)(pr.K - kc - 1) * (2.0 * avg + 3.0) + 2.0 * cur + 2.0;
+      const double tiles = fmax((double)pr.Ty / pr.segs_f, (double)pr.Tx / pr.segs_g);
+      const double us = phases * (10.0 + 0.6 * tiles);
+      level = min(kLevels - 1, max(0, 14 - ilogb(fmax(us, 1.0))));
+    }
+    level = __shfl_sync(0xffffffffu, level, 0);
+  }
   __threadfence();
   __syncwarp();
   if (next == kSplit) {
     const int nx = pr.Rx;
-    enqueue_warp(P, pr.Rx + pr.Ry,
+    enqueue_warp(P, level, pr.Rx + pr.Ry,
                  [&](int i) { return i < nx ? make_int4(pi, kSplit, i, 0) : make_int4(pi, kSplit, i - nx, 1); },
                  abort_flag);
   } else if (next == kFup) {
     const int s = pr.segs_f;
-    enqueue_warp(P, pr.Rx * s, [&](int i) { return make_int4(pi, kFup, i / s, i % s); }, abort_flag);
+    enqueue_warp(P, level, pr.Rx * s, [&](int i) { return make_int4(pi, kFup, i / s, i % s); }, abort_flag);
   } else if (next == kGup) {
     const int s = pr.segs_g;
-    enqueue_warp(P, pr.Ry * s, [&](int i) { return make_int4(pi, kGup, i / s, i % s); }, abort_flag);
+    enqueue_warp(P, level, pr.Ry * s, [&](int i) { return make_int4(pi, kGup, i / s, i % s); }, abort_flag);
   } else if (next == kMap) {
-    enqueue_warp(P, pr.Rx, [&](int i) { return make_int4(pi, kMap, i, 0); }, abort_flag);
+    enqueue_warp(P, level, pr.Rx, [&](int i) { return make_int4(pi, kMap, i, 0); }, abort_flag);
   } else {
     // the problem is done; the last one releases every CTA with an exit task
     unsigned prev = 0;
     if (lane == 0) prev = atom_sub_acq_rel_u32(P.remaining, 1u);
     prev = __shfl_sync(0xffffffffu, prev, 0);
     if (prev == 1u)
-      enqueue_warp(P, (int)gridDim.x, [&](int) { return make_int4(-1, kExit, 0, 0); }, abort_flag);
+      enqueue_warp(P, kLevels - 1, (int)gridDim.x, [&](int) { return make_int4(-1, kExit, 0, 0); }, abort_flag);
   }
 }
 
@@ -964,6 +1088,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) progot_batch_tc(const Params P) {
         bar_lse_all();
         if (wg == 0) {
           rs += sh.ms[kt & 1][row_local].x;
+          // the centre in shared memory (its reads below cannot alias the stores of x)
+          if (row_local < 64) sh.mu_s[row_local] = __ldcg(pr.mu + row_local);
+          bar_wg0();
           float o[2][32];
           const bool okv = !dead && warp_wait_bar(&sh.o_full, (uint32_t)(mt & 1), abort_flag, P);
           if (okv) {
@@ -979,17 +1106,25 @@ __global__ void __launch_bounds__(NTHREADS, 1) progot_batch_tc(const Params P) {
             dead = true;
           }
           if (okv && row_ok) {
-            // x <- x + alpha (T - x), T = (O / R) / sqrt(c) + mu
+            // x <- x + alpha (T - x), T = O / R + mu (the y operand of P Y~ is y - mu);
+            // each half's loads before its stores
             const int k = __ldcg(&pr.st->k);
             const StepC& C = pr.sc[k];
             const int d = pr.d;
             float* xr = pr.X + i * d;
+            const float inv_rs = 1.f / rs;
 #pragma unroll
-            for (int c = 0; c < 64; ++c) {
-              if (c < d) {
-                const float tx = fmaf(o[c >> 5][c & 31] / rs, C.inv_sc, __ldcg(pr.mu + c));
-                const float xv = __ldcg(xr + c);
-                xr[c] = fmaf(C.alpha, tx - xv, xv);
+            for (int h = 0; h < 2; ++h) {
+              float xv[32];
+#pragma unroll
+              for (int e = 0; e < 32; ++e) xv[e] = 32 * h + e < d ? __ldcg(xr + 32 * h + e) : 0.f;
+#pragma unroll
+              for (int e = 0; e < 32; ++e) {
+                const int c = 32 * h + e;
+                if (c < d) {
+                  const float tx = fmaf(o[h][e], inv_rs, sh.mu_s[c]);
+                  xr[c] = fmaf(C.alpha, tx - xv[e], xv[e]);
+                }
               }
             }
             if (k == pr.K - 1 && pr.f_last != nullptr) pr.f_last[i] = __ldcg(pr.f[__ldcg(&pr.st->fcur)] + i);
@@ -999,7 +1134,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) progot_batch_tc(const Params P) {
       } else {
         // MOM / SPLIT on the CUDA cores
         if (t.y == kMom) task_mom(pr, t.z, t.w, smem);
-        else task_split(pr, t.z, t.w, split3);
+        else task_split(pr, t.z, t.w, split3, sh.mu_sp, reinterpret_cast<double*>(smem + OFF_P));
         fence_proxy_global();  // the operand and bias rows are read by TMA in later phases
         bar_lse_all();
       }
@@ -1156,9 +1291,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) progot_batch_tc(const Params P) {
 // Queue and per-problem state at the start of a run.
 __global__ void batch_init_kernel(Params P, const int4* __restrict__ init, int64_t n_init, PState* states, int count) {
   const int64_t q = (int64_t)P.qmask + 1;
-  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < q; s += (int64_t)gridDim.x * blockDim.x) {
-    P.qseq[s] = (unsigned long long)(s < n_init ? s + 1 : s);
-    if (s < n_init) P.qslots[s] = init[s];
+  // level 0 starts with the initial tasks, the other levels empty
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < kLevels * q; s += (int64_t)gridDim.x * blockDim.x) {
+    const bool pre = s < n_init;
+    P.qseq[s] = (unsigned long long)(pre ? s % q + 1 : s % q);
+    if (pre) P.qslots[s] = init[s];
   }
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < count; p += (int64_t)gridDim.x * blockDim.x) {
     PState z;
@@ -1173,9 +1310,12 @@ __global__ void batch_init_kernel(Params P, const int4* __restrict__ init, int64
     z.best_err = INFINITY;
     states[p] = z;
   }
+  if (blockIdx.x == 0 && threadIdx.x < kLevels) {
+    P.qctl[64 * threadIdx.x] = 0ull;
+    P.qctl[64 * threadIdx.x + 16] = threadIdx.x == 0 ? (unsigned long long)n_init : 0ull;
+    P.qctl[64 * threadIdx.x + 32] = threadIdx.x == 0 ? (unsigned long long)n_init : 0ull;
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    *P.qhead = 0ull;
-    *P.qtail = (unsigned long long)n_init;
     *P.remaining = (unsigned)count;
     *P.fault = 0;
   }
@@ -1272,8 +1412,8 @@ Totals totals_of(const progot_problem* probs, int32_t count, int sms) {
   t.qsize = 1024;
   while (t.qsize < need) t.qsize <<= 1;
   t.bytes += al256((size_t)count * sizeof(Prob));
-  t.bytes += al256((size_t)t.qsize * sizeof(int4)) + al256((size_t)t.qsize * 8);
-  t.bytes += 256;                                               // head, tail, remaining, fault
+  t.bytes += al256((size_t)tc::bat::kLevels * t.qsize * sizeof(int4)) + al256((size_t)tc::bat::kLevels * t.qsize * 8);
+  t.bytes += 512 * tc::bat::kLevels + 256;                      // heads, tails, counts; remaining, fault
   t.bytes += al256((size_t)t.n_init * sizeof(int4));
   t.bytes += al256((size_t)count * sizeof(PState));
   t.bytes += al256(t.counters * 4);
@@ -1379,8 +1519,9 @@ int progot_batch_plan_create(const progot_problem* problems, int32_t count, int3
     return r;
   };
   pl->d_probs = reinterpret_cast<Prob*>(take((size_t)count * sizeof(Prob)));
-  int4* qslots = reinterpret_cast<int4*>(take((size_t)tot.qsize * sizeof(int4)));
-  unsigned long long* qseq = reinterpret_cast<unsigned long long*>(take((size_t)tot.qsize * 8));
+  int4* qslots = reinterpret_cast<int4*>(take((size_t)tc::bat::kLevels * tot.qsize * sizeof(int4)));
+  unsigned long long* qseq = reinterpret_cast<unsigned long long*>(take((size_t)tc::bat::kLevels * tot.qsize * 8));
+  char* qctl = take(512 * tc::bat::kLevels);
   char* ctl = take(256);
   pl->d_init = reinterpret_cast<int4*>(take((size_t)tot.n_init * sizeof(int4)));
   pl->n_init = tot.n_init;
@@ -1394,10 +1535,9 @@ int progot_batch_plan_create(const progot_problem* problems, int32_t count, int3
   P.probs = pl->d_probs;
   P.qslots = qslots;
   P.qseq = qseq;
-  P.qhead = reinterpret_cast<unsigned long long*>(ctl);
-  P.qtail = reinterpret_cast<unsigned long long*>(ctl + 8);
-  P.remaining = reinterpret_cast<unsigned*>(ctl + 16);
-  P.fault = reinterpret_cast<int32_t*>(ctl + 20);
+  P.qctl = reinterpret_cast<unsigned long long*>(qctl);
+  P.remaining = reinterpret_cast<unsigned*>(ctl);
+  P.fault = reinterpret_cast<int32_t*>(ctl + 4);
   P.qmask = (unsigned long long)tot.qsize - 1ull;
   P.wait_ns = wait_limit_setting();
   P.split3 = precision == PROGOT_BF16X3 ? 1 : 0;
@@ -1479,8 +1619,7 @@ int progot_batch_plan_create(const progot_problem* problems, int32_t count, int3
       StepC& c = hs[k];
       memset(&c, 0, sizeof(c));
       c.tau = p.tau[k];
-      c.sc = (float)std::sqrt(2.0 * kLog2e / eps);
-      c.inv_sc = (float)std::sqrt(eps / (2.0 * kLog2e));
+      c.c = (float)(2.0 * kLog2e / eps);
       c.bscale = (float)(kLog2e / eps);
       c.inv_eps_f = (float)(1.0 / eps);
       const double cl = eps * kLn2;
