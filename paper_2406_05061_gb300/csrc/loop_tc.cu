@@ -38,6 +38,7 @@
 
 #include <algorithm>
 #include <cstddef>
+#include <vector>
 
 #include "progot_internal.h"
 #include "sweep_epilogue.cuh"
@@ -74,14 +75,13 @@ struct Shared {
   int32_t entry_done;
   alignas(16) SolverState st;  // the stop test's state as this CTA computed it (copied in 16-byte pieces)
   float ered[4];
-  int32_t cslot[8];         // partial slots of the row block's first eight contributors (CTA order)
-  int32_t cfirst, ccount;   // the row block's first contributor and their number
-  float2 ms[2][128];
-  float2 seg[2][128];
+  int32_t cslot[8];         // partial slots of the row block's first eight contributors (combine order)
+  int32_t cbase, ccount;    // the row block's contributor list in the tables and its length
+  float2 seg[2][2][128];    // a segment's (max, sum) per row, by segment parity and LSE warpgroup
 };
 
 static_assert(offsetof(Shared, st) % 16 == 0, "the state is copied into shared memory in 16-byte pieces");
-static_assert(offsetof(Shared, ms) % 8 == 0 && offsetof(Shared, seg) % 8 == 0, "float2 slots");
+static_assert(offsetof(Shared, seg) % 8 == 0, "float2 slots");
 static_assert(sizeof(Shared) % 16 == 0, "the control block follows 16-byte aligned buffers");
 
 struct Layout {
@@ -127,6 +127,13 @@ struct Side {
   unsigned long long* cnt;  // [R] arrivals per row block (monotonic over the loop)
   unsigned long long* done; // finished row blocks (monotonic over the loop)
   float2* partial;          // [G * maxseg * 128] (max, sum) slots
+  // the work split (host-built): CTA c's segments segs[c maxseg + k] = (row block, first
+  // tile, end tile), k < nseg[c]; row block r's contributors are the partial slots
+  // cslot[cptr[r] .. cptr[r + 1]) (slot = CTA * maxseg + segment), in combine order
+  const int4* segs;
+  const int32_t* nseg;
+  const int32_t* cptr;
+  const int32_t* cslot;
   int32_t R, T;
   int64_t nA, nB;
 };
@@ -319,9 +326,7 @@ __device__ __forceinline__ float2 combine_fast(float2 p, float2 q) {
   return make_float2(M, p.y * fast_exp2(p.x - M) + q.y * fast_exp2(q.x - M));
 }
 
-// Named barriers: 1 = both LSE warpgroups (256), 3 = epilogue warps (64),
-// 4 + wg = LSE warpgroup wg (128).
-__device__ __forceinline__ void bar_lse_all() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+// Named barriers: 3 = epilogue warps (64), 4 + wg = LSE warpgroup wg (128).
 __device__ __forceinline__ void bar_epi() { asm volatile("bar.sync 3, 64;" ::: "memory"); }
 __device__ __forceinline__ void bar_wg(int wg) { asm volatile("bar.sync %0, 128;" ::"r"(4 + wg) : "memory"); }
 
@@ -331,6 +336,15 @@ __device__ __forceinline__ void bar_wg(int wg) { asm volatile("bar.sync %0, 128;
 // g's row blocks with 1.
 __device__ __forceinline__ uint32_t flag_of(int it, int side) { return (uint32_t)(2 * it + side + 2); }
 __device__ __forceinline__ uint32_t flag_wanted(int it, int side) { return (uint32_t)(2 * it + side + 1); }
+
+__device__ __forceinline__ Seg seg_at(const Side& Sd, int c, int k, int maxseg) {
+  const int4 v = __ldg(Sd.segs + (int64_t)c * maxseg + k);
+  Seg sg;
+  sg.r = v.x;
+  sg.t0 = v.y;
+  sg.t1 = v.z;
+  return sg;
+}
 
 
 // ------------------------------------------------------------------ kernel
@@ -368,7 +382,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mbar_init(&sh.tmem_empty[b], 4);
       mbar_init(&sh.a_full[b], 1);
       mbar_init(&sh.a_empty[b], 1);
-      mbar_init(&sh.seg_full[b], 128);
+      mbar_init(&sh.seg_full[b], 256);
       mbar_init(&sh.seg_empty[b], 64);
     }
     mbar_init(&sh.drain, 1);
@@ -421,10 +435,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // bias rows of B: f-update: g of the previous g-update; g-update: this iteration's f
         const CUtensorMap* mBb = sd == 0 ? ((it & 1) ? &mYb1 : &mYb0) : ((it & 1) ? &mXb1 : &mXb0);
         const uint32_t want = flag_wanted(it, sd);
-        const Split sp = make_split(Sd.R, Sd.T, G);
-        const int nseg = num_segments(sp, c);
+        const int nseg = __ldg(Sd.nseg + c);
         for (int k = 0; k < nseg && ok; ++k, ++ka) {
-          const Seg sg = segment(sp, c, k);
+          const Seg sg = seg_at(Sd, c, k, P.maxseg);
           const int ai = ka % NA;
           ok = warp_wait_bar(&sh.a_empty[ai], (uint32_t)(((ka / NA) & 1) ^ 1), abort_flag, P);
           if (!ok) break;
@@ -492,10 +505,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
       for (int sd = 0; sd < 2 && ok; ++sd) {
         const Side& Sd = P.side[sd];
-        const Split sp = make_split(Sd.R, Sd.T, G);
-        const int nseg = num_segments(sp, c);
+        const int nseg = __ldg(Sd.nseg + c);
         for (int k = 0; k < nseg && ok; ++k, ++ka) {
-          const Seg sg = segment(sp, c, k);
+          const Seg sg = seg_at(Sd, c, k, P.maxseg);
           const int ai = ka % NA;
           ok = warp_wait_bar(&sh.a_full[ai], (uint32_t)((ka / NA) & 1), abort_flag, P);
           if (!ok) break;
@@ -570,10 +582,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
       for (int sd = 0; sd < 2; ++sd) {
         const Side& Sd = P.side[sd];
-        const Split sp = make_split(Sd.R, Sd.T, G);
-        const int nseg = num_segments(sp, c);
+        const int nseg = __ldg(Sd.nseg + c);
         for (int k = 0; k < nseg; ++k, ++kseg) {
-          const Seg sg = segment(sp, c, k);
+          const Seg sg = seg_at(Sd, c, k, P.maxseg);
           float m_run = -INFINITY, s_run = 0.f;
           for (int t = sg.t0; t < sg.t1; ++t, ++tl) {
             if ((tl & 1) != wg) continue;
@@ -643,20 +654,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             m_run = NAN;
             s_run = NAN;
           }
-          // merge warpgroup 1 into warpgroup 0, then hand the segment to the epilogue warps
-          if (wg == 1) sh.ms[kseg & 1][row_local] = make_float2(m_run, s_run);
-          bar_lse_all();
-          if (wg == 1) continue;
-          {
-            const float2 o = sh.ms[kseg & 1][row_local];
-            const float2 mrg = lse_combine(make_float2(m_run, s_run), o);
-            const bool bad = isnan(o.y) || isnan(s_run);
-            m_run = bad ? NAN : mrg.x;
-            s_run = bad ? NAN : mrg.y;
-          }
+          // both warpgroups hand their part of the segment to the epilogue warps (which
+          // merge them), so that neither waits for the other at a segment's end
           const int sl = kseg & 1;
           wait_bar(&sh.seg_empty[sl], (uint32_t)(((kseg >> 1) & 1) ^ 1), abort_flag, P);
-          sh.seg[sl][row_local] = make_float2(m_run, s_run);
+          sh.seg[sl][wg][row_local] = make_float2(m_run, s_run);
           mbar_arrive(&sh.seg_full[sl]);
         }
       }
@@ -665,20 +667,50 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // ------------------------------------------------------------ epilogue warps and stop decision
     const int etid = threadIdx.x - EPI_TID0;  // 0..63
     int kseg = 0;
+    // ---- stop test of iteration it (warp 10), once every row block of the f-update is done
+    auto decide = [&](int it) {
+      if (etid < 32) {
+        bool okc = true;
+        if (etid == 0) {
+          okc = wait_counter(P.side[1].done, (unsigned long long)it * (unsigned long long)P.side[1].R, abort_flag,
+                             P) &&
+                wait_counter(P.side[0].done, (unsigned long long)(it + 1) * (unsigned long long)P.side[0].R,
+                             abort_flag, P);
+          __threadfence();
+        }
+        okc = __shfl_sync(0xffffffffu, okc ? 1 : 0, 0) != 0;
+        __syncwarp();  // the other lanes' loads below follow lane 0's acquire
+        const double err =
+            okc ? sum_errpart_warp(P.errpart + (int64_t)(it & 1) * P.side[0].R, P.side[0].R) : (double)NAN;
+        if (etid == 0) {
+          SolverState st = sh.st;
+          if (okc) {
+            f_update_transition(st, err, P.side[0].p);
+          } else {
+            st.done = 1;
+            st.status = kNumeric;  // reported as PROGOT_ERR_TIMEOUT by the host (fault word)
+          }
+          sh.st = st;
+          sh.dec_stop[it & 1] = st.done;
+          if (c == 0) *P.state = st;
+          mbar_arrive(&sh.dec_full);
+        }
+      }
+      bar_epi();  // both epilogue warps see the decision
+    };
+
     for (int it = P.seq0; it < it_end; ++it) {
       for (int sd = 0; sd < 2; ++sd) {
         const Side& Sd = P.side[sd];
         const SweepParams& p = Sd.p;
-        const Split sp = make_split(Sd.R, Sd.T, G);
-        const int nseg = num_segments(sp, c);
-        const bool skip = sd == 1 && sh.st.done != 0;  // the stop test ended the loop: g stays
+        const int nseg = __ldg(Sd.nseg + c);
         const int fcur = sh.st.fcur;
         const float* pot_cur = (sd == 0) ? (fcur == 0 ? Sd.out0 : Sd.out1) : nullptr;
         float* out = (sd == 0) ? (fcur == 0 ? Sd.out1 : Sd.out0) : Sd.out0;
         __nv_bfloat16* bout = Sd.bias_out[sd == 0 ? (it & 1) : ((it + 1) & 1)];
         const uint32_t flag = flag_of(it, sd);
         for (int k = 0; k < nseg; ++k, ++kseg) {
-          const Seg sg = segment(sp, c, k);
+          const Seg sg = seg_at(Sd, c, k, P.maxseg);
           const int sl = kseg & 1;
           // the rows' epilogue inputs do not depend on the sweep: load them while the LSE
           // warps finish the segment
@@ -691,23 +723,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             rin[h].w = 0.f;
             if (i < Sd.nA) rin[h] = row_inputs(p, i, pot_cur);
           }
-          // the row block's contributors and their partial slots, once per segment (the
-          // work split's 64-bit divisions stay off the finisher's path); the previous
-          // segment's readers passed the barrier at its end
+          // the row block's contributors and their partial slots, once per segment, from the
+          // split's tables; the previous segment's readers passed the barrier at its end
           if (etid < 8) {
-            int c_first, c_last;
-            contributors(sp, sg.r, &c_first, &c_last);
-            const int cc = c_first + etid;
-            if (cc <= c_last) sh.cslot[etid] = cc * P.maxseg + seg_of(sp, sg.r, cc);
+            const int p0 = __ldg(Sd.cptr + sg.r), p1 = __ldg(Sd.cptr + sg.r + 1);
+            if (p0 + etid < p1) sh.cslot[etid] = __ldg(Sd.cslot + p0 + etid);
             if (etid == 0) {
-              sh.cfirst = c_first;
-              sh.ccount = c_last - c_first + 1;
+              sh.cbase = p0;
+              sh.ccount = p1 - p0;
             }
           }
           const bool okw = wait_bar(&sh.seg_full[sl], (uint32_t)((kseg >> 1) & 1), abort_flag, P);
+          // merge of the two LSE warpgroups' parts (a NaN part, from an aborted wait, stays NaN)
           float2 mv[2];
-          mv[0] = okw ? sh.seg[sl][etid] : make_float2(NAN, NAN);
-          mv[1] = okw ? sh.seg[sl][etid + 64] : make_float2(NAN, NAN);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const float2 a = sh.seg[sl][0][etid + 64 * h], b = sh.seg[sl][1][etid + 64 * h];
+            const float2 mrg = lse_combine(a, b);
+            mv[h] = (!okw || isnan(a.y) || isnan(b.y)) ? make_float2(NAN, NAN) : mrg;
+          }
           mbar_arrive(&sh.seg_empty[sl]);
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
@@ -715,15 +749,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if ((int64_t)sg.r * BM + rl < Sd.nA) Sd.partial[((int64_t)c * P.maxseg + k) * BM + rl] = mv[h];
           }
           bar_epi();  // all rows' partial stores (and the contributor slots) happen before the arrival
-          const int c_first = sh.cfirst, ncc = sh.ccount;
+          const int ncc = sh.ccount, own = c * P.maxseg + k;
           if (etid == 0) {
             const unsigned long long prev = atom_add_acq_rel_u64(&Sd.cnt[sg.r], 1ull);
             sh.e_last = (prev + 1 == (unsigned long long)(it + 1) * (unsigned long long)ncc);
           }
           bar_epi();
           if (sh.e_last) {
+            const bool skip = sd == 1 && sh.st.done != 0;  // the stop test ended the loop: g stays
             // the other contributors' partials of both rows, loads issued together (this
-            // CTA's own from registers), then combined in CTA order
+            // segment's own from registers), then combined in the tables' order
             constexpr int kMaxC = 8;
             float2 pv[2][kMaxC];
 #pragma unroll
@@ -731,7 +766,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               const int rl = etid + 64 * h;
 #pragma unroll
               for (int q = 0; q < kMaxC; ++q)
-                if (q < ncc) pv[h][q] = (c_first + q == c) ? mv[h] : __ldcg(&Sd.partial[(int64_t)sh.cslot[q] * BM + rl]);
+                if (q < ncc) pv[h][q] = (sh.cslot[q] == own) ? mv[h] : __ldcg(&Sd.partial[(int64_t)sh.cslot[q] * BM + rl]);
             }
             float e[2];
 #pragma unroll
@@ -745,10 +780,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 for (int q = 0; q < kMaxC; ++q)
                   if (q < ncc) acc = combine_fast(acc, pv[h][q]);
                 for (int q = kMaxC; q < ncc; ++q) {
-                  const int cc = c_first + q;
-                  acc = combine_fast(acc, cc == c ? mv[h]
-                                                  : __ldcg(&Sd.partial[((int64_t)cc * P.maxseg + seg_of(sp, sg.r, cc)) *
-                                                                           BM + rl]));
+                  const int slot = __ldg(Sd.cslot + sh.cbase + q);
+                  acc = combine_fast(acc, slot == own ? mv[h] : __ldcg(&Sd.partial[(int64_t)slot * BM + rl]));
                 }
                 const float Lr = acc.x + __log2f(acc.y);
                 if (!skip) {
@@ -781,37 +814,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
           bar_epi();
         }
-        if (sd == 0) {
-          // ---- stop test of iteration it (warp 10), once every row block of the f-update is done
-          if (etid < 32) {
-            bool okc = true;
-            if (etid == 0) {
-              okc = wait_counter(P.side[1].done, (unsigned long long)it * (unsigned long long)P.side[1].R, abort_flag,
-                                 P) &&
-                    wait_counter(P.side[0].done, (unsigned long long)(it + 1) * (unsigned long long)P.side[0].R,
-                                 abort_flag, P);
-              __threadfence();
-            }
-            okc = __shfl_sync(0xffffffffu, okc ? 1 : 0, 0) != 0;
-            __syncwarp();  // the other lanes' loads below follow lane 0's acquire
-            const double err =
-                okc ? sum_errpart_warp(P.errpart + (int64_t)(it & 1) * P.side[0].R, P.side[0].R) : (double)NAN;
-            if (etid == 0) {
-              SolverState st = sh.st;
-              if (okc) {
-                f_update_transition(st, err, P.side[0].p);
-              } else {
-                st.done = 1;
-                st.status = kNumeric;  // reported as PROGOT_ERR_TIMEOUT by the host (fault word)
-              }
-              sh.st = st;
-              sh.dec_stop[it & 1] = st.done;
-              if (c == 0) *P.state = st;
-              mbar_arrive(&sh.dec_full);
-            }
-          }
-          bar_epi();  // both epilogue warps see the decision
-        }
+        if (sd == 0) decide(it);
       }
       if (sh.st.done) break;
     }
@@ -866,15 +869,52 @@ bool loop_tc_supported(int bn, int nkb, int split3) {
   return s >= 2 && (bn == 128 || bn == 256);
 }
 
+// ---- work split of the loop (host-built tables): the (row block, column tile) grid of
+// a sweep cut over the CTAs as in the per-update kernel (tc::Split), laid out for the
+// kernel as per-CTA segment lists and per-row-block contributor lists (in CTA order, the
+// order of the combine), so that no 64-bit division of the split runs on the GPU.
+struct SideTables {
+  std::vector<int4> segs;
+  std::vector<int32_t> nseg, cptr, cslot;
+  int maxseg = 0;
+};
+
+// ms_force: segment stride of the tables (the larger maxseg of both sides), 0 = own.
+static void side_tables(int R, int T, int G, SideTables* out, int ms_force = 0) {
+  const tc::Split sp = tc::make_split(R, T, G);
+  int ms = 1;
+  for (int c = 0; c < G; ++c) ms = std::max(ms, tc::num_segments(sp, c));
+  out->maxseg = ms;
+  if (ms_force >= ms) ms = ms_force;
+  out->segs.assign((size_t)G * ms, make_int4(0, 0, 0, 0));
+  out->nseg.assign((size_t)G, 0);
+  std::vector<std::vector<int32_t>> by_row((size_t)R);
+  for (int c = 0; c < G; ++c) {
+    const int ns = tc::num_segments(sp, c);
+    out->nseg[c] = ns;
+    for (int k = 0; k < ns; ++k) {
+      const tc::Seg sg = tc::segment(sp, c, k);
+      out->segs[(size_t)c * ms + k] = make_int4(sg.r, sg.t0, sg.t1, 0);
+      by_row[sg.r].push_back(c * ms + k);  // CTAs in increasing order
+    }
+  }
+  out->cptr.assign((size_t)R + 1, 0);
+  out->cslot.clear();
+  for (int r = 0; r < R; ++r) {
+    out->cptr[r + 1] = out->cptr[r] + (int32_t)by_row[r].size();
+    out->cslot.insert(out->cslot.end(), by_row[r].begin(), by_row[r].end());
+  }
+}
+
 void loop_tc_plan(int64_t n, int64_t m, int bn, int sms, int* G, int* maxseg) {
   const int64_t Rx = (n + tc::BM - 1) / tc::BM, Ry = (m + tc::BM - 1) / tc::BM;
   const int64_t Tx = (n + bn - 1) / bn, Ty = (m + bn - 1) / bn;
   const int g = (int)std::min<int64_t>(std::min<int64_t>(Rx * Ty, Ry * Tx), sms);
-  int ms = 1;
-  const tc::Split s0 = tc::make_split((int)Rx, (int)Ty, g), s1 = tc::make_split((int)Ry, (int)Tx, g);
-  for (int c = 0; c < g; ++c) ms = std::max(ms, std::max(tc::num_segments(s0, c), tc::num_segments(s1, c)));
+  SideTables a, b;
+  side_tables((int)Rx, (int)Ty, g, &a);
+  side_tables((int)Ry, (int)Tx, g, &b);
   *G = g;
-  *maxseg = ms;
+  *maxseg = std::max(a.maxseg, b.maxseg);
 }
 
 size_t loop_tc_smem(int bn, int nkb, int split3) {
@@ -939,6 +979,33 @@ cudaError_t launch_sinkhorn_loop_tc(const LoopLaunch& Lq, cudaStream_t stream) {
     d.e_lo = (float)(s.p.eps - (double)d.e_hi);
     d.w_hi = (float)wl;
     d.w_lo = (float)(wl - (double)d.w_hi);
+  }
+  // the work split's tables (the same as loop_tc_plan's), copied to the workspace
+  {
+    SideTables tab[2];
+    for (int sd = 0; sd < 2; ++sd) {
+      side_tables(P.side[sd].R, P.side[sd].T, Lq.G, &tab[sd], Lq.maxseg);
+      if (tab[sd].maxseg > Lq.maxseg) return cudaErrorInvalidValue;
+      const LoopSideLaunch& ls = Lq.side[sd];
+      if ((int64_t)tab[sd].segs.size() > ls.table_slots || (int64_t)tab[sd].cslot.size() > ls.table_slots)
+        return cudaErrorInvalidValue;
+      cudaError_t e = cudaMemcpyAsync(ls.segs, tab[sd].segs.data(), sizeof(int4) * tab[sd].segs.size(),
+                                      cudaMemcpyHostToDevice, stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ls.nseg, tab[sd].nseg.data(), sizeof(int32_t) * tab[sd].nseg.size(),
+                            cudaMemcpyHostToDevice, stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ls.cptr, tab[sd].cptr.data(), sizeof(int32_t) * tab[sd].cptr.size(),
+                            cudaMemcpyHostToDevice, stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ls.cslot, tab[sd].cslot.data(), sizeof(int32_t) * tab[sd].cslot.size(),
+                            cudaMemcpyHostToDevice, stream);
+      if (e != cudaSuccess) return e;
+      P.side[sd].segs = reinterpret_cast<const int4*>(ls.segs);
+      P.side[sd].nseg = ls.nseg;
+      P.side[sd].cptr = ls.cptr;
+      P.side[sd].cslot = ls.cslot;
+    }
   }
   P.errpart = Lq.errpart;
   P.state = Lq.state;

@@ -188,6 +188,10 @@ struct Workspace {
   float2* lpart;    // (max, sum) slots: f-update bank, then g-update bank (lslots each)
   int64_t lslots;
   int64_t lrb;      // rbmax of the carve (row-block capacity of lcnt and lerr)
+  int4* ltab_segs;  // work-split tables of both sides: segments [2][lslots], contributor slots
+  int32_t* ltab_cslot;  // [2][lslots], contributor offsets [2][rbmax + 1], segment counts [2][sms]
+  int32_t* ltab_cptr;
+  int32_t* ltab_nseg;
   double* lerr;     // [2][rbmax] error partials by iteration parity
   size_t bytes;
 };
@@ -277,6 +281,10 @@ static size_t ws_layout(const WsDims& w, Workspace* out, char* base) {
   ws.lslots = w.tc ? w.rbmax + 3 * (int64_t)num_sms() : 0;
   ws.lpart = (float2*)take(sizeof(float2) * 2 * (size_t)ws.lslots * 128);
   ws.lrb = w.rbmax;
+  ws.ltab_segs = (int4*)take(sizeof(int4) * 2 * (size_t)ws.lslots);
+  ws.ltab_cslot = (int32_t*)take(sizeof(int32_t) * 2 * (size_t)ws.lslots);
+  ws.ltab_cptr = (int32_t*)take(w.tc ? sizeof(int32_t) * 2 * ((size_t)w.rbmax + 1) : 0);
+  ws.ltab_nseg = (int32_t*)take(w.tc ? sizeof(int32_t) * 2 * (size_t)num_sms() : 0);
   ws.lerr = (double*)take(w.tc ? sizeof(double) * 2 * (size_t)w.rbmax : 0);
   ws.bytes = off;
   if (out) *out = ws;
@@ -581,6 +589,11 @@ static int sinkhorn_loop_persistent(SweepParams pf, SweepParams pg, int64_t n, i
   F.cnt = ws.lcnt;
   F.done = ws.lcnt + 2 * rb;
   F.partial = ws.lpart;
+  F.segs = ws.ltab_segs;
+  F.cslot = ws.ltab_cslot;
+  F.cptr = ws.ltab_cptr;
+  F.nseg = ws.ltab_nseg;
+  F.table_slots = ws.lslots;
   Gs.p = pg;
   Gs.out0 = g;
   Gs.out1 = nullptr;
@@ -591,6 +604,11 @@ static int sinkhorn_loop_persistent(SweepParams pf, SweepParams pg, int64_t n, i
   Gs.cnt = ws.lcnt + rb;
   Gs.done = ws.lcnt + 2 * rb + 1;
   Gs.partial = ws.lpart + ws.lslots * 128;
+  Gs.segs = ws.ltab_segs + ws.lslots;
+  Gs.cslot = ws.ltab_cslot + ws.lslots;
+  Gs.cptr = ws.ltab_cptr + (rb + 1);
+  Gs.nseg = ws.ltab_nseg + num_sms();
+  Gs.table_slots = ws.lslots;
   const CUtensorMap* maps[12] = {&ops.xh_a, &ops.xl_a, &ops.yh_a, &ops.yl_a, &ops.xh_b, &ops.xl_b,
                                  &ops.yh_b, &ops.yl_b, &ops.xb,   &xb2_map,   &ops.yb,   &yb2_map};
   for (int q = 0; q < 12; ++q) L.maps[q] = maps[q];

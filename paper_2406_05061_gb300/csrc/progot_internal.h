@@ -121,6 +121,13 @@ struct LoopSideLaunch {
   unsigned long long* cnt;   // [row blocks] arrival counters, zero at the loop's start
   unsigned long long* done;  // finished row blocks, zero at the loop's start
   float2* partial;           // (max, sum) slots of this side's sweeps
+  // device buffers for the work split's tables (filled by the launch): segs (int4) and
+  // cslot hold table_slots entries each, cptr row blocks + 1, nseg one entry per CTA
+  void* segs;
+  int32_t* nseg;
+  int32_t* cptr;
+  int32_t* cslot;
+  int64_t table_slots;
 };
 struct LoopLaunch {
   LoopSideLaunch side[2];
@@ -146,6 +153,7 @@ int device_sm_count();
 int fail_message(int code, const char* msg);  // sets the last-error text, returns code
 cudaError_t launch_fill_u32(uint32_t* p, int64_t n, uint32_t v, cudaStream_t s);
 bool loop_tc_supported(int bn, int nkb, int split3);
+
 void loop_tc_plan(int64_t n, int64_t m, int bn, int sms, int* G, int* maxseg);
 size_t loop_tc_smem(int bn, int nkb, int split3);
 
