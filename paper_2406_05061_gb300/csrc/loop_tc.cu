@@ -54,6 +54,7 @@ constexpr int TMEM_COLS = 512;
 constexpr int A_TILE_BYTES = BM * KB * 2;
 constexpr int A_BIAS_BYTES = BM * 32;  // 128 rows x 16 bf16 of ones (32-byte swizzle)
 constexpr int BIAS_SLOTS = 2;          // bias-row ring, one slot per tile
+constexpr int SEG_RING = 8;            // segments the LSE warps may be ahead of the epilogue warps
 
 struct Shared {
   uint64_t full[8];
@@ -65,8 +66,8 @@ struct Shared {
   uint64_t a_full[2];
   uint64_t a_empty[2];
   uint64_t drain;
-  uint64_t seg_full[2];
-  uint64_t seg_empty[2];
+  uint64_t seg_full[SEG_RING];   // a segment's partials are in global memory (256 LSE threads)
+  uint64_t seg_empty[SEG_RING];
   uint64_t dec_full;        // one phase per iteration: the stop decision is in dec_stop
   uint32_t tmem_base;
   int32_t abort_flag;
@@ -77,11 +78,9 @@ struct Shared {
   float ered[4];
   int32_t cslot[8];         // partial slots of the row block's first eight contributors (combine order)
   int32_t cbase, ccount;    // the row block's contributor list in the tables and its length
-  float2 seg[2][2][128];    // a segment's (max, sum) per row, by segment parity and LSE warpgroup
 };
 
 static_assert(offsetof(Shared, st) % 16 == 0, "the state is copied into shared memory in 16-byte pieces");
-static_assert(offsetof(Shared, seg) % 8 == 0, "float2 slots");
 static_assert(sizeof(Shared) % 16 == 0, "the control block follows 16-byte aligned buffers");
 
 struct Layout {
@@ -126,7 +125,7 @@ struct Side {
   float c_hi, c_lo, e_hi, e_lo, w_hi, w_lo;
   unsigned long long* cnt;  // [R] arrivals per row block (monotonic over the loop)
   unsigned long long* done; // finished row blocks (monotonic over the loop)
-  float2* partial;          // [G * maxseg * 128] (max, sum) slots
+  float2* partial;          // [G * maxseg][2][128] (max, sum) per segment slot, LSE warpgroup and row
   // the work split (host-built): CTA c's segments segs[c maxseg + k] = (row block, first
   // tile, end tile), k < nseg[c]; row block r's contributors are the partial slots
   // cslot[cptr[r] .. cptr[r + 1]) (slot = CTA * maxseg + segment), in combine order
@@ -382,6 +381,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mbar_init(&sh.tmem_empty[b], 4);
       mbar_init(&sh.a_full[b], 1);
       mbar_init(&sh.a_empty[b], 1);
+    }
+    for (int b = 0; b < SEG_RING; ++b) {
       mbar_init(&sh.seg_full[b], 256);
       mbar_init(&sh.seg_empty[b], 64);
     }
@@ -654,11 +655,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             m_run = NAN;
             s_run = NAN;
           }
-          // both warpgroups hand their part of the segment to the epilogue warps (which
-          // merge them), so that neither waits for the other at a segment's end
-          const int sl = kseg & 1;
-          wait_bar(&sh.seg_empty[sl], (uint32_t)(((kseg >> 1) & 1) ^ 1), abort_flag, P);
-          sh.seg[sl][wg][row_local] = make_float2(m_run, s_run);
+          // both warpgroups write their part of the segment to its partial slot (the row
+          // block's finisher merges them) and count the segment as handed over, so that
+          // neither waits for the other and the epilogue warps only count arrivals
+          const int sl = kseg % SEG_RING;
+          if ((int64_t)sg.r * BM + row_local < Sd.nA)
+            Sd.partial[(((int64_t)c * P.maxseg + k) * 2 + wg) * BM + row_local] = make_float2(m_run, s_run);
+          wait_bar(&sh.seg_empty[sl], (uint32_t)(((kseg / SEG_RING) & 1) ^ 1), abort_flag, P);
           mbar_arrive(&sh.seg_full[sl]);
         }
       }
@@ -711,7 +714,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const uint32_t flag = flag_of(it, sd);
         for (int k = 0; k < nseg; ++k, ++kseg) {
           const Seg sg = seg_at(Sd, c, k, P.maxseg);
-          const int sl = kseg & 1;
+          const int sl = kseg % SEG_RING;
           // the rows' epilogue inputs do not depend on the sweep: load them while the LSE
           // warps finish the segment
           RowIn rin[2];
@@ -733,40 +736,50 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               sh.ccount = p1 - p0;
             }
           }
-          const bool okw = wait_bar(&sh.seg_full[sl], (uint32_t)((kseg >> 1) & 1), abort_flag, P);
-          // merge of the two LSE warpgroups' parts (a NaN part, from an aborted wait, stays NaN)
-          float2 mv[2];
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const float2 a = sh.seg[sl][0][etid + 64 * h], b = sh.seg[sl][1][etid + 64 * h];
-            const float2 mrg = lse_combine(a, b);
-            mv[h] = (!okw || isnan(a.y) || isnan(b.y)) ? make_float2(NAN, NAN) : mrg;
-          }
+          // the segment's partials are in global memory once the LSE warps arrived (their
+          // stores precede the arrival; the release of the arrival atomic below covers them)
+          wait_bar(&sh.seg_full[sl], (uint32_t)((kseg / SEG_RING) & 1), abort_flag, P);
           mbar_arrive(&sh.seg_empty[sl]);
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int rl = etid + 64 * h;
-            if ((int64_t)sg.r * BM + rl < Sd.nA) Sd.partial[((int64_t)c * P.maxseg + k) * BM + rl] = mv[h];
-          }
-          bar_epi();  // all rows' partial stores (and the contributor slots) happen before the arrival
-          const int ncc = sh.ccount, own = c * P.maxseg + k;
           if (etid == 0) {
             const unsigned long long prev = atom_add_acq_rel_u64(&Sd.cnt[sg.r], 1ull);
-            sh.e_last = (prev + 1 == (unsigned long long)(it + 1) * (unsigned long long)ncc);
+            sh.e_last = (prev + 1 == (unsigned long long)(it + 1) * (unsigned long long)sh.ccount);
           }
           bar_epi();
+          const int ncc = sh.ccount;
           if (sh.e_last) {
             const bool skip = sd == 1 && sh.st.done != 0;  // the stop test ended the loop: g stays
-            // the other contributors' partials of both rows, loads issued together (this
-            // segment's own from registers), then combined in the tables' order
-            constexpr int kMaxC = 8;
-            float2 pv[2][kMaxC];
+            // the contributors' partials of both rows (each contributor: the two LSE
+            // warpgroups' parts, merged as one segment), four contributors' loads issued
+            // together, combined in the tables' order
+            float2 acc[2];
+            acc[0] = make_float2(-INFINITY, 0.f);
+            acc[1] = make_float2(-INFINITY, 0.f);
+            for (int q0 = 0; q0 < ncc; q0 += 4) {
+              float2 pa[2][4], pb[2][4];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const int rl = etid + 64 * h;
+              for (int j = 0; j < 4; ++j) {
+                const int q = q0 + j;
+                if (q < ncc) {
+                  const int slot = q < 8 ? sh.cslot[q] : __ldg(Sd.cslot + sh.cbase + q);
 #pragma unroll
-              for (int q = 0; q < kMaxC; ++q)
-                if (q < ncc) pv[h][q] = (sh.cslot[q] == own) ? mv[h] : __ldcg(&Sd.partial[(int64_t)sh.cslot[q] * BM + rl]);
+                  for (int h = 0; h < 2; ++h) {
+                    const int rl = etid + 64 * h;
+                    pa[h][j] = __ldcg(&Sd.partial[((int64_t)slot * 2 + 0) * BM + rl]);
+                    pb[h][j] = __ldcg(&Sd.partial[((int64_t)slot * 2 + 1) * BM + rl]);
+                  }
+                }
+              }
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                if (q0 + j < ncc) {
+#pragma unroll
+                  for (int h = 0; h < 2; ++h) {
+                    const float2 mrg = lse_combine(pa[h][j], pb[h][j]);
+                    const float2 v = (isnan(pa[h][j].y) || isnan(pb[h][j].y)) ? make_float2(NAN, NAN) : mrg;
+                    acc[h] = combine_fast(acc[h], v);
+                  }
+                }
+              }
             }
             float e[2];
 #pragma unroll
@@ -775,15 +788,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               const int rl = etid + 64 * h;
               const int64_t i = (int64_t)sg.r * BM + rl;
               if (i < Sd.nA) {
-                float2 acc = make_float2(-INFINITY, 0.f);
-#pragma unroll
-                for (int q = 0; q < kMaxC; ++q)
-                  if (q < ncc) acc = combine_fast(acc, pv[h][q]);
-                for (int q = kMaxC; q < ncc; ++q) {
-                  const int slot = __ldg(Sd.cslot + sh.cbase + q);
-                  acc = combine_fast(acc, slot == own ? mv[h] : __ldcg(&Sd.partial[(int64_t)slot * BM + rl]));
-                }
-                const float Lr = acc.x + __log2f(acc.y);
+                const float Lr = acc[h].x + __log2f(acc[h].y);
                 if (!skip) {
                   float val;
                   e[h] = loop_row_potential(Sd, sd, i, Lr, rin[h], out, &val);

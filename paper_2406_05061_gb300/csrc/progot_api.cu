@@ -279,7 +279,8 @@ static size_t ws_layout(const WsDims& w, Workspace* out, char* base) {
   // G * maxseg <= R + 2 G slots of 128 rows per bank (each CTA's segments: its whole row
   // blocks, plus at most two partial ones of the contiguous remainder)
   ws.lslots = w.tc ? w.rbmax + 3 * (int64_t)num_sms() : 0;
-  ws.lpart = (float2*)take(sizeof(float2) * 2 * (size_t)ws.lslots * 128);
+  // (max, sum) per slot, LSE warpgroup and row; one bank per update direction
+  ws.lpart = (float2*)take(sizeof(float2) * 2 * (size_t)ws.lslots * 2 * 128);
   ws.lrb = w.rbmax;
   ws.ltab_segs = (int4*)take(sizeof(int4) * 2 * (size_t)ws.lslots);
   ws.ltab_cslot = (int32_t*)take(sizeof(int32_t) * 2 * (size_t)ws.lslots);
@@ -603,7 +604,7 @@ static int sinkhorn_loop_persistent(SweepParams pf, SweepParams pg, int64_t n, i
   Gs.flag_in = ws.lflag;
   Gs.cnt = ws.lcnt + rb;
   Gs.done = ws.lcnt + 2 * rb + 1;
-  Gs.partial = ws.lpart + ws.lslots * 128;
+  Gs.partial = ws.lpart + ws.lslots * 2 * 128;
   Gs.segs = ws.ltab_segs + ws.lslots;
   Gs.cslot = ws.ltab_cslot + ws.lslots;
   Gs.cptr = ws.ltab_cptr + (rb + 1);
