@@ -436,3 +436,48 @@ def test_benchmark_workload_every_step_teacher_forced_bf16x3(nat):
     row, col = fp64_marginals(host(full.x_last), p.y, host(full.f_last), host(full.g_all[K - 1]), eps[-1])
     l1 = np.abs(row - 1.0 / 8192).sum() + np.abs(col - 1.0 / 8192).sum()
     assert l1 <= TOL_MIXED, l1
+
+
+def test_large_coupling_progot_sampled_steps_bf16x3(nat):
+    """The large coupling configuration as the bench runs it: two 32-component mixtures on
+    the unit sphere, n = m = 65536, d = 256, K = 16 constant-speed steps, bf16x3, tau = 1e-4,
+    eps_k from the GPU's Alg. 4 on the held-out draw. Steps 1, 8 and 16 are teacher-forced
+    on 32 sampled rows: the oracle applies eq. (7) with the GPU's g^(k) to the GPU's
+    X^(k-1) (from solves truncated after step k - 1, whose g's equal the full solve's bit
+    for bit), and the GPU's displacement must match it within map RMS 1e-3; the sampled
+    rows' float64 row sums of (f^(k), g^(k)), scaled to all rows, stay within 1e-3."""
+    p = W.sphere_mixture_pair(65536, 65536, 256, seed=2)
+    yt = W.heldout_target(p)
+    K = 16
+    alpha = nat.progot_schedule_alpha(K, "constant")
+    tau = [1e-4] * K
+    x, y = dev(p.x), dev(p.y)
+    eps, _, _ = nat.progot_schedule_eps(x, y, dev(yt), alpha, tau=tau[-1], precision="bf16x3")
+    eps = [float(e) for e in eps]
+    full = nat.progot_solve(x, y, alpha, eps, tau, max_iter=10000, precision="bf16x3")
+    assert full.status == nat.PROGOT_OK, nat.last_error()
+    rows = np.random.default_rng(57).choice(65536, 32, replace=False)
+    Y64 = p.y.astype(np.float64)
+
+    def upto(k):  # X^(k) and f^(k) from the solve cut after step k (k = 0: the input cloud)
+        if k == 0:
+            return p.x.astype(np.float64), None
+        part = nat.progot_solve(x, y, alpha[:k], eps[:k], tau[:k], max_iter=10000, precision="bf16x3")
+        assert part.status == nat.PROGOT_OK, nat.last_error()
+        assert torch.equal(part.g_all, full.g_all[:k])
+        return host(part.x_out), host(part.f_last)
+
+    for k in (0, 7, K - 1):  # steps 1, 8, 16
+        X_prev, _ = upto(k)
+        if k < K - 1:
+            X_k, f_k = upto(k + 1)
+        else:
+            assert np.array_equal(host(full.x_last), X_prev)
+            X_k, f_k = host(full.x_out), host(full.f_last)
+        g_k = host(full.g_all[k])
+        T_ref = O.entropic_map(X_prev[rows], Y64, g_k, eps[k])
+        T_gpu = (X_k[rows] - (1.0 - alpha[k]) * X_prev[rows]) / alpha[k]
+        assert map_rms_rel(T_gpu, T_ref, p.y) <= TOL_MIXED, (k, map_rms_rel(T_gpu, T_ref, p.y))
+        r = np.array([np.exp((f_k[i] + g_k - O.cost_matrix_rows(X_prev[i:i + 1], Y64)[0]) / eps[k]).sum()
+                      for i in rows])
+        assert np.abs(r - 1.0 / 65536).sum() * 65536 / len(rows) <= TOL_MIXED, k
