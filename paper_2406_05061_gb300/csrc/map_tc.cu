@@ -11,7 +11,8 @@
 //     region. The B operand is the tile's own S operand Y~ = sqrt(c) (y - mu) (bf16
 //     hi/lo) read a second time as an MN-major matrix (its 128-byte rows are the K index
 //     j, each holding the 64 coordinates), so a stage is released only after the tile's
-//     P Y~ products; T_i = (O_i / R_i) / sqrt(c) + mu.
+//     P Y~ products; T_i = (O_i / R_i) / sqrt(c) + mu. With hi parts only (split3 = 0)
+//     each product is the single Xh Yh or Ph Yh term and the lo tiles are not loaded.
 // CTA = 10 warps: warp 0 TMA producer (A row block once per segment; per tile the
 // B hi/lo tiles with their bias rows into one of three stages), warp 1 MMA issuer (S of
 // tile q + 1 is issued before P Y~ of tile q, so the exponentials of tile q overlap the
@@ -81,6 +82,7 @@ struct MapTcParams {
   float alpha;
   float inv_sc;      // 1 / sqrt(c): the B operand is sqrt(c) (y - mu)
   const float* mu;   // d: centre of the operands
+  int32_t split3;    // 1: hi/lo operands, three products; 0: hi parts only, one product
 };
 
 __device__ __forceinline__ void mt_bar_all() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
@@ -185,9 +187,9 @@ __global__ void __launch_bounds__(MT_NTHREADS, 1)
       ok = warp_wait(&sh.a_empty, (uint32_t)((k & 1) ^ 1), abort_flag);
       if (!ok) break;
       if (elect_one()) {
-        mbar_arrive_expect_tx(&sh.a_full, 2 * MT_TILE);
+        mbar_arrive_expect_tx(&sh.a_full, mp.split3 ? 2 * MT_TILE : MT_TILE);
         tma_load_2d(smem + MT_OFF_A, &mapAh, &sh.a_full, 0, sg.r * BM);
-        tma_load_2d(smem + MT_OFF_A + MT_TILE, &mapAl, &sh.a_full, 0, sg.r * BM);
+        if (mp.split3) tma_load_2d(smem + MT_OFF_A + MT_TILE, &mapAl, &sh.a_full, 0, sg.r * BM);
       }
       __syncwarp();
       a_issued = k + 1;
@@ -197,9 +199,9 @@ __global__ void __launch_bounds__(MT_NTHREADS, 1)
         if (!ok) break;
         unsigned char* st = smem + MT_OFF_ST + s * MT_ST_BYTES;
         if (elect_one()) {
-          mbar_arrive_expect_tx(&sh.full[s], 2 * MT_TILE + MT_BIAS);
+          mbar_arrive_expect_tx(&sh.full[s], (mp.split3 ? 2 * MT_TILE : MT_TILE) + MT_BIAS);
           tma_load_2d(st, &mapBh, &sh.full[s], 0, t * MT_BN);
-          tma_load_2d(st + MT_TILE, &mapBl, &sh.full[s], 0, t * MT_BN);
+          if (mp.split3) tma_load_2d(st + MT_TILE, &mapBl, &sh.full[s], 0, t * MT_BN);
           tma_load_2d(st + 2 * MT_TILE, &mapBbias, &sh.full[s], 0, t * MT_BN);
         }
         __syncwarp();
@@ -215,6 +217,7 @@ __global__ void __launch_bounds__(MT_NTHREADS, 1)
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     const uint64_t ones = desc_sw32(smem_u32(smem + MT_OFF_ONES));
+    const int split3 = mp.split3;
     const uint32_t a_hi = smem_u32(smem + MT_OFF_A), a_lo = a_hi + MT_TILE;
     const uint32_t p0 = smem_u32(smem + MT_OFF_P);
     bool ok = true;
@@ -238,8 +241,10 @@ __global__ void __launch_bounds__(MT_NTHREADS, 1)
           for (int kk = 0; kk < 4; ++kk) {
             const uint64_t adv = (uint64_t)(kk * 2), bdv = (uint64_t)(kk * 128);
             umma_py(tmem_base + MT_O_COL, ah + adv, bh + bdv, (first && h == 0 && kk == 0) ? 0u : 1u);
-            umma_py(tmem_base + MT_O_COL, ah + adv, bl + bdv, 1u);
-            umma_py(tmem_base + MT_O_COL, al + adv, bh + bdv, 1u);
+            if (split3) {
+              umma_py(tmem_base + MT_O_COL, ah + adv, bl + bdv, 1u);
+              umma_py(tmem_base + MT_O_COL, al + adv, bh + bdv, 1u);
+            }
           }
           // buffer h is next used by tile qq + 1, i.e. by the other warpgroup: each
           // warpgroup waits on its own barriers, so neither mistakes the other's release
@@ -275,8 +280,10 @@ __global__ void __launch_bounds__(MT_NTHREADS, 1)
           for (int kk = 0; kk < 4; ++kk) {
             const uint64_t adv = (uint64_t)(kk * 2);
             umma<MT_BN>(d_tmem, ah + adv, bh + adv, kk > 0 ? 1u : 0u);
-            umma<MT_BN>(d_tmem, ah + adv, bl + adv, 1u);
-            umma<MT_BN>(d_tmem, al + adv, bh + adv, 1u);
+            if (split3) {
+              umma<MT_BN>(d_tmem, ah + adv, bl + adv, 1u);
+              umma<MT_BN>(d_tmem, al + adv, bh + adv, 1u);
+            }
           }
           umma<MT_BN>(d_tmem, ones, bb, 1u);
           umma_commit(&sh.tmem_full[b]);
@@ -510,8 +517,8 @@ size_t map_sweep_tc_smem() { return tc::MT_SMEM_TOTAL; }
 cudaError_t launch_map_sweep_tc(const float* X, float* out, const float* L, int64_t nA, int64_t nB, int32_t d,
                                 float alpha, const void* mapAh, const void* mapAl, const void* mapBh,
                                 const void* mapBl, const void* mapBbias, float inv_sc, const float* mu,
-                                float* Opart, float* Rpart, unsigned* cnt, int G, int maxseg, int32_t* fault,
-                                cudaStream_t stream) {
+                                float* Opart, float* Rpart, unsigned* cnt, int G, int maxseg, int32_t split3,
+                                int32_t* fault, cudaStream_t stream) {
   static thread_local bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(tc::map_sweep_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -537,6 +544,7 @@ cudaError_t launch_map_sweep_tc(const float* X, float* out, const float* L, int6
   mp.alpha = alpha;
   mp.inv_sc = inv_sc;
   mp.mu = mu;
+  mp.split3 = split3;
   tc::map_sweep_tc<<<G, tc::MT_NTHREADS, tc::MT_SMEM_TOTAL, stream>>>(
       *reinterpret_cast<const CUtensorMap*>(mapAh), *reinterpret_cast<const CUtensorMap*>(mapAl),
       *reinterpret_cast<const CUtensorMap*>(mapBh), *reinterpret_cast<const CUtensorMap*>(mapBl),

@@ -224,9 +224,9 @@ static WsDims ws_dims(int64_t n, int64_t m, int32_t d, int32_t precision = PROGO
   w.opart_elems = rows_cap * d;
   w.rpart_elems = rows_cap;
   if (w.tc && w.dp <= 256) {
-    // tensor-core map steps: G * maxseg <= R + 3 G partial slots of 128 rows x 64
+    // tensor-core map steps: G * maxseg <= R + 3 G partial slots of 128 rows x dp
     const int64_t slots = w.rbmax + 3 * (int64_t)num_sms();
-    w.opart_elems = std::max<int64_t>(w.opart_elems, slots * BMr * 64);
+    w.opart_elems = std::max<int64_t>(w.opart_elems, slots * BMr * w.dp);
     w.rpart_elems = std::max<int64_t>(w.rpart_elems, slots * BMr);
   }
   return w;
@@ -394,8 +394,8 @@ struct TcOps {
   CUtensorMap xh_a, xl_a, yh_a, yl_a, xh_b, xl_b, yh_b, yl_b, xb, yb;
   // tensor-core map step (dp = 64): y-side bias rows in 128-row boxes
   CUtensorMap yb128;
-  // tensor-core map step for 64 < d <= 256: y operand and bias rows in 64-row boxes
-  CUtensorMap yh_m64, yl_m64, yb_m64;
+  // tensor-core map step for 64 < d <= 256: y operand and bias rows in 32-row boxes
+  CUtensorMap yh_m32, yl_m32, yb_m32;
   // centre mu of the operands and the squared norms |x_i - mu|^2, |y_j - mu|^2 that
   // the tensor-core sweeps use in place of |x_i|^2, |y_j|^2
   const float* mu = nullptr;
@@ -447,10 +447,11 @@ static int prep_tc(const float* x, int64_t n, const float* y, int64_t m, int32_t
   if (!rc && dp == 64) {
     rc = make_map(&ops->yb128, ws.yb, cdiv(m, 256) * 256, 16, 128);
   }
-  if (!rc && dp > 64 && map_tc_wide_supported(ops->nkb)) {
-    rc = make_map(&ops->yh_m64, ws.yh, m, dp, 64);
-    if (!rc) rc = make_map(&ops->yl_m64, yl, m, dp, 64);
-    if (!rc) rc = make_map(&ops->yb_m64, ws.yb, cdiv(m, 256) * 256, 16, 64);
+  if (!rc && dp > 64 && map_tc_onepass_supported(ops->nkb)) {
+    const int bt = map_tc_onepass_tile_cols();
+    rc = make_map(&ops->yh_m32, ws.yh, m, dp, bt);
+    if (!rc) rc = make_map(&ops->yl_m32, yl, m, dp, bt);
+    if (!rc) rc = make_map(&ops->yb_m32, ws.yb, cdiv(m, 256) * 256, 16, bt);
   }
   if (rc) return rc;
   const float bscale = (float)(kLog2e / eps);
@@ -878,22 +879,20 @@ static int map_step(float* X, int64_t n, const float* y, int64_t m, int32_t d, c
     const bool rec = prof_begin(r, s, kProfMap);
     CK(launch_map_sweep_tc(X, X, ws.L, n, m, d, (float)alpha, &ops->xh_a, &ops->xl_a, &ops->yh_a, &ops->yl_a,
                            &ops->yb128, (float)std::sqrt(eps / (2.0 * kLog2e)), ops->mu, ws.Opart, ws.Rpart,
-                           ws.mcnt, G, maxseg, ws.fault, s));
+                           ws.mcnt, G, maxseg, ops->split3, ws.fault, s));
     if (rec) prof_end(r, s, kProfMap, (double)n * (double)m);
     if (t_prof.on) t_prof.worked[kProfMap] += 1;
     return PROGOT_OK;
   }
-  if (tc && ops->nkb > 1 && map_tc_wide_supported(ops->nkb) && g_map_tc.load()) {
-    // 64 < d <= 256: one launch per chunk of 64 output coordinates, S recomputed per chunk
+  if (tc && ops->nkb > 1 && map_tc_onepass_supported(ops->nkb) && g_map_tc.load()) {
+    // 64 < d <= 256: one launch, S once per tile, all output coordinates in TMEM
     int G = 0, maxseg = 0;
-    tc_plan(n, m, 64, num_sms(), &G, &maxseg);
+    tc_plan(n, m, map_tc_onepass_tile_cols(), num_sms(), &G, &maxseg);
     ProfRec r;
     const bool rec = prof_begin(r, s, kProfMap);
-    const int dch = (int)cdiv(d, 64);
-    for (int oc = 0; oc < dch; ++oc)
-      CK(launch_map_sweep_tc_wide(X, X, ws.L, n, m, d, ops->nkb, oc, (float)alpha, &ops->xh_a, &ops->xl_a,
-                                  &ops->yh_m64, &ops->yl_m64, &ops->yb_m64, (float)std::sqrt(eps / (2.0 * kLog2e)),
-                                  ops->mu, ws.Opart, ws.Rpart, ws.mcnt, G, maxseg, ws.fault, s));
+    CK(launch_map_sweep_tc_onepass(X, X, ws.L, n, m, d, ops->nkb, (float)alpha, &ops->xh_a, &ops->xl_a,
+                                   &ops->yh_m32, &ops->yl_m32, &ops->yb_m32, (float)std::sqrt(eps / (2.0 * kLog2e)),
+                                   ops->mu, ws.Opart, ws.Rpart, ws.mcnt, G, maxseg, ops->split3, ws.fault, s));
     if (rec) prof_end(r, s, kProfMap, (double)n * (double)m);
     if (t_prof.on) t_prof.worked[kProfMap] += 1;
     return PROGOT_OK;

@@ -1,6 +1,7 @@
 """The tensor-core map step for 64 < d <= 256 (Alg. 2's displacement and Alg. 3) against
 the FP64 oracle: the progressive map on query clouds with ragged sizes, a full ProgOT
-solve, in-place use, and the 65536-point, d = 256 configuration on sampled rows."""
+solve, in-place use, the 65536-point, d = 256 configuration on sampled rows, and the
+hi-only precision on the tensor-core maps of every width."""
 import numpy as np
 import pytest
 
@@ -38,11 +39,12 @@ def map_rms_rel(T_gpu, T_ref, Y):
 
 
 @pytest.mark.parametrize("nq,m,d,K", [(333, 517, 96, 1), (1000, 700, 128, 3), (129, 130, 200, 2), (700, 1100, 256, 2),
-                                      (257, 65, 130, 1)])
+                                      (257, 65, 130, 1), (1, 31, 65, 1), (130, 33, 256, 2)])
 def test_wide_map_apply_parity_bf16x3(nat, nq, m, d, K):
-    """Alg. 3 with given g^(k) on the bf16x3 path (tensor-core map, one launch per chunk of
-    64 coordinates) against the oracle's progressive map from the same g (float32 round
-    trip), map RMS relative to the target spread <= 1e-3."""
+    """Alg. 3 with given g^(k) on the bf16x3 path (tensor-core map, S once per 32-column
+    tile and every 64-coordinate chunk of O in TMEM) against the oracle's progressive map
+    from the same g (float32 round trip), map RMS relative to the target spread <= 1e-3;
+    ragged m below one tile and a single query row included."""
     p = W.gmm_pair(nq, m, d, seed=5 * nq + d, k=4)
     rng = np.random.default_rng(d + nq)
     base = 0.05 * O.mean_cost(p.x, p.y)
@@ -100,3 +102,27 @@ def test_wide_map_full_size_sphere_d256_sampled(nat):
     rows = np.random.default_rng(5).choice(65536, 32, replace=False)
     T_ref = O.entropic_map(X64[rows], Y64, g.astype(np.float32).astype(np.float64), eps)
     assert map_rms_rel(host(out)[rows], T_ref, p.y) <= TOL_MIXED
+
+
+@pytest.mark.parametrize("d", [64, 128, 256])
+def test_hi_only_precision_map_and_solve(nat, d):
+    """precision = bf16 (hi parts only, one product per term) on the tensor-core maps for
+    d <= 64 and d > 64: the map step within 1e-2 of the oracle's, a K = 2 solve within
+    1e-2 of the oracle's solve, and bf16x3 at least as accurate on the same step."""
+    p = W.gmm_pair(500, 450, d, seed=41 + d, k=4)
+    eps = [0.05 * O.mean_cost(p.x, p.y)]
+    g = np.random.default_rng(d).normal(size=(1, 450)) * eps[0]
+    ref = O.progot_map(p.x, p.y, g.astype(np.float32).astype(np.float64), eps, [1.0])
+    errs = {}
+    for prec in ("bf16", "bf16x3"):
+        out = nat.entropic_map_apply(dev(p.x), dev(p.y), dev(g), eps, [1.0], precision=prec)
+        errs[prec] = map_rms_rel(host(out), ref, p.y)
+    assert errs["bf16"] <= 1e-2
+    assert errs["bf16x3"] <= min(errs["bf16"], TOL_MIXED)
+    K = 2
+    alpha = O.alpha_schedule(K)
+    e0 = O.mean_cost(p.x, p.y) / 20
+    res = nat.progot_solve(dev(p.x), dev(p.y), alpha, [3 * e0, e0], [1e-3] * K, max_iter=5000, precision="bf16")
+    assert res.status == nat.PROGOT_OK, nat.last_error()
+    ref = O.progot(None, p.x, None, p.y, [3 * e0, e0], alpha, [1e-6] * K)
+    assert map_rms_rel(host(res.x_out), ref.x_out, p.y) <= 1e-2
