@@ -487,6 +487,51 @@ def run_sweeps(args, rank, world, local):
     return 0
 
 
+def run_mapsteps(args, rank, world, local):
+    """Map steps alone (Alg. 3's displacement with a given g, K = 1, alpha = 1) on the
+    large coupling's clouds: two 32-component mixtures on the unit sphere, d = 256,
+    n = m = --map-n (65536 by default), eps = mean cost / 20, bf16x3. Each step is the
+    operand split, the tensor-core log-sum-exp pass and the map kernel; reports the time
+    per map kernel launch and its TFLOP/s (12 d flop per pair: S and P Y~, three products
+    each). A single-kernel case for profiling at smaller --map-n."""
+    import torch
+    from paper_2406_05061_gb300 import native
+    torch.cuda.set_device(local)
+    n = args.map_n
+    p = W.sphere_mixture_pair(n, n, 256, seed=2)
+    x, y = torch.from_numpy(p.x).cuda(), torch.from_numpy(p.y).cuda()
+    ws = native.Workspace(p.n, p.m, p.d, args.precision)
+    eps = native.progot_mean_cost(x, y, workspace=ws) / 20.0
+    g = torch.from_numpy((np.random.default_rng(4).normal(size=(1, p.m)) * 0.1 * eps).astype(np.float32)).cuda()
+    out = torch.empty_like(x)
+    run = lambda: native.entropic_map_apply(x, y, g, [eps], [1.0], precision=args.precision, out=out, workspace=ws)
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize()
+    native.profile(True, period=1)
+    native.launch_count(reset=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    mp = native.profile_read("map_sweep")
+    lse = native.profile_read("lse_sweep")
+    native.profile(False)
+    per_ms = mp["ms"] / max(1, mp["launches"])
+    split = 3.0 if args.precision == "bf16x3" else 1.0
+    tf = 4.0 * p.d * split * p.n * p.m / (per_ms * 1e-3) / 1e12
+    line = {"metric": "map_step_ms", "value": per_ms, "unit": "ms/map kernel launch", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": False, "dtype": args.precision,
+            "data": "synthetic", "config": {"workload": "mapsteps_sphere32_d256", "n": p.n, "m": p.m, "d": p.d,
+                                            "eps": eps, "launches_timed": mp["launches"]},
+            "tflops": tf, "lse_pass_ms": lse["ms"] / max(1, lse["launches"]),
+            "step_ms": e0.elapsed_time(e1) / args.steps, "gpu_launches": native.launch_count()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_blur(args, rank, world, local):
     """The de-blurring benchmark of Sec. 5.3 on synthetic images: n grey 32 x 32 images
     (d = 1024) against their Gaussian blurs; by Prop. 3 the optimal coupling is Id / n.
@@ -655,8 +700,9 @@ def main():
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the other precision's solves on the same workload (other_precisions)")
     ap.add_argument("--workload", default="gmm8_8192_d64",
-                    choices=sorted(WORKLOADS) + ["batched256", "serving", "blur", "coupling", "sweeps"])
+                    choices=sorted(WORKLOADS) + ["batched256", "serving", "blur", "coupling", "sweeps", "mapsteps"])
     ap.add_argument("--iters", type=int, default=30, help="sweeps: Sinkhorn iterations per solve")
+    ap.add_argument("--map-n", type=int, default=65536, help="mapsteps: points per cloud")
     ap.add_argument("--blur-n", type=int, default=60000, help="blur: number of images (32 x 32)")
     ap.add_argument("--sigma", type=float, default=2.0, help="blur: kernel width")
     ap.add_argument("--requests", type=int, default=240, help="serving: requests replayed from the stream")
@@ -676,6 +722,8 @@ def main():
         return run_blur(args, rank, world, local) if rank == 0 else 0
     if args.workload == "sweeps":
         return run_sweeps(args, rank, world, local) if rank == 0 else 0
+    if args.workload == "mapsteps":
+        return run_mapsteps(args, rank, world, local) if rank == 0 else 0
     if args.workload == "serving":
         return run_serving(args, rank, world, local)
 

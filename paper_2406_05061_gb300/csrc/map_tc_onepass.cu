@@ -12,11 +12,15 @@
 //     operand of chunk oc is the tile's K block oc of Y~, the very block S read, read
 //     again as an MN-major matrix; O holds all d coordinates (up to 256 TMEM columns).
 // With hi parts only (split3 = 0) each product is the single hi x hi term and the lo
-// blocks are not loaded. So S is formed once per (row, column) pair, where a chunk-per-launch map forms it once
-// per chunk. A stage holds a tile's K blocks (hi and lo) and bias rows from the S
-// products until its P Y~ products; the X row block (all K blocks, hi and lo) stays
-// resident for a segment. The MMA warp issues S(q + 1) before P Y~(q), so the
-// exponentials of tile q overlap the products of tile q + 1.
+// blocks are not loaded. So S is formed once per (row, column) pair, where a map run
+// chunk by chunk forms it once per chunk.
+// Operands in place: the X row block's hi part sits in TMEM (the A operand of the Xh Yh
+// and Xh Yl products, written by warpgroup 1 from the bf16 operand rows at each
+// segment's start), its lo part in shared memory (TMA); so four stages fit, each holding
+// a tile's K blocks (hi and lo) and bias rows from the S products until its P Y~
+// products, and three tiles' copies are in flight while a fourth is in use. The MMA
+// warp issues S and P Y~ in whichever order their inputs arrive, so the exponentials of
+// tile q overlap the products of tile q + 1 and P Y~(q) does not wait for a later copy.
 // CTA = 10 warps: producer, MMA issuer, two LSE warpgroups alternating tiles (one P
 // buffer shared in tile order); at a segment's end warpgroup 0 moves O to a per-CTA
 // partial slot and the last CTA of a row block combines the slots in CTA order
@@ -34,23 +38,25 @@ namespace tc {
 
 constexpr int OP_BN = 32;                      // columns j per tile
 constexpr int OP_NTHREADS = 320;
-constexpr int OP_TMEM_COLS = 512;              // S buffers at [0, 32) and [32, 64), O at [256, 256 + d)
+constexpr int OP_TMEM_COLS = 512;              // S buffers [0, 64), X hi [64, 64 + 32 nkb), O [256, 256 + 64 nkb)
+constexpr uint32_t OP_X_COL = 64;
 constexpr uint32_t OP_O_COL = 256;
 constexpr uint32_t OP_A_TILE = 128 * 64 * 2;   // 16 KB: one K block of the X row block (hi or lo)
 constexpr uint32_t OP_B_TILE = 32 * 64 * 2;    // 4 KB: one K block of a 32-row Y tile (hi or lo)
 constexpr uint32_t OP_BIAS = 32 * 32;          // 1 KB: 32 bias rows x 16 bf16
 constexpr uint32_t OP_P_HALF = 128 * 32 * 2;   // 8 KB: the P tile (hi or lo), 128 rows x 32 bf16
-constexpr int OP_NST = 2;                      // operand stages
+constexpr int OP_NST = 4;                      // operand stages
 constexpr int OP_MAXKB = 4;                    // d <= 256
 
 struct OpLayout {
-  uint32_t a_lo, ones, st, st_bytes, st_lo, st_bias, p, ctrl, total;
+  uint32_t ones, st, st_bytes, st_lo, st_bias, p, ctrl, total;
 };
 
 struct OpShared {
   uint64_t full[OP_NST], empty[OP_NST];
   uint64_t tmem_full[2], tmem_empty[2];
-  uint64_t a_full, a_empty;
+  uint64_t a_full, a_empty;  // X lo copied / the segment's S products done (X hi, X lo free)
+  uint64_t x_full;           // X hi written to TMEM (the 4 warps of warpgroup 1 arrive)
   uint64_t p_full, p_empty;  // the P buffer written (4 warps arrive) / consumed (commit)
   uint64_t o_full, o_empty;
   uint64_t drain;
@@ -62,12 +68,12 @@ struct OpShared {
   int32_t slot[8];
 };
 
-// A (hi, lo), the ones of the bias product, the stages (K blocks hi, K blocks lo, bias
-// rows), the P tile (hi, lo), the control block; offsets from a 1024-aligned base.
+// X lo (the K blocks of the row block), the ones of the bias product, the stages (K
+// blocks hi, K blocks lo, bias rows), the P tile (hi, lo), the control block; offsets
+// from a 1024-aligned base.
 __host__ __device__ inline OpLayout op_layout(int nkb) {
   OpLayout L;
-  L.a_lo = (uint32_t)nkb * OP_A_TILE;
-  L.ones = 2 * L.a_lo;
+  L.ones = (uint32_t)nkb * OP_A_TILE;
   L.st = L.ones + 4096;
   L.st_lo = (uint32_t)nkb * OP_B_TILE;
   L.st_bias = 2 * L.st_lo;
@@ -92,6 +98,7 @@ struct MapOnepassParams {
   float alpha;
   float inv_sc;
   const float* mu;
+  const uint32_t* xh;  // bf16 hi rows of the X operand (nA x 64 nkb, pairs packed in 32-bit words)
   int32_t split3;    // 1: hi/lo operands, three products; 0: hi parts only, one product
 };
 
@@ -129,6 +136,40 @@ __device__ __forceinline__ void op_umma(uint32_t d_tmem, uint64_t adesc, uint64_
       : "memory");
 }
 
+// Non-blocking test of the phase with the given parity (mbarrier.test_wait: no suspend,
+// so one role's barrier does not hold up the check of the other's).
+__device__ __forceinline__ bool op_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// The same with A read from TMEM (K-major: lane = row, two bf16 per 32-bit column).
+__device__ __forceinline__ void op_umma_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                           uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// 32 lanes x 32 columns of 32 bits from registers (one row per thread).
+__device__ __forceinline__ void op_tmem_st32(uint32_t taddr, const uint32_t* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
+      "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
+      "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+      : "memory");
+}
 __device__ __forceinline__ uint32_t op_bf2_bits(__nv_bfloat162 v) { return *reinterpret_cast<uint32_t*>(&v); }
 __device__ __forceinline__ void op_split8(const float* v, uint4& hi, uint4& lo) {
   uint32_t h[4], l[4];
@@ -173,6 +214,7 @@ __global__ void __launch_bounds__(OP_NTHREADS, 1)
     mbar_init(&sh.p_empty, 1);
     mbar_init(&sh.a_full, 1);
     mbar_init(&sh.a_empty, 1);
+    mbar_init(&sh.x_full, 4);
     mbar_init(&sh.o_full, 1);
     mbar_init(&sh.o_empty, 4);
     mbar_init(&sh.drain, 1);
@@ -206,11 +248,11 @@ __global__ void __launch_bounds__(OP_NTHREADS, 1)
       ok = warp_wait(&sh.a_empty, (uint32_t)((k & 1) ^ 1), abort_flag);
       if (!ok) break;
       if (elect_one()) {
-        mbar_arrive_expect_tx(&sh.a_full, nh * (uint32_t)nkb * OP_A_TILE);
-        for (int kb = 0; kb < nkb; ++kb) {
-          tma_load_2d(smem + kb * OP_A_TILE, &mapAh, &sh.a_full, kb * KB, sg.r * BM);
-          if (mp.split3) tma_load_2d(smem + Lo.a_lo + kb * OP_A_TILE, &mapAl, &sh.a_full, kb * KB, sg.r * BM);
-        }
+        // X lo into shared memory (X hi goes to TMEM through warpgroup 1); with hi parts
+        // only the barrier still completes, with no bytes
+        mbar_arrive_expect_tx(&sh.a_full, mp.split3 ? (uint32_t)nkb * OP_A_TILE : 0u);
+        if (mp.split3)
+          for (int kb = 0; kb < nkb; ++kb) tma_load_2d(smem + kb * OP_A_TILE, &mapAl, &sh.a_full, kb * KB, sg.r * BM);
       }
       __syncwarp();
       a_issued = k + 1;
@@ -238,94 +280,135 @@ __global__ void __launch_bounds__(OP_NTHREADS, 1)
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
+    // Two streams over the CTA's tiles in order, S(q) and P Y~(q), issued in whichever
+    // order their inputs arrive, S at most one tile ahead of the oldest tile still
+    // without P Y~: so S(q + 1) runs while the exponentials of tile q are computed, and
+    // an LSE warpgroup never waits on the P buffer's barrier more than one phase ahead
+    // of it (a parity wait two phases early would pass on the older phase and overwrite
+    // P before its products read it). The copies run up to three tiles ahead through
+    // the four stages. S and P Y~ write different TMEM columns, so the order of issue
+    // changes no result.
     const uint64_t ones = desc_sw32(smem_u32(smem + Lo.ones));
     const int split3 = mp.split3;
-    const uint32_t a_hi = smem_u32(smem), a_lo = a_hi + Lo.a_lo;
+    const uint32_t a_lo = smem_u32(smem);
     const uint32_t p0 = smem_u32(smem + Lo.p);
     const uint32_t id_s = make_idesc(BM, OP_BN);
     const uint32_t id_py = make_idesc(BM, 64) | (1u << 16);  // B MN-major
-    bool ok = true;
-    int q = 0, oseg = 0;
-    int pend = -1, pend_stage = 0;
-    bool pend_first = false, pend_last = false;
-    // O[:, chunk] += P Y~[:, chunk] for every chunk, from the P buffer and the tile's
-    // stage (its K block oc is the chunk's B operand); the stage and P go back after it
-    auto issue_py = [&](int qq, int stage, bool first, bool last) -> bool {
-      if (first && oseg > 0 && !warp_wait(&sh.o_empty, (uint32_t)((oseg - 1) & 1), abort_flag)) return false;
-      if (!warp_wait(&sh.p_full, (uint32_t)(qq & 1), abort_flag)) return false;
-      tc_fence_after();
-      const uint32_t st = smem_u32(smem + Lo.st + stage * Lo.st_bytes);
-      const uint64_t ah = op_desc_sw64(p0), al = op_desc_sw64(p0 + OP_P_HALF);
-      if (elect_one()) {
-        for (int oc = 0; oc < nkb; ++oc) {
-          const uint64_t bh = op_desc_mn(st + oc * OP_B_TILE), bl = op_desc_mn(st + Lo.st_lo + oc * OP_B_TILE);
-          const uint32_t d_o = tmem_base + OP_O_COL + (uint32_t)(oc * 64);
-#pragma unroll
-          for (int kk = 0; kk < 2; ++kk) {
-            // +32 bytes per K = 16 step in P's 64-byte rows; +16 rows (2048 bytes) of the Y block
-            const uint64_t adv = (uint64_t)(kk * 2), bdv = (uint64_t)(kk * 128);
-            op_umma(d_o, ah + adv, bh + bdv, id_py, (first && kk == 0) ? 0u : 1u);
-            if (split3) {
-              op_umma(d_o, ah + adv, bl + bdv, id_py, 1u);
-              op_umma(d_o, al + adv, bh + bdv, id_py, 1u);
-            }
-          }
-        }
-        umma_commit(&sh.p_empty);
-        umma_commit(&sh.empty[stage]);
-        if (last) umma_commit(&sh.o_full);
-      }
-      __syncwarp();
-      if (last) ++oseg;
-      return true;
-    };
-    int u = 0;
-    for (int k = 0; k < nseg && ok; ++k) {
+    int total = 0;
+    for (int k = 0; k < nseg; ++k) {
       const Seg sg = segment(sp, c, k);
-      ok = warp_wait(&sh.a_full, (uint32_t)(k & 1), abort_flag);
-      if (!ok) break;
-      tc_fence_after();
-      for (int t = sg.t0; t < sg.t1 && ok; ++t, ++q, ++u) {
-        const int b = q & 1, s = u % OP_NST;
-        ok = warp_wait(&sh.tmem_empty[b], (uint32_t)(((q >> 1) & 1) ^ 1), abort_flag);
-        if (!ok) break;
-        ok = warp_wait(&sh.full[s], (uint32_t)((u / OP_NST) & 1), abort_flag);
-        if (!ok) break;
-        tc_fence_after();
-        const uint32_t st = smem_u32(smem + Lo.st + s * Lo.st_bytes);
-        const uint32_t d_tmem = tmem_base + (uint32_t)(b * OP_BN);
-        if (elect_one()) {
-          for (int kb = 0; kb < nkb; ++kb) {
-            const uint64_t bh = desc_sw128(st + kb * OP_B_TILE), bl = desc_sw128(st + Lo.st_lo + kb * OP_B_TILE);
-            const uint64_t ah = desc_sw128(a_hi + kb * OP_A_TILE), al = desc_sw128(a_lo + kb * OP_A_TILE);
+      total += sg.t1 - sg.t0;
+    }
+    bool ok = true;
+    // S stream: segment, its tiles, the tile's column index and CTA tile index
+    int ks = 0, qs = 0;
+    Seg sgs = segment(sp, c, 0);
+    int ts = sgs.t0;
+    bool a_pending = true;  // the segment's A row block not yet seen
+    // P Y~ stream
+    int kp = 0, qp = 0, oseg = 0;
+    Seg sgp = sgs;
+    int tpp = sgp.t0;
+    unsigned long long t_idle = 0;
+    uint32_t spins = 0;
+    while (ok && qp < total) {
+      bool progressed = false;
+      if (qs < total && qs <= qp + 1) {
+        bool r = !a_pending ||
+                 (op_test_wait(&sh.a_full, (uint32_t)(ks & 1)) && op_test_wait(&sh.x_full, (uint32_t)(ks & 1)));
+        r = r && op_test_wait(&sh.tmem_empty[qs & 1], (uint32_t)(((qs >> 1) & 1) ^ 1));
+        r = r && op_test_wait(&sh.full[qs % OP_NST], (uint32_t)((qs / OP_NST) & 1));
+        if (__all_sync(0xffffffffu, r)) {
+          tc_fence_after();
+          const int b = qs & 1;
+          const uint32_t st = smem_u32(smem + Lo.st + (qs % OP_NST) * Lo.st_bytes);
+          const uint32_t d_tmem = tmem_base + (uint32_t)(b * OP_BN);
+          const bool seg_end = (ts == sgs.t1 - 1);
+          if (elect_one()) {
+            for (int kb = 0; kb < nkb; ++kb) {
+              const uint64_t bh = desc_sw128(st + kb * OP_B_TILE), bl = desc_sw128(st + Lo.st_lo + kb * OP_B_TILE);
+              const uint64_t al = desc_sw128(a_lo + kb * OP_A_TILE);
 #pragma unroll
-            for (int kk = 0; kk < KB / 16; ++kk) {
-              const uint64_t adv = (uint64_t)(kk * 2);
-              op_umma(d_tmem, ah + adv, bh + adv, id_s, (kb > 0 || kk > 0) ? 1u : 0u);
-              if (split3) {
-                op_umma(d_tmem, ah + adv, bl + adv, id_s, 1u);
-                op_umma(d_tmem, al + adv, bh + adv, id_s, 1u);
+              for (int kk = 0; kk < KB / 16; ++kk) {
+                // K = 16 step: 8 TMEM columns of X hi, +32 bytes in the 128-byte swizzle atom
+                const uint32_t ax = tmem_base + OP_X_COL + (uint32_t)(kb * 32 + kk * 8);
+                const uint64_t adv = (uint64_t)(kk * 2);
+                op_umma_ta(d_tmem, ax, bh + adv, id_s, (kb > 0 || kk > 0) ? 1u : 0u);
+                if (split3) {
+                  op_umma_ta(d_tmem, ax, bl + adv, id_s, 1u);
+                  op_umma(d_tmem, al + adv, bh + adv, id_s, 1u);
+                }
               }
             }
+            op_umma(d_tmem, ones, desc_sw32(st + Lo.st_bias), id_s, 1u);
+            umma_commit(&sh.tmem_full[b]);
+            if (seg_end) umma_commit(&sh.a_empty);
           }
-          op_umma(d_tmem, ones, desc_sw32(st + Lo.st_bias), id_s, 1u);
-          umma_commit(&sh.tmem_full[b]);
-          if (t == sg.t1 - 1) umma_commit(&sh.a_empty);
+          __syncwarp();
+          a_pending = false;
+          ++qs;
+          if (++ts == sgs.t1 && ++ks < nseg) {
+            sgs = segment(sp, c, ks);
+            ts = sgs.t0;
+            a_pending = true;
+          }
+          progressed = true;
         }
-        __syncwarp();
-        // P Y~ of the previous tile after S of this one
-        if (pend >= 0) {
-          ok = issue_py(pend, pend_stage, pend_first, pend_last);
-          pend = -1;
-          if (!ok) break;
+      }
+      if (qp < qs) {
+        // O[:, chunk] += P Y~[:, chunk] for every chunk, from the P buffer and the tile's
+        // stage (its K block oc is the chunk's B operand); the stage and P go back after it
+        const bool first = (tpp == sgp.t0), last = (tpp == sgp.t1 - 1);
+        bool r = !(first && oseg > 0) || op_test_wait(&sh.o_empty, (uint32_t)((oseg - 1) & 1));
+        r = r && op_test_wait(&sh.p_full, (uint32_t)(qp & 1));
+        if (__all_sync(0xffffffffu, r)) {
+          tc_fence_after();
+          const int stage = qp % OP_NST;
+          const uint32_t st = smem_u32(smem + Lo.st + stage * Lo.st_bytes);
+          const uint64_t ah = op_desc_sw64(p0), al = op_desc_sw64(p0 + OP_P_HALF);
+          if (elect_one()) {
+            for (int oc = 0; oc < nkb; ++oc) {
+              const uint64_t bh = op_desc_mn(st + oc * OP_B_TILE), bl = op_desc_mn(st + Lo.st_lo + oc * OP_B_TILE);
+              const uint32_t d_o = tmem_base + OP_O_COL + (uint32_t)(oc * 64);
+#pragma unroll
+              for (int kk = 0; kk < 2; ++kk) {
+                // +32 bytes per K = 16 step in P's 64-byte rows; +16 rows (2048 bytes) of the Y block
+                const uint64_t adv = (uint64_t)(kk * 2), bdv = (uint64_t)(kk * 128);
+                op_umma(d_o, ah + adv, bh + bdv, id_py, (first && kk == 0) ? 0u : 1u);
+                if (split3) {
+                  op_umma(d_o, ah + adv, bl + bdv, id_py, 1u);
+                  op_umma(d_o, al + adv, bh + bdv, id_py, 1u);
+                }
+              }
+            }
+            umma_commit(&sh.p_empty);
+            umma_commit(&sh.empty[stage]);
+            if (last) umma_commit(&sh.o_full);
+          }
+          __syncwarp();
+          if (last) ++oseg;
+          ++qp;
+          if (++tpp == sgp.t1 && ++kp < nseg) {
+            sgp = segment(sp, c, kp);
+            tpp = sgp.t0;
+          }
+          progressed = true;
         }
-        pend = q;
-        pend_stage = s;
-        pend_first = (t == sg.t0);
-        pend_last = (t == sg.t1 - 1);
+      }
+      if (progressed) {
+        spins = 0;
+      } else if ((++spins & 255) == 0) {
+        // bounded: no input for kWaitNs, or another role gave up
+        const unsigned long long now = global_ns();
+        if (spins == 256) t_idle = now;
+        if (*abort_flag) ok = false;
+        else if (now - t_idle > kWaitNs) {
+          *abort_flag = 1;
+          ok = false;
+        }
+        ok = __all_sync(0xffffffffu, ok) != 0;
       }
     }
-    if (ok && pend >= 0) ok = issue_py(pend, pend_stage, pend_first, pend_last);
     if (elect_one()) umma_commit(&sh.drain);
     __syncwarp();
     warp_wait(&sh.drain, 0, abort_flag, true);
@@ -344,6 +427,32 @@ __global__ void __launch_bounds__(OP_NTHREADS, 1)
       const Seg sg = segment(sp, c, k);
       const int64_t i = (int64_t)sg.r * BM + row_local;
       const bool row_ok = i < mp.nA;
+      if (wg == 1 && !dead) {
+        // X hi of this row block into TMEM once the previous segment's S products are
+        // done (one row per thread, 32 columns = 64 bf16 per store; zeros past the cloud)
+        if (!warp_wait(&sh.a_empty, (uint32_t)((k & 1) ^ 1), abort_flag)) {
+          dead = true;
+        } else {
+          tc_fence_after();
+          const uint4* src = reinterpret_cast<const uint4*>(mp.xh + i * (int64_t)(nkb * 32));
+          for (int kb = 0; kb < nkb; ++kb) {
+            uint32_t w[32];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const uint4 u4 = row_ok ? __ldg(src + kb * 8 + e) : make_uint4(0u, 0u, 0u, 0u);
+              w[4 * e] = u4.x;
+              w[4 * e + 1] = u4.y;
+              w[4 * e + 2] = u4.z;
+              w[4 * e + 3] = u4.w;
+            }
+            op_tmem_st32(tmem_base + ((uint32_t)(quarter * 32) << 16) + OP_X_COL + (uint32_t)(kb * 32), w);
+          }
+          asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&sh.x_full);
+        }
+      }
       const float Lr = row_ok ? mp.L[i] : 0.f;
       float rs = 0.f;
       for (int t = sg.t0; t < sg.t1; ++t, ++tl) {
@@ -542,8 +651,8 @@ int map_tc_onepass_tile_cols() { return tc::OP_BN; }
 cudaError_t launch_map_sweep_tc_onepass(const float* X, float* out, const float* L, int64_t nA, int64_t nB,
                                         int32_t d, int32_t nkb, float alpha, const void* mapAh, const void* mapAl,
                                         const void* mapBh, const void* mapBl, const void* mapBbias, float inv_sc,
-                                        const float* mu, float* Opart, float* Rpart, unsigned* cnt, int G, int maxseg,
-                                        int32_t split3, int32_t* fault, cudaStream_t stream) {
+                                        const float* mu, const void* xh, float* Opart, float* Rpart, unsigned* cnt,
+                                        int G, int maxseg, int32_t split3, int32_t* fault, cudaStream_t stream) {
   if (!map_tc_onepass_supported(nkb)) return cudaErrorInvalidValue;
   const size_t smem = tc::op_layout(nkb).total;
   static thread_local size_t attr_bytes = 0;
@@ -573,6 +682,7 @@ cudaError_t launch_map_sweep_tc_onepass(const float* X, float* out, const float*
   mp.inv_sc = inv_sc;
   mp.mu = mu;
   mp.split3 = split3;
+  mp.xh = reinterpret_cast<const uint32_t*>(xh);
   tc::map_sweep_tc_onepass<<<G, tc::OP_NTHREADS, smem, stream>>>(
       *reinterpret_cast<const CUtensorMap*>(mapAh), *reinterpret_cast<const CUtensorMap*>(mapAl),
       *reinterpret_cast<const CUtensorMap*>(mapBh), *reinterpret_cast<const CUtensorMap*>(mapBl),

@@ -99,14 +99,15 @@ size_t map_sweep_tc_smem();
 // The same for 64 < d <= 256 in one pass (map_tc_onepass.cu): tiles of 32 columns (B maps
 // and bias rows in 32-row boxes) whose K blocks all stay in one stage, S formed once per
 // tile and every chunk of 64 output coordinates accumulated in TMEM; Opart slots hold
-// 128 rows x 64 nkb floats.
+// 128 rows x 64 nkb floats. xh is the bf16 hi operand of X (nA x 64 nkb, the buffer the
+// A maps describe), read directly into TMEM.
 bool map_tc_onepass_supported(int nkb);
 int map_tc_onepass_tile_cols();
 cudaError_t launch_map_sweep_tc_onepass(const float* X, float* out, const float* L, int64_t nA, int64_t nB,
                                         int32_t d, int32_t nkb, float alpha, const void* mapAh, const void* mapAl,
                                         const void* mapBh, const void* mapBl, const void* mapBbias, float inv_sc,
-                                        const float* mu, float* Opart, float* Rpart, unsigned* cnt, int G, int maxseg,
-                                        int32_t split3, int32_t* fault, cudaStream_t stream);
+                                        const float* mu, const void* xh, float* Opart, float* Rpart, unsigned* cnt,
+                                        int G, int maxseg, int32_t split3, int32_t* fault, cudaStream_t stream);
 int tc_stages(int nkb, int split3);
 int tc_tile_cols(int nkb, int split3);  // 128 or 256
 

@@ -89,17 +89,19 @@ def test_progot_solve_parity_bf16x3_wide(nat, d):
     assert map_rms_rel(host(res.x_out), ref.x_out, p.y) <= TOL_MIXED
 
 
-def test_wide_map_full_size_sphere_d256_sampled(nat):
-    """65536 x 65536 points on the sphere in d = 256 (the large coupling configuration):
-    one bf16x3 map step with a given g, checked on 32 sampled rows computed one by one by
-    the oracle."""
-    p = W.sphere_mixture_pair(65536, 65536, 256, seed=2)
+@pytest.mark.parametrize("n", [4096, 65536])
+def test_wide_map_full_size_sphere_d256_sampled(nat, n):
+    """n x n points on the sphere in d = 256 (65536: the large coupling configuration;
+    4096: every CTA runs tens of tiles over several row blocks, so the operand stages,
+    TMEM buffers and the P hand-off all wrap): one bf16x3 map step with a given g,
+    checked on 32 sampled rows computed one by one by the oracle."""
+    p = W.sphere_mixture_pair(n, n, 256, seed=2)
     X64, Y64 = p.x.astype(np.float64), p.y.astype(np.float64)
-    sub = np.random.default_rng(0).choice(65536, 1024, replace=False)
+    sub = np.random.default_rng(0).choice(n, 1024, replace=False)
     eps = O.mean_cost(X64[sub], Y64[sub]) / 20
-    g = np.random.default_rng(4).normal(size=65536) * 0.1 * eps
+    g = np.random.default_rng(4).normal(size=n) * 0.1 * eps
     out = nat.entropic_map_apply(dev(p.x), dev(p.y), dev(g.reshape(1, -1)), [eps], [1.0], precision="bf16x3")
-    rows = np.random.default_rng(5).choice(65536, 32, replace=False)
+    rows = np.random.default_rng(5).choice(n, 32, replace=False)
     T_ref = O.entropic_map(X64[rows], Y64, g.astype(np.float32).astype(np.float64), eps)
     assert map_rms_rel(host(out)[rows], T_ref, p.y) <= TOL_MIXED
 
