@@ -6,11 +6,11 @@
 //   S = X Y~^T over all K blocks of the operands (bf16 hi/lo pre-scaled by sqrt(c), three
 //     products, beta added by one more K = 16 step) into one of two 32-column TMEM
 //     buffers (tiles of 32 columns j);
-//   O[:, chunk] += P Y~[:, chunk] for every chunk of 64 output coordinates, with P_ij =
+//   O += P Y~ over all d coordinates at once (N = 64 nkb <= 256), with P_ij =
 //     2^{t_ij - L_i} written by the LSE warps into shared memory as bf16 hi/lo (K-major,
-//     64-byte swizzle, K = 32 columns of the tile), three products per chunk; the B
-//     operand of chunk oc is the tile's K block oc of Y~, the very block S read, read
-//     again as an MN-major matrix; O holds all d coordinates (up to 256 TMEM columns).
+//     64-byte swizzle, K = 32 columns of the tile), three products; the B operand is the
+//     tile's K blocks of Y~, the very blocks S read, read again as one MN-major matrix
+//     whose 64-coordinate column groups are the K blocks; O takes up to 256 TMEM columns.
 // With hi parts only (split3 = 0) each product is the single hi x hi term and the lo
 // blocks are not loaded. So S is formed once per (row, column) pair, where a map run
 // chunk by chunk forms it once per chunk.
@@ -115,12 +115,13 @@ __device__ __forceinline__ uint64_t op_desc_sw64(uint32_t saddr) {
   d |= (uint64_t)4 << 61;  // 64-byte swizzle
   return d;
 }
-// The stage's K-major Y block read as MN-major (rows of 128 B along K = j, 64 coordinates
-// each, 8-row groups 1024 B apart).
+// The stage's K-major Y blocks read as one MN-major matrix: rows of 128 B along K = j
+// (64 coordinates each, 8-row groups 1024 B apart), the next 64 coordinates in the next
+// K block, OP_B_TILE bytes on (the leading offset between 64-wide column groups).
 __device__ __forceinline__ uint64_t op_desc_mn(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)(1024 >> 4) << 16;
+  d |= (uint64_t)(OP_B_TILE >> 4) << 16;
   d |= (uint64_t)(1024 >> 4) << 32;
   d |= (uint64_t)1 << 46;
   d |= (uint64_t)2 << 61;
@@ -293,7 +294,7 @@ __global__ void __launch_bounds__(OP_NTHREADS, 1)
     const uint32_t a_lo = smem_u32(smem);
     const uint32_t p0 = smem_u32(smem + Lo.p);
     const uint32_t id_s = make_idesc(BM, OP_BN);
-    const uint32_t id_py = make_idesc(BM, 64) | (1u << 16);  // B MN-major
+    const uint32_t id_py = make_idesc(BM, 64 * nkb) | (1u << 16);  // N = every coordinate, B MN-major
     int total = 0;
     for (int k = 0; k < nseg; ++k) {
       const Seg sg = segment(sp, c, k);
@@ -356,8 +357,8 @@ __global__ void __launch_bounds__(OP_NTHREADS, 1)
         }
       }
       if (qp < qs) {
-        // O[:, chunk] += P Y~[:, chunk] for every chunk, from the P buffer and the tile's
-        // stage (its K block oc is the chunk's B operand); the stage and P go back after it
+        // O += P Y~ over every coordinate, from the P buffer and the tile's stage (its K
+        // blocks are the B operand's column groups); the stage and P go back after it
         const bool first = (tpp == sgp.t0), last = (tpp == sgp.t1 - 1);
         bool r = !(first && oseg > 0) || op_test_wait(&sh.o_empty, (uint32_t)((oseg - 1) & 1));
         r = r && op_test_wait(&sh.p_full, (uint32_t)(qp & 1));
@@ -367,18 +368,16 @@ __global__ void __launch_bounds__(OP_NTHREADS, 1)
           const uint32_t st = smem_u32(smem + Lo.st + stage * Lo.st_bytes);
           const uint64_t ah = op_desc_sw64(p0), al = op_desc_sw64(p0 + OP_P_HALF);
           if (elect_one()) {
-            for (int oc = 0; oc < nkb; ++oc) {
-              const uint64_t bh = op_desc_mn(st + oc * OP_B_TILE), bl = op_desc_mn(st + Lo.st_lo + oc * OP_B_TILE);
-              const uint32_t d_o = tmem_base + OP_O_COL + (uint32_t)(oc * 64);
+            const uint64_t bh = op_desc_mn(st), bl = op_desc_mn(st + Lo.st_lo);
+            const uint32_t d_o = tmem_base + OP_O_COL;
 #pragma unroll
-              for (int kk = 0; kk < 2; ++kk) {
-                // +32 bytes per K = 16 step in P's 64-byte rows; +16 rows (2048 bytes) of the Y block
-                const uint64_t adv = (uint64_t)(kk * 2), bdv = (uint64_t)(kk * 128);
-                op_umma(d_o, ah + adv, bh + bdv, id_py, (first && kk == 0) ? 0u : 1u);
-                if (split3) {
-                  op_umma(d_o, ah + adv, bl + bdv, id_py, 1u);
-                  op_umma(d_o, al + adv, bh + bdv, id_py, 1u);
-                }
+            for (int kk = 0; kk < 2; ++kk) {
+              // +32 bytes per K = 16 step in P's 64-byte rows; +16 rows (2048 bytes) of the Y blocks
+              const uint64_t adv = (uint64_t)(kk * 2), bdv = (uint64_t)(kk * 128);
+              op_umma(d_o, ah + adv, bh + bdv, id_py, (first && kk == 0) ? 0u : 1u);
+              if (split3) {
+                op_umma(d_o, ah + adv, bl + bdv, id_py, 1u);
+                op_umma(d_o, al + adv, bh + bdv, id_py, 1u);
               }
             }
             umma_commit(&sh.p_empty);
