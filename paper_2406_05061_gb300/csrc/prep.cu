@@ -254,6 +254,26 @@ cudaError_t launch_lse_uncenter(float* L, const float* X, int64_t n, int32_t d, 
   return cudaGetLastError();
 }
 
+// L_i = (eps log w_i + |a_i|^2 - f_i) / (eps ln2): the row log-sum-exp (log2 units) that
+// an f-update wrote as the potential f_i = eps log w_i + |a_i|^2 - eps ln2 L_i, recovered
+// from f in float64 (w = NULL: uniform weights, log w_i = log_w_uniform).
+__global__ void lse_from_potential_kernel(const float* __restrict__ f, const float* __restrict__ an,
+                                          const float* __restrict__ w, double log_w_uniform, double eps, int64_t n,
+                                          float* __restrict__ L) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double logw = w ? log((double)w[i]) : log_w_uniform;
+  L[i] = (float)((eps * logw + (double)an[i] - (double)f[i]) / (eps * 0.69314718055994530942));
+}
+
+cudaError_t launch_lse_from_potential(const float* f, const float* an, const float* w, double log_w_uniform,
+                                      double eps, int64_t n, float* L, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  lse_from_potential_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(f, an, w, log_w_uniform, eps, n, L);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_scale(float* v, int64_t n, float factor, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   scale_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(v, n, factor);

@@ -405,6 +405,9 @@ struct TcOps {
   int split3 = 0;
   int bn = 128;
   bool on = false;
+  // ws.L holds the row log-sum-exps of t against the y-side bias rows (the map step's
+  // stabiliser), written by the persistent loop from its last f-update
+  bool lse_ready = false;
 };
 
 // Split sqrt(2 log2(e) / eps) (X - mu) and (Y - mu) into bf16 hi/lo and describe them
@@ -418,6 +421,7 @@ static int prep_tc(const float* x, int64_t n, const float* y, int64_t m, int32_t
                    const Workspace& ws, TcOps* ops, cudaStream_t s, const float* f_cur = nullptr,
                    const float* g_cur = nullptr) {
   ops->on = precision != PROGOT_FP32;
+  ops->lse_ready = false;
   if (!ops->on) return PROGOT_OK;
   const int32_t dp = pad64(d);
   ops->nkb = dp / 64;
@@ -556,7 +560,7 @@ static int lse_sweep(const SweepParams& p, int32_t precision, cudaStream_t s, co
 // f_a, g in g, and the y-side bias rows (ws.yb) hold g for a map step at the same eps.
 static int sinkhorn_loop_persistent(SweepParams pf, SweepParams pg, int64_t n, int64_t m, int32_t max_iter,
                                     double tau, float* f_a, float* f_b, float* g, const Workspace& ws,
-                                    const TcOps& ops, int32_t* iters_out, double* err_out, cudaStream_t s) {
+                                    TcOps& ops, int32_t* iters_out, double* err_out, cudaStream_t s) {
   pf.An = ops.xnc;
   pf.Bn = ops.ync;
   pg.An = ops.ync;
@@ -656,6 +660,14 @@ static int sinkhorn_loop_persistent(SweepParams pf, SweepParams pg, int64_t n, i
     t_prof.recs.push_back(pr);
     t_prof.seq[kProfLse] += sweeps;
     t_prof.worked[kProfLse] += sweeps;
+  }
+  // The loop stops after an f-update whose result it does not adopt (f stays the iterate
+  // the stop test measured, g is unchanged): that update formed f_new from exactly the
+  // t_ij = c x~.y~ + beta(g) of a map step that follows, so its row log-sum-exps, read
+  // back from f_new, are the map step's L and spare it a sweep.
+  if (fin.status != kNumeric) {
+    CK(launch_lse_from_potential(fin.fcur == 0 ? f_b : f_a, ops.xnc, pf.wA, pf.log_w_uniform, pf.eps, n, ws.L, s));
+    ops.lse_ready = true;
   }
   if (fin.fcur == 1) CK(cudaMemcpyAsync(f_a, f_b, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
   // the map step that may follow reads g through the y-side bias rows
@@ -869,7 +881,10 @@ static int map_step(float* X, int64_t n, const float* y, int64_t m, int32_t d, c
   pl.out = ws.L;
   pl.mode = kModeLse;
   apply_cost(pl, cost, eps);
-  int rc = tc ? lse_sweep(pl, precision, s, ops, true, &ws) : lse_sweep(pl, PROGOT_FP32, s);
+  // the persistent loop that produced g may already have left L in ws.L
+  int rc = (tc && ops->lse_ready) ? PROGOT_OK
+           : tc                   ? lse_sweep(pl, precision, s, ops, true, &ws)
+                                  : lse_sweep(pl, PROGOT_FP32, s);
   if (rc) return rc;
   if (tc && ops->nkb == 1 && g_map_tc.load()) {
     // d <= 64: S and P Y both on the tensor cores (P Y reuses the centred, scaled y operand)

@@ -51,6 +51,10 @@ cudaError_t launch_row_sqnorm(const float* X, int64_t n, int32_t d, float* out, 
 // partial: reduce_parts() * 2 * d doubles of scratch.
 cudaError_t launch_center(const float* X, int64_t n, const float* Y, int64_t m, int32_t d, double* partial, float* mu,
                           cudaStream_t s);
+// L_i = (eps log w_i + |a_i|^2 - f_i) / (eps ln2) from a potential an f-update wrote
+// (w = NULL: log w_i = log_w_uniform).
+cudaError_t launch_lse_from_potential(const float* f, const float* an, const float* w, double log_w_uniform,
+                                      double eps, int64_t n, float* L, cudaStream_t s);
 cudaError_t launch_lse_uncenter(float* L, const float* X, int64_t n, int32_t d, const float* mu, float bscale,
                                 cudaStream_t s);
 cudaError_t launch_scale(float* v, int64_t n, float factor, cudaStream_t s);
