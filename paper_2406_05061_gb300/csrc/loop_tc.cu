@@ -366,6 +366,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   volatile int32_t* abort_flag = &sh.abort_flag;
   constexpr uint32_t B_TILE_BYTES = (uint32_t)BN * KB * 2, BIAS_TILE_BYTES = (uint32_t)BN * 32;
   constexpr int RB_PER_TILE = BN / BM;  // row blocks of B under one column tile
+  constexpr int NC = BN / 64;           // 32-column TMEM loads of one LSE warpgroup per tile
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -378,7 +379,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&sh.tmem_full[b], 1);
-      mbar_init(&sh.tmem_empty[b], 4);
+      mbar_init(&sh.tmem_empty[b], 8);  // every LSE warp reads its columns of each tile
       mbar_init(&sh.a_full[b], 1);
       mbar_init(&sh.a_empty[b], 1);
     }
@@ -571,7 +572,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int wg = (warp - 2) >> 2;
     const int quarter = warp & 3;
     const int row_local = quarter * 32 + lane;
-    int tl = 0, jt = 0, kseg = 0;
+    int tl = 0, kseg = 0;
     bool dead = false;
     for (int it = P.seq0; it < it_end; ++it) {
       if (it > P.seq0) {
@@ -588,67 +589,62 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const Seg sg = seg_at(Sd, c, k, P.maxseg);
           float m_run = -INFINITY, s_run = 0.f;
           for (int t = sg.t0; t < sg.t1; ++t, ++tl) {
-            if ((tl & 1) != wg) continue;
-            const uint32_t ph = (uint32_t)(jt & 1);
-            ++jt;
+            // both warpgroups take every tile, warpgroup wg its columns wg BN / 2 ..: the
+            // accumulator goes back to the MMA warp as soon as both halves are in
+            // registers, and the exponentials overlap the next tile's products
+            const uint32_t ph = (uint32_t)((tl >> 1) & 1);
             if (dead) continue;
             int okv = 0;
-            if (lane == 0) okv = wait_bar(&sh.tmem_full[wg], ph, abort_flag, P) ? 1 : 0;
+            if (lane == 0) okv = wait_bar(&sh.tmem_full[tl & 1], ph, abort_flag, P) ? 1 : 0;
             if (__shfl_sync(0xffffffffu, okv, 0) == 0) {
               dead = true;
               continue;
             }
             __syncwarp();
             tc_fence_after();
-            const uint32_t taddr0 = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(wg * BN);
-#pragma unroll 1
-            for (int half = 0; half < BN / 128; ++half) {
-              const uint32_t taddr = taddr0 + (uint32_t)(half * 128);
-              float v[4][32];
-              PROGOT_TMEM_LD32(taddr + 0, v[0]);
-              PROGOT_TMEM_LD32(taddr + 32, v[1]);
-              PROGOT_TMEM_LD32(taddr + 64, v[2]);
-              PROGOT_TMEM_LD32(taddr + 96, v[3]);
-              tmem_wait_ld();
-              if (half == BN / 128 - 1) {
-                // the whole accumulator is in registers: hand the TMEM buffer back
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&sh.tmem_empty[wg]);
+            const uint32_t taddr =
+                tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((tl & 1) * BN + wg * (BN / 2));
+            float v[NC][32];
+#pragma unroll
+            for (int cc = 0; cc < NC; ++cc) PROGOT_TMEM_LD32(taddr + 32 * cc, v[cc]);
+            tmem_wait_ld();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh.tmem_empty[tl & 1]);
+            float mx[2 * NC];
+#pragma unroll
+            for (int q = 0; q < 2 * NC; ++q) mx[q] = v[q >> 1][(q & 1) * 16];
+#pragma unroll
+            for (int cc = 0; cc < NC; ++cc)
+#pragma unroll
+              for (int i = 1; i < 16; i += 2) {
+                mx[cc * 2] = max3(mx[cc * 2], v[cc][i], v[cc][i + 1 < 16 ? i + 1 : i]);
+                mx[cc * 2 + 1] = max3(mx[cc * 2 + 1], v[cc][16 + i], v[cc][16 + (i + 1 < 16 ? i + 1 : i)]);
               }
-              float mx[8];
+            float tmax = mx[0];
 #pragma unroll
-              for (int q = 0; q < 8; ++q) mx[q] = v[q >> 1][(q & 1) * 16];
+            for (int q = 1; q < 2 * NC; ++q) tmax = fmaxf(tmax, mx[q]);
+            const float mnew = fmaxf(m_run, tmax);
+            if (mnew != -INFINITY) {
+              const uint64_t negm = pack2(-mnew, -mnew);
+              uint64_t acc[4];
 #pragma unroll
-              for (int cc = 0; cc < 4; ++cc)
+              for (int q = 0; q < 4; ++q) acc[q] = 0ull;
 #pragma unroll
-                for (int i = 1; i < 16; i += 2) {
-                  mx[cc * 2] = max3(mx[cc * 2], v[cc][i], v[cc][i + 1 < 16 ? i + 1 : i]);
-                  mx[cc * 2 + 1] = max3(mx[cc * 2 + 1], v[cc][16 + i], v[cc][16 + (i + 1 < 16 ? i + 1 : i)]);
+              for (int cc = 0; cc < NC; ++cc)
+#pragma unroll
+                for (int i = 0; i < 32; i += 2) {
+                  float a0, a1;
+                  unpack2(add2(pack2(v[cc][i], v[cc][i + 1]), negm), a0, a1);
+                  acc[(i >> 1) & 3] = add2(acc[(i >> 1) & 3], pack2(fast_exp2(a0), fast_exp2(a1)));
                 }
-              const float tmax = max3(max3(mx[0], mx[1], mx[2]), max3(mx[3], mx[4], mx[5]), fmaxf(mx[6], mx[7]));
-              const float mnew = fmaxf(m_run, tmax);
-              if (mnew != -INFINITY) {
-                const uint64_t negm = pack2(-mnew, -mnew);
-                uint64_t acc[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) acc[q] = 0ull;
-#pragma unroll
-                for (int cc = 0; cc < 4; ++cc)
-#pragma unroll
-                  for (int i = 0; i < 32; i += 2) {
-                    float a0, a1;
-                    unpack2(add2(pack2(v[cc][i], v[cc][i + 1]), negm), a0, a1);
-                    acc[(i >> 1) & 3] = add2(acc[(i >> 1) & 3], pack2(fast_exp2(a0), fast_exp2(a1)));
-                  }
-                float s0, s1, s2, s3, s4, s5, s6, s7;
-                unpack2(acc[0], s0, s1);
-                unpack2(acc[1], s2, s3);
-                unpack2(acc[2], s4, s5);
-                unpack2(acc[3], s6, s7);
-                s_run = s_run * fast_exp2(m_run - mnew) + (((s0 + s1) + (s2 + s3)) + ((s4 + s5) + (s6 + s7)));
-                m_run = mnew;
-              }
+              float s0, s1, s2, s3, s4, s5, s6, s7;
+              unpack2(acc[0], s0, s1);
+              unpack2(acc[1], s2, s3);
+              unpack2(acc[2], s4, s5);
+              unpack2(acc[3], s6, s7);
+              s_run = s_run * fast_exp2(m_run - mnew) + (((s0 + s1) + (s2 + s3)) + ((s4 + s5) + (s6 + s7)));
+              m_run = mnew;
             }
           }
           if (dead) {
