@@ -268,27 +268,42 @@ __device__ __forceinline__ void write_bias_row(__nv_bfloat16* row16, float beta)
 
 // Poll the ready flags of row blocks [r0, r1) until each is at least `want` (acquire);
 // bounded. Called by one lane.
-__device__ __forceinline__ bool wait_flags(const uint32_t* flags, int r0, int r1, uint32_t want,
-                                           volatile int32_t* abort_flag, const Params& P) {
-  for (int r = r0; r < r1; ++r) {
-    if (ld_acquire_u32(flags + r) >= want) continue;
+// Whole warp: lane l polls the ready flag of row block r0 + l (r1 - r0 <= 32), so the
+// flags under a tile are read in parallel rather than one after another; returns once
+// every flag carries want (the lanes' acquires are ordered before the caller's later
+// accesses by the warp barrier at the end), false on abort or past the wait limit.
+__device__ __forceinline__ bool wait_flags_warp(const uint32_t* flags, int r0, int r1, uint32_t want,
+                                                volatile int32_t* abort_flag, const Params& P) {
+  const int lane = threadIdx.x & 31;
+  const bool mine = r0 + lane < r1;
+  bool seen = !mine || ld_acquire_u32(flags + r0 + lane) >= want;
+  bool ok = true;
+  if (!__all_sync(0xffffffffu, seen)) {
     const unsigned long long t0 = global_ns();
     for (uint32_t i = 1;; ++i) {
-      if (ld_acquire_u32(flags + r) >= want) break;
+      if (!seen) seen = ld_acquire_u32(flags + r0 + lane) >= want;
+      if (__all_sync(0xffffffffu, seen)) break;
       if ((i & 15) == 0) {
-        if (*abort_flag || grid_aborted(P)) {
-          *abort_flag = 1;
-          return false;
+        int stop = 0;
+        if (lane == 0) {
+          if (*abort_flag || grid_aborted(P)) {
+            *abort_flag = 1;
+            stop = 1;
+          } else if (global_ns() - t0 > P.wait_ns) {
+            *abort_flag = 1;
+            atomicExch(P.fault, 1);
+            stop = 1;
+          }
         }
-        if (global_ns() - t0 > P.wait_ns) {
-          *abort_flag = 1;
-          atomicExch(P.fault, 1);
-          return false;
+        if (__shfl_sync(0xffffffffu, stop, 0)) {
+          ok = false;
+          break;
         }
       }
     }
   }
-  return true;
+  __syncwarp();
+  return ok;
 }
 
 // New potential of row i from its log2-sum-exp L (Alg. 1's update, the row constant
@@ -362,7 +377,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const Layout L = layout(BN, P.nkb, P.split3, P.stages, P.a_bufs);
   Shared& sh = *reinterpret_cast<Shared*>(smem + L.ctrl);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c = blockIdx.x, G = P.G, nkb = P.nkb, S = P.stages, NA = P.a_bufs;
+  const int c = blockIdx.x, nkb = P.nkb, S = P.stages, NA = P.a_bufs;
   volatile int32_t* abort_flag = &sh.abort_flag;
   constexpr uint32_t B_TILE_BYTES = (uint32_t)BN * KB * 2, BIAS_TILE_BYTES = (uint32_t)BN * 32;
   constexpr int RB_PER_TILE = BN / BM;  // row blocks of B under one column tile
@@ -470,18 +485,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const int bs = ub % BIAS_SLOTS;
             ok = warp_wait_bar(&sh.bias_empty[bs], (uint32_t)(((ub / BIAS_SLOTS) & 1) ^ 1), abort_flag, P);
             if (!ok) break;
-            int okf = 1;
-            if (lane == 0) {
-              const int r0 = t * RB_PER_TILE, r1 = min(Sd.RB, r0 + RB_PER_TILE);
-              okf = wait_flags(Sd.flag_in, r0, r1, want, abort_flag, P) ? 1 : 0;
-              if (okf) {
-                mbar_arrive_expect_tx(&sh.bias_full[bs], BIAS_TILE_BYTES);
-                asm volatile("fence.proxy.async.global;" ::: "memory");
-                tma_load_2d(smem + L.bias0 + bs * L.bias_slot, mBb, &sh.bias_full[bs], 0, t * BN);
-              }
-            }
-            ok = __shfl_sync(0xffffffffu, okf, 0) != 0;
+            const int r0 = t * RB_PER_TILE, r1 = min(Sd.RB, r0 + RB_PER_TILE);
+            ok = wait_flags_warp(Sd.flag_in, r0, r1, want, abort_flag, P);
             if (!ok) break;
+            if (lane == 0) {
+              mbar_arrive_expect_tx(&sh.bias_full[bs], BIAS_TILE_BYTES);
+              asm volatile("fence.proxy.async.global;" ::: "memory");
+              tma_load_2d(smem + L.bias0 + bs * L.bias_slot, mBb, &sh.bias_full[bs], 0, t * BN);
+            }
+            __syncwarp();
             ++ub;
           }
         }
