@@ -476,10 +476,12 @@ int progot_set_stall_window(int32_t iters);
 
 /*
  * progot_set_map_tc - choose the kernel of the map step (Alg. 2 / Alg. 3) on the
- * tensor-core paths (PROGOT_BF16X3, PROGOT_BF16) for d <= 64: 1 (default) runs S = X Y^T
- * and P Y on tcgen05 (P and the centred, scaled Y in bf16 hi/lo, three products, float32
- * accumulation in TMEM); 0 runs P Y on float32 CUDA cores after the tensor-core LSE
- * pass (the path for d > 64 and PROGOT_FP32). Process-wide setting.
+ * tensor-core paths (PROGOT_BF16X3, PROGOT_BF16) for d <= 256: 1 (default) runs S = X Y^T
+ * and P Y on tcgen05 (P and the centred, scaled Y in bf16 hi/lo, three products with
+ * PROGOT_BF16X3 and one with PROGOT_BF16, float32 accumulation in TMEM; for 64 < d <= 256
+ * in one pass over Y with every output coordinate in TMEM); 0 runs P Y on float32 CUDA
+ * cores after the tensor-core LSE pass (the path for d > 256 and PROGOT_FP32).
+ * Process-wide setting.
  */
 int progot_set_map_tc(int32_t on);
 

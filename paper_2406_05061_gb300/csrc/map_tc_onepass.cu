@@ -187,7 +187,7 @@ __device__ __forceinline__ void op_split8(const float* v, uint4& hi, uint4& lo) 
 }
 
 __global__ void __launch_bounds__(OP_NTHREADS, 1)
-    map_sweep_tc_onepass(const __grid_constant__ CUtensorMap mapAh, const __grid_constant__ CUtensorMap mapAl,
+    map_sweep_tc_onepass(const __grid_constant__ CUtensorMap mapAl,
                          const __grid_constant__ CUtensorMap mapBh, const __grid_constant__ CUtensorMap mapBl,
                          const __grid_constant__ CUtensorMap mapBbias, MapOnepassParams mp) {
   extern __shared__ unsigned char smem_raw[];
@@ -648,7 +648,7 @@ bool map_tc_onepass_supported(int nkb) {
 int map_tc_onepass_tile_cols() { return tc::OP_BN; }
 
 cudaError_t launch_map_sweep_tc_onepass(const float* X, float* out, const float* L, int64_t nA, int64_t nB,
-                                        int32_t d, int32_t nkb, float alpha, const void* mapAh, const void* mapAl,
+                                        int32_t d, int32_t nkb, float alpha, const void* mapAl,
                                         const void* mapBh, const void* mapBl, const void* mapBbias, float inv_sc,
                                         const float* mu, const void* xh, float* Opart, float* Rpart, unsigned* cnt,
                                         int G, int maxseg, int32_t split3, int32_t* fault, cudaStream_t stream) {
@@ -683,7 +683,7 @@ cudaError_t launch_map_sweep_tc_onepass(const float* X, float* out, const float*
   mp.split3 = split3;
   mp.xh = reinterpret_cast<const uint32_t*>(xh);
   tc::map_sweep_tc_onepass<<<G, tc::OP_NTHREADS, smem, stream>>>(
-      *reinterpret_cast<const CUtensorMap*>(mapAh), *reinterpret_cast<const CUtensorMap*>(mapAl),
+      *reinterpret_cast<const CUtensorMap*>(mapAl),
       *reinterpret_cast<const CUtensorMap*>(mapBh), *reinterpret_cast<const CUtensorMap*>(mapBl),
       *reinterpret_cast<const CUtensorMap*>(mapBbias), mp);
   count_launch();

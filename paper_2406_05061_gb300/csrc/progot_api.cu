@@ -905,7 +905,7 @@ static int map_step(float* X, int64_t n, const float* y, int64_t m, int32_t d, c
     tc_plan(n, m, map_tc_onepass_tile_cols(), num_sms(), &G, &maxseg);
     ProfRec r;
     const bool rec = prof_begin(r, s, kProfMap);
-    CK(launch_map_sweep_tc_onepass(X, X, ws.L, n, m, d, ops->nkb, (float)alpha, &ops->xh_a, &ops->xl_a,
+    CK(launch_map_sweep_tc_onepass(X, X, ws.L, n, m, d, ops->nkb, (float)alpha, &ops->xl_a,
                                    &ops->yh_m32, &ops->yl_m32, &ops->yb_m32, (float)std::sqrt(eps / (2.0 * kLog2e)),
                                    ops->mu, ws.xh, ws.Opart, ws.Rpart, ws.mcnt, G, maxseg, ops->split3, ws.fault, s));
     if (rec) prof_end(r, s, kProfMap, (double)n * (double)m);

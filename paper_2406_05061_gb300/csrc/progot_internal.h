@@ -108,7 +108,7 @@ size_t map_sweep_tc_smem();
 bool map_tc_onepass_supported(int nkb);
 int map_tc_onepass_tile_cols();
 cudaError_t launch_map_sweep_tc_onepass(const float* X, float* out, const float* L, int64_t nA, int64_t nB,
-                                        int32_t d, int32_t nkb, float alpha, const void* mapAh, const void* mapAl,
+                                        int32_t d, int32_t nkb, float alpha, const void* mapAl,
                                         const void* mapBh, const void* mapBl, const void* mapBbias, float inv_sc,
                                         const float* mu, const void* xh, float* Opart, float* Rpart, unsigned* cnt,
                                         int G, int maxseg, int32_t split3, int32_t* fault, cudaStream_t stream);
