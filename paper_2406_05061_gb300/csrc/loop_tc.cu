@@ -362,7 +362,9 @@ __device__ __forceinline__ Seg seg_at(const Side& Sd, int c, int k, int maxseg) 
 
 
 // ------------------------------------------------------------------ kernel
-template <int BN>
+// NKB: the operands' K blocks when fixed at compile time (1: d <= 64, the MMA warp's issue
+// path then has no runtime K loop), 0 when read from P.nkb.
+template <int BN, int NKB>
 __global__ void __launch_bounds__(NTHREADS, 1)
     sinkhorn_loop_tc(const __grid_constant__ CUtensorMap mXh_a, const __grid_constant__ CUtensorMap mXl_a,
                      const __grid_constant__ CUtensorMap mYh_a, const __grid_constant__ CUtensorMap mYl_a,
@@ -377,7 +379,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const Layout L = layout(BN, P.nkb, P.split3, P.stages, P.a_bufs);
   Shared& sh = *reinterpret_cast<Shared*>(smem + L.ctrl);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c = blockIdx.x, nkb = P.nkb, S = P.stages, NA = P.a_bufs;
+  const int nkb = NKB > 0 ? NKB : P.nkb;
+  const int c = blockIdx.x, S = P.stages, NA = P.a_bufs;
   volatile int32_t* abort_flag = &sh.abort_flag;
   constexpr uint32_t B_TILE_BYTES = (uint32_t)BN * KB * 2, BIAS_TILE_BYTES = (uint32_t)BN * 32;
   constexpr int RB_PER_TILE = BN / BM;  // row blocks of B under one column tile
@@ -936,12 +939,12 @@ size_t loop_tc_smem(int bn, int nkb, int split3) {
   return tc::loop::layout(bn, nkb, split3, s, na).total;
 }
 
-template <int BN>
+template <int BN, int NKB>
 static cudaError_t launch_loop(const tc::loop::Params& P, size_t smem, const void* const* maps, cudaStream_t stream) {
   static thread_local size_t attr_bytes = 0;
   if (smem > attr_bytes) {
-    cudaError_t e =
-        cudaFuncSetAttribute(tc::loop::sinkhorn_loop_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(tc::loop::sinkhorn_loop_tc<BN, NKB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_bytes = smem;
   }
@@ -957,8 +960,8 @@ static cudaError_t launch_loop(const tc::loop::Params& P, size_t smem, const voi
   cfg.numAttrs = 1;
   const CUtensorMap* m[12];
   for (int q = 0; q < 12; ++q) m[q] = reinterpret_cast<const CUtensorMap*>(maps[q]);
-  return cudaLaunchKernelEx(&cfg, tc::loop::sinkhorn_loop_tc<BN>, *m[0], *m[1], *m[2], *m[3], *m[4], *m[5], *m[6],
-                            *m[7], *m[8], *m[9], *m[10], *m[11], P);
+  return cudaLaunchKernelEx(&cfg, tc::loop::sinkhorn_loop_tc<BN, NKB>, *m[0], *m[1], *m[2], *m[3], *m[4], *m[5],
+                            *m[6], *m[7], *m[8], *m[9], *m[10], *m[11], P);
 }
 
 cudaError_t launch_sinkhorn_loop_tc(const LoopLaunch& Lq, cudaStream_t stream) {
@@ -1033,7 +1036,9 @@ cudaError_t launch_sinkhorn_loop_tc(const LoopLaunch& Lq, cudaStream_t stream) {
   P.seq0 = Lq.seq0;
   P.niter = Lq.niter;
   const size_t smem = tc::loop::layout(Lq.bn, Lq.nkb, Lq.split3, stages, a_bufs).total;
-  cudaError_t e = Lq.bn == 256 ? launch_loop<256>(P, smem, Lq.maps, stream) : launch_loop<128>(P, smem, Lq.maps, stream);
+  cudaError_t e = Lq.bn == 128 ? launch_loop<128, 0>(P, smem, Lq.maps, stream)
+                  : Lq.nkb == 1 ? launch_loop<256, 1>(P, smem, Lq.maps, stream)
+                                : launch_loop<256, 0>(P, smem, Lq.maps, stream);
   count_launch();
   return e;
 }
