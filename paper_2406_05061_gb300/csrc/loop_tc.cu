@@ -439,6 +439,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     int u = 0, ka = 0, ub = 0;  // stage units, A segments, bias tiles issued
+    int s_cur = 0;              // ring position of unit u (kept without division)
+    uint32_t s_par = 0;         // parity of that stage's fills so far
     bool ok = true;
     for (int it = P.seq0; it < it_end && ok; ++it) {
       if (it > P.seq0) {
@@ -472,9 +474,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           __syncwarp();
           for (int t = sg.t0; t < sg.t1 && ok; ++t) {
             for (int kb = 0; kb < nkb; ++kb, ++u) {
-              const int s = u % S;
-              ok = warp_wait_bar(&sh.empty[s], (uint32_t)(((u / S) & 1) ^ 1), abort_flag, P);
+              const int s = s_cur;
+              ok = warp_wait_bar(&sh.empty[s], s_par ^ 1u, abort_flag, P);
               if (!ok) break;
+              if (++s_cur == S) {
+                s_cur = 0;
+                s_par ^= 1u;
+              }
               unsigned char* st = smem + L.stage0 + s * L.stage_bytes;
               if (elect_one()) {
                 mbar_arrive_expect_tx(&sh.full[s], B_TILE_BYTES * (P.split3 ? 2u : 1u));
@@ -514,7 +520,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // ------------------------------------------------------------ MMA issuer
     const uint64_t abias = desc_sw32(smem_u32(smem + L.a_bias));
     bool ok = true;
-    int u = 0, tl = 0, ka = 0;
+    int tl = 0, ka = 0;
+    int s_cur = 0;          // stage of the next B block (ring position, kept without division)
+    uint32_t s_par = 0;     // the parity of its fill
     for (int it = P.seq0; it < it_end && ok; ++it) {
       if (it > P.seq0) {
         warp_wait_bar(&sh.dec_full, (uint32_t)((it - 1 - P.seq0) & 1), abort_flag, P, true);
@@ -537,9 +545,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if (!ok) break;
             tc_fence_after();
             const uint32_t d_tmem = tmem_base + (uint32_t)(b * BN);
-            for (int kb = 0; kb < nkb; ++kb, ++u) {
-              const int s = u % S;
-              ok = warp_wait_bar(&sh.full[s], (uint32_t)((u / S) & 1), abort_flag, P);
+            for (int kb = 0; kb < nkb; ++kb) {
+              const int s = s_cur;
+              ok = warp_wait_bar(&sh.full[s], s_par, abort_flag, P);
+              if (++s_cur == S) {
+                s_cur = 0;
+                s_par ^= 1u;
+              }
               if (!ok) break;
               tc_fence_after();
               const uint32_t st = smem_u32(smem + L.stage0 + s * L.stage_bytes);
