@@ -53,13 +53,13 @@ def make_problem(wl):
 # only while the kernel's sources are the ones captured: their SHA-256 prefix is
 # checked at run time, else traffic is null.
 CAPTURED_TRAFFIC = {
-    # per sweep: one launch of 62 sweeps read 4.64 MB and wrote 0.29 MB (the operands stay
+    # per sweep: one launch of 62 sweeps read 4.64 MB and wrote 0.33 MB (the operands stay
     # in L2 across the sweeps of a launch)
     ("sinkhorn_loop_tc", "gmm8_8192_d64", "bf16x3"): dict(
-        bytes=79583.0,
+        bytes=80177.5,
         sources=("paper_2406_05061_gb300/csrc/loop_tc.cu", "paper_2406_05061_gb300/csrc/sweep_epilogue.cuh",
                  "paper_2406_05061_gb300/csrc/progot_common.cuh", "paper_2406_05061_gb300/csrc/tc_common.cuh"),
-        sha256=('0c77aac9ae3096be', 'bcfd55d39f4813fc', 'b26a7aa138618011', '735cd6a3dff3d7d7')),
+        sha256=('5548fe58d07b55bd', 'bcfd55d39f4813fc', 'b26a7aa138618011', '735cd6a3dff3d7d7')),
     ("lse_sweep_tc", "gmm8_8192_d64", "bf16x3"): dict(
         bytes=4627456.0,
         sources=("paper_2406_05061_gb300/csrc/sweep_tc.cu", "paper_2406_05061_gb300/csrc/sweep_epilogue.cuh",

@@ -518,46 +518,49 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
-    const uint64_t abias = desc_sw32(smem_u32(smem + L.a_bias));
-    bool ok = true;
-    int tl = 0, ka = 0;
-    int s_cur = 0;          // stage of the next B block (ring position, kept without division)
-    uint32_t s_par = 0;     // the parity of its fill
-    for (int it = P.seq0; it < it_end && ok; ++it) {
-      if (it > P.seq0) {
-        warp_wait_bar(&sh.dec_full, (uint32_t)((it - 1 - P.seq0) & 1), abort_flag, P, true);
-        if (sh.dec_stop[(it - 1) & 1] || *abort_flag) break;
-      }
-      for (int sd = 0; sd < 2 && ok; ++sd) {
-        const Side& Sd = P.side[sd];
-        const int nseg = __ldg(Sd.nseg + c);
-        for (int k = 0; k < nseg && ok; ++k, ++ka) {
-          const Seg sg = seg_at(Sd, c, k, P.maxseg);
-          const int ai = ka % NA;
-          ok = warp_wait_bar(&sh.a_full[ai], (uint32_t)((ka / NA) & 1), abort_flag, P);
-          if (!ok) break;
-          tc_fence_after();
-          const uint32_t a_hi = smem_u32(smem + L.a0 + ai * L.a_stride);
-          const uint32_t a_lo = a_hi + L.a_lo_off;
-          for (int t = sg.t0; t < sg.t1 && ok; ++t, ++tl) {
-            const int b = tl & 1;
-            ok = warp_wait_bar(&sh.tmem_empty[b], (uint32_t)(((tl >> 1) & 1) ^ 1), abort_flag, P);
+    // One thread runs the whole issue loop (a product is issued by a single thread): no
+    // per-wait votes or elections between tiles, whose bookkeeping sits between one
+    // tile's last product and the next tile's first; the other lanes wait at the end.
+    if (lane == 0) {
+      const uint64_t abias = desc_sw32(smem_u32(smem + L.a_bias));
+      bool ok = true;
+      int tl = 0, ka = 0;
+      int s_cur = 0;          // stage of the next B block (ring position, kept without division)
+      uint32_t s_par = 0;     // the parity of its fill
+      for (int it = P.seq0; it < it_end && ok; ++it) {
+        if (it > P.seq0) {
+          wait_bar(&sh.dec_full, (uint32_t)((it - 1 - P.seq0) & 1), abort_flag, P, true);
+          if (sh.dec_stop[(it - 1) & 1] || *abort_flag) break;
+        }
+        for (int sd = 0; sd < 2 && ok; ++sd) {
+          const Side& Sd = P.side[sd];
+          const int nseg = __ldg(Sd.nseg + c);
+          for (int k = 0; k < nseg && ok; ++k, ++ka) {
+            const Seg sg = seg_at(Sd, c, k, P.maxseg);
+            const int ai = ka % NA;
+            ok = wait_bar(&sh.a_full[ai], (uint32_t)((ka / NA) & 1), abort_flag, P);
             if (!ok) break;
             tc_fence_after();
-            const uint32_t d_tmem = tmem_base + (uint32_t)(b * BN);
-            for (int kb = 0; kb < nkb; ++kb) {
-              const int s = s_cur;
-              ok = warp_wait_bar(&sh.full[s], s_par, abort_flag, P);
-              if (++s_cur == S) {
-                s_cur = 0;
-                s_par ^= 1u;
-              }
+            const uint32_t a_hi = smem_u32(smem + L.a0 + ai * L.a_stride);
+            const uint32_t a_lo = a_hi + L.a_lo_off;
+            for (int t = sg.t0; t < sg.t1 && ok; ++t, ++tl) {
+              const int b = tl & 1;
+              ok = wait_bar(&sh.tmem_empty[b], (uint32_t)(((tl >> 1) & 1) ^ 1), abort_flag, P);
               if (!ok) break;
               tc_fence_after();
-              const uint32_t st = smem_u32(smem + L.stage0 + s * L.stage_bytes);
-              const uint64_t bh = desc_sw128(st), bl = desc_sw128(st + L.b_lo_off);
-              const uint64_t ah = desc_sw128(a_hi + kb * A_TILE_BYTES), al = desc_sw128(a_lo + kb * A_TILE_BYTES);
-              if (elect_one()) {
+              const uint32_t d_tmem = tmem_base + (uint32_t)(b * BN);
+              for (int kb = 0; kb < nkb; ++kb) {
+                const int s = s_cur;
+                ok = wait_bar(&sh.full[s], s_par, abort_flag, P);
+                if (++s_cur == S) {
+                  s_cur = 0;
+                  s_par ^= 1u;
+                }
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t st = smem_u32(smem + L.stage0 + s * L.stage_bytes);
+                const uint64_t bh = desc_sw128(st), bl = desc_sw128(st + L.b_lo_off);
+                const uint64_t ah = desc_sw128(a_hi + kb * A_TILE_BYTES), al = desc_sw128(a_lo + kb * A_TILE_BYTES);
 #pragma unroll
                 for (int kk = 0; kk < KB / 16; ++kk) {
                   // +32 bytes per K = 16 step inside the 128-byte swizzle atom (encoded >> 4)
@@ -570,30 +573,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
                 umma_commit(&sh.empty[s]);
               }
-              __syncwarp();
-            }
-            if (!ok) break;
-            // bias: t_ij = c (a_i . b_j) + beta_j, once the producer has the row blocks' bias rows
-            const int bs = tl % BIAS_SLOTS;  // one bias slot per tile, in tile order
-            ok = warp_wait_bar(&sh.bias_full[bs], (uint32_t)((tl / BIAS_SLOTS) & 1), abort_flag, P);
-            if (!ok) break;
-            tc_fence_after();
-            if (elect_one()) {
+              if (!ok) break;
+              // bias: t_ij = c (a_i . b_j) + beta_j, once the producer has the row blocks' bias rows
+              const int bs = tl % BIAS_SLOTS;  // one bias slot per tile, in tile order
+              ok = wait_bar(&sh.bias_full[bs], (uint32_t)((tl / BIAS_SLOTS) & 1), abort_flag, P);
+              if (!ok) break;
+              tc_fence_after();
               umma<BN>(d_tmem, abias, desc_sw32(smem_u32(smem + L.bias0 + bs * L.bias_slot)), 1u);
               umma_commit(&sh.bias_empty[bs]);
               umma_commit(&sh.tmem_full[b]);
             }
-            __syncwarp();
+            if (!ok) break;
+            umma_commit(&sh.a_empty[ai]);
           }
-          if (!ok) break;
-          if (elect_one()) umma_commit(&sh.a_empty[ai]);
-          __syncwarp();
         }
       }
+      umma_commit(&sh.drain);
+      wait_bar(&sh.drain, 0, abort_flag, P, true);
     }
-    if (elect_one()) umma_commit(&sh.drain);
     __syncwarp();
-    warp_wait_bar(&sh.drain, 0, abort_flag, P, true);
   } else if (threadIdx.x < EPI_TID0) {
     // ------------------------------------------------------------ LSE warps
     const int wg = (warp - 2) >> 2;
