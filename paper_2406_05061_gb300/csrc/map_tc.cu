@@ -2,7 +2,9 @@
 // d <= 64:
 //   T_i = sum_j 2^{t_ij - L_i} y_j / sum_j 2^{t_ij - L_i},   x_i <- x_i + alpha (T_i - x_i),
 // with t_ij = c (x_i . y_j) + beta_j in log2 units (the LSE sweep's t) and L_i from that
-// sweep. Both products run on the tensor cores:
+// sweep or from the Sinkhorn loop's last f-update (the same t; the kernel normalises by its
+// own row sums, so L only stabilises the exponentials). Both products run on the tensor
+// cores:
 //   S = X Y^T as in the LSE sweep (bf16 hi/lo operands pre-scaled by sqrt(c), three
 //     products, beta added by one more K = 16 step) into one of two TMEM buffers;
 //   O += P Y~ with P_ij = 2^{t_ij - L_i} written by the LSE warps into shared memory as

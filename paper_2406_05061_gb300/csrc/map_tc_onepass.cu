@@ -1,8 +1,9 @@
 // Tensor-core (tcgen05) barycentric displacement of Alg. 2 / Alg. 3 for 64 < d <= 256 in
 // one pass over the target cloud:
 //   T_i = sum_j 2^{t_ij - L_i} y_j / sum_j 2^{t_ij - L_i},   x_i <- x_i + alpha (T_i - x_i),
-// with t_ij = c (x_i . y_j) + beta_j in log2 units and L_i from a log-sum-exp pass, as in
-// the d <= 64 kernel (map_tc.cu):
+// with t_ij = c (x_i . y_j) + beta_j in log2 units and L_i a stabiliser close to the row's
+// log-sum-exp (from a log-sum-exp pass, or from the Sinkhorn loop's last f-update, which
+// used the same g), as in the d <= 64 kernel (map_tc.cu):
 //   S = X Y~^T over all K blocks of the operands (bf16 hi/lo pre-scaled by sqrt(c), three
 //     products, beta added by one more K = 16 step) into one of two 32-column TMEM
 //     buffers (tiles of 32 columns j);
@@ -19,8 +20,9 @@
 // segment's start), its lo part in shared memory (TMA); so four stages fit, each holding
 // a tile's K blocks (hi and lo) and bias rows from the S products until its P Y~
 // products, and three tiles' copies are in flight while a fourth is in use. The MMA
-// warp issues S and P Y~ in whichever order their inputs arrive, so the exponentials of
-// tile q overlap the products of tile q + 1 and P Y~(q) does not wait for a later copy.
+// warp issues S and P Y~ in whichever order their inputs arrive (S at most one tile
+// ahead), so the exponentials of tile q overlap the products of tile q + 1 and P Y~(q)
+// does not wait for a later copy.
 // CTA = 10 warps: producer, MMA issuer, two LSE warpgroups alternating tiles (one P
 // buffer shared in tile order); at a segment's end warpgroup 0 moves O to a per-CTA
 // partial slot and the last CTA of a row block combines the slots in CTA order
